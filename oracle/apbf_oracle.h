@@ -1,0 +1,128 @@
+/*
+ * apbf_oracle.h -- plain, slow CPU reference of one Adaptive Position-Based
+ * Fluids time step (Koster & Kruger 2016, Sec. 3-5, Fig. 7).
+ *
+ * TEST INFRASTRUCTURE ONLY. This library is called by the tests, by the
+ * package's smoke check and by the benchmark's CPU-baseline leg. The product
+ * path (the CUDA library) never links, loads or calls it, and the two share
+ * no code.
+ *
+ * Precision: every integer decision of the step (LOD level, cell index,
+ * neighbour predicate) and the prediction that feeds it are evaluated in
+ * IEEE FP32 operation by operation (no contraction), because the scene's
+ * state is FP32 and these decisions must be reproducible exactly. The solver
+ * arithmetic (density, lambda, position corrections, velocity, XSPH) runs in
+ * FP64 from the FP32 values; the new state is rounded to FP32 at the end of
+ * the step.
+ *
+ * Return codes: 0 ok, -1 invalid argument, -2 caller capacity too small,
+ * -3 allocation failure.
+ */
+#ifndef APBF_ORACLE_H
+#define APBF_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_LOD_FIXED 0
+#define ORC_LOD_DTC 1
+
+#define ORC_LAMBDA_STALE 0     /* inactive neighbours keep their last lambda */
+#define ORC_LAMBDA_ZERO 1      /* inactive neighbours contribute lambda = 0 */
+#define ORC_LAMBDA_RECOMPUTE 2 /* lambda recomputed for every particle each iteration */
+
+typedef struct orc_params {
+    /* Scene values exactly as the solver receives them (FP32). */
+    float h, dt, mass, rho0, eps, scorr_k, scorr_dq, xsph_c;
+    int32_t scorr_n;
+    float gravity[3];
+    float grid_lo[3], grid_hi[3]; /* static uniform-grid extent */
+    float box_lo[3], box_hi[3];   /* collision box of this step (inside the grid) */
+    int32_t n_min, n_max, lod_mode;
+    float eye[3];
+    float d_near, d_far;          /* d_near >= d_far: automatic range */
+    int32_t lambda_mode;          /* ORC_LAMBDA_* */
+    int32_t lod_rounding;         /* 0: equal-width bins, 1: rounded interpolation */
+} orc_params;
+
+typedef struct orc_record {
+    /* Optional outputs of one step (NULL = not recorded), caller-owned.
+       "pre-sort order" is the state order at the start of the step;
+       "sorted order" is the order after the stable counting sort, which is
+       also the state order after the step. */
+    float *xpred;           /* 3n, pre-sort order, FP32 prediction incl. box clamp */
+    int32_t *level_presort; /* n, pre-sort order */
+    uint32_t *keys;         /* n, pre-sort order */
+    int32_t *order;         /* n, sorted slot -> pre-sort index */
+    uint32_t *cell_start;   /* ncell + 1 */
+    int64_t cell_cap;       /* capacity of cell_start */
+    int32_t *nbr_off;       /* n + 1, CSR over sorted slots */
+    int32_t *nbr_idx;       /* neighbour sorted slots */
+    int64_t nbr_cap;        /* capacity of nbr_idx */
+    int32_t *active_count;  /* n_max + 2 entries: |P_l|, l = 0 .. n_max + 1 */
+    int32_t rec_iters;      /* record iterations 1 .. rec_iters of lam/rho/xs */
+    double *lam;            /* rec_iters * n, sorted: lambda after the lambda pass of iteration l */
+    double *rho;            /* rec_iters * n, sorted: density at iteration l (NaN if inactive) */
+    double *xs;             /* rec_iters * 3n, sorted: x* after the update of iteration l */
+    double *x_final;        /* 3n, sorted: new position before rounding */
+    double *v_final;        /* 3n, sorted: new velocity before rounding */
+    float d_range[2];       /* out: distance range used by the LOD */
+    int32_t dims[3];        /* out: grid cells per axis */
+} orc_record;
+
+/* SPH kernels (Eq. 6 uses W; Eq. 7 uses grad W): poly6 and spiky. */
+double orc_poly6(double r2, double h);
+double orc_spiky(double r, double h);
+void orc_spiky_grad(const double r[3], double h, double g[3]);
+
+/* Density of an interior particle of a jitter-free cubic lattice. */
+double orc_rest_density(double h, double mass, double spacing);
+
+/* Grid cells per axis: floor((hi - lo) * inv_h) + 1 in FP32, inv_h = 1/h in FP32. */
+int orc_grid_dims(const orc_params *p, int32_t dims[3]);
+
+/* Sec. 4.1 DTC model + Eq. 8: per-particle level from the camera distance. */
+int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *level, float range[2]);
+
+/* Fig. 7 lines 1-4 plus the box clamp, FP32. */
+int orc_predict(const orc_params *p, int32_t n, const float *x, const float *v, float *xpred);
+
+/* Cell index of each position (FP32). */
+int orc_cell_keys(const orc_params *p, int32_t n, const float *xpos, uint32_t *keys);
+
+/* Stable counting sort by key: order[slot] = input index; cell_start has ncell + 1 entries. */
+int orc_counting_sort(int32_t n, const uint32_t *keys, int64_t ncell, int32_t *order, uint32_t *cell_start);
+
+/* Neighbour sets {j != i : |x_i - x_j|^2 < h^2} (FP32 predicate) by a cell
+   list, reported in input indices, each list ascending. */
+int orc_neighbors(const orc_params *p, int32_t n, const float *x, int32_t *off, int32_t *idx, int64_t cap);
+
+/* Eq. 4-6 for particle i: density, constraint value, gradients
+   grad[0..2] = d C_i / d x_i and grad[3(k+1)..] = d C_i / d x_{nbr k}, and lambda. */
+int orc_constraint(const orc_params *p, int32_t n, const double *xs, const int32_t *nbr_off,
+                   const int32_t *nbr_idx, int32_t i, double *rho, double *C, double *grad,
+                   double *lambda);
+
+/* Eq. 7 with the tensile term for every particle (no clamp). */
+int orc_delta_p(const orc_params *p, int32_t n, const double *xs, const double *lam,
+                const int32_t *nbr_off, const int32_t *nbr_idx, double *dp);
+
+/* XSPH velocity smoothing over the given neighbour sets. */
+int orc_xsph(const orc_params *p, int32_t n, const double *xs, const double *v,
+             const int32_t *nbr_off, const int32_t *nbr_idx, double *vout);
+
+/* One APBF step (Fig. 7). x, v (3n) and id (n) are the state in its current
+   order; on return they hold the new state in sorted order. */
+int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, orc_record *rec);
+
+/* Density diagnostic at the given positions (fresh neighbour search):
+   stats = {mean |rho/rho0-1|, max |rho/rho0-1|, mean (rho/rho0-1), mean max(0, rho/rho0-1)}. */
+int orc_density_stats(const orc_params *p, int32_t n, const float *x, double *rho, double stats[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,71 @@
+"""Input generator (seeded, deterministic, shaped like the workloads) and the
+Table 1 performance-improvement metric."""
+import math
+import os
+
+import numpy as np
+
+from paper_1608_04721_gb300 import metrics, scenes as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1.txt")
+
+
+def test_splitmix64_reference_values():
+    # splitmix64 with state 0: the first outputs of the published generator
+    # (state advanced by the golden gamma before mixing).
+    out = S.splitmix64(np.arange(1, 4, dtype=np.uint64) * S.GOLDEN)
+    assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_lattice_shape_order_and_jitter():
+    cfg = S.config_dam_break_4k()
+    x, v = S.make_scene(cfg)
+    assert x.shape == (4096, 3) and x.dtype == np.float32 and not v.any()
+    ideal = np.stack(np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij"), -1)
+    ideal = ideal[..., ::-1].reshape(-1, 3) * 0.05 + 0.025    # x fastest
+    dev = x.astype(np.float64) - ideal
+    assert np.abs(dev).max() <= 0.001 + 1e-6 and np.abs(dev).max() > 0.0009
+    assert abs(dev.mean()) < 1e-4
+    x2, _ = S.make_scene(cfg)
+    assert np.array_equal(x, x2)
+    x3, _ = S.make_scene(cfg.replace(seed=7))
+    assert not np.array_equal(x, x3)
+
+
+def test_workload_sizes():
+    assert S.config_dam_break_4k().n == 4096
+    assert S.config_dam_break_131k().n == 131072
+    assert S.config_ocean_1m().n == 1048576
+    c = S.config_ocean_1m()
+    x = S.lattice_positions(c.replace(lattice=(4, 4, 4)))
+    assert np.all(x >= 0)
+
+
+def test_scene_drivers():
+    c = S.config_ocean_1m()
+    lo0, hi0 = S.box_at(c, 0)
+    assert lo0[0] == 0.0 and hi0[0] == np.float32(9.6)
+    lo_half, _ = S.box_at(c, int(round(1.0 / c.dt)))   # t = 1 s = T/2: wall fully in
+    assert abs(lo_half[0] - 1.0) < 1e-3
+    eyes = np.array([S.camera_at(c, s)[0] for s in range(0, c.steps, 7)])
+    assert np.all((eyes[:, 2] > 3.5) & (eyes[:, 2] < 5.3))
+    e0, d0 = S.camera_at(c, 0)
+    assert abs(np.linalg.norm(d0) - 1) < 1e-6
+    assert np.allclose(S.camera_at(c, c.steps)[0], e0)
+
+
+def test_table1_improvement_definition():
+    """Every printed improvement of Table 1 equals T_PBF(N_max)/T_APBF - 1 in
+    percent, rounded half up."""
+    rows = [ln.split() for ln in open(GOLDEN) if ln.strip() and not ln.startswith("#")]
+    checked = 0
+    for scen in {r[0] for r in rows}:
+        rs = [r for r in rows if r[0] == scen]
+        pbf_max = max((r for r in rs if r[2] == "PBF"), key=lambda r: int(r[3]))
+        for r in rs:
+            if r[2].startswith("APBF"):
+                for col, icol in ((4, 6), (5, 7)):
+                    imp = metrics.improvement(float(pbf_max[col]), float(r[col]))
+                    assert math.floor(100 * imp + 0.5) == int(r[icol]), (scen, r)
+                    checked += 1
+    assert checked == 12
