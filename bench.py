@@ -1,0 +1,459 @@
+"""Benchmark of the adaptive PBF step on one GB300 (or N replicas).
+
+Workload (default): 1,048,576 particles (128x128x64 block in a 9.6x6.4x4.8 m
+basin with an oscillating wall, spline camera), APBF with N_i in 3..15 from
+the distance to the camera, beside plain PBF with N = 15 on identical inputs.
+A "step" is one simulation step of Fig. 7 (all stages) of that scene.
+
+Metric: APBF ms/step (lower is better), with PBF(N_max) ms/step, the
+performance improvement T_PBF/T_APBF - 1 (Table 1), p50/p99 step latency,
+particle-iterations/s and the density error of both runs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the scene (the single-scene
+solver does not shard); rank 0 prints the JSON line with the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1608_04721_gb300 import metrics, scenes  # noqa: E402
+
+METRIC = "APBF ms/step @1M particles vs PBF N_max, same GPU & density error; p50/p99 latency"
+UNIT = "ms/step"
+FP32_LANES_PER_SM = 128
+SMS = 152
+SM_MAX_MHZ = 2070.0
+# algorithmic FP32 operations per in-range neighbour pair (sqrt and divide count 1)
+FLOPS_PER_PAIR = {"lambda": 25, "deltap": 28, "finalize": 26}
+STAGE_NAMES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
+               "finalize"]
+
+
+def workload(name: str, lod: str):
+    if name == "ocean_1m":
+        cfg = scenes.config_ocean_1m()
+    elif name == "dam_break_131k":
+        cfg = scenes.config_dam_break_131k()
+    elif name == "dam_break_4k":
+        cfg = scenes.config_dam_break_4k().replace(lod_mode=scenes.LOD_DTC, n_min=2, n_max=4, camera="fixed",
+                                                   eye=(-1.0, 0.8, 0.8))
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if lod == "pbf":
+        cfg = cfg.replace(lod_mode=scenes.LOD_FIXED, n_min=cfg.n_max)
+    return cfg
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    """Host-side process group (gloo) for barriers and the max over ranks;
+    the data path has no collective."""
+
+    def __init__(self):
+        self.ws, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as td
+
+            td.init_process_group(backend="gloo")
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        return self.reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self.reduce(x, "sum")
+
+    def reduce(self, x: float, op: str) -> float:
+        if not self.pg:
+            return float(x)
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        mx = max(num(r[2]) for r in rows)
+        reasons = set()
+        for r in rows:
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6), ("sw_thermal_slowdown", 7),
+                              ("sw_power_cap", 8)):
+                if r[col].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(num(r[3]) for r in rows)}
+
+
+def kernels_per_step(cfg) -> int:
+    dtc = cfg.lod_mode == scenes.LOD_DTC
+    k = 1 + 2 + 1 + 1 + 1 + 1  # predict, scan (2), scatter, reorder, neighbors, finalize
+    if dtc:
+        k += 1  # camera-distance range
+        if cfg.n_max > cfg.n_min:
+            k += 3  # level histogram, scan, scatter
+    return k + 2 * cfg.n_max
+
+
+def make_scene(apbf, cfg, rho0, stream=None):
+    x, v = scenes.make_scene(cfg)
+    return apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, rho0), stream=stream)
+
+
+def drive(apbf, scene, cfg, step):
+    eye, d = scenes.camera_at(cfg, step)
+    lo, hi = scenes.box_at(cfg, step)
+    apbf.apbf_set_camera(scene, eye, d)
+    apbf.apbf_set_box(scene, lo, hi)
+
+
+def timed_run(apbf, torch, scene, cfg, warmup, steps, first_step=0):
+    """Warm-up, then `steps` steps bracketed by CUDA events on the scene's
+    stream; returns (total ms, per-step ms list, particle-iterations)."""
+    stream = torch.cuda.current_stream()
+    s = first_step
+    for _ in range(warmup):
+        drive(apbf, scene, cfg, s)
+        apbf.apbf_step(scene, 1)
+        s += 1
+    apbf.apbf_sync(scene)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for k in range(steps):
+        drive(apbf, scene, cfg, s)
+        apbf.apbf_step(scene, 1)
+        evs[k + 1].record(stream)
+        s += 1
+    torch.cuda.synchronize()
+    apbf.apbf_sync(scene)
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return evs[0].elapsed_time(evs[-1]), per, s
+
+
+def stage_profile(apbf, scene, cfg, first_step, steps):
+    """Per-stage CUDA-event times over `steps` eager steps, plus the neighbour
+    pairs each step's solver passes visited."""
+    apbf.apbf_set_timing(scene, True)
+    apbf.apbf_timing_report(scene)  # reset
+    pairs = 0
+    nbr_pairs = 0
+    iters = 0
+    ms_tot = np.zeros(len(STAGE_NAMES))
+    ln_tot = np.zeros(len(STAGE_NAMES))
+    s = first_step
+    for _ in range(steps):
+        drive(apbf, scene, cfg, s)
+        apbf.apbf_step(scene, 1)
+        info = apbf.apbf_get_step_info(scene)
+        pairs += info["lambda_pairs"]
+        nbr_pairs += info["neighbor_pairs"]
+        iters += info["particle_iterations"]
+        ms, ln = apbf.apbf_timing_report(scene)
+        ms_tot += ms
+        ln_tot += ln
+        s += 1
+    apbf.apbf_set_timing(scene, False)
+    return ms_tot, ln_tot, pairs, nbr_pairs, iters, s
+
+
+def read_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload_name}.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_1608_04721_gb300", "csrc", "kernels.cu"), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == kernel and not ln.startswith("#"):
+            kv = dict(p.split("=", 1) for p in parts[1:] if "=" in p)
+            if kv.get("source") == digest:
+                return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def cpu_baseline(cfg, n_full, budget_s=20.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: the bottom z-layers of the same block (same basin, camera,
+    wall, LOD range), one step, time scaled by particles to the full scene."""
+    import oracle
+
+    rho0 = float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
+    nx, ny, nz = cfg.lattice
+    layers = max(1, nz // 4)
+    sub = cfg.replace(lattice=(nx, ny, layers))
+    x, v = scenes.make_scene(sub)
+    eye, _ = scenes.camera_at(cfg, 0)
+    lo, hi = scenes.box_at(cfg, 0)
+    p = oracle.make_params(sub, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi)
+    t0 = time.perf_counter()
+    oracle.step(p, x, v)
+    dt = time.perf_counter() - t0
+    scale = n_full / sub.n
+    return {"value": dt * 1e3 * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle step of {sub.n} of the {n_full} particles (bottom {layers} of {nz} lattice "
+                      f"layers, same basin, camera, wall and N_i range), time x {scale:g}",
+            "sample_seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the host cores, on this arm's
+    workload; each step is a bounded sample (the bottom lattice layers of the
+    same scene), the per-step time scaled by particles."""
+    ws, rank, _ = dist_env()
+    cfg = workload(args.workload, "apbf")
+    if rank != 0:
+        return 0
+    import oracle
+
+    rho0 = float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
+    nx, ny, nz = cfg.lattice
+    # calibrate on one layer, then size the sample so W + K steps take ~budget
+    budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "150"))
+    cal = cfg.replace(lattice=(nx, ny, 1))
+    xc, vc = scenes.make_scene(cal)
+    eye, _ = scenes.camera_at(cfg, 0)
+    lo, hi = scenes.box_at(cfg, 0)
+    t0 = time.perf_counter()
+    oracle.step(oracle.make_params(cal, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi), xc, vc)
+    per_layer = max(time.perf_counter() - t0, 1e-4)
+    layers = int(max(1, min(nz, budget / max(1, args.steps + args.warmup) / per_layer)))
+    sub = cfg.replace(lattice=(nx, ny, layers))
+    x, v = scenes.make_scene(sub)
+    ids = np.arange(sub.n, dtype=np.int32)
+    times = []
+    for s in range(args.warmup + args.steps):
+        eye, _ = scenes.camera_at(cfg, s)
+        lo, hi = scenes.box_at(cfg, s)
+        p = oracle.make_params(sub, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi)
+        t0 = time.perf_counter()
+        st = oracle.step(p, x, v, ids)
+        dt = time.perf_counter() - t0
+        x, v, ids = st.x, st.v, st.ids
+        if s >= args.warmup:
+            times.append(dt * 1e3 * cfg.n / sub.n)
+    value = float(np.mean(times))
+    sample = (f"each step: one oracle step of {sub.n} of the {cfg.n} particles (bottom {layers} of {nz} lattice "
+              f"layers, same basin, camera, wall and N_i range), time x {cfg.n / sub.n:g}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "particles": cfg.n, "n_range": f"{cfg.n_min}..{cfg.n_max}",
+                       "lod": "distance to camera"},
+            "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ocean_1m", choices=["ocean_1m", "dam_break_131k", "dam_break_4k"])
+    ap.add_argument("--profile-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-pbf", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_1608_04721_gb300 import apbf, build
+
+    d = Dist()
+    torch.cuda.set_device(d.local)
+    build.build()
+    apbf.lib()
+    cfg = workload(args.workload, "apbf")
+    pbf_cfg = workload(args.workload, "pbf")
+    rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))
+
+    scene = make_scene(apbf, cfg, rho0)
+    pbf = None if args.no_pbf else make_scene(apbf, pbf_cfg, rho0)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    # ---- APBF, device-resident inputs
+    d.barrier()
+    torch.cuda.synchronize()
+    tot, per, s_next = timed_run(apbf, torch, scene, cfg, args.warmup, args.steps)
+    torch.cuda.synchronize()
+    d.barrier()
+    ms_step = d.max(tot / args.steps)
+    apbf_density = apbf.apbf_density_stats(scene)
+    # ---- PBF(N_max) on identical inputs and drivers
+    pbf_line = None
+    if pbf is not None:
+        d.barrier()
+        ptot, pper, _ = timed_run(apbf, torch, pbf, pbf_cfg, args.warmup, args.steps)
+        d.barrier()
+        pbf_ms = d.max(ptot / args.steps)
+        pbf_density = apbf.apbf_density_stats(pbf)
+        pbf_line = {"ms_per_step": pbf_ms, "p50_ms": metrics.percentile(pper, 50),
+                    "p99_ms": metrics.percentile(pper, 99), "n": pbf_cfg.n_max,
+                    "density": [float(v) for v in pbf_density]}
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e_scene = make_scene(apbf, cfg, rho0)
+        host_pos = torch.empty((cfg.n, 3), dtype=torch.float32, pin_memory=True).numpy()
+        for k in range(args.warmup):
+            drive(apbf, e2e_scene, cfg, k)
+            apbf.apbf_step(e2e_scene, 1)
+            apbf.apbf_read_state(e2e_scene, pos=host_pos, vel=False)
+        d.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            drive(apbf, e2e_scene, cfg, args.warmup + k)   # camera + wall: host -> device
+            apbf.apbf_step(e2e_scene, 1)
+            apbf.apbf_read_state(e2e_scene, pos=host_pos, vel=False)  # positions: device -> host
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        d.barrier()
+        e2e_ms = d.max(e2e_ms)
+        e2e = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 64, "d2h_bytes_per_step": 12 * cfg.n + 4,
+               "what": "per step: apbf_set_camera + apbf_set_box (64 B upload), apbf_step, "
+                       "apbf_read_state of all positions into pinned host memory (synchronising)"}
+        apbf.apbf_destroy_scene(e2e_scene)
+    clock_info = clocks.stop()
+
+    # ---- per-stage device times (eager launches with events) for the roofline
+    ms_st, ln_st, pairs, nbr_pairs, iters, _ = stage_profile(apbf, scene, cfg, s_next, args.profile_steps)
+    stage_ms = {STAGE_NAMES[k]: float(ms_st[k] / args.profile_steps) for k in range(len(STAGE_NAMES))}
+    top = max(("lambda", "deltap"), key=lambda k: stage_ms[k])
+    k_top = STAGE_NAMES.index(top)
+    launches = max(1.0, float(ln_st[k_top]))
+    avg_launch_s = ms_st[k_top] / launches * 1e-3
+    flops_per_launch = FLOPS_PER_PAIR[top] * pairs / launches
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    traffic = read_traffic(f"{top}_kernel", cfg.name)
+    roofline = {"bound": "alu", "kernel": f"{top}_kernel", "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+                "flops_per_pair": FLOPS_PER_PAIR[top], "pairs_per_launch": pairs / launches,
+                "avg_launch_us": avg_launch_s * 1e6}
+    particle_iters_per_step = iters / args.profile_steps
+    value = ms_step
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "particles": cfg.n, "n_range": f"{cfg.n_min}..{cfg.n_max}",
+                   "lod": "distance to camera, automatic range", "pbf_n": pbf_cfg.n_max,
+                   "parallelism": f"replicas x{d.ws}" if d.ws > 1 else "single GPU",
+                   "l2": "no flush: each step touches ~0.3 GB (> 129 MB L2)",
+                   "launch": "captured CUDA graph per step"},
+        "p50_ms": metrics.percentile(per, 50), "p99_ms": metrics.percentile(per, 99),
+        "particle_iterations_per_step": particle_iters_per_step,
+        "particle_iterations_per_s": d.sum(particle_iters_per_step / (ms_step * 1e-3)),
+        "neighbor_pairs_per_step": nbr_pairs / args.profile_steps,
+        "density": {"apbf": [float(v) for v in apbf_density],
+                    "fields": ["mean|rho/rho0-1|", "max|rho/rho0-1|", "mean(rho/rho0-1)", "mean max(0,rho/rho0-1)"]},
+        "pbf_nmax": pbf_line,
+        "improvement": metrics.improvement(pbf_line["ms_per_step"], ms_step) if pbf_line else None,
+        "roofline": roofline,
+        "stage_ms_per_step": stage_ms,
+        "e2e": e2e,
+        "gpu_launches": kernels_per_step(cfg) * args.steps,
+        "clocks": clock_info,
+    }
+    if pbf_line:
+        line["density"]["pbf_nmax"] = pbf_line["density"]
+        line["density"]["mean_abs_diff_points"] = 100 * abs(apbf_density[0] - pbf_line["density"][0])
+    if d.rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, cfg.n)
+    apbf.apbf_destroy_scene(scene)
+    if pbf is not None:
+        apbf.apbf_destroy_scene(pbf)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

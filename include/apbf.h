@@ -1,0 +1,245 @@
+/*
+ * apbf.h -- C ABI of the GB300 (sm_103a) Adaptive Position-Based Fluids step.
+ *
+ * Method: Koster & Kruger, "Adaptive Position-Based Fluids: Improving
+ * Performance of Fluid Simulations for Real-Time Applications", IJCGA 6(3),
+ * 2016. One call of apbf_step() advances a scene by the simulation loop of
+ * Fig. 7 (Sec. 5): external forces and prediction (lines 1-4), neighbour
+ * discovery by a counting-sort uniform grid with particle reordering (lines
+ * 5-6, Sec. 6), N_max Jacobi solver iterations of the density constraint
+ * (Eq. 4-7, lines 12-23) in which particle i is active only in iterations
+ * 1..N_i (Eq. 9-11), and the velocity/position update (lines 24-27). N_i is
+ * the particle's level of detail (Eq. 8) from its distance to the camera
+ * (Sec. 4.1, DTC model).
+ *
+ * Conventions for every entry point:
+ *  - Returns apbf_status; nothing aborts, throws or exits.
+ *  - "host" pointers are ordinary CPU memory owned by the caller and only
+ *    read/written during the call. "device" pointers are CUDA global memory.
+ *  - Calls on one scene are not thread-safe; different scenes are independent.
+ *  - All GPU work of a scene is issued on the stream given at creation, in
+ *    call order. apbf_step() returns before the GPU finishes; a GPU-side error
+ *    (e.g. a neighbour-list overflow) is reported by the next synchronising
+ *    call (apbf_read_state, apbf_density_stats, apbf_sync, apbf_debug_read)
+ *    and then sticks to the scene: every later call returns it.
+ *  - Positions and velocities are FP32, 3 values per particle (x, y, z),
+ *    in particle-id order (the order of apbf_scene_desc.pos).
+ */
+#ifndef APBF_H
+#define APBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define APBF_API __attribute__((visibility("default")))
+#else
+#define APBF_API
+#endif
+
+typedef enum apbf_status {
+    APBF_OK = 0,
+    APBF_ERR_INVALID_ARG = 1,       /* bad pointer, size, value or range (nothing was changed) */
+    APBF_ERR_OUT_OF_MEMORY = 2,     /* device allocation failed, or the caller's arena is too small */
+    APBF_ERR_CUDA = 3,              /* a CUDA runtime call failed (message in apbf_last_error) */
+    APBF_ERR_TIMEOUT = 4,           /* a bounded device-side wait gave up */
+    APBF_ERR_BAD_STATE = 5,         /* call not valid in the scene's current state */
+    APBF_ERR_NEIGHBOR_OVERFLOW = 6, /* a particle had more neighbours than max_neighbors */
+    APBF_ERR_NOT_SUPPORTED = 7      /* option outside what this build implements */
+} apbf_status;
+
+/* Level-of-detail models (Sec. 4.1). */
+#define APBF_LOD_FIXED 0u /* plain PBF: every particle runs n_max iterations */
+#define APBF_LOD_DTC 1u   /* distance to camera (Sec. 4.1) */
+#define APBF_LOD_DTVS 2u  /* distance to the visible surface: reserved, APBF_ERR_NOT_SUPPORTED */
+
+/* apbf_scene_desc.flags */
+#define APBF_FLAG_NO_GRAPH 1u /* issue the step's kernels one by one instead of replaying a CUDA graph */
+
+/*
+ * Scene description. Units are SI (m, s, kg). Values are FP32 as the
+ * solver uses them.
+ *
+ *  n            particles, 0 <= n < 2^27.
+ *  pos, vel     host, 3n floats each in particle-id order; vel may be NULL (zero).
+ *               Copied at creation; the caller keeps ownership.
+ *  grid_lo/hi   static uniform-grid extent (cells of size h). Every particle
+ *               must lie inside it. Cells per axis: floor((hi-lo)*(1/h)) + 1
+ *               (FP32), at most 2047 (x, y) and 1023 (z).
+ *  box_lo/hi    collision box (contacts, Fig. 7 line 18), inside the grid extent.
+ *  h            smoothing length = neighbour radius = cell size, > 0.
+ *  dt           time step, > 0.
+ *  mass         particle mass (uniform), > 0; w = 1/mass (Sec. 3).
+ *  rho0         rest density (Eq. 5), > 0 (see apbf_rest_density).
+ *  eps          relaxation added to the denominator of Eq. 4, >= 0.
+ *  scorr_k, scorr_dq, scorr_n
+ *               tensile term s_corr = -k (W(r)/W(dq))^n added to lambda_i +
+ *               lambda_j in Eq. 7; k in m^2 (lambda's unit), 0 <= dq < h, n <= 16.
+ *  xsph_c       XSPH viscosity, v_i += c sum_j (m/rho0) (v_j - v_i) W_ij.
+ *  gravity      external acceleration f_ext (Fig. 7 line 2).
+ *  n_min, n_max iteration range, 1 <= n_min <= n_max <= 255 (Eq. 8: levels 1..N_l).
+ *  lod_mode     APBF_LOD_FIXED or APBF_LOD_DTC.
+ *  stabil_iters, stabil_s
+ *               pre-stabilisation (Fig. 7 lines 7-11) of the set of Eq. 11 for
+ *               l = S. Only S <= 1 (empty set) is supported; S > 1 returns
+ *               APBF_ERR_NOT_SUPPORTED.
+ *  max_neighbors neighbour-list capacity per particle, 0 = 128, at most 255.
+ *  flags        APBF_FLAG_*.
+ */
+typedef struct apbf_scene_desc {
+    uint32_t n;
+    const float *pos;
+    const float *vel;
+    float grid_lo[3], grid_hi[3];
+    float box_lo[3], box_hi[3];
+    float h, dt, mass, rho0, eps;
+    float scorr_k, scorr_dq;
+    uint32_t scorr_n;
+    float xsph_c;
+    float gravity[3];
+    uint32_t n_min, n_max, lod_mode;
+    uint32_t stabil_iters, stabil_s;
+    uint32_t max_neighbors;
+    uint32_t flags;
+} apbf_scene_desc;
+
+typedef struct apbf_scene apbf_scene;
+
+/* Per-step counters of the last completed apbf_step (apbf_step_info). */
+typedef struct apbf_step_info {
+    uint64_t particle_iterations;   /* sum_i N_i = sum_l |P_l| (Eq. 10) */
+    uint64_t neighbor_pairs;        /* sum_i |neighbours of i| */
+    uint64_t lambda_pairs;          /* pairs visited by all lambda passes: sum_l sum_{i in P_l} |nbrs i| */
+    uint32_t active_count[256];     /* |P_l| for l = 0..255 (l > n_max: 0) */
+    float d_range[2];               /* distance range used by the LOD (0, 0 when fixed) */
+} apbf_step_info;
+
+/* Human-readable name of a status code (static string). */
+APBF_API const char *apbf_status_string(apbf_status s);
+
+/* Eq. 6 at an interior particle of a jitter-free cubic lattice of the given
+ * spacing, self term included (poly6 kernel), computed on the host in FP64.
+ * Host-only; needs no GPU. rho0 (host) receives the value. */
+APBF_API apbf_status apbf_rest_density(float h, float mass, float spacing, double *rho0);
+
+/* Device bytes a scene with this description needs (host-only, no GPU). */
+APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes);
+
+/*
+ * Create a scene on the current CUDA device.
+ *  desc          host; validated (APBF_ERR_INVALID_ARG / NOT_SUPPORTED on failure).
+ *  cuda_stream   a cudaStream_t of the current device (NULL = the legacy default stream).
+ *  device_arena  device memory of at least apbf_scene_bytes() bytes, 256-byte
+ *                aligned, owned by the caller and kept alive until
+ *                apbf_destroy_scene; or NULL, in which case the library
+ *                allocates (cudaMalloc) and frees it.
+ *  arena_bytes   size of device_arena (ignored when NULL).
+ *  out           host; receives the scene handle (NULL on failure).
+ * Synchronises the stream once (the initial upload).
+ */
+APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *desc, void *cuda_stream, void *device_arena,
+                                       size_t arena_bytes, apbf_scene **out);
+
+/* Camera of the DTC model (Sec. 4.1), used from the next apbf_step on.
+ *  eye, dir  host, 3 floats; dir is stored for view-dependent models and must be finite.
+ *  d_near < d_far: user-defined distance range; otherwise the range is the
+ *  min/max camera distance over the scene at the start of each step (Sec. 4.1). */
+APBF_API apbf_status apbf_set_camera(apbf_scene *scene, const float eye[3], const float dir[3], float d_near,
+                                     float d_far);
+
+/* Move the collision box (e.g. an oscillating wall) from the next step on.
+ * lo, hi: host, 3 floats, grid_lo <= lo < hi <= grid_hi. */
+APBF_API apbf_status apbf_set_box(apbf_scene *scene, const float lo[3], const float hi[3]);
+
+/* Enqueue nsteps simulation steps (Fig. 7) on the scene's stream. Asynchronous. */
+APBF_API apbf_status apbf_step(apbf_scene *scene, uint32_t nsteps);
+
+/* Synchronise and copy the state to host buffers in particle-id order.
+ * Each pointer may be NULL to skip it: pos, vel (3n floats), n_iter (n bytes:
+ * the N_i of the last step, 0 before the first), rho (n floats: the density
+ * of each particle's last lambda pass in the last step, 0 before the first). */
+APBF_API apbf_status apbf_read_state(apbf_scene *scene, float *pos, float *vel, uint8_t *n_iter, float *rho);
+
+/* Synchronise and report density-error statistics of the current positions
+ * (Fig. 9): stats (host, 4 doubles) = {mean |rho/rho0-1|, max |rho/rho0-1|,
+ * mean (rho/rho0-1), mean max(0, rho/rho0-1)}, with a fresh neighbour search.
+ * Does not change the simulation state. */
+APBF_API apbf_status apbf_density_stats(apbf_scene *scene, double stats[4]);
+
+/* Synchronise and return the counters of the last step (host struct). */
+APBF_API apbf_status apbf_get_step_info(apbf_scene *scene, apbf_step_info *info);
+
+/* Wait for the scene's queued work; returns the first error seen. */
+APBF_API apbf_status apbf_sync(apbf_scene *scene);
+
+/* Last error message of the scene (library-owned, valid until the next call
+ * on the scene), or of the last failed create when scene is NULL. */
+APBF_API const char *apbf_last_error(const apbf_scene *scene);
+
+/* Release the scene and the memory it allocated (NULL-safe). Synchronises. */
+APBF_API void apbf_destroy_scene(apbf_scene *scene);
+
+/* ---------------------------------------------------------------- timing */
+
+/* Stage identifiers (timing and debug). */
+#define APBF_STAGE_LOD_RANGE 0u  /* a1: camera-distance min/max */
+#define APBF_STAGE_PREDICT 1u    /* a1-a4: level, prediction, cell hash, histogram */
+#define APBF_STAGE_SCAN 2u       /* a4/a6: exclusive scan = cell start/end */
+#define APBF_STAGE_SCATTER 3u    /* a4: slot scatter */
+#define APBF_STAGE_REORDER 4u    /* a4/a5: stable rank and reorder */
+#define APBF_STAGE_NEIGHBORS 5u  /* neighbour lists (Fig. 7 line 6) */
+#define APBF_STAGE_LEVELS 6u     /* a7: active-set partition */
+#define APBF_STAGE_LAMBDA 7u     /* a8 */
+#define APBF_STAGE_DELTAP 8u     /* a9 */
+#define APBF_STAGE_FINALIZE 9u   /* a10 */
+#define APBF_STAGE_COUNT 10u
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing of apbf_step. While
+ * enabled, steps are issued kernel by kernel (no graph replay). */
+APBF_API apbf_status apbf_set_timing(apbf_scene *scene, int enable);
+
+/* Synchronise and report, per stage (APBF_STAGE_COUNT entries each, host):
+ * the summed device time in ms and the number of kernel launches timed since
+ * the last report; then reset the counters. */
+APBF_API apbf_status apbf_timing_report(apbf_scene *scene, double *ms, uint64_t *launches);
+
+/* ----------------------------------------------------- test-only exports */
+
+/* Run one fresh step of the current state up to and including a stage
+ * (iteration 1..n_max for LAMBDA / DELTAP). The state (positions, velocities,
+ * order) is not advanced unless stage == APBF_STAGE_FINALIZE. */
+APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint32_t iteration);
+
+#define APBF_DBG_KEYS 0u          /* u32[n]  cell key, pre-sort (state) order */
+#define APBF_DBG_STATE_IDS 1u     /* u32[n]  particle ids in state order */
+#define APBF_DBG_LEVEL_PRESORT 2u /* u8[n]   N_i, pre-sort order */
+#define APBF_DBG_SORTED_IDS 3u    /* u32[n]  particle ids in sorted order */
+#define APBF_DBG_CELL_START 4u    /* u32[ncell+1] */
+#define APBF_DBG_XPRED 5u         /* float4[n] predicted positions (FP32), sorted */
+#define APBF_DBG_LEVEL 6u         /* u8[n]   N_i, sorted */
+#define APBF_DBG_NBR_COUNT 7u     /* u8[n]   neighbour count, sorted */
+#define APBF_DBG_NBR 8u           /* u32[max_neighbors*n]: entry k of particle p at k*n+p,
+                                     low 27 bits = sorted slot, high 5 bits = cell offset code */
+#define APBF_DBG_ACTIVE 9u        /* u32[n]  sorted slots, active-set order (P_l = prefix) */
+#define APBF_DBG_LEVEL_COUNT 10u  /* u32[n_max+2] |P_l|, l = 0..n_max+1 */
+#define APBF_DBG_LAMBDA 11u       /* float[n] lambda after the stage, sorted */
+#define APBF_DBG_RHO 12u          /* float[n] density of the last lambda pass, sorted */
+#define APBF_DBG_XSTAR 13u        /* float4[n] current x* (absolute FP32), sorted */
+#define APBF_DBG_DRANGE 14u       /* float[2] LOD distance range */
+
+/* Copy a debug field (see APBF_DBG_*) to host memory of `bytes` bytes
+ * (must equal the field's size). Synchronises. */
+APBF_API apbf_status apbf_debug_read(apbf_scene *scene, uint32_t field, void *host, size_t bytes);
+
+/* Sizes of the scene's grid: dims (3 ints), ncell, max_neighbors (host outputs). */
+APBF_API apbf_status apbf_debug_dims(apbf_scene *scene, int32_t dims[3], uint32_t *ncell,
+                                     uint32_t *max_neighbors);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APBF_H */

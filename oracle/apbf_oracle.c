@@ -596,11 +596,38 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
         goto done;
     /* Fig. 7 lines 1-4 (FP32). */
     orc_predict(p, n, x, v, xpred);
-    /* Fig. 7 lines 5-6: stable counting sort by cell, then neighbour sets. */
+    /* Fig. 7 lines 5-6: counting sort by cell, ties by particle id (the
+       counting sort is stable and is fed the particles in id order), then
+       neighbour sets. */
     orc_cell_keys(p, n, xpred, keys);
-    rc = orc_counting_sort(n, keys, ncell, order, start);
-    if (rc)
-        goto done;
+    {
+        int32_t *pos_of_id = (int32_t *)malloc(sizeof(int32_t) * nn);
+        uint32_t *keys_by_id = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+        if (!pos_of_id || !keys_by_id) {
+            free(pos_of_id);
+            free(keys_by_id);
+            rc = -3;
+            goto done;
+        }
+        rc = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            if (id[i] < 0 || id[i] >= n)
+                rc = -1;
+            else
+                pos_of_id[id[i]] = i;
+        }
+        if (rc == 0) {
+            for (int32_t k = 0; k < n; ++k)
+                keys_by_id[k] = keys[pos_of_id[k]];
+            rc = orc_counting_sort(n, keys_by_id, ncell, order, start);
+            for (int32_t s = 0; s < n && rc == 0; ++s)
+                order[s] = pos_of_id[order[s]];
+        }
+        free(pos_of_id);
+        free(keys_by_id);
+        if (rc)
+            goto done;
+    }
     for (int32_t s = 0; s < n; ++s) {
         int32_t i = order[s];
         memcpy(xs32 + 3 * s, xpred + 3 * i, 3 * sizeof(float));

@@ -51,8 +51,8 @@ typedef struct orc_params {
 typedef struct orc_record {
     /* Optional outputs of one step (NULL = not recorded), caller-owned.
        "pre-sort order" is the state order at the start of the step;
-       "sorted order" is the order after the stable counting sort, which is
-       also the state order after the step. */
+       "sorted order" is the order after the counting sort (by cell key, ties
+       by particle id), which is also the state order after the step. */
     float *xpred;           /* 3n, pre-sort order, FP32 prediction incl. box clamp */
     int32_t *level_presort; /* n, pre-sort order */
     uint32_t *keys;         /* n, pre-sort order */
@@ -114,8 +114,10 @@ int orc_delta_p(const orc_params *p, int32_t n, const double *xs, const double *
 int orc_xsph(const orc_params *p, int32_t n, const double *xs, const double *v,
              const int32_t *nbr_off, const int32_t *nbr_idx, double *vout);
 
-/* One APBF step (Fig. 7). x, v (3n) and id (n) are the state in its current
-   order; on return they hold the new state in sorted order. */
+/* One APBF step (Fig. 7). x, v (3n) and id (n, a permutation of 0..n-1)
+   are the state in its current order; on return they hold the new state in
+   sorted order (cell key, then particle id). The result does not depend on
+   the order of the input. */
 int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, orc_record *rec);
 
 /* Density diagnostic at the given positions (fresh neighbour search):

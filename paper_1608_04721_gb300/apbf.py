@@ -1,0 +1,368 @@
+"""Thin ctypes binding of the C ABI in include/apbf.h (same names).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library libapbf.so. PyTorch, when present, lends device memory (the scene
+arena) and the current CUDA stream. If the library has not been built the
+import still works, but the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapbf.so")
+
+# status codes
+APBF_OK = 0
+APBF_ERR_INVALID_ARG = 1
+APBF_ERR_OUT_OF_MEMORY = 2
+APBF_ERR_CUDA = 3
+APBF_ERR_TIMEOUT = 4
+APBF_ERR_BAD_STATE = 5
+APBF_ERR_NEIGHBOR_OVERFLOW = 6
+APBF_ERR_NOT_SUPPORTED = 7
+
+APBF_LOD_FIXED = 0
+APBF_LOD_DTC = 1
+APBF_LOD_DTVS = 2
+APBF_FLAG_NO_GRAPH = 1
+
+STAGES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
+          "finalize"]
+(APBF_STAGE_LOD_RANGE, APBF_STAGE_PREDICT, APBF_STAGE_SCAN, APBF_STAGE_SCATTER, APBF_STAGE_REORDER,
+ APBF_STAGE_NEIGHBORS, APBF_STAGE_LEVELS, APBF_STAGE_LAMBDA, APBF_STAGE_DELTAP, APBF_STAGE_FINALIZE) = range(10)
+APBF_STAGE_COUNT = 10
+
+(APBF_DBG_KEYS, APBF_DBG_STATE_IDS, APBF_DBG_LEVEL_PRESORT, APBF_DBG_SORTED_IDS, APBF_DBG_CELL_START,
+ APBF_DBG_XPRED, APBF_DBG_LEVEL, APBF_DBG_NBR_COUNT, APBF_DBG_NBR, APBF_DBG_ACTIVE, APBF_DBG_LEVEL_COUNT,
+ APBF_DBG_LAMBDA, APBF_DBG_RHO, APBF_DBG_XSTAR, APBF_DBG_DRANGE) = range(15)
+
+
+class apbf_scene_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint32),
+        ("pos", C.POINTER(C.c_float)),
+        ("vel", C.POINTER(C.c_float)),
+        ("grid_lo", C.c_float * 3), ("grid_hi", C.c_float * 3),
+        ("box_lo", C.c_float * 3), ("box_hi", C.c_float * 3),
+        ("h", C.c_float), ("dt", C.c_float), ("mass", C.c_float), ("rho0", C.c_float), ("eps", C.c_float),
+        ("scorr_k", C.c_float), ("scorr_dq", C.c_float),
+        ("scorr_n", C.c_uint32),
+        ("xsph_c", C.c_float),
+        ("gravity", C.c_float * 3),
+        ("n_min", C.c_uint32), ("n_max", C.c_uint32), ("lod_mode", C.c_uint32),
+        ("stabil_iters", C.c_uint32), ("stabil_s", C.c_uint32),
+        ("max_neighbors", C.c_uint32),
+        ("flags", C.c_uint32),
+    ]
+
+
+class apbf_step_info(C.Structure):
+    _fields_ = [
+        ("particle_iterations", C.c_uint64),
+        ("neighbor_pairs", C.c_uint64),
+        ("lambda_pairs", C.c_uint64),
+        ("active_count", C.c_uint32 * 256),
+        ("d_range", C.c_float * 2),
+    ]
+
+
+EXPORTS = [
+    "apbf_status_string", "apbf_rest_density", "apbf_scene_bytes", "apbf_create_scene", "apbf_set_camera",
+    "apbf_set_box", "apbf_step", "apbf_read_state", "apbf_density_stats", "apbf_get_step_info", "apbf_sync",
+    "apbf_last_error", "apbf_destroy_scene", "apbf_set_timing", "apbf_timing_report", "apbf_debug_step_to",
+    "apbf_debug_read", "apbf_debug_dims",
+]
+
+_lib = None
+
+
+class ApbfError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {_status_name(status)} ({status}): {message}")
+        self.status = status
+
+
+def _status_name(st: int) -> str:
+    try:
+        return lib().apbf_status_string(st).decode()
+    except Exception:
+        return str(st)
+
+
+def lib():
+    """The loaded libapbf.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                               f"g.build()\"` (there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        P, V = C.POINTER, C.c_void_p
+        L.apbf_status_string.restype = C.c_char_p
+        L.apbf_status_string.argtypes = [C.c_int]
+        L.apbf_rest_density.argtypes = [C.c_float, C.c_float, C.c_float, P(C.c_double)]
+        L.apbf_scene_bytes.argtypes = [P(apbf_scene_desc), P(C.c_size_t)]
+        L.apbf_create_scene.argtypes = [P(apbf_scene_desc), V, V, C.c_size_t, P(V)]
+        L.apbf_set_camera.argtypes = [V, P(C.c_float), P(C.c_float), C.c_float, C.c_float]
+        L.apbf_set_box.argtypes = [V, P(C.c_float), P(C.c_float)]
+        L.apbf_step.argtypes = [V, C.c_uint32]
+        L.apbf_read_state.argtypes = [V, P(C.c_float), P(C.c_float), P(C.c_uint8), P(C.c_float)]
+        L.apbf_density_stats.argtypes = [V, P(C.c_double)]
+        L.apbf_get_step_info.argtypes = [V, P(apbf_step_info)]
+        L.apbf_sync.argtypes = [V]
+        L.apbf_last_error.restype = C.c_char_p
+        L.apbf_last_error.argtypes = [V]
+        L.apbf_destroy_scene.restype = None
+        L.apbf_destroy_scene.argtypes = [V]
+        L.apbf_set_timing.argtypes = [V, C.c_int]
+        L.apbf_timing_report.argtypes = [V, P(C.c_double), P(C.c_uint64)]
+        L.apbf_debug_step_to.argtypes = [V, C.c_uint32, C.c_uint32]
+        L.apbf_debug_read.argtypes = [V, C.c_uint32, V, C.c_size_t]
+        L.apbf_debug_dims.argtypes = [V, P(C.c_int32), P(C.c_uint32), P(C.c_uint32)]
+        for f in EXPORTS:
+            if f not in ("apbf_status_string", "apbf_last_error", "apbf_destroy_scene"):
+                getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str, scene=None):
+    if st != APBF_OK:
+        h = scene.handle if scene is not None else None
+        raise ApbfError(st, where, lib().apbf_last_error(h).decode())
+
+
+def _fptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Scene:
+    """Handle of a created scene; keeps the arena and inputs alive."""
+
+    def __init__(self, handle, n, desc, keep):
+        self.handle = handle
+        self.n = n
+        self.desc = desc
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().apbf_destroy_scene(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def make_desc(*, pos: np.ndarray, vel: Optional[np.ndarray] = None, grid_lo, grid_hi, box_lo=None, box_hi=None,
+              h: float, dt: float, mass: float, rho0: float, eps: float, scorr_k: float, scorr_dq: float,
+              scorr_n: int, xsph_c: float, gravity, n_min: int, n_max: int, lod_mode: int, stabil_iters: int = 0,
+              stabil_s: int = 1, max_neighbors: int = 0, flags: int = 0):
+    """Fill an apbf_scene_desc; returns (desc, arrays to keep alive)."""
+    pos = np.ascontiguousarray(pos, np.float32).reshape(-1, 3)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float32).reshape(-1, 3)
+    d = apbf_scene_desc()
+    d.n = pos.shape[0]
+    d.pos = _fptr(pos) if pos.size else None
+    d.vel = _fptr(vel) if vel is not None and vel.size else None
+    d.grid_lo[:] = [float(v) for v in grid_lo]
+    d.grid_hi[:] = [float(v) for v in grid_hi]
+    d.box_lo[:] = [float(v) for v in (grid_lo if box_lo is None else box_lo)]
+    d.box_hi[:] = [float(v) for v in (grid_hi if box_hi is None else box_hi)]
+    d.h, d.dt, d.mass, d.rho0, d.eps = h, dt, mass, rho0, eps
+    d.scorr_k, d.scorr_dq, d.scorr_n, d.xsph_c = scorr_k, scorr_dq, scorr_n, xsph_c
+    d.gravity[:] = [float(v) for v in gravity]
+    d.n_min, d.n_max, d.lod_mode = n_min, n_max, lod_mode
+    d.stabil_iters, d.stabil_s, d.max_neighbors, d.flags = stabil_iters, stabil_s, max_neighbors, flags
+    return d, (pos, vel)
+
+
+def desc_from_config(cfg, pos, vel, rho0: float, **over):
+    """apbf_scene_desc from a scenes.SceneConfig (plain field mapping)."""
+    kw = dict(pos=pos, vel=vel, grid_lo=cfg.box_lo, grid_hi=cfg.box_hi, h=cfg.h, dt=cfg.dt, mass=cfg.mass,
+              rho0=rho0, eps=cfg.eps, scorr_k=cfg.scorr_k, scorr_dq=cfg.scorr_dq, scorr_n=cfg.scorr_n,
+              xsph_c=cfg.xsph_c, gravity=cfg.gravity, n_min=cfg.n_min, n_max=cfg.n_max, lod_mode=cfg.lod_mode)
+    kw.update(over)
+    return make_desc(**kw)
+
+
+# ------------------------------------------------------------ entry points
+
+def apbf_status_string(status: int) -> str:
+    return lib().apbf_status_string(status).decode()
+
+
+def apbf_rest_density(h: float, mass: float, spacing: float) -> float:
+    out = C.c_double()
+    _check(lib().apbf_rest_density(h, mass, spacing, C.byref(out)), "apbf_rest_density")
+    return out.value
+
+
+def apbf_scene_bytes(desc) -> int:
+    d = desc[0] if isinstance(desc, tuple) else desc
+    out = C.c_size_t()
+    _check(lib().apbf_scene_bytes(C.byref(d), C.byref(out)), "apbf_scene_bytes")
+    return out.value
+
+
+def apbf_create_scene(desc, stream=None, device_arena="torch") -> Scene:
+    """desc: apbf_scene_desc or the (desc, keep) pair of make_desc.
+    stream: a CUDA stream handle (int) or a torch.cuda.Stream; None = torch's
+    current stream (or the default stream without torch).
+    device_arena: "torch" (a torch.uint8 CUDA tensor lent to the library),
+    None (the library allocates), or a torch tensor / (pointer, bytes) pair."""
+    keep = ()
+    if isinstance(desc, tuple):
+        desc, keep = desc
+    torch = None
+    try:
+        import torch as _torch
+        torch = _torch if _torch.cuda.is_available() else None
+    except Exception:
+        torch = None
+    if stream is None:
+        stream_ptr = torch.cuda.current_stream().cuda_stream if torch is not None else 0
+    elif hasattr(stream, "cuda_stream"):
+        stream_ptr = stream.cuda_stream
+    else:
+        stream_ptr = int(stream)
+    arena_ptr, arena_bytes, arena_keep = None, 0, None
+    if isinstance(device_arena, str) and device_arena == "torch":
+        if torch is not None:
+            nbytes = apbf_scene_bytes(desc)
+            arena_keep = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = arena_keep.data_ptr()
+            arena_ptr = (base + 255) // 256 * 256
+            arena_bytes = nbytes
+    elif device_arena is None:
+        pass
+    elif hasattr(device_arena, "data_ptr"):
+        arena_keep = device_arena
+        arena_ptr = device_arena.data_ptr()
+        arena_bytes = device_arena.numel() * device_arena.element_size()
+    else:
+        arena_ptr, arena_bytes = int(device_arena[0]), int(device_arena[1])
+    h = C.c_void_p()
+    st = lib().apbf_create_scene(C.byref(desc), C.c_void_p(stream_ptr), C.c_void_p(arena_ptr), arena_bytes,
+                                 C.byref(h))
+    _check(st, "apbf_create_scene")
+    return Scene(h, desc.n, desc, (keep, arena_keep))
+
+
+def apbf_set_camera(scene: Scene, eye, direction=(1.0, 0.0, 0.0), d_near: float = 0.0, d_far: float = 0.0):
+    e = (C.c_float * 3)(*[float(v) for v in eye])
+    d = (C.c_float * 3)(*[float(v) for v in direction])
+    _check(lib().apbf_set_camera(scene.handle, e, d, d_near, d_far), "apbf_set_camera", scene)
+
+
+def apbf_set_box(scene: Scene, lo, hi):
+    a = (C.c_float * 3)(*[float(v) for v in lo])
+    b = (C.c_float * 3)(*[float(v) for v in hi])
+    _check(lib().apbf_set_box(scene.handle, a, b), "apbf_set_box", scene)
+
+
+def apbf_step(scene: Scene, nsteps: int = 1):
+    _check(lib().apbf_step(scene.handle, nsteps), "apbf_step", scene)
+
+
+def apbf_read_state(scene: Scene, pos=True, vel=True, n_iter=False, rho=False):
+    """Each argument: False (skip), True (allocate) or a preallocated numpy
+    array (e.g. in pinned memory). Returns a dict of the requested arrays in
+    particle-id order."""
+    n = scene.n
+    out = {}
+
+    def take(name, want, shape, dtype):
+        if want is False or want is None:
+            return None
+        a = np.empty(shape, dtype) if want is True else want
+        assert a.dtype == dtype and a.flags["C_CONTIGUOUS"] and a.size == int(np.prod(shape))
+        out[name] = a
+        return a
+
+    p = take("pos", pos, (n, 3), np.float32)
+    v = take("vel", vel, (n, 3), np.float32)
+    it = take("n_iter", n_iter, (n,), np.uint8)
+    r = take("rho", rho, (n,), np.float32)
+    st = lib().apbf_read_state(scene.handle, _fptr(p), _fptr(v),
+                               None if it is None else it.ctypes.data_as(C.POINTER(C.c_uint8)), _fptr(r))
+    _check(st, "apbf_read_state", scene)
+    return out
+
+
+def apbf_density_stats(scene: Scene) -> np.ndarray:
+    out = np.zeros(4)
+    _check(lib().apbf_density_stats(scene.handle, out.ctypes.data_as(C.POINTER(C.c_double))),
+           "apbf_density_stats", scene)
+    return out
+
+
+def apbf_get_step_info(scene: Scene) -> dict:
+    info = apbf_step_info()
+    _check(lib().apbf_get_step_info(scene.handle, C.byref(info)), "apbf_get_step_info", scene)
+    return dict(particle_iterations=int(info.particle_iterations), neighbor_pairs=int(info.neighbor_pairs),
+                lambda_pairs=int(info.lambda_pairs), active_count=np.array(info.active_count[:], np.int64),
+                d_range=np.array(info.d_range[:], np.float32))
+
+
+def apbf_sync(scene: Scene):
+    _check(lib().apbf_sync(scene.handle), "apbf_sync", scene)
+
+
+def apbf_last_error(scene: Optional[Scene] = None) -> str:
+    return lib().apbf_last_error(scene.handle if scene is not None else None).decode()
+
+
+def apbf_destroy_scene(scene: Scene):
+    if scene.handle:
+        lib().apbf_destroy_scene(scene.handle)
+        scene.handle = None
+
+
+def apbf_set_timing(scene: Scene, enable: bool):
+    _check(lib().apbf_set_timing(scene.handle, 1 if enable else 0), "apbf_set_timing", scene)
+
+
+def apbf_timing_report(scene: Scene):
+    ms = np.zeros(APBF_STAGE_COUNT)
+    ln = np.zeros(APBF_STAGE_COUNT, np.uint64)
+    _check(lib().apbf_timing_report(scene.handle, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                    ln.ctypes.data_as(C.POINTER(C.c_uint64))), "apbf_timing_report", scene)
+    return ms, ln
+
+
+def apbf_debug_step_to(scene: Scene, stage: int, iteration: int = 0):
+    _check(lib().apbf_debug_step_to(scene.handle, stage, iteration), "apbf_debug_step_to", scene)
+
+
+def apbf_debug_dims(scene: Scene):
+    dims = (C.c_int32 * 3)()
+    ncell, mx = C.c_uint32(), C.c_uint32()
+    _check(lib().apbf_debug_dims(scene.handle, dims, C.byref(ncell), C.byref(mx)), "apbf_debug_dims", scene)
+    return np.array(dims[:], np.int32), ncell.value, mx.value
+
+
+def apbf_debug_read(scene: Scene, field: int) -> np.ndarray:
+    n = scene.n
+    dims, ncell, mx = apbf_debug_dims(scene)
+    n_max = int(scene.desc.n_max)
+    shapes = {
+        APBF_DBG_KEYS: ((n,), np.uint32), APBF_DBG_STATE_IDS: ((n,), np.uint32),
+        APBF_DBG_LEVEL_PRESORT: ((n,), np.uint8), APBF_DBG_SORTED_IDS: ((n,), np.uint32),
+        APBF_DBG_CELL_START: ((ncell + 1,), np.uint32), APBF_DBG_XPRED: ((n, 4), np.float32),
+        APBF_DBG_LEVEL: ((n,), np.uint8), APBF_DBG_NBR_COUNT: ((n,), np.uint8),
+        APBF_DBG_NBR: ((mx, n), np.uint32), APBF_DBG_ACTIVE: ((n,), np.uint32),
+        APBF_DBG_LEVEL_COUNT: ((n_max + 2,), np.uint32), APBF_DBG_LAMBDA: ((n,), np.float32),
+        APBF_DBG_RHO: ((n,), np.float32), APBF_DBG_XSTAR: ((n, 4), np.float32),
+        APBF_DBG_DRANGE: ((2,), np.float32),
+    }
+    shape, dt = shapes[field]
+    a = np.empty(shape, dt)
+    _check(lib().apbf_debug_read(scene.handle, field, C.c_void_p(a.ctypes.data if a.size else 0), a.nbytes),
+           "apbf_debug_read", scene)
+    return a

@@ -1,0 +1,858 @@
+// Host side of the C ABI declared in include/apbf.h: validation, the device
+// arena, step orchestration (eager launches or a captured CUDA graph),
+// readback, diagnostics, timing and test-only exports.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "apbf_internal.h"
+
+using namespace apbf;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t kAlign = 256;
+constexpr uint32_t kCounterSlots = 2 + 256 + 2;  // pairs, lambda pairs, per-bin pairs, diagnostic scratch
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+apbf_status fail(apbf_scene *s, apbf_status st, const std::string &m)
+{
+    if (s) {
+        s->msg = m;
+        if (st == APBF_ERR_CUDA || st == APBF_ERR_NEIGHBOR_OVERFLOW || st == APBF_ERR_TIMEOUT)
+            s->sticky = st;
+    } else {
+        g_create_error = m;
+    }
+    return st;
+}
+
+apbf_status cuda_fail(apbf_scene *s, cudaError_t e, const char *where)
+{
+    return fail(s, APBF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define APBF_CUDA(s, expr)                                \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess)                            \
+            return cuda_fail((s), e_, #expr);             \
+    } while (0)
+
+bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// Derived constants of a description; returns an error message or "".
+std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
+{
+    st = APBF_ERR_INVALID_ARG;
+    if (!d)
+        return "desc is NULL";
+    if (d->n >= (1u << kSlotBits))
+        return "n must be below 2^27";
+    if (d->n > 0 && !d->pos)
+        return "pos is NULL";
+    if (!(d->h > 0.0f) || !std::isfinite(d->h))
+        return "h must be positive and finite";
+    if (!(d->dt > 0.0f) || !std::isfinite(d->dt))
+        return "dt must be positive and finite";
+    if (!(d->mass > 0.0f) || !std::isfinite(d->mass))
+        return "mass must be positive and finite";
+    if (!(d->rho0 > 0.0f) || !std::isfinite(d->rho0))
+        return "rho0 must be positive and finite";
+    if (!(d->eps >= 0.0f) || !std::isfinite(d->eps))
+        return "eps must be >= 0 and finite";
+    if (!std::isfinite(d->scorr_k) || !(d->scorr_dq >= 0.0f) || !(d->scorr_dq < d->h) || d->scorr_n > 16)
+        return "tensile term needs finite k, 0 <= dq < h and n <= 16";
+    if (!std::isfinite(d->xsph_c) || !finite3(d->gravity))
+        return "xsph_c and gravity must be finite";
+    if (d->n_min < 1 || d->n_max < d->n_min || d->n_max > 255)
+        return "need 1 <= n_min <= n_max <= 255";
+    if (d->lod_mode == APBF_LOD_DTVS) {
+        st = APBF_ERR_NOT_SUPPORTED;
+        return "the DTVS adaption model is not built";
+    }
+    if (d->lod_mode != APBF_LOD_FIXED && d->lod_mode != APBF_LOD_DTC)
+        return "unknown lod_mode";
+    if (d->stabil_s > 1) {
+        st = APBF_ERR_NOT_SUPPORTED;
+        return "pre-stabilisation with S > 1 is not built (S <= 1 makes its set empty)";
+    }
+    if (d->max_neighbors > 255)
+        return "max_neighbors must be <= 255";
+    if (d->flags & ~APBF_FLAG_NO_GRAPH)
+        return "unknown flag";
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(d->grid_lo[a]) || !std::isfinite(d->grid_hi[a]) || !std::isfinite(d->box_lo[a]) ||
+            !std::isfinite(d->box_hi[a]))
+            return "grid and box bounds must be finite";
+        if (!(d->grid_lo[a] <= d->box_lo[a] && d->box_lo[a] < d->box_hi[a] && d->box_hi[a] <= d->grid_hi[a]))
+            return "need grid_lo <= box_lo < box_hi <= grid_hi on every axis";
+    }
+    sc = StepConst{};
+    sc.n = d->n;
+    sc.inv_h = 1.0f / d->h;
+    int dims[3];
+    for (int a = 0; a < 3; ++a) {
+        volatile float ext = d->grid_hi[a] - d->grid_lo[a];
+        volatile float t = ext * sc.inv_h;
+        double fl = std::floor((double)t);
+        if (fl > 4096.0)
+            return "grid too large for the cell packing";
+        dims[a] = (int)fl + 1;
+        sc.glo[a] = d->grid_lo[a];
+    }
+    if (dims[0] > 2047 || dims[1] > 2047 || dims[2] > 1023)
+        return "grid must have at most 2047 x 2047 x 1023 cells";
+    uint64_t ncell = (uint64_t)dims[0] * dims[1] * dims[2];
+    if (ncell >= (1ull << 31))
+        return "grid has too many cells";
+    sc.nx = dims[0];
+    sc.ny = dims[1];
+    sc.nz = dims[2];
+    sc.ncell = (uint32_t)ncell;
+    sc.h = d->h;
+    sc.h2 = d->h * d->h;
+    sc.dt = d->dt;
+    sc.inv_dt = (float)(1.0 / (double)d->dt);
+    for (int a = 0; a < 3; ++a)
+        sc.g[a] = d->gravity[a];
+    // local-origin lattice spacing: h rounded to 8 significant bits
+    int e2;
+    double f = std::frexp((double)d->h, &e2);
+    sc.q = (float)std::ldexp(std::nearbyint(f * 256.0), e2 - 8);
+    for (int a = 0; a < 3; ++a) {
+        double m = std::nearbyint((double)d->grid_lo[a] / (double)sc.q);
+        if (std::fabs(m) + dims[a] + 2 > 32767.0)
+            return "grid origin too far from 0 relative to h";
+        sc.m[a] = (int32_t)m;
+    }
+    const double PI = 3.14159265358979323846;
+    const double h = d->h, m = d->mass, rho0 = d->rho0, w = 1.0 / m;
+    const double poly6 = 315.0 / (64.0 * PI * std::pow(h, 9));
+    const double spiky = 45.0 / (PI * std::pow(h, 6));
+    const double h2 = h * h;
+    sc.mass_poly6 = (float)(m * poly6);
+    sc.h6 = (float)(h2 * h2 * h2);
+    sc.inv_rho0 = (float)(1.0 / rho0);
+    sc.c_lam = (float)(w * (m * spiky / rho0) * (m * spiky / rho0));
+    sc.eps = d->eps;
+    sc.c_dp = (float)(-(w * m / rho0) * spiky);
+    const double dq = d->scorr_dq;
+    sc.inv_wdq = (float)(1.0 / (h2 - dq * dq));
+    sc.neg_k = -d->scorr_k;
+    sc.scorr_n = d->scorr_n;
+    sc.c_xsph = (float)((double)d->xsph_c * (m / rho0) * poly6);
+    sc.n_min = d->lod_mode == APBF_LOD_FIXED ? d->n_max : d->n_min;
+    sc.n_max = d->n_max;
+    sc.K = sc.n_max - sc.n_min + 1;
+    sc.lod_mode = d->lod_mode;
+    sc.max_nbr = d->max_neighbors ? d->max_neighbors : kDefaultMaxNeighbors;
+    sc.level_tiles = (d->n + kLevelTile - 1) / kLevelTile;
+    sc.rho0 = d->rho0;
+    st = APBF_OK;
+    return "";
+}
+
+struct Layout {
+    size_t total = 0;
+    size_t off[40] = {};
+    int k = 0;
+    size_t add(size_t bytes)
+    {
+        size_t o = total;
+        total = align_up(total + (bytes ? bytes : 1));
+        off[k++] = o;
+        return o;
+    }
+};
+
+// Carves the arena; with base == nullptr only measures.
+size_t carve(const StepConst &sc, char *base, Buffers &b)
+{
+    const size_t n = sc.n ? sc.n : 1;
+    const size_t ncell4 = (sc.ncell + 3) / 4 * 4;
+    const size_t tiles = (sc.ncell + kScanTile - 1) / kScanTile;
+    const size_t lvl_e = (size_t)sc.K * (sc.level_tiles ? sc.level_tiles : 1);
+    const size_t dblocks = (n + kBlock - 1) / kBlock;
+    Layout L;
+    auto P = [&](size_t bytes) -> char * { size_t o = L.add(bytes); return base ? base + o : nullptr; };
+    b.state_x = (float4 *)P(16 * n);
+    b.state_v = (float4 *)P(16 * n);
+    b.state_id = (uint32_t *)P(4 * n);
+    b.key = (uint32_t *)P(4 * n);
+    b.slot = (uint32_t *)P(4 * n);
+    b.lvl = (uint8_t *)P(n);
+    b.cnt = (uint32_t *)P(4 * ncell4);
+    b.start = (uint32_t *)P(4 * (size_t)(sc.ncell + 1));
+    b.tile_sums = (uint32_t *)P(4 * tiles);
+    b.tmp = (uint32_t *)P(4 * n);
+    b.recA = (float4 *)P(16 * n);
+    b.recB = (float4 *)P(16 * n);
+    b.xs32 = (float4 *)P(16 * n);
+    b.xt = (float4 *)P(16 * n);
+    b.id_s = (uint32_t *)P(4 * n);
+    b.cell_s = (uint32_t *)P(4 * n);
+    b.lvl_s = (uint8_t *)P(n);
+    b.nbr_cnt = (uint8_t *)P(n);
+    b.nbr = (uint32_t *)P(4 * (size_t)sc.max_nbr * n);
+    b.rho = (float *)P(4 * n);
+    b.act = (uint32_t *)P(4 * n);
+    b.lvl_hist = (uint32_t *)P(4 * lvl_e);
+    b.lvl_off = (uint32_t *)P(4 * lvl_e);
+    b.lvl_count = (uint32_t *)P(4 * 258);
+    b.counters = (unsigned long long *)P(8 * kCounterSlots);
+    b.drange = (uint32_t *)P(8);
+    b.err = (uint32_t *)P(4);
+    b.dyn = (DynParams *)P(sizeof(DynParams));
+    b.stage_f = (float *)P(12 * n);
+    b.stage_u8 = (uint8_t *)P(n);
+    b.dbg4 = (float4 *)P(16 * n);
+    b.partials = (double *)P(32 * dblocks);
+    b.dstats = (double *)P(32);
+    return L.total;
+}
+
+cudaEvent_t get_event(apbf_scene *s)
+{
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Runs one launch group, bracketed by timing events when timing is on.
+template <typename F>
+cudaError_t timed(apbf_scene *s, cudaStream_t st, uint32_t stage, F &&fn)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (s->timing) {
+        a = get_event(s);
+        b = get_event(s);
+        cudaEventRecord(a, st);
+    }
+    cudaError_t e = fn();
+    if (s->timing) {
+        cudaEventRecord(b, st);
+        s->timed.push_back({stage, a, b});
+    }
+    return e;
+}
+
+constexpr uint32_t kStageAll = 0xffffffffu;
+
+// Enqueue one step of Fig. 7 on `st`, stopping after `stop_stage` (at
+// iteration `stop_iter` for the lambda / delta-p stages).
+apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, uint32_t stop_iter)
+{
+    const StepConst &sc = s->sc;
+    const Buffers &b = s->b;
+    const bool dtc = sc.lod_mode == APBF_LOD_DTC;
+    cudaError_t e;
+    if (dtc) {  // always captured; unused when the camera gives a distance range
+        e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
+            cudaMemsetAsync(b.drange, 0x7f, 4, st);  // 0x7f7f7f7f = 3.4e38f
+            cudaMemsetAsync(b.drange + 1, 0, 4, st);
+            return launch_lod_range(sc, b, st);
+        });
+        if (e != cudaSuccess)
+            return cuda_fail(s, e, "lod_range");
+    }
+    if (stop_stage == APBF_STAGE_LOD_RANGE)
+        return APBF_OK;
+    if ((e = timed(s, st, APBF_STAGE_PREDICT, [&] { return launch_predict_hash(sc, b, st, false); })) != cudaSuccess)
+        return cuda_fail(s, e, "predict_hash");
+    if (stop_stage == APBF_STAGE_PREDICT)
+        return APBF_OK;
+    if ((e = timed(s, st, APBF_STAGE_SCAN, [&] { return launch_scan(sc, b, st); })) != cudaSuccess)
+        return cuda_fail(s, e, "scan");
+    if (stop_stage == APBF_STAGE_SCAN)
+        return APBF_OK;
+    if ((e = timed(s, st, APBF_STAGE_SCATTER, [&] { return launch_scatter(sc, b, st); })) != cudaSuccess)
+        return cuda_fail(s, e, "scatter");
+    if (stop_stage == APBF_STAGE_SCATTER)
+        return APBF_OK;
+    if ((e = timed(s, st, APBF_STAGE_REORDER, [&] { return launch_reorder(sc, b, st, false); })) != cudaSuccess)
+        return cuda_fail(s, e, "reorder");
+    s->cur_buf = 0;
+    if (stop_stage == APBF_STAGE_REORDER)
+        return APBF_OK;
+    e = timed(s, st, APBF_STAGE_NEIGHBORS, [&] {
+        cudaMemsetAsync(b.counters, 0, 8 * (2 + 256), st);
+        return launch_neighbors(sc, b, st);
+    });
+    if (e != cudaSuccess)
+        return cuda_fail(s, e, "neighbors");
+    if (stop_stage == APBF_STAGE_NEIGHBORS)
+        return APBF_OK;
+    if (dtc && sc.K > 1) {
+        if ((e = timed(s, st, APBF_STAGE_LEVELS, [&] { return launch_levels(sc, b, st); })) != cudaSuccess)
+            return cuda_fail(s, e, "levels");
+    }
+    if (stop_stage == APBF_STAGE_LEVELS)
+        return APBF_OK;
+    for (uint32_t l = 1; l <= sc.n_max; ++l) {
+        const bool dense = l <= sc.n_min;
+        e = timed(s, st, APBF_STAGE_LAMBDA, [&] { return launch_lambda(sc, b, st, l, dense, s->grid_iter); });
+        if (e != cudaSuccess)
+            return cuda_fail(s, e, "lambda");
+        s->cur_buf = 1;
+        if (stop_stage == APBF_STAGE_LAMBDA && stop_iter == l)
+            return APBF_OK;
+        e = timed(s, st, APBF_STAGE_DELTAP, [&] { return launch_deltap(sc, b, st, l, dense, s->grid_iter); });
+        if (e != cudaSuccess)
+            return cuda_fail(s, e, "deltap");
+        s->cur_buf = 0;
+        if (stop_stage == APBF_STAGE_DELTAP && stop_iter == l)
+            return APBF_OK;
+    }
+    if ((e = timed(s, st, APBF_STAGE_FINALIZE, [&] { return launch_finalize(sc, b, st); })) != cudaSuccess)
+        return cuda_fail(s, e, "finalize");
+    return APBF_OK;
+}
+
+apbf_status upload_dyn(apbf_scene *s)
+{
+    if (!s->dyn_dirty)
+        return APBF_OK;
+    int k = s->dyn_slot;
+    s->dyn_slot = (s->dyn_slot + 1) % 16;
+    APBF_CUDA(s, cudaEventSynchronize(s->dyn_ev[k]));  // the previous copy out of this slot is done
+    s->dyn_pinned[k] = s->dyn;
+    APBF_CUDA(s, cudaMemcpyAsync(s->b.dyn, &s->dyn_pinned[k], sizeof(DynParams), cudaMemcpyHostToDevice, s->stream));
+    APBF_CUDA(s, cudaEventRecord(s->dyn_ev[k], s->stream));
+    s->dyn_dirty = false;
+    return APBF_OK;
+}
+
+apbf_status check_device_errors(apbf_scene *s)
+{
+    uint32_t *h = (uint32_t *)s->pinned_small;
+    APBF_CUDA(s, cudaMemcpyAsync(h, s->b.err, 4, cudaMemcpyDeviceToHost, s->stream));
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (*h & kErrNeighborOverflow)
+        return fail(s, APBF_ERR_NEIGHBOR_OVERFLOW,
+                    "a particle had more neighbours than max_neighbors (" + std::to_string(s->sc.max_nbr) + ")");
+    return APBF_OK;
+}
+
+apbf_status enter(apbf_scene *s)
+{
+    if (!s)
+        return APBF_ERR_INVALID_ARG;
+    if (s->sticky != APBF_OK)
+        return s->sticky;
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev != s->device)
+        APBF_CUDA(s, cudaSetDevice(s->device));
+    return APBF_OK;
+}
+
+apbf_status build_graph(apbf_scene *s)
+{
+    APBF_CUDA(s, cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal));
+    apbf_status st = enqueue_step(s, s->capture_stream, kStageAll, 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->capture_stream, &g);
+    if (st != APBF_OK) {
+        if (g)
+            cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(s, e, "cudaStreamEndCapture");
+    s->graph = g;
+    APBF_CUDA(s, cudaGraphInstantiate(&s->gexec, g, 0));
+    return APBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+APBF_API const char *apbf_status_string(apbf_status st)
+{
+    switch (st) {
+    case APBF_OK: return "ok";
+    case APBF_ERR_INVALID_ARG: return "invalid argument";
+    case APBF_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case APBF_ERR_CUDA: return "CUDA error";
+    case APBF_ERR_TIMEOUT: return "device wait timed out";
+    case APBF_ERR_BAD_STATE: return "bad state";
+    case APBF_ERR_NEIGHBOR_OVERFLOW: return "neighbour list overflow";
+    case APBF_ERR_NOT_SUPPORTED: return "not supported";
+    }
+    return "unknown status";
+}
+
+APBF_API apbf_status apbf_rest_density(float h, float mass, float spacing, double *rho0)
+{
+    if (!rho0 || !(h > 0.0f) || !(mass > 0.0f) || !(spacing > 0.0f) || !std::isfinite(h) || !std::isfinite(spacing))
+        return APBF_ERR_INVALID_ARG;
+    // Eq. 6 summed over the lattice points within h of the centre particle.
+    const double PI = 3.14159265358979323846;
+    const double hd = h, s = spacing, c = 315.0 / (64.0 * PI * std::pow(hd, 9));
+    const int r = (int)std::ceil(hd / s) + 1;
+    double sum = 0.0;
+    for (int i = -r; i <= r; ++i)
+        for (int j = -r; j <= r; ++j)
+            for (int k = -r; k <= r; ++k) {
+                double d2 = (double)(i * i + j * j + k * k) * s * s;
+                double u = hd * hd - d2;
+                if (u > 0.0)
+                    sum += u * u * u;
+            }
+    *rho0 = (double)mass * c * sum;
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes)
+{
+    if (!bytes)
+        return APBF_ERR_INVALID_ARG;
+    StepConst sc;
+    apbf_status st;
+    std::string m = derive(desc, sc, st);
+    if (st != APBF_OK)
+        return fail(nullptr, st, m);
+    Buffers b;
+    *bytes = carve(sc, nullptr, b);
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stream, void *device_arena,
+                                       size_t arena_bytes, apbf_scene **out)
+{
+    if (!out)
+        return fail(nullptr, APBF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    StepConst sc;
+    apbf_status st;
+    std::string m = derive(d, sc, st);
+    if (st != APBF_OK)
+        return fail(nullptr, st, m);
+    for (uint32_t i = 0; i < 3 * d->n; ++i)
+        if (!std::isfinite(d->pos[i]) || (d->vel && !std::isfinite(d->vel[i])))
+            return fail(nullptr, APBF_ERR_INVALID_ARG, "positions and velocities must be finite");
+    for (uint32_t i = 0; i < d->n; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (!(d->pos[3 * i + a] >= d->grid_lo[a] && d->pos[3 * i + a] <= d->grid_hi[a]))
+                return fail(nullptr, APBF_ERR_INVALID_ARG, "particle " + std::to_string(i) + " lies outside the grid");
+    if (device_arena && ((uintptr_t)device_arena % kAlign))
+        return fail(nullptr, APBF_ERR_INVALID_ARG, "device_arena must be 256-byte aligned");
+
+    apbf_scene *s = new (std::nothrow) apbf_scene();
+    if (!s)
+        return fail(nullptr, APBF_ERR_OUT_OF_MEMORY, "host allocation failed");
+    s->sc = sc;
+    for (int a = 0; a < 3; ++a)
+        s->grid_hi[a] = d->grid_hi[a];
+    s->flags = d->flags;
+    s->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](apbf_status code, const std::string &msg) {
+        g_create_error = msg;
+        apbf_destroy_scene(s);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    size_t need = carve(sc, nullptr, s->b);
+    if (device_arena) {
+        if (arena_bytes < need)
+            return bail(APBF_ERR_OUT_OF_MEMORY, "device_arena is smaller than apbf_scene_bytes()");
+        s->arena = device_arena;
+        s->arena_bytes = arena_bytes;
+    } else {
+        e = cudaMalloc(&s->arena, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->arena = nullptr;
+            return bail(APBF_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        s->own_arena = true;
+        s->arena_bytes = need;
+    }
+    carve(sc, (char *)s->arena, s->b);
+    const Buffers &b = s->b;
+    const size_t n = sc.n;
+
+    if ((e = cudaHostAlloc(&s->pinned_small, 4096, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaHostAlloc((void **)&s->dyn_pinned, 16 * sizeof(DynParams), cudaHostAllocDefault)) != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 16; ++k)
+        if ((e = cudaEventCreateWithFlags(&s->dyn_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(APBF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    if ((e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+
+    // initial state, particle-id order
+    std::vector<float4> hx(n ? n : 1), hv(n ? n : 1);
+    std::vector<uint32_t> hid(n ? n : 1);
+    for (size_t i = 0; i < n; ++i) {
+        hx[i] = make_float4(d->pos[3 * i], d->pos[3 * i + 1], d->pos[3 * i + 2], 0.0f);
+        hv[i] = d->vel ? make_float4(d->vel[3 * i], d->vel[3 * i + 1], d->vel[3 * i + 2], 0.0f)
+                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        hid[i] = (uint32_t)i;
+    }
+    std::vector<uint32_t> lc(258, 0u);
+    for (uint32_t l = 0; l <= sc.n_max; ++l)
+        lc[l] = sc.n;  // every particle is active in every iteration until a partition says otherwise
+    s->dyn = DynParams{};
+    for (int a = 0; a < 3; ++a) {
+        s->dyn.box_lo[a] = d->box_lo[a];
+        s->dyn.box_hi[a] = d->box_hi[a];
+    }
+    s->dyn.auto_range = 1;
+    cudaStream_t st0 = s->stream;
+    if ((e = cudaMemsetAsync(s->arena, 0, need, st0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b.state_x, hx.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b.state_v, hv.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b.state_id, hid.data(), 4 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b.lvl_count, lc.data(), 4 * 258, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st0)) != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("initial upload: ") + cudaGetErrorString(e));
+    s->dyn_dirty = true;
+    s->grid_iter = iteration_grid(s->sms > 0 ? s->sms : 1);
+    *out = s;
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_set_camera(apbf_scene *s, const float eye[3], const float dir[3], float d_near, float d_far)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!eye || !dir || !finite3(eye) || !finite3(dir) || !std::isfinite(d_near) || !std::isfinite(d_far))
+        return fail(s, APBF_ERR_INVALID_ARG, "camera values must be finite and non-NULL");
+    for (int a = 0; a < 3; ++a)
+        s->dyn.eye[a] = eye[a];
+    s->dyn.d_near = d_near;
+    s->dyn.d_far = d_far;
+    s->dyn.auto_range = (d_near < d_far) ? 0u : 1u;
+    s->dyn_dirty = true;
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_set_box(apbf_scene *s, const float lo[3], const float hi[3])
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!lo || !hi || !finite3(lo) || !finite3(hi))
+        return fail(s, APBF_ERR_INVALID_ARG, "box bounds must be finite and non-NULL");
+    for (int a = 0; a < 3; ++a)
+        if (!(s->sc.glo[a] <= lo[a] && lo[a] < hi[a] && hi[a] <= s->grid_hi[a]))
+            return fail(s, APBF_ERR_INVALID_ARG, "need grid_lo <= lo < hi <= grid_hi on every axis");
+    for (int a = 0; a < 3; ++a) {
+        s->dyn.box_lo[a] = lo[a];
+        s->dyn.box_hi[a] = hi[a];
+    }
+    s->dyn_dirty = true;
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_step(apbf_scene *s, uint32_t nsteps)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (s->sc.n == 0) {
+        s->stepped = true;
+        return APBF_OK;
+    }
+    const bool eager = s->timing || (s->flags & APBF_FLAG_NO_GRAPH);
+    for (uint32_t k = 0; k < nsteps; ++k) {
+        if ((st = upload_dyn(s)) != APBF_OK)
+            return st;
+        if (eager) {
+            if ((st = enqueue_step(s, s->stream, kStageAll, 0)) != APBF_OK)
+                return st;
+        } else {
+            if (!s->gexec && (st = build_graph(s)) != APBF_OK)
+                return st;
+            APBF_CUDA(s, cudaGraphLaunch(s->gexec, s->stream));
+        }
+    }
+    APBF_CUDA(s, cudaGetLastError());
+    s->stepped = true;
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_read_state(apbf_scene *s, float *pos, float *vel, uint8_t *n_iter, float *rho)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if ((st = check_device_errors(s)) != APBF_OK)
+        return st;
+    const size_t n = s->sc.n;
+    if (n == 0)
+        return APBF_OK;
+    float *outs_f[3] = {pos, vel, nullptr};
+    for (uint32_t what = 0; what < 2; ++what) {
+        if (!outs_f[what])
+            continue;
+        APBF_CUDA(s, launch_unpermute(s->sc, s->b, s->stream, what));
+        APBF_CUDA(s, cudaMemcpyAsync(outs_f[what], s->b.stage_f, 12 * n, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (n_iter) {
+        APBF_CUDA(s, launch_unpermute(s->sc, s->b, s->stream, 2));
+        APBF_CUDA(s, cudaMemcpyAsync(n_iter, s->b.stage_u8, n, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (rho) {
+        APBF_CUDA(s, launch_unpermute(s->sc, s->b, s->stream, 3));
+        APBF_CUDA(s, cudaMemcpyAsync(rho, s->b.stage_f, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+    }
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_density_stats(apbf_scene *s, double stats[4])
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!stats)
+        return fail(s, APBF_ERR_INVALID_ARG, "stats is NULL");
+    stats[0] = stats[1] = stats[2] = stats[3] = 0.0;
+    if (s->sc.n == 0)
+        return check_device_errors(s);
+    Buffers bb = s->b;
+    bb.counters = s->b.counters + (kCounterSlots - 2);  // keep the step's counters
+    cudaStream_t q = s->stream;
+    int nb = 0;
+    APBF_CUDA(s, launch_predict_hash(s->sc, bb, q, true));
+    APBF_CUDA(s, launch_scan(s->sc, bb, q));
+    APBF_CUDA(s, launch_scatter(s->sc, bb, q));
+    APBF_CUDA(s, launch_reorder(s->sc, bb, q, true));
+    APBF_CUDA(s, launch_neighbors(s->sc, bb, q));
+    APBF_CUDA(s, launch_density(s->sc, bb, q, &nb));
+    double *h = (double *)s->pinned_small + 8;
+    APBF_CUDA(s, cudaMemcpyAsync(h, s->b.dstats, 32, cudaMemcpyDeviceToHost, q));
+    if ((st = check_device_errors(s)) != APBF_OK)
+        return st;
+    for (int k = 0; k < 4; ++k)
+        stats[k] = h[k];
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!info)
+        return fail(s, APBF_ERR_INVALID_ARG, "info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    if ((st = check_device_errors(s)) != APBF_OK)
+        return st;
+    const StepConst &sc = s->sc;
+    if (sc.n == 0 || !s->stepped)
+        return APBF_OK;
+    std::vector<unsigned long long> c(kCounterSlots);
+    std::vector<uint32_t> lc(258);
+    float dr[2];
+    APBF_CUDA(s, cudaMemcpy(c.data(), s->b.counters, 8 * kCounterSlots, cudaMemcpyDeviceToHost));
+    APBF_CUDA(s, cudaMemcpy(lc.data(), s->b.lvl_count, 4 * 258, cudaMemcpyDeviceToHost));
+    APBF_CUDA(s, cudaMemcpy(dr, s->b.drange, 8, cudaMemcpyDeviceToHost));
+    const bool partitioned = sc.lod_mode == APBF_LOD_DTC && sc.K > 1;
+    info->neighbor_pairs = c[0];
+    for (uint32_t l = 0; l < 256; ++l) {
+        uint32_t a = 0;
+        if (l <= sc.n_max)
+            a = partitioned ? lc[l] : sc.n;
+        info->active_count[l] = a;
+        if (l >= 1)
+            info->particle_iterations += a;
+    }
+    if (partitioned) {
+        for (uint32_t bin = 0; bin < sc.K; ++bin)
+            info->lambda_pairs += c[2 + bin] * (unsigned long long)(sc.n_max - bin);
+    } else {
+        info->lambda_pairs = c[0] * (unsigned long long)sc.n_max;
+    }
+    if (sc.lod_mode == APBF_LOD_DTC) {
+        if (s->dyn.auto_range) {
+            info->d_range[0] = dr[0];
+            info->d_range[1] = dr[1];
+        } else {
+            info->d_range[0] = s->dyn.d_near;
+            info->d_range[1] = s->dyn.d_far;
+        }
+    }
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_sync(apbf_scene *s)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    return check_device_errors(s);
+}
+
+APBF_API const char *apbf_last_error(const apbf_scene *s)
+{
+    if (!s)
+        return g_create_error.c_str();
+    return s->msg.c_str();
+}
+
+APBF_API void apbf_destroy_scene(apbf_scene *s)
+{
+    if (!s)
+        return;
+    if (s->stream || s->arena)
+        cudaStreamSynchronize(s->stream);
+    if (s->gexec)
+        cudaGraphExecDestroy(s->gexec);
+    if (s->graph)
+        cudaGraphDestroy(s->graph);
+    if (s->capture_stream)
+        cudaStreamDestroy(s->capture_stream);
+    for (auto &t : s->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : s->ev_pool)
+        cudaEventDestroy(e);
+    for (int k = 0; k < 16; ++k)
+        if (s->dyn_ev[k])
+            cudaEventDestroy(s->dyn_ev[k]);
+    if (s->dyn_pinned)
+        cudaFreeHost(s->dyn_pinned);
+    if (s->pinned_small)
+        cudaFreeHost(s->pinned_small);
+    if (s->own_arena && s->arena)
+        cudaFree(s->arena);
+    delete s;
+}
+
+APBF_API apbf_status apbf_set_timing(apbf_scene *s, int enable)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    s->timing = enable != 0;
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_timing_report(apbf_scene *s, double *ms, uint64_t *launches)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!ms || !launches)
+        return fail(s, APBF_ERR_INVALID_ARG, "outputs are NULL");
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    for (auto &t : s->timed) {
+        float v = 0.0f;
+        APBF_CUDA(s, cudaEventElapsedTime(&v, t.a, t.b));
+        s->stage_ms[t.stage] += v;
+        s->stage_launches[t.stage] += 1;
+        s->ev_pool.push_back(t.a);
+        s->ev_pool.push_back(t.b);
+    }
+    s->timed.clear();
+    for (uint32_t k = 0; k < APBF_STAGE_COUNT; ++k) {
+        ms[k] = s->stage_ms[k];
+        launches[k] = s->stage_launches[k];
+        s->stage_ms[k] = 0.0;
+        s->stage_launches[k] = 0;
+    }
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_debug_step_to(apbf_scene *s, uint32_t stage, uint32_t iteration)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (stage >= APBF_STAGE_COUNT)
+        return fail(s, APBF_ERR_INVALID_ARG, "unknown stage");
+    if ((stage == APBF_STAGE_LAMBDA || stage == APBF_STAGE_DELTAP) && (iteration < 1 || iteration > s->sc.n_max))
+        return fail(s, APBF_ERR_INVALID_ARG, "iteration must be in 1..n_max");
+    if (s->sc.n == 0)
+        return APBF_OK;
+    if ((st = upload_dyn(s)) != APBF_OK)
+        return st;
+    st = enqueue_step(s, s->stream, stage == APBF_STAGE_FINALIZE ? kStageAll : stage, iteration);
+    if (st != APBF_OK)
+        return st;
+    if (stage < APBF_STAGE_SCAN)  // the scan, which clears the cell counts, did not run
+        APBF_CUDA(s, cudaMemsetAsync(s->b.cnt, 0, 4 * (size_t)((s->sc.ncell + 3) / 4 * 4), s->stream));
+    if (stage == APBF_STAGE_FINALIZE)
+        s->stepped = true;
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, size_t bytes)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    const StepConst &sc = s->sc;
+    const Buffers &b = s->b;
+    const size_t n = sc.n;
+    const void *src = nullptr;
+    size_t size = 0;
+    const float4 *cur = s->cur_buf ? b.recB : b.recA;
+    switch (field) {
+    case APBF_DBG_KEYS: src = b.key; size = 4 * n; break;
+    case APBF_DBG_STATE_IDS: src = b.state_id; size = 4 * n; break;
+    case APBF_DBG_LEVEL_PRESORT: src = b.lvl; size = n; break;
+    case APBF_DBG_SORTED_IDS: src = b.id_s; size = 4 * n; break;
+    case APBF_DBG_CELL_START: src = b.start; size = 4 * ((size_t)sc.ncell + 1); break;
+    case APBF_DBG_XPRED: src = b.xs32; size = 16 * n; break;
+    case APBF_DBG_LEVEL: src = b.lvl_s; size = n; break;
+    case APBF_DBG_NBR_COUNT: src = b.nbr_cnt; size = n; break;
+    case APBF_DBG_NBR: src = b.nbr; size = 4 * (size_t)sc.max_nbr * n; break;
+    case APBF_DBG_ACTIVE: src = b.act; size = 4 * n; break;
+    case APBF_DBG_LEVEL_COUNT: src = b.lvl_count; size = 4 * ((size_t)sc.n_max + 2); break;
+    case APBF_DBG_LAMBDA:
+        APBF_CUDA(s, launch_debug_lambda(sc, b, cur, s->stream));
+        src = b.stage_f;
+        size = 4 * n;
+        break;
+    case APBF_DBG_RHO: src = b.rho; size = 4 * n; break;
+    case APBF_DBG_XSTAR:
+        APBF_CUDA(s, launch_debug_xstar(sc, b, cur, s->stream));
+        src = b.dbg4;
+        size = 16 * n;
+        break;
+    case APBF_DBG_DRANGE: src = b.drange; size = 8; break;
+    default: return fail(s, APBF_ERR_INVALID_ARG, "unknown debug field");
+    }
+    if (bytes != size || (size && !host))
+        return fail(s, APBF_ERR_INVALID_ARG, "debug_read size mismatch: field needs " + std::to_string(size) + " bytes");
+    if (size)
+        APBF_CUDA(s, cudaMemcpyAsync(host, src, size, cudaMemcpyDeviceToHost, s->stream));
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    return check_device_errors(s);
+}
+
+APBF_API apbf_status apbf_debug_dims(apbf_scene *s, int32_t dims[3], uint32_t *ncell, uint32_t *max_neighbors)
+{
+    if (!s || !dims || !ncell || !max_neighbors)
+        return APBF_ERR_INVALID_ARG;
+    dims[0] = s->sc.nx;
+    dims[1] = s->sc.ny;
+    dims[2] = s->sc.nz;
+    *ncell = s->sc.ncell;
+    *max_neighbors = s->sc.max_nbr;
+    return APBF_OK;
+}
+
+}  // extern "C"

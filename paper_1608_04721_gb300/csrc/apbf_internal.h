@@ -1,0 +1,157 @@
+// Internal types of the CUDA implementation of include/apbf.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "apbf.h"
+
+namespace apbf {
+
+constexpr uint32_t kDefaultMaxNeighbors = 128;
+constexpr uint32_t kSlotBits = 27;  // neighbour entry: slot (27 bits) | cell offset code (5 bits)
+constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
+constexpr int kBlock = 256;          // threads per block of the per-particle kernels
+constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
+constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
+
+// Device error word bits.
+constexpr uint32_t kErrNeighborOverflow = 1u;
+
+// Step constants, fixed for a scene's lifetime (passed by value as kernel
+// arguments and therefore baked into the captured step graph).
+struct StepConst {
+    uint32_t n;
+    uint32_t ncell;
+    int32_t nx, ny, nz;
+    float glo[3];
+    float inv_h;        // fl(1/h), the cell-hash scale
+    float h;
+    float h2;           // fl(h*h): the FP32 neighbour predicate bound
+    float dt, inv_dt;
+    float g[3];
+    // local-origin lattice: origin of cell c on axis a is (float)(m[a] + c) * q,
+    // exact for |m + c| < 2^16 because q has at most 8 significant bits.
+    float q;
+    int32_t m[3];
+    // solver coefficients (FP32 from FP64 host values)
+    float mass_poly6;   // m * 315 / (64 pi h^9)
+    float h6;           // (h^2)^3: self term of the density sum
+    float inv_rho0;
+    float c_lam;        // w (m * 45/(pi h^6) / rho0)^2
+    float eps;
+    float c_dp;         // -(w m / rho0) * 45/(pi h^6)
+    float inv_wdq;      // 1 / (h^2 - dq^2)
+    float neg_k;        // -k
+    uint32_t scorr_n;
+    float c_xsph;       // c (m / rho0) * 315/(64 pi h^9)
+    uint32_t n_min, n_max, K, lod_mode;
+    uint32_t max_nbr;
+    uint32_t level_tiles;
+    float rho0;         // rest density as given (FP32)
+};
+
+// Per-step values that callers change between steps (device copy read by kernels).
+struct DynParams {
+    float box_lo[4];
+    float box_hi[4];
+    float eye[4];
+    float d_near, d_far;
+    uint32_t auto_range;
+    uint32_t pad;
+};
+
+struct Buffers {
+    float4 *state_x, *state_v;
+    uint32_t *state_id;
+    uint32_t *key, *slot;
+    uint8_t *lvl;
+    uint32_t *cnt, *start, *tile_sums, *tmp;
+    float4 *recA, *recB, *xs32, *xt;
+    uint32_t *id_s, *cell_s;
+    uint8_t *lvl_s, *nbr_cnt;
+    uint32_t *nbr;
+    float *rho;
+    uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
+    unsigned long long *counters;  // [0] pairs, [1] lambda pairs
+    uint32_t *drange;              // float bits of d_min, d_max
+    uint32_t *err;
+    DynParams *dyn;
+    float *stage_f;                // 3n floats readback staging
+    uint8_t *stage_u8;             // n bytes readback staging
+    float4 *dbg4;                  // n float4 debug staging
+    double *partials;              // diagnostic partial sums
+    double *dstats;                // 4 doubles
+};
+
+struct TimedLaunch {
+    uint32_t stage;
+    cudaEvent_t a, b;
+};
+
+}  // namespace apbf
+
+struct apbf_scene {
+    int device = 0;
+    apbf::StepConst sc{};
+    float grid_hi[3] = {};
+    apbf::Buffers b{};
+    cudaStream_t stream = nullptr;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    bool own_arena = false;
+    uint32_t flags = 0;
+    int sms = 0;
+    int grid_iter = 0;  // persistent grid of the iteration kernels
+    // dynamic parameters
+    apbf::DynParams dyn{};
+    bool dyn_dirty = true;
+    apbf::DynParams *dyn_pinned = nullptr;  // ring of pinned upload slots
+    cudaEvent_t dyn_ev[16] = {};
+    int dyn_slot = 0;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    // state
+    bool stepped = false;
+    int cur_buf = 0;  // debug: 0 = recA, 1 = recB holds the current positions
+    apbf_status sticky = APBF_OK;
+    std::string msg;
+    // timing
+    bool timing = false;
+    std::vector<apbf::TimedLaunch> timed;
+    std::vector<cudaEvent_t> ev_pool;
+    double stage_ms[APBF_STAGE_COUNT] = {};
+    uint64_t stage_launches[APBF_STAGE_COUNT] = {};
+    // host pinned scratch for small readbacks
+    void *pinned_small = nullptr;
+};
+
+namespace apbf {
+
+// Kernel launchers (kernels.cu). Each returns cudaGetLastError().
+cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
+cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense,
+                          int grid);
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense,
+                          int grid);
+cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what);
+cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks);
+cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);
+cudaError_t launch_debug_lambda(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);
+cudaError_t launch_fixed_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
+int iteration_grid(int sms);
+
+}  // namespace apbf

@@ -1,0 +1,920 @@
+// CUDA kernels of one Adaptive Position-Based Fluids step (Fig. 7, Sec. 5),
+// written for sm_103a. Host orchestration lives in apbf_capi.cu.
+//
+// Data layout (structure of arrays, sorted by cell after the reorder):
+//   state_x, state_v  float4 per particle (w unused), the state between steps
+//   recA / recB       float4 per particle: position relative to the particle's
+//                     cell origin (xyz) and lambda (w); the two Jacobi buffers
+//   xs32              float4 absolute predicted position (FP32), for the
+//                     neighbour predicate
+//   xt                float4 start-of-step position relative to the cell origin
+//   nbr               u32 neighbour entries, entry k of particle p at k*n + p
+//                     (a warp of consecutive particles reads one 128-byte line
+//                     per k); low 27 bits: sorted slot, high 5 bits: which of
+//                     the 27 neighbour cells the neighbour was found in.
+//
+// Positions inside the solver are stored relative to the particle's cell
+// origin (m + c) * q, with q = h rounded to 8 significant bits so that every
+// origin and every origin difference (+-q per axis) is exact in FP32. The
+// difference of two positions is then (p_i - p_j) + dtab[code] with |p| ~ h,
+// which keeps FP32 rounding at the scale of h instead of the scale of the
+// domain (a 10 m basin has an FP32 spacing of ~1e-6 m).
+#include "apbf_internal.h"
+
+namespace apbf {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ float3 predict_position(float4 x, float4 v, const StepConst &sc, const DynParams *dyn)
+{
+    // Fig. 7 lines 1-4 in FP32, rounded after every operation (no FMA):
+    // v' = v + dt g, x* = x + dt v', then the box clamp.
+    float vx = __fadd_rn(v.x, __fmul_rn(sc.dt, sc.g[0]));
+    float vy = __fadd_rn(v.y, __fmul_rn(sc.dt, sc.g[1]));
+    float vz = __fadd_rn(v.z, __fmul_rn(sc.dt, sc.g[2]));
+    float px = __fadd_rn(x.x, __fmul_rn(sc.dt, vx));
+    float py = __fadd_rn(x.y, __fmul_rn(sc.dt, vy));
+    float pz = __fadd_rn(x.z, __fmul_rn(sc.dt, vz));
+    px = fminf(fmaxf(px, dyn->box_lo[0]), dyn->box_hi[0]);
+    py = fminf(fmaxf(py, dyn->box_lo[1]), dyn->box_hi[1]);
+    pz = fminf(fmaxf(pz, dyn->box_lo[2]), dyn->box_hi[2]);
+    return make_float3(px, py, pz);
+}
+
+__device__ __forceinline__ int cell_axis(float p, float lo, float inv_h, int dim)
+{
+    float t = __fmul_rn(__fsub_rn(p, lo), inv_h);
+    int c = (int)floorf(t);
+    return min(max(c, 0), dim - 1);
+}
+
+__device__ __forceinline__ int3 cell_of(float3 p, const StepConst &sc)
+{
+    return make_int3(cell_axis(p.x, sc.glo[0], sc.inv_h, sc.nx), cell_axis(p.y, sc.glo[1], sc.inv_h, sc.ny),
+                     cell_axis(p.z, sc.glo[2], sc.inv_h, sc.nz));
+}
+
+__device__ __forceinline__ uint32_t pack_cell(int3 c) { return (uint32_t)c.x | ((uint32_t)c.y << 11) | ((uint32_t)c.z << 22); }
+
+__device__ __forceinline__ int3 unpack_cell(uint32_t v)
+{
+    return make_int3((int)(v & 2047u), (int)((v >> 11) & 2047u), (int)(v >> 22));
+}
+
+__device__ __forceinline__ float3 cell_origin(int3 c, const StepConst &sc)
+{
+    return make_float3((float)(sc.m[0] + c.x) * sc.q, (float)(sc.m[1] + c.y) * sc.q, (float)(sc.m[2] + c.z) * sc.q);
+}
+
+__device__ __forceinline__ float camera_distance(float4 x, const DynParams *dyn)
+{
+    float dx = __fsub_rn(x.x, dyn->eye[0]);
+    float dy = __fsub_rn(x.y, dyn->eye[1]);
+    float dz = __fsub_rn(x.z, dyn->eye[2]);
+    float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+    return __fsqrt_rn(d2);
+}
+
+// Sec. 4.1 / Eq. 8: linear interpolation of the distance range onto the level
+// range, near -> n_max, as K equal-width bins (FP32).
+__device__ __forceinline__ uint32_t lod_level(float d, float dmin, float dmax, const StepConst &sc)
+{
+    float span = __fsub_rn(dmax, dmin);
+    float t = 0.0f;
+    if (span > 0.0f)
+        t = __fdiv_rn(__fsub_rn(d, dmin), span);
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    int b = (int)floorf(__fmul_rn(t, (float)sc.K));
+    b = min(b, (int)sc.K - 1);
+    return sc.n_max - (uint32_t)b;
+}
+
+// Cell-origin difference o_i - o_j = -(offset) q for the 27 neighbour cells.
+__device__ __forceinline__ void fill_dtab(float4 *dtab, float q)
+{
+    if (threadIdx.x < 27) {
+        int c = threadIdx.x;
+        float ox = (float)(c % 3 - 1), oy = (float)((c / 3) % 3 - 1), oz = (float)(c / 9 - 1);
+        dtab[c] = make_float4(-ox * q, -oy * q, -oz * q, 0.0f);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_minf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Block-wide sum of a u32 (any multiple-of-32 block size <= 1024), result in every thread.
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sh32)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0)
+        sh32[w] = v;
+    __syncthreads();
+    uint32_t t = (lane < nw) ? sh32[lane] : 0u;
+    t = warp_sum(t);
+    return t;
+}
+
+// Block-wide exclusive scan of a u32; returns the exclusive prefix, *total the sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t *sh32, uint32_t *total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o)
+            inc += y;
+    }
+    __syncthreads();
+    if (lane == 31)
+        sh32[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = (lane < nw) ? sh32[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        if (lane < nw)
+            sh32[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t warp_prefix = (w > 0) ? sh32[w - 1] : 0u;
+    *total = sh32[nw - 1];
+    return warp_prefix + inc - v;
+}
+
+// ------------------------------------------------------------- a1: range
+
+__global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers b)
+{
+    __shared__ float smin[kBlock / 32], smax[kBlock / 32];
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    float dmin = 3.0e38f, dmax = 0.0f;
+    if (i < sc.n) {
+        float d = camera_distance(b.state_x[i], b.dyn);
+        dmin = d;
+        dmax = d;
+    }
+    dmin = warp_minf(dmin);
+    dmax = warp_maxf(dmax);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        smin[w] = dmin;
+        smax[w] = dmax;
+    }
+    __syncthreads();
+    if (w == 0) {
+        dmin = lane < kBlock / 32 ? smin[lane] : 3.0e38f;
+        dmax = lane < kBlock / 32 ? smax[lane] : 0.0f;
+        dmin = warp_minf(dmin);
+        dmax = warp_maxf(dmax);
+        if (lane == 0) {
+            // distances are >= 0, so their bit patterns order like the values
+            atomicMin(&b.drange[0], __float_as_uint(dmin));
+            atomicMax(&b.drange[1], __float_as_uint(dmax));
+        }
+    }
+}
+
+// ------------------------------------- a1-a4: level, predict, hash, count
+
+__global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buffers b, int diag)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = i < sc.n;
+    uint32_t key = 0xffffffffu;
+    if (valid) {
+        float4 x = b.state_x[i];
+        float3 p;
+        if (diag) {
+            p = make_float3(x.x, x.y, x.z);
+        } else {
+            uint32_t lv = sc.n_max;
+            if (sc.lod_mode == APBF_LOD_DTC) {
+                const DynParams *dyn = b.dyn;
+                float dmin = dyn->d_near, dmax = dyn->d_far;
+                if (dyn->auto_range) {
+                    dmin = __uint_as_float(b.drange[0]);
+                    dmax = __uint_as_float(b.drange[1]);
+                }
+                lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
+            }
+            b.lvl[i] = (uint8_t)lv;
+            p = predict_position(x, b.state_v[i], sc, b.dyn);
+        }
+        int3 c = cell_of(p, sc);
+        key = ((uint32_t)c.z * (uint32_t)sc.ny + (uint32_t)c.y) * (uint32_t)sc.nx + (uint32_t)c.x;
+        b.key[i] = key;
+    }
+    // warp-aggregated histogram: one atomic per distinct cell in the warp
+    unsigned peers = __match_any_sync(kFull, key);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader)
+        base = atomicAdd(&b.cnt[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (valid)
+        b.slot[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+// ------------------------------------------------ a4/a6: scan = cell start
+
+__global__ void __launch_bounds__(1024) scan_reduce_kernel(const uint32_t *__restrict__ cnt, uint32_t ncell,
+                                                           uint32_t *__restrict__ tile_sums)
+{
+    __shared__ uint32_t sh[32];
+    uint32_t base = blockIdx.x * kScanTile + threadIdx.x * 4;
+    uint32_t s = 0;
+    if (base + 3 < ncell) {
+        uint4 v = *reinterpret_cast<const uint4 *>(cnt + base);
+        s = v.x + v.y + v.z + v.w;
+    } else {
+        for (uint32_t k = base; k < ncell && k < base + 4; ++k)
+            s += cnt[k];
+    }
+    s = block_sum_u32(s, sh);
+    if (threadIdx.x == 0)
+        tile_sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) scan_apply_kernel(uint32_t *__restrict__ cnt, uint32_t ncell,
+                                                          const uint32_t *__restrict__ tile_sums,
+                                                          uint32_t *__restrict__ start, uint32_t n)
+{
+    __shared__ uint32_t sh[32];
+    uint32_t pre = 0;
+    for (uint32_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x)
+        pre += tile_sums[t];
+    pre = block_sum_u32(pre, sh);
+    uint32_t base = blockIdx.x * kScanTile + threadIdx.x * 4;
+    uint32_t v[4] = {0u, 0u, 0u, 0u};
+    if (base + 3 < ncell) {
+        uint4 q = *reinterpret_cast<const uint4 *>(cnt + base);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+        *reinterpret_cast<uint4 *>(cnt + base) = make_uint4(0u, 0u, 0u, 0u);  // ready for the next step
+    } else {
+        for (uint32_t k = 0; k < 4; ++k)
+            if (base + k < ncell) {
+                v[k] = cnt[base + k];
+                cnt[base + k] = 0u;
+            }
+    }
+    uint32_t total;
+    uint32_t ex = block_exclusive_scan_u32(v[0] + v[1] + v[2] + v[3], sh, &total);
+    uint32_t run = pre + ex;
+    for (uint32_t k = 0; k < 4; ++k) {
+        if (base + k < ncell)
+            start[base + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        start[ncell] = n;
+}
+
+// ------------------------------------------ a4: slot scatter (particle ids)
+
+__global__ void __launch_bounds__(kBlock) scatter_kernel(StepConst sc, Buffers b)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < sc.n)
+        b.tmp[b.start[b.key[i]] + b.slot[i]] = b.state_id[i];
+}
+
+// ------------------------------------------ a4/a5: stable rank + reorder
+
+__global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b, int diag)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n)
+        return;
+    uint32_t k = b.key[i];
+    uint32_t s0 = b.start[k], s1 = b.start[k + 1];
+    // order within a cell by particle id: rank = number of this cell's
+    // particles with a smaller id (the slots hold ids in atomic arrival order)
+    const uint32_t id = b.state_id[i];
+    uint32_t r = 0;
+    for (uint32_t j = s0; j < s1; ++j)
+        r += (b.tmp[j] < id) ? 1u : 0u;
+    uint32_t p = s0 + r;
+    float4 x = b.state_x[i];
+    float3 xp = diag ? make_float3(x.x, x.y, x.z) : predict_position(x, b.state_v[i], sc, b.dyn);
+    int3 c = cell_of(xp, sc);
+    b.xs32[p] = make_float4(xp.x, xp.y, xp.z, 0.0f);
+    b.cell_s[p] = pack_cell(c);
+    if (!diag) {
+        float3 o = cell_origin(c, sc);
+        b.recA[p] = make_float4(__fsub_rn(xp.x, o.x), __fsub_rn(xp.y, o.y), __fsub_rn(xp.z, o.z), 0.0f);
+        b.xt[p] = make_float4(__fsub_rn(x.x, o.x), __fsub_rn(x.y, o.y), __fsub_rn(x.z, o.z), 0.0f);
+        b.id_s[p] = id;
+        b.lvl_s[p] = b.lvl[i];
+    }
+}
+
+// ----------------------------------------------- neighbour lists (l. 5-6)
+
+__global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b)
+{
+    __shared__ uint32_t sh[32];
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t cnt = 0;
+    if (p < sc.n) {
+        float4 xi = b.xs32[p];
+        int3 c = unpack_cell(b.cell_s[p]);
+        const size_t n = sc.n;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int cz = c.z + dz;
+            if (cz < 0 || cz >= sc.nz)
+                continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int cy = c.y + dy;
+                if (cy < 0 || cy >= sc.ny)
+                    continue;
+                uint32_t row = ((uint32_t)cz * (uint32_t)sc.ny + (uint32_t)cy) * (uint32_t)sc.nx;
+                int x0 = max(c.x - 1, 0), x1 = min(c.x + 1, sc.nx - 1);
+                for (int cx = x0; cx <= x1; ++cx) {
+                    uint32_t code = (uint32_t)((cx - c.x + 1) + 3 * (dy + 1) + 9 * (dz + 1)) << kSlotBits;
+                    uint32_t j0 = b.start[row + cx], j1 = b.start[row + cx + 1];
+                    for (uint32_t j = j0; j < j1; ++j) {
+                        if (j == p)
+                            continue;
+                        float4 xj = b.xs32[j];
+                        // FP32 predicate, rounded after every operation
+                        float dx = __fsub_rn(xi.x, xj.x);
+                        float dy2 = __fsub_rn(xi.y, xj.y);
+                        float dz2 = __fsub_rn(xi.z, xj.z);
+                        float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy2, dy2));
+                        r2 = __fadd_rn(r2, __fmul_rn(dz2, dz2));
+                        if (r2 < sc.h2) {
+                            if (cnt < sc.max_nbr)
+                                b.nbr[(size_t)cnt * n + p] = j | code;
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+        }
+        if (cnt > sc.max_nbr) {
+            atomicOr(b.err, kErrNeighborOverflow);
+            cnt = sc.max_nbr;
+        }
+        b.nbr_cnt[p] = (uint8_t)cnt;
+    }
+    uint32_t tot = block_sum_u32(cnt, sh);
+    if (threadIdx.x == 0 && tot)
+        atomicAdd(&b.counters[0], (unsigned long long)tot);
+}
+
+// ---------------------------------------- a7: active sets by stable partition
+// Particles are partitioned by level, highest first, stable in sorted-slot
+// order within a level. P_l is then the prefix of act of length |P_l|.
+
+__global__ void __launch_bounds__(kLevelTile) level_hist_kernel(StepConst sc, Buffers b)
+{
+    extern __shared__ uint32_t sh[];  // K counts, K pair sums
+    const uint32_t K = sc.K;
+    for (uint32_t k = threadIdx.x; k < 2 * K; k += blockDim.x)
+        sh[k] = 0u;
+    __syncthreads();
+    uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
+    if (p < sc.n) {
+        uint32_t bin = sc.n_max - b.lvl_s[p];
+        atomicAdd(&sh[bin], 1u);
+        atomicAdd(&sh[K + bin], (uint32_t)b.nbr_cnt[p]);
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x) {
+        b.lvl_hist[(size_t)k * sc.level_tiles + blockIdx.x] = sh[k];
+        if (sh[K + k])
+            atomicAdd(&b.counters[2 + k], (unsigned long long)sh[K + k]);
+    }
+}
+
+__global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers b)
+{
+    __shared__ uint32_t sh[32];
+    const uint32_t E = sc.K * sc.level_tiles;
+    const uint32_t chunk = (E + blockDim.x - 1) / blockDim.x;
+    const uint32_t e0 = min(E, threadIdx.x * chunk), e1 = min(E, e0 + chunk);
+    uint32_t s = 0;
+    for (uint32_t e = e0; e < e1; ++e)
+        s += b.lvl_hist[e];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan_u32(s, sh, &total);
+    for (uint32_t e = e0; e < e1; ++e) {
+        uint32_t v = b.lvl_hist[e];
+        b.lvl_off[e] = run;
+        run += v;
+    }
+    __syncthreads();
+    for (uint32_t l = threadIdx.x; l <= sc.n_max + 1; l += blockDim.x) {
+        uint32_t c;
+        if (l > sc.n_max)
+            c = 0;
+        else if (l <= sc.n_min)
+            c = sc.n;
+        else {
+            uint32_t bin_end = sc.n_max - l + 1;  // bins 0..n_max-l hold levels >= l
+            c = (bin_end >= sc.K) ? sc.n : b.lvl_off[(size_t)bin_end * sc.level_tiles];
+        }
+        b.lvl_count[l] = c;
+    }
+}
+
+__global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc, Buffers b)
+{
+    extern __shared__ uint32_t wc[];  // 32 warps x K
+    const uint32_t K = sc.K;
+    for (uint32_t k = threadIdx.x; k < 32 * K; k += blockDim.x)
+        wc[k] = 0u;
+    __syncthreads();
+    uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
+    bool valid = p < sc.n;
+    uint32_t bin = valid ? (sc.n_max - b.lvl_s[p]) : 0xffffffffu;
+    unsigned peers = __match_any_sync(kFull, bin);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int leader = __ffs(peers) - 1;
+    uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    if (valid && lane == leader)
+        wc[w * K + bin] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (valid) {
+        uint32_t pos = b.lvl_off[(size_t)bin * sc.level_tiles + blockIdx.x] + rank;
+        for (int v = 0; v < w; ++v)
+            pos += wc[v * K + bin];
+        b.act[pos] = p;
+    }
+}
+
+// ---------------------------------------------------------- a8: lambda pass
+// Iteration l, threads over P_{l-1}: particles of P_l compute rho and lambda
+// (Eq. 4-6) from A and write (position, lambda) to B; particles that finished
+// in iteration l-1 copy their final position into B and keep their lambda
+// there, so inactive neighbours enter Eq. 7 with their last lambda.
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kBlock) lambda_kernel(StepConst sc, const float4 *__restrict__ A,
+                                                        float4 *__restrict__ B, float *__restrict__ rho_out,
+                                                        const uint32_t *__restrict__ act,
+                                                        const uint32_t *__restrict__ nbr,
+                                                        const uint8_t *__restrict__ nbr_cnt,
+                                                        const uint32_t *__restrict__ lvl_count, uint32_t l)
+{
+    __shared__ float4 dtab[27];
+    fill_dtab(dtab, sc.q);
+    __syncthreads();
+    const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
+    const uint32_t cnt_prev = DENSE ? sc.n : lvl_count[l - 1];
+    const size_t n = sc.n;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_prev; t += gridDim.x * blockDim.x) {
+        const uint32_t p = DENSE ? t : act[t];
+        const float4 ai = A[p];
+        if (!DENSE && t >= cnt_l) {
+            B[p] = make_float4(ai.x, ai.y, ai.z, B[p].w);
+            continue;
+        }
+        const uint32_t nn = nbr_cnt[p];
+        float racc = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, s2 = 0.0f;
+        const uint32_t *e_ptr = nbr + p;
+        for (uint32_t k = 0; k < nn; ++k) {
+            const uint32_t e = __ldg(e_ptr + (size_t)k * n);
+            const float4 o = dtab[e >> kSlotBits];
+            const float4 aj = __ldg(&A[e & kSlotMask]);
+            const float dx = (ai.x - aj.x) + o.x;
+            const float dy = (ai.y - aj.y) + o.y;
+            const float dz = (ai.z - aj.z) + o.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2) {
+                const float u = sc.h2 - r2;
+                racc += u * u * u;
+                if (r2 > 0.0f) {
+                    const float ir = rsqrtf(r2);
+                    const float hr = sc.h - r2 * ir;
+                    const float gw = hr * hr * ir;  // |grad W| / (45/(pi h^6)) / r
+                    gx += gw * dx;
+                    gy += gw * dy;
+                    gz += gw * dz;
+                    s2 += gw * gw * r2;
+                }
+            }
+        }
+        const float rho = sc.mass_poly6 * (sc.h6 + racc);
+        const float C = rho * sc.inv_rho0 - 1.0f;
+        const float denom = sc.c_lam * (gx * gx + gy * gy + gz * gz + s2) + sc.eps;
+        const float lam = -C / denom;
+        B[p] = make_float4(ai.x, ai.y, ai.z, lam);
+        rho_out[p] = rho;
+    }
+}
+
+// ------------------------------------------- a9: position correction pass
+// Iteration l, threads over P_l: Eq. 7 with the tensile term from B, box
+// contact, Jacobi update written to A.
+
+template <int NPOW>
+__device__ __forceinline__ float powi(float x, uint32_t n)
+{
+    if (NPOW == 4) {
+        float x2 = x * x;
+        return x2 * x2;
+    }
+    float r = 1.0f;
+    for (uint32_t e = 0; e < n; ++e)
+        r *= x;
+    return r;
+}
+
+template <bool DENSE, int NPOW>
+__global__ void __launch_bounds__(kBlock) deltap_kernel(StepConst sc, const float4 *__restrict__ B,
+                                                        float4 *__restrict__ A, const uint32_t *__restrict__ act,
+                                                        const uint32_t *__restrict__ nbr,
+                                                        const uint8_t *__restrict__ nbr_cnt,
+                                                        const uint32_t *__restrict__ cell_s,
+                                                        const uint32_t *__restrict__ lvl_count,
+                                                        const DynParams *__restrict__ dyn, uint32_t l)
+{
+    __shared__ float4 dtab[27];
+    fill_dtab(dtab, sc.q);
+    __syncthreads();
+    const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
+    const size_t n = sc.n;
+    const float blo0 = dyn->box_lo[0], blo1 = dyn->box_lo[1], blo2 = dyn->box_lo[2];
+    const float bhi0 = dyn->box_hi[0], bhi1 = dyn->box_hi[1], bhi2 = dyn->box_hi[2];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_l; t += gridDim.x * blockDim.x) {
+        const uint32_t p = DENSE ? t : act[t];
+        const float4 bi = B[p];
+        const uint32_t nn = nbr_cnt[p];
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        const uint32_t *e_ptr = nbr + p;
+        for (uint32_t k = 0; k < nn; ++k) {
+            const uint32_t e = __ldg(e_ptr + (size_t)k * n);
+            const float4 o = dtab[e >> kSlotBits];
+            const float4 bj = __ldg(&B[e & kSlotMask]);
+            const float dx = (bi.x - bj.x) + o.x;
+            const float dy = (bi.y - bj.y) + o.y;
+            const float dz = (bi.z - bj.z) + o.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2 && r2 > 0.0f) {
+                const float ir = rsqrtf(r2);
+                const float hr = sc.h - r2 * ir;
+                const float gw = hr * hr * ir;
+                const float u = (sc.h2 - r2) * sc.inv_wdq;  // W(r) / W(dq) = u^3
+                const float scorr = sc.neg_k * powi<NPOW>(u * u * u, sc.scorr_n);
+                const float f = (bi.w + bj.w + scorr) * gw;
+                ax += f * dx;
+                ay += f * dy;
+                az += f * dz;
+            }
+        }
+        // new position, clamped to the box expressed relative to the cell origin
+        const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
+        float px = bi.x + sc.c_dp * ax;
+        float py = bi.y + sc.c_dp * ay;
+        float pz = bi.z + sc.c_dp * az;
+        px = fminf(fmaxf(px, blo0 - og.x), bhi0 - og.x);
+        py = fminf(fmaxf(py, blo1 - og.y), bhi1 - og.y);
+        pz = fminf(fmaxf(pz, blo2 - og.z), bhi2 - og.z);
+        A[p] = make_float4(px, py, pz, bi.w);
+    }
+}
+
+// ------------------------------------------ a10: velocity, XSPH, commit
+
+__global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers b)
+{
+    __shared__ float4 dtab[27];
+    fill_dtab(dtab, sc.q);
+    __syncthreads();
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sc.n)
+        return;
+    const size_t n = sc.n;
+    const float4 af = b.recA[p];
+    const float4 x0 = b.xt[p];
+    const float vx = (af.x - x0.x) * sc.inv_dt;
+    const float vy = (af.y - x0.y) * sc.inv_dt;
+    const float vz = (af.z - x0.z) * sc.inv_dt;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    const uint32_t nn = b.nbr_cnt[p];
+    for (uint32_t k = 0; k < nn; ++k) {
+        const uint32_t e = __ldg(b.nbr + (size_t)k * n + p);
+        const uint32_t j = e & kSlotMask;
+        const float4 o = dtab[e >> kSlotBits];
+        const float4 aj = __ldg(&b.recA[j]);
+        const float dx = (af.x - aj.x) + o.x;
+        const float dy = (af.y - aj.y) + o.y;
+        const float dz = (af.z - aj.z) + o.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < sc.h2) {
+            const float u = sc.h2 - r2;
+            const float W = u * u * u;
+            const float4 xj = __ldg(&b.xt[j]);
+            sx += ((aj.x - xj.x) * sc.inv_dt - vx) * W;
+            sy += ((aj.y - xj.y) * sc.inv_dt - vy) * W;
+            sz += ((aj.z - xj.z) * sc.inv_dt - vz) * W;
+        }
+    }
+    const float3 og = cell_origin(unpack_cell(b.cell_s[p]), sc);
+    const DynParams *dyn = b.dyn;
+    float px = fminf(fmaxf(og.x + af.x, dyn->box_lo[0]), dyn->box_hi[0]);
+    float py = fminf(fmaxf(og.y + af.y, dyn->box_lo[1]), dyn->box_hi[1]);
+    float pz = fminf(fmaxf(og.z + af.z, dyn->box_lo[2]), dyn->box_hi[2]);
+    b.state_x[p] = make_float4(px, py, pz, 0.0f);
+    b.state_v[p] = make_float4(vx + sc.c_xsph * sx, vy + sc.c_xsph * sy, vz + sc.c_xsph * sz, 0.0f);
+    b.state_id[p] = b.id_s[p];
+}
+
+// ------------------------------------------------------- readback helpers
+
+__global__ void __launch_bounds__(kBlock) unpermute_kernel(StepConst sc, Buffers b, uint32_t what)
+{
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sc.n)
+        return;
+    uint32_t id = b.state_id[p];
+    if (what == 0 || what == 1) {
+        float4 v = (what == 0) ? b.state_x[p] : b.state_v[p];
+        b.stage_f[3 * (size_t)id + 0] = v.x;
+        b.stage_f[3 * (size_t)id + 1] = v.y;
+        b.stage_f[3 * (size_t)id + 2] = v.z;
+    } else if (what == 2) {
+        b.stage_u8[id] = b.lvl_s[p];
+    } else {
+        b.stage_f[id] = b.rho[p];
+    }
+}
+
+// density diagnostic (Fig. 9): rho at the current positions, FP64 partial sums
+__global__ void __launch_bounds__(kBlock) density_kernel(StepConst sc, Buffers b, double rho0)
+{
+    __shared__ double sh[4][kBlock / 32];
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    double ea = 0.0, em = 0.0, es = 0.0, ep = 0.0;
+    if (p < sc.n) {
+        const size_t n = sc.n;
+        const float4 xi = b.xs32[p];
+        float racc = 0.0f;
+        const uint32_t nn = b.nbr_cnt[p];
+        for (uint32_t k = 0; k < nn; ++k) {
+            const uint32_t j = b.nbr[(size_t)k * n + p] & kSlotMask;
+            const float4 xj = b.xs32[j];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2) {
+                const float u = sc.h2 - r2;
+                racc += u * u * u;
+            }
+        }
+        const double e = (double)(sc.mass_poly6 * (sc.h6 + racc)) / rho0 - 1.0;
+        ea = fabs(e);
+        em = fabs(e);
+        es = e;
+        ep = e > 0.0 ? e : 0.0;
+    }
+    ea = warp_sum(ea);
+    es = warp_sum(es);
+    ep = warp_sum(ep);
+    em = warp_max(em);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][w] = ea;
+        sh[1][w] = em;
+        sh[2][w] = es;
+        sh[3][w] = ep;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, m = 0, s = 0, q = 0;
+        for (int v = 0; v < kBlock / 32; ++v) {
+            a += sh[0][v];
+            m = fmax(m, sh[1][v]);
+            s += sh[2][v];
+            q += sh[3][v];
+        }
+        b.partials[4 * (size_t)blockIdx.x + 0] = a;
+        b.partials[4 * (size_t)blockIdx.x + 1] = m;
+        b.partials[4 * (size_t)blockIdx.x + 2] = s;
+        b.partials[4 * (size_t)blockIdx.x + 3] = q;
+    }
+}
+
+__global__ void __launch_bounds__(32) density_final_kernel(const double *__restrict__ partials, int nblocks,
+                                                           uint32_t n, double *__restrict__ out)
+{
+    // one warp, fixed summation order
+    double a = 0, m = 0, s = 0, q = 0;
+    for (int k = threadIdx.x; k < nblocks; k += 32) {
+        a += partials[4 * k + 0];
+        m = fmax(m, partials[4 * k + 1]);
+        s += partials[4 * k + 2];
+        q += partials[4 * k + 3];
+    }
+    a = warp_sum(a);
+    s = warp_sum(s);
+    q = warp_sum(q);
+    m = warp_max(m);
+    if (threadIdx.x == 0) {
+        out[0] = n ? a / n : 0.0;
+        out[1] = m;
+        out[2] = n ? s / n : 0.0;
+        out[3] = n ? q / n : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) debug_xstar_kernel(StepConst sc, Buffers b, const float4 *__restrict__ rec)
+{
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sc.n)
+        return;
+    const float4 r = rec[p];
+    const float3 og = cell_origin(unpack_cell(b.cell_s[p]), sc);
+    b.dbg4[p] = make_float4(og.x + r.x, og.y + r.y, og.z + r.z, 0.0f);
+}
+
+__global__ void __launch_bounds__(kBlock) debug_lambda_kernel(StepConst sc, Buffers b, const float4 *__restrict__ rec)
+{
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < sc.n)
+        b.stage_f[p] = rec[p].w;
+}
+
+inline unsigned blocks_for(uint32_t n, int bs) { return (unsigned)((n + (uint32_t)bs - 1) / (uint32_t)bs); }
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+
+cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        lod_range_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
+{
+    if (sc.n)
+        predict_hash_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, diag ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    unsigned tiles = blocks_for(sc.ncell, kScanTile);
+    scan_reduce_kernel<<<tiles, 1024, 0, s>>>(b.cnt, sc.ncell, b.tile_sums);
+    scan_apply_kernel<<<tiles, 1024, 0, s>>>(b.cnt, sc.ncell, b.tile_sums, b.start, sc.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        scatter_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
+{
+    if (sc.n)
+        reorder_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, diag ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        neighbors_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    level_hist_kernel<<<sc.level_tiles, kLevelTile, 2 * sc.K * sizeof(uint32_t), s>>>(sc, b);
+    level_scan_kernel<<<1, 1024, 0, s>>>(sc, b);
+    level_scatter_kernel<<<sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int grid)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    if (dense)
+        lambda_kernel<true><<<grid, kBlock, 0, s>>>(sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_count, l);
+    else
+        lambda_kernel<false><<<grid, kBlock, 0, s>>>(sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_count, l);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int grid)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    const bool p4 = sc.scorr_n == 4;
+#define APBF_DP(D, P)                                                                                          \
+    deltap_kernel<D, P><<<grid, kBlock, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s, b.lvl_count, \
+                                                b.dyn, l)
+    if (dense && p4)
+        APBF_DP(true, 4);
+    else if (dense)
+        APBF_DP(true, -1);
+    else if (p4)
+        APBF_DP(false, 4);
+    else
+        APBF_DP(false, -1);
+#undef APBF_DP
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        finalize_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what)
+{
+    if (sc.n)
+        unpermute_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, what);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks)
+{
+    int nb = (int)blocks_for(sc.n, kBlock);
+    *nblocks = nb;
+    if (sc.n)
+        density_kernel<<<nb, kBlock, 0, s>>>(sc, b, (double)sc.rho0);
+    density_final_kernel<<<1, 32, 0, s>>>(b.partials, nb, sc.n, b.dstats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s)
+{
+    if (sc.n)
+        debug_xstar_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_lambda(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s)
+{
+    if (sc.n)
+        debug_lambda_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, rec);
+    return cudaGetLastError();
+}
+
+int iteration_grid(int sms)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, deltap_kernel<false, 4>, kBlock, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 4;
+    return sms * occ;
+}
+
+}  // namespace apbf

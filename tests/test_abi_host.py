@@ -1,0 +1,108 @@
+"""The C-ABI library loads and exports every entry point include/apbf.h
+declares; host-only calls (no GPU) behave as documented."""
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1608_04721_gb300 import apbf, build, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "apbf.h")).read()
+    return sorted(set(re.findall(r"APBF_API\s+[\w\s\*]+?\b(apbf_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) == 18
+    out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
+    assert set(names) <= exported
+    assert exported <= set(names), "library exports symbols the header does not declare"
+    assert sorted(apbf.EXPORTS) == names
+    L = apbf.lib()
+    for nm in names:
+        assert getattr(L, nm) is not None
+
+
+def test_rest_density_matches_closed_form():
+    rho = apbf.apbf_rest_density(0.1, 1.0, 0.05)
+    # FP32 h and spacing: compare with the lattice shell closed form at those values
+    h, s = float(np.float32(0.1)), float(np.float32(0.05))
+    closed = 315 / (64 * math.pi * h ** 9) * sum(
+        m * (h * h - q * s * s) ** 3 for m, q in ((1, 0), (6, 1), (12, 2), (8, 3)))
+    assert abs(rho - closed) / closed < 1e-12
+    assert abs(rho - 8078.2013351575) / 8078.2 < 1e-6
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_rest_density(-1.0, 1.0, 0.05)
+
+
+def _desc(**over):
+    cfg = scenes.config_dam_break_4k().replace(lattice=(4, 4, 4))
+    x, v = scenes.make_scene(cfg)
+    kw = dict(rho0=8078.2)
+    kw.update(over)
+    return apbf.desc_from_config(cfg, over.pop("pos", x), v, **kw)
+
+
+def test_scene_bytes_scale_with_particles():
+    b1 = apbf.apbf_scene_bytes(_desc())
+    cfg = scenes.config_ocean_1m()
+    x = np.zeros((1048576, 3), np.float32) + 1.0
+    d = apbf.desc_from_config(cfg, x, None, 8078.2)
+    b2 = apbf.apbf_scene_bytes(d)
+    assert b1 > 0 and b2 > 100 * b1
+    # about 0.6 kB per particle with 128 neighbour slots, well inside 280 GB
+    assert 400 * 1048576 < b2 < 1200 * 1048576
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(h=0.0), apbf.APBF_ERR_INVALID_ARG),
+    (dict(dt=-1.0), apbf.APBF_ERR_INVALID_ARG),
+    (dict(rho0=0.0), apbf.APBF_ERR_INVALID_ARG),
+    (dict(n_min=0), apbf.APBF_ERR_INVALID_ARG),
+    (dict(n_min=5, n_max=4), apbf.APBF_ERR_INVALID_ARG),
+    (dict(n_max=256), apbf.APBF_ERR_INVALID_ARG),
+    (dict(lod_mode=apbf.APBF_LOD_DTVS), apbf.APBF_ERR_NOT_SUPPORTED),
+    (dict(lod_mode=9), apbf.APBF_ERR_INVALID_ARG),
+    (dict(stabil_s=3, stabil_iters=2), apbf.APBF_ERR_NOT_SUPPORTED),
+    (dict(max_neighbors=300), apbf.APBF_ERR_INVALID_ARG),
+    (dict(box_lo=(-1.0, 0.0, 0.0)), apbf.APBF_ERR_INVALID_ARG),
+    (dict(scorr_dq=0.2), apbf.APBF_ERR_INVALID_ARG),
+    (dict(flags=8), apbf.APBF_ERR_INVALID_ARG),
+])
+def test_invalid_descriptions_are_rejected_on_the_host(over, status):
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_create_scene(_desc(**over), stream=0, device_arena=None)
+    assert e.value.status == status
+    assert apbf.apbf_last_error()
+
+
+def test_non_finite_or_outside_positions_are_rejected():
+    cfg = scenes.config_dam_break_4k().replace(lattice=(4, 4, 4))
+    x, v = scenes.make_scene(cfg)
+    x[3, 1] = np.nan
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, 8078.2), stream=0, device_arena=None)
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    x[3, 1] = 5.0  # outside the 1.6 m grid
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, 8078.2), stream=0, device_arena=None)
+    assert "outside" in apbf.apbf_last_error()
+
+
+def test_status_strings():
+    assert apbf.apbf_status_string(0) == "ok"
+    assert "overflow" in apbf.apbf_status_string(apbf.APBF_ERR_NEIGHBOR_OVERFLOW)

@@ -1,0 +1,348 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer stages (LOD levels, cell keys, sorted order, cell starts, neighbour
+sets, active sets) must match bit-exactly; FP32 results must match the FP64
+oracle within the stated tolerances:
+  rho_i           relative 1e-5
+  lambda_i        1e-5 * max_i |lambda_ref| (C_i ~ 0 in the interior makes a
+                  per-particle relative error meaningless)
+  positions       1e-5 * h after each iteration and after the step
+  velocities      1e-5 * h / dt (the position tolerance over one step)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_04721_gb300 import apbf, build, scenes
+
+pytestmark = pytest.mark.gpu
+
+SLOT = (1 << 27) - 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    apbf.lib()
+
+
+def rest_density(cfg) -> float:
+    return float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
+
+
+def make(cfg, *, eye=None, d_near=0.0, d_far=0.0, box=None, step=0, **over):
+    x, v = scenes.make_scene(cfg)
+    r0 = rest_density(cfg)
+    scene = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0, **over))
+    if eye is None:
+        eye = scenes.camera_at(cfg, step)[0]
+    lo, hi = (scenes.box_at(cfg, step) if box is None else box)
+    apbf.apbf_set_camera(scene, eye, (1.0, 0.0, 0.0), d_near, d_far)
+    apbf.apbf_set_box(scene, lo, hi)
+    p = oracle.make_params(cfg, rho0=r0, eye=eye, d_near=d_near, d_far=d_far, box_lo=lo, box_hi=hi,
+                           **{k: v for k, v in over.items() if k in ("n_min", "n_max", "lod_mode")})
+    return scene, p, x, v
+
+
+def cell_coords(keys, dims):
+    keys = keys.astype(np.int64)
+    return np.stack([keys % dims[0], (keys // dims[0]) % dims[1], keys // (dims[0] * dims[1])], 1)
+
+
+def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
+    n = cfg.n
+    n_max = int(p.n_max)
+    st = oracle.step(p, x, v, record=True, rec_iters=n_max if iters else 1)
+    # a1-a3: levels and keys, pre-sort (= id) order
+    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_PREDICT)
+    assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_KEYS), st.keys)
+    assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_PRESORT).astype(np.int32),
+                          st.level_presort)
+    # a4-a6 and the neighbour lists
+    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_NEIGHBORS)
+    assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_SORTED_IDS).astype(np.int32), st.order)
+    assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_CELL_START), st.cell_start)
+    xpred = apbf.apbf_debug_read(scene, apbf.APBF_DBG_XPRED)[:, :3]
+    assert np.array_equal(xpred, st.xpred[st.order])
+    cnt = apbf.apbf_debug_read(scene, apbf.APBF_DBG_NBR_COUNT).astype(np.int64)
+    nbr = apbf.apbf_debug_read(scene, apbf.APBF_DBG_NBR)
+    assert np.array_equal(cnt, np.diff(st.nbr_off))
+    dims, _, _ = apbf.apbf_debug_dims(scene)
+    cells = cell_coords(st.keys[st.order], dims)
+    rows = range(n) if sample is None else sample
+    for q in rows:
+        e = nbr[: cnt[q], q]
+        got = e & SLOT
+        ref = st.nbr_idx[st.nbr_off[q]:st.nbr_off[q + 1]]
+        assert np.array_equal(np.sort(got), np.sort(ref)), q
+        code = (e >> 27).astype(np.int64)
+        off = np.stack([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], 1)
+        assert np.array_equal(cells[got] - cells[q], off), q
+    lvl = st.level_presort[st.order]
+    if cfg.lod_mode == scenes.LOD_DTC and p.n_max > p.n_min:
+        apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
+        lc = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_COUNT).astype(np.int64)
+        assert np.array_equal(lc, st.active_count)
+        act = apbf.apbf_debug_read(scene, apbf.APBF_DBG_ACTIVE).astype(np.int64)
+        assert np.array_equal(act, np.lexsort((np.arange(n), -lvl)))
+    # a8-a9 per iteration
+    h = float(p.h)
+    for l in range(1, (n_max if iters else 1) + 1):
+        apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LAMBDA, l)
+        lam = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LAMBDA).astype(np.float64)
+        rho = apbf.apbf_debug_read(scene, apbf.APBF_DBG_RHO).astype(np.float64)
+        lam_ref = st.lam[l - 1]
+        scale = np.abs(lam_ref).max()
+        err = np.abs(lam - lam_ref).max()
+        assert err <= 1e-5 * scale, f"iteration {l}: lambda error {err:.3g} vs scale {scale:.3g}"
+        act = lvl >= l
+        rerr = np.abs(rho[act] / st.rho[l - 1][act] - 1).max()
+        assert rerr <= 1e-5, f"iteration {l}: rho relative error {rerr:.3g}"
+        if not iters:
+            break
+        apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_DELTAP, l)
+        xs = apbf.apbf_debug_read(scene, apbf.APBF_DBG_XSTAR)[:, :3].astype(np.float64)
+        xerr = np.abs(xs - st.xs[l - 1]).max()
+        assert xerr <= 1e-5 * h, f"iteration {l}: x* error {xerr:.3g} m"
+    return st
+
+
+def check_final(cfg, scene, p, st):
+    apbf.apbf_step(scene, 1)
+    got = apbf.apbf_read_state(scene, pos=True, vel=True, n_iter=True)
+    inv = np.argsort(st.ids)
+    h = float(p.h)
+    xerr = np.abs(got["pos"].astype(np.float64) - st.x[inv]).max()
+    verr = np.abs(got["vel"].astype(np.float64) - st.v[inv]).max()
+    assert xerr <= 1e-5 * h, f"positions after the step differ by {xerr:.3g} m"
+    assert verr <= 1e-5 * h / float(p.dt), f"velocities after the step differ by {verr:.3g} m/s"
+    lv, _ = oracle.lod_levels(p, scenes.make_scene(cfg)[0])
+    assert np.array_equal(got["n_iter"].astype(np.int32), lv)
+    lo, hi = np.asarray(p.box_lo[:], np.float32), np.asarray(p.box_hi[:], np.float32)
+    assert np.all(got["pos"] >= lo) and np.all(got["pos"] <= hi)
+
+
+SMALL = {
+    "pbf_4096": lambda: (scenes.config_dam_break_4k(), {}),
+    "apbf_5200": lambda: (scenes.config_dam_break_4k().replace(lattice=(20, 20, 13), lod_mode=scenes.LOD_DTC,
+                                                               n_min=2, n_max=7, camera="fixed",
+                                                               eye=(-1.0, 0.5, 0.3)), {}),
+    "apbf_ragged_1000_user_range": lambda: (
+        scenes.config_dam_break_4k().replace(lattice=(10, 10, 10), lod_mode=scenes.LOD_DTC, n_min=1, n_max=5,
+                                             camera="fixed", eye=(-0.5, 0.2, 0.9)),
+        dict(d_near=0.7, d_far=1.3)),
+    "apbf_33": lambda: (scenes.config_dam_break_4k().replace(lattice=(11, 3, 1), lod_mode=scenes.LOD_DTC,
+                                                             n_min=1, n_max=3, camera="fixed", eye=(2.0, 0.1, 0.1)),
+                        {}),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_stagewise_parity_small(name):
+    cfg, kw = SMALL[name]()
+    scene, p, x, v = make(cfg, **kw)
+    st = check_stages(cfg, scene, p, x, v)
+    check_final(cfg, scene, p, st)
+
+
+def test_one_step_parity_131k():
+    cfg = scenes.config_dam_break_131k()
+    scene, p, x, v = make(cfg)
+    rng = np.random.default_rng(0)
+    st = check_stages(cfg, scene, p, x, v, sample=rng.choice(cfg.n, 4096, replace=False))
+    check_final(cfg, scene, p, st)
+
+
+def test_one_step_parity_1m_bench_configuration():
+    """The benchmark's workload (1,048,576 particles, N_i in 3..15, moving
+    wall and spline camera) in the launch configuration the benchmark times
+    (captured graph): all integer stages, sampled neighbour sets, lambda and
+    rho of the first iteration for every particle, and the final state."""
+    cfg = scenes.config_ocean_1m()
+    scene, p, x, v = make(cfg, step=0)
+    rng = np.random.default_rng(1)
+    st = check_stages(cfg, scene, p, x, v, iters=False, sample=rng.choice(cfg.n, 2048, replace=False))
+    check_final(cfg, scene, p, st)
+
+
+def test_apbf_with_every_level_at_nmax_is_bitwise_pbf():
+    """Eq. 9-11: with every N_i = N_max, P_l = P_1 and APBF is PBF. The camera
+    range puts every particle at the nearest level, so the adaptive scene
+    still runs the level partition and the compacted-list kernels."""
+    base = scenes.config_dam_break_4k().replace(lattice=(16, 16, 12))
+    x, v = scenes.make_scene(base)
+    r0 = rest_density(base)
+    a = apbf.apbf_create_scene(apbf.desc_from_config(base, x, v, r0, n_min=6, n_max=6,
+                                                     lod_mode=apbf.APBF_LOD_FIXED))
+    b = apbf.apbf_create_scene(apbf.desc_from_config(base, x, v, r0, n_min=2, n_max=6, lod_mode=apbf.APBF_LOD_DTC))
+    apbf.apbf_set_camera(b, (-1.0, 0.3, 0.3), (1.0, 0.0, 0.0), 50.0, 60.0)
+    for s in (a, b):
+        apbf.apbf_step(s, 3)
+    ra = apbf.apbf_read_state(a, pos=True, vel=True)
+    rb = apbf.apbf_read_state(b, pos=True, vel=True)
+    assert np.array_equal(ra["pos"], rb["pos"]) and np.array_equal(ra["vel"], rb["vel"])
+
+
+def test_graph_replay_equals_eager_launches_bitwise():
+    cfg = scenes.config_dam_break_4k().replace(lattice=(16, 16, 12), lod_mode=scenes.LOD_DTC, n_min=2, n_max=6,
+                                               camera="fixed", eye=(-1.0, 0.4, 0.4))
+    x, v = scenes.make_scene(cfg)
+    r0 = rest_density(cfg)
+    g = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    e = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0, flags=apbf.APBF_FLAG_NO_GRAPH))
+    for s in (g, e):
+        apbf.apbf_set_camera(s, cfg.eye)
+        for k in range(4):
+            apbf.apbf_set_box(s, (0.02 * k, 0.0, 0.0), (1.6, 1.6, 1.6))
+            apbf.apbf_step(s, 1)
+    a = apbf.apbf_read_state(g, pos=True, vel=True, n_iter=True, rho=True)
+    b = apbf.apbf_read_state(e, pos=True, vel=True, n_iter=True, rho=True)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_checkpoint_resume_is_bitwise():
+    cfg = scenes.config_dam_break_4k().replace(lod_mode=scenes.LOD_DTC, n_min=2, n_max=5, camera="fixed",
+                                               eye=(-1.0, 0.5, 0.5))
+    x, v = scenes.make_scene(cfg)
+    r0 = rest_density(cfg)
+    full = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    apbf.apbf_set_camera(full, cfg.eye)
+    apbf.apbf_step(full, 3)
+    mid = apbf.apbf_read_state(full, pos=True, vel=True)
+    apbf.apbf_step(full, 4)
+    end = apbf.apbf_read_state(full, pos=True, vel=True)
+    res = apbf.apbf_create_scene(apbf.desc_from_config(cfg, mid["pos"], mid["vel"], r0))
+    apbf.apbf_set_camera(res, cfg.eye)
+    apbf.apbf_step(res, 4)
+    got = apbf.apbf_read_state(res, pos=True, vel=True)
+    assert np.array_equal(got["pos"], end["pos"]) and np.array_equal(got["vel"], end["vel"])
+
+
+def test_multi_step_density_statistics_match_oracle():
+    """20 steps of the 4096-particle dam break (chaotic): mean and max
+    |rho/rho0 - 1| of the GPU and the oracle agree within 0.2 points."""
+    cfg = scenes.config_dam_break_4k()
+    scene, p, x, v = make(cfg)
+    apbf.apbf_step(scene, cfg.steps)
+    gpu = apbf.apbf_density_stats(scene)
+    xo, vo, _ = oracle.run(lambda s: p, x, v, cfg.steps)
+    ref = oracle.density_stats(p, xo)
+    assert abs(gpu[0] - ref[0]) <= 0.002, (gpu, ref)
+    assert abs(gpu[1] - ref[1]) <= 0.002, (gpu, ref)
+    # the GPU diagnostic at identical positions agrees far more tightly
+    pos = apbf.apbf_read_state(scene, pos=True, vel=False)["pos"]
+    same = oracle.density_stats(p, pos)
+    assert np.allclose(gpu, same, rtol=1e-5, atol=1e-6), (gpu, same)
+
+
+def test_empty_scene():
+    cfg = scenes.config_dam_break_4k()
+    d = apbf.make_desc(pos=np.zeros((0, 3), np.float32), grid_lo=cfg.box_lo, grid_hi=cfg.box_hi, h=cfg.h, dt=cfg.dt,
+                       mass=1.0, rho0=8078.2, eps=cfg.eps, scorr_k=cfg.scorr_k, scorr_dq=cfg.scorr_dq,
+                       scorr_n=cfg.scorr_n, xsph_c=cfg.xsph_c, gravity=cfg.gravity, n_min=1, n_max=3,
+                       lod_mode=apbf.APBF_LOD_DTC)
+    s = apbf.apbf_create_scene(d)
+    apbf.apbf_set_camera(s, (0, 0, 0))
+    apbf.apbf_step(s, 2)
+    out = apbf.apbf_read_state(s, pos=True, vel=True, n_iter=True, rho=True)
+    assert out["pos"].shape == (0, 3)
+    assert np.array_equal(apbf.apbf_density_stats(s), np.zeros(4))
+
+
+def test_single_particle_free_fall_matches_oracle():
+    cfg = scenes.config_dam_break_4k()
+    x = np.array([[0.8, 0.8, 1.2]], np.float32)
+    v = np.array([[0.3, 0.0, -0.5]], np.float32)
+    r0 = rest_density(cfg)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    p = oracle.make_params(cfg, rho0=r0)
+    for _ in range(5):
+        apbf.apbf_step(s, 1)
+        st = oracle.step(p, x, v)
+        x, v = st.x, st.v
+    got = apbf.apbf_read_state(s, pos=True, vel=True)
+    assert np.abs(got["pos"] - x).max() <= 1e-6 and np.abs(got["vel"] - v).max() <= 1e-5
+
+
+def test_one_cell_cluster_and_box_faces():
+    """All particles in one cell (every pair a neighbour) and particles on the
+    box's upper faces (last cell index)."""
+    cfg = scenes.config_dam_break_4k()
+    rng = np.random.default_rng(3)
+    x = (0.42 + 0.03 * rng.random((24, 3))).astype(np.float32)
+    x[:4] = np.float32(1.6)
+    x[4:8, 2] = np.float32(0.0)
+    v = np.zeros_like(x)
+    r0 = rest_density(cfg)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    p = oracle.make_params(cfg, rho0=r0)
+    st = oracle.step(p, x, v, record=True)
+    apbf.apbf_debug_step_to(s, apbf.APBF_STAGE_NEIGHBORS)
+    assert np.array_equal(apbf.apbf_debug_read(s, apbf.APBF_DBG_SORTED_IDS).astype(np.int32), st.order)
+    cnt = apbf.apbf_debug_read(s, apbf.APBF_DBG_NBR_COUNT).astype(np.int64)
+    assert np.array_equal(cnt, np.diff(st.nbr_off))
+    apbf.apbf_step(s, 1)
+    got = apbf.apbf_read_state(s, pos=True, vel=True)
+    inv = np.argsort(st.ids)
+    assert np.abs(got["pos"] - st.x[inv]).max() <= 1e-6
+
+
+def test_neighbor_overflow_is_reported_and_sticky():
+    cfg = scenes.config_dam_break_4k()
+    rng = np.random.default_rng(4)
+    x = (0.8 + 0.02 * rng.random((100, 3))).astype(np.float32)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, None, rest_density(cfg), max_neighbors=16))
+    apbf.apbf_step(s, 1)
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_read_state(s)
+    assert e.value.status == apbf.APBF_ERR_NEIGHBOR_OVERFLOW
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_step(s, 1)
+    assert e.value.status == apbf.APBF_ERR_NEIGHBOR_OVERFLOW
+    # other scenes are unaffected
+    y, w = scenes.make_scene(cfg.replace(lattice=(4, 4, 4)))
+    ok = apbf.apbf_create_scene(apbf.desc_from_config(cfg, y, w, rest_density(cfg)))
+    apbf.apbf_step(ok, 1)
+    apbf.apbf_read_state(ok)
+
+
+def test_moving_wall_steps_match_oracle_for_a_few_steps():
+    cfg = scenes.config_dam_break_4k().replace(lattice=(12, 12, 8), wall="oscillate_xlo", wall_amplitude=0.2,
+                                               wall_period=0.2, lod_mode=scenes.LOD_DTC, n_min=2, n_max=5,
+                                               camera="fixed", eye=(2.5, 0.4, 0.3))
+    x, v = scenes.make_scene(cfg)
+    r0 = rest_density(cfg)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    ids = np.arange(cfg.n, dtype=np.int32)
+    for k in range(3):
+        lo, hi = scenes.box_at(cfg, k)
+        apbf.apbf_set_box(s, lo, hi)
+        apbf.apbf_set_camera(s, cfg.eye)
+        apbf.apbf_step(s, 1)
+        p = oracle.make_params(cfg, rho0=r0, eye=cfg.eye, box_lo=lo, box_hi=hi)
+        st = oracle.step(p, x, v, ids)
+        x, v, ids = st.x, st.v, st.ids
+    got = apbf.apbf_read_state(s, pos=True)
+    inv = np.argsort(ids)
+    # three chaotic steps: FP32 vs FP64 rounding grows, still far below h
+    assert np.abs(got["pos"] - x[inv]).max() <= 1e-4 * cfg.h
+    assert np.all(got["pos"][:, 0] >= scenes.box_at(cfg, 2)[0][0])
+
+
+def test_invalid_calls_on_a_live_scene():
+    cfg = scenes.config_dam_break_4k().replace(lattice=(4, 4, 4))
+    x, v = scenes.make_scene(cfg)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, rest_density(cfg)))
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_set_box(s, (0, 0, 0), (2.0, 1.6, 1.6))
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_set_camera(s, (np.nan, 0, 0))
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_debug_step_to(s, apbf.APBF_STAGE_LAMBDA, 99)
+    apbf.apbf_step(s, 1)  # still usable
+    apbf.apbf_sync(s)
