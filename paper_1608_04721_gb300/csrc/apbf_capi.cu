@@ -523,7 +523,7 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
         (e = cudaStreamSynchronize(st0)) != cudaSuccess)
         return bail(APBF_ERR_CUDA, std::string("initial upload: ") + cudaGetErrorString(e));
     s->dyn_dirty = true;
-    s->grid_iter = iteration_grid(s->sms > 0 ? s->sms : 1);
+    s->grid_iter = s->sms > 0 ? s->sms : 1;  // the launchers scale by each kernel's occupancy
     *out = s;
     return APBF_OK;
 }

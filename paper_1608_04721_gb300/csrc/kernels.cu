@@ -103,6 +103,40 @@ __device__ __forceinline__ void fill_dtab(float4 *dtab, float q)
     }
 }
 
+// Neighbour batch depth and the minimum resident blocks per SM the solver
+// kernels are compiled for (register budget); tuned on the GB300.
+#ifndef APBF_UNROLL
+#define APBF_UNROLL 4
+#endif
+#ifndef APBF_SOLVER_MIN_BLOCKS
+#define APBF_SOLVER_MIN_BLOCKS 6
+#endif
+constexpr uint32_t kNoEntry = 0xffffffffu;  // code 31: never a valid neighbour entry
+constexpr int kUnroll = APBF_UNROLL;
+
+// Visit the neighbour entries of one particle in batches of kUnroll: the
+// batch's entries are loaded first, then its records, then f runs on each,
+// so a thread has kUnroll independent gathers in flight.
+template <typename F>
+__device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ e_ptr, size_t stride, uint32_t nn,
+                                                  const float4 *__restrict__ rec, F &&f)
+{
+    for (uint32_t k = 0; k < nn; k += kUnroll) {
+        uint32_t e[kUnroll];
+        float4 r[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            e[u] = (k + u < nn) ? __ldg(e_ptr + (size_t)(k + u) * stride) : kNoEntry;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            r[u] = (e[u] != kNoEntry) ? __ldg(&rec[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (e[u] != kNoEntry)
+                f(e[u], r[u]);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -495,7 +529,7 @@ __global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc,
 // there, so inactive neighbours enter Eq. 7 with their last lambda.
 
 template <bool DENSE>
-__global__ void __launch_bounds__(kBlock) lambda_kernel(StepConst sc, const float4 *__restrict__ A,
+__global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) lambda_kernel(StepConst sc, const float4 *__restrict__ A,
                                                         float4 *__restrict__ B, float *__restrict__ rho_out,
                                                         const uint32_t *__restrict__ act,
                                                         const uint32_t *__restrict__ nbr,
@@ -517,11 +551,8 @@ __global__ void __launch_bounds__(kBlock) lambda_kernel(StepConst sc, const floa
         }
         const uint32_t nn = nbr_cnt[p];
         float racc = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, s2 = 0.0f;
-        const uint32_t *e_ptr = nbr + p;
-        for (uint32_t k = 0; k < nn; ++k) {
-            const uint32_t e = __ldg(e_ptr + (size_t)k * n);
+        for_each_neighbor(nbr + p, n, nn, A, [&](uint32_t e, const float4 &aj) {
             const float4 o = dtab[e >> kSlotBits];
-            const float4 aj = __ldg(&A[e & kSlotMask]);
             const float dx = (ai.x - aj.x) + o.x;
             const float dy = (ai.y - aj.y) + o.y;
             const float dz = (ai.z - aj.z) + o.z;
@@ -539,7 +570,7 @@ __global__ void __launch_bounds__(kBlock) lambda_kernel(StepConst sc, const floa
                     s2 += gw * gw * r2;
                 }
             }
-        }
+        });
         const float rho = sc.mass_poly6 * (sc.h6 + racc);
         const float C = rho * sc.inv_rho0 - 1.0f;
         const float denom = sc.c_lam * (gx * gx + gy * gy + gz * gz + s2) + sc.eps;
@@ -567,7 +598,7 @@ __device__ __forceinline__ float powi(float x, uint32_t n)
 }
 
 template <bool DENSE, int NPOW>
-__global__ void __launch_bounds__(kBlock) deltap_kernel(StepConst sc, const float4 *__restrict__ B,
+__global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) deltap_kernel(StepConst sc, const float4 *__restrict__ B,
                                                         float4 *__restrict__ A, const uint32_t *__restrict__ act,
                                                         const uint32_t *__restrict__ nbr,
                                                         const uint8_t *__restrict__ nbr_cnt,
@@ -587,11 +618,8 @@ __global__ void __launch_bounds__(kBlock) deltap_kernel(StepConst sc, const floa
         const float4 bi = B[p];
         const uint32_t nn = nbr_cnt[p];
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        const uint32_t *e_ptr = nbr + p;
-        for (uint32_t k = 0; k < nn; ++k) {
-            const uint32_t e = __ldg(e_ptr + (size_t)k * n);
+        for_each_neighbor(nbr + p, n, nn, B, [&](uint32_t e, const float4 &bj) {
             const float4 o = dtab[e >> kSlotBits];
-            const float4 bj = __ldg(&B[e & kSlotMask]);
             const float dx = (bi.x - bj.x) + o.x;
             const float dy = (bi.y - bj.y) + o.y;
             const float dz = (bi.z - bj.z) + o.z;
@@ -607,7 +635,7 @@ __global__ void __launch_bounds__(kBlock) deltap_kernel(StepConst sc, const floa
                 ay += f * dy;
                 az += f * dz;
             }
-        }
+        });
         // new position, clamped to the box expressed relative to the cell origin
         const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
         float px = bi.x + sc.c_dp * ax;
@@ -638,22 +666,35 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
     const float vz = (af.z - x0.z) * sc.inv_dt;
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     const uint32_t nn = b.nbr_cnt[p];
-    for (uint32_t k = 0; k < nn; ++k) {
-        const uint32_t e = __ldg(b.nbr + (size_t)k * n + p);
-        const uint32_t j = e & kSlotMask;
-        const float4 o = dtab[e >> kSlotBits];
-        const float4 aj = __ldg(&b.recA[j]);
-        const float dx = (af.x - aj.x) + o.x;
-        const float dy = (af.y - aj.y) + o.y;
-        const float dz = (af.z - aj.z) + o.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < sc.h2) {
-            const float u = sc.h2 - r2;
-            const float W = u * u * u;
-            const float4 xj = __ldg(&b.xt[j]);
-            sx += ((aj.x - xj.x) * sc.inv_dt - vx) * W;
-            sy += ((aj.y - xj.y) * sc.inv_dt - vy) * W;
-            sz += ((aj.z - xj.z) * sc.inv_dt - vz) * W;
+    const uint32_t *e_ptr = b.nbr + p;
+    for (uint32_t k = 0; k < nn; k += kUnroll) {
+        uint32_t e[kUnroll];
+        float4 aj[kUnroll], xj[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            e[u] = (k + u < nn) ? __ldg(e_ptr + (size_t)(k + u) * n) : kNoEntry;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool ok = e[u] != kNoEntry;
+            aj[u] = ok ? __ldg(&b.recA[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            xj[u] = ok ? __ldg(&b.xt[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (e[u] == kNoEntry)
+                continue;
+            const float4 o = dtab[e[u] >> kSlotBits];
+            const float dx = (af.x - aj[u].x) + o.x;
+            const float dy = (af.y - aj[u].y) + o.y;
+            const float dz = (af.z - aj[u].z) + o.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2) {
+                const float w = sc.h2 - r2;
+                const float W = w * w * w;
+                sx += ((aj[u].x - xj[u].x) * sc.inv_dt - vx) * W;
+                sy += ((aj[u].y - xj[u].y) * sc.inv_dt - vy) * W;
+                sz += ((aj[u].z - xj[u].z) * sc.inv_dt - vz) * W;
+            }
         }
     }
     const float3 og = cell_origin(unpack_cell(b.cell_s[p]), sc);
@@ -782,6 +823,28 @@ __global__ void __launch_bounds__(kBlock) debug_lambda_kernel(StepConst sc, Buff
 
 inline unsigned blocks_for(uint32_t n, int bs) { return (unsigned)((n + (uint32_t)bs - 1) / (uint32_t)bs); }
 
+// Resident blocks of kBlock threads per SM for a kernel (cached per function).
+int occupancy(const void *fn)
+{
+    static const void *keys[16];
+    static int vals[16];
+    for (int k = 0; k < 16; ++k)
+        if (keys[k] == fn)
+            return vals[k];
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 4;
+    }
+    for (int k = 0; k < 16; ++k)
+        if (!keys[k]) {
+            keys[k] = fn;
+            vals[k] = occ;
+            break;
+        }
+    return occ;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers
@@ -839,8 +902,9 @@ cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int grid)
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms)
 {
+    const int grid = sms * occupancy(dense ? (const void *)lambda_kernel<true> : (const void *)lambda_kernel<false>);
     if (!sc.n)
         return cudaGetLastError();
     if (dense)
@@ -850,11 +914,14 @@ cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s,
     return cudaGetLastError();
 }
 
-cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int grid)
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms)
 {
     if (!sc.n)
         return cudaGetLastError();
     const bool p4 = sc.scorr_n == 4;
+    const void *fn = dense ? (p4 ? (const void *)deltap_kernel<true, 4> : (const void *)deltap_kernel<true, -1>)
+                           : (p4 ? (const void *)deltap_kernel<false, 4> : (const void *)deltap_kernel<false, -1>);
+    const int grid = sms * occupancy(fn);
 #define APBF_DP(D, P)                                                                                          \
     deltap_kernel<D, P><<<grid, kBlock, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s, b.lvl_count, \
                                                 b.dyn, l)
@@ -908,13 +975,6 @@ cudaError_t launch_debug_lambda(const StepConst &sc, const Buffers &b, const flo
     return cudaGetLastError();
 }
 
-int iteration_grid(int sms)
-{
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, deltap_kernel<false, 4>, kBlock, 0) != cudaSuccess ||
-        occ < 1)
-        occ = 4;
-    return sms * occ;
-}
+int iteration_grid(int sms) { return sms; }
 
 }  // namespace apbf
