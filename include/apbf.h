@@ -224,23 +224,18 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint3
 #define APBF_DBG_NBR_COUNT 7u     /* u8[n]   neighbour count, sorted */
 #define APBF_DBG_NBR 8u           /* u32[max_neighbors*n]: entry k of particle p at k*n+p,
                                      low 27 bits = sorted slot, high 5 bits = cell offset code */
-#define APBF_DBG_ACTIVE 9u        /* u32[ntiles] tiles (16 cells of a grid row) by level, highest first,
-                                     then by tile id; the tiles holding P_l are a prefix */
+#define APBF_DBG_ACTIVE 9u        /* u32[n]  sorted slots, active-set order (P_l = prefix) */
 #define APBF_DBG_LEVEL_COUNT 10u  /* u32[n_max+2] |P_l|, l = 0..n_max+1 */
 #define APBF_DBG_LAMBDA 11u       /* float[n] lambda after the stage, sorted */
 #define APBF_DBG_RHO 12u          /* float[n] density of the last lambda pass, sorted */
 #define APBF_DBG_XSTAR 13u        /* float4[n] current x* (absolute FP32), sorted */
 #define APBF_DBG_DRANGE 14u       /* float[2] LOD distance range */
-#define APBF_DBG_TILE_LEVEL 15u   /* u8[ntiles] highest level in each tile (0: empty) */
-#define APBF_DBG_TILE_COUNT 16u   /* u32[n_max+2] tiles with level >= l, l = 0..n_max+1 */
 
 /* Copy a debug field (see APBF_DBG_*) to host memory of `bytes` bytes
  * (must equal the field's size). Synchronises. */
 APBF_API apbf_status apbf_debug_read(apbf_scene *scene, uint32_t field, void *host, size_t bytes);
 
-/* Sizes of the scene's grid: dims (3 ints), ncell, max_neighbors (host
- * outputs). Tiles: ntiles = ceil(dims[0] / 16) * dims[1] * dims[2], tile
- * t covering cells 16 (t mod ceil(dims[0]/16)) .. +15 of row t div ceil(dims[0]/16). */
+/* Sizes of the scene's grid: dims (3 ints), ncell, max_neighbors (host outputs). */
 APBF_API apbf_status apbf_debug_dims(apbf_scene *scene, int32_t dims[3], uint32_t *ncell,
                                      uint32_t *max_neighbors);
 

@@ -39,9 +39,7 @@ APBF_STAGE_COUNT = 10
 
 (APBF_DBG_KEYS, APBF_DBG_STATE_IDS, APBF_DBG_LEVEL_PRESORT, APBF_DBG_SORTED_IDS, APBF_DBG_CELL_START,
  APBF_DBG_XPRED, APBF_DBG_LEVEL, APBF_DBG_NBR_COUNT, APBF_DBG_NBR, APBF_DBG_ACTIVE, APBF_DBG_LEVEL_COUNT,
- APBF_DBG_LAMBDA, APBF_DBG_RHO, APBF_DBG_XSTAR, APBF_DBG_DRANGE, APBF_DBG_TILE_LEVEL,
- APBF_DBG_TILE_COUNT) = range(17)
-TILE_X = 16  # cells per solver tile along x
+ APBF_DBG_LAMBDA, APBF_DBG_RHO, APBF_DBG_XSTAR, APBF_DBG_DRANGE) = range(15)
 
 
 class apbf_scene_desc(C.Structure):
@@ -353,17 +351,15 @@ def apbf_debug_read(scene: Scene, field: int) -> np.ndarray:
     n = scene.n
     dims, ncell, mx = apbf_debug_dims(scene)
     n_max = int(scene.desc.n_max)
-    ntiles = int((dims[0] + TILE_X - 1) // TILE_X) * int(dims[1]) * int(dims[2])
     shapes = {
         APBF_DBG_KEYS: ((n,), np.uint32), APBF_DBG_STATE_IDS: ((n,), np.uint32),
         APBF_DBG_LEVEL_PRESORT: ((n,), np.uint8), APBF_DBG_SORTED_IDS: ((n,), np.uint32),
         APBF_DBG_CELL_START: ((ncell + 1,), np.uint32), APBF_DBG_XPRED: ((n, 4), np.float32),
         APBF_DBG_LEVEL: ((n,), np.uint8), APBF_DBG_NBR_COUNT: ((n,), np.uint8),
-        APBF_DBG_NBR: ((mx, n), np.uint32), APBF_DBG_ACTIVE: ((ntiles,), np.uint32),
+        APBF_DBG_NBR: ((mx, n), np.uint32), APBF_DBG_ACTIVE: ((n,), np.uint32),
         APBF_DBG_LEVEL_COUNT: ((n_max + 2,), np.uint32), APBF_DBG_LAMBDA: ((n,), np.float32),
         APBF_DBG_RHO: ((n,), np.float32), APBF_DBG_XSTAR: ((n, 4), np.float32),
-        APBF_DBG_DRANGE: ((2,), np.float32), APBF_DBG_TILE_LEVEL: ((ntiles,), np.uint8),
-        APBF_DBG_TILE_COUNT: ((n_max + 2,), np.uint32),
+        APBF_DBG_DRANGE: ((2,), np.float32),
     }
     shape, dt = shapes[field]
     a = np.empty(shape, dt)

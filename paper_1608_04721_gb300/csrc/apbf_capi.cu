@@ -153,11 +153,8 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.K = sc.n_max - sc.n_min + 1;
     sc.lod_mode = d->lod_mode;
     sc.max_nbr = d->max_neighbors ? d->max_neighbors : kDefaultMaxNeighbors;
-    sc.part_blocks = (d->n + kPartBlock - 1) / kPartBlock;
+    sc.level_tiles = (d->n + kLevelTile - 1) / kLevelTile;
     sc.rho0 = d->rho0;
-    sc.tiles_per_row = (uint32_t)((sc.nx + kTileX - 1) / kTileX);
-    sc.ntiles = sc.tiles_per_row * (uint32_t)sc.ny * (uint32_t)sc.nz;
-    sc.tile_blocks = (sc.ntiles + kPartBlock - 1) / kPartBlock;
     st = APBF_OK;
     return "";
 }
@@ -181,9 +178,8 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     const size_t n = sc.n ? sc.n : 1;
     const size_t ncell4 = (sc.ncell + 3) / 4 * 4;
     const size_t tiles = (sc.ncell + kScanTile - 1) / kScanTile;
-    const size_t lvl_e = (size_t)sc.K * (sc.part_blocks ? sc.part_blocks : 1);
-    const size_t tile_e = (size_t)(sc.n_max + 1) * sc.tile_blocks;
-    const size_t dblocks = 4096;  // >= persistent grid of the density kernel
+    const size_t lvl_e = (size_t)sc.K * (sc.level_tiles ? sc.level_tiles : 1);
+    const size_t dblocks = (n + kBlock - 1) / kBlock;
     Layout L;
     auto P = [&](size_t bytes) -> char * { size_t o = L.add(bytes); return base ? base + o : nullptr; };
     b.state_x = (float4 *)P(16 * n);
@@ -204,16 +200,12 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.cell_s = (uint32_t *)P(4 * n);
     b.lvl_s = (uint8_t *)P(n);
     b.nbr_cnt = (uint8_t *)P(n);
-    b.nbr = (uint16_t *)P(2 * (size_t)sc.max_nbr * n);
+    b.nbr = (uint32_t *)P(4 * (size_t)sc.max_nbr * n);
     b.rho = (float *)P(4 * n);
+    b.act = (uint32_t *)P(4 * n);
     b.lvl_hist = (uint32_t *)P(4 * lvl_e);
     b.lvl_off = (uint32_t *)P(4 * lvl_e);
     b.lvl_count = (uint32_t *)P(4 * 258);
-    b.tile_lvl = (uint8_t *)P(sc.ntiles);
-    b.tile_hist = (uint32_t *)P(4 * tile_e);
-    b.tile_off = (uint32_t *)P(4 * tile_e);
-    b.tile_list = (uint32_t *)P(4 * (size_t)sc.ntiles);
-    b.tile_count = (uint32_t *)P(4 * 258);
     b.counters = (unsigned long long *)P(8 * kCounterSlots);
     b.drange = (uint32_t *)P(8);
     b.err = (uint32_t *)P(4);
@@ -221,7 +213,6 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.stage_f = (float *)P(12 * n);
     b.stage_u8 = (uint8_t *)P(n);
     b.dbg4 = (float4 *)P(16 * n);
-    b.dbg_nbr = (uint32_t *)b.stage_f;  // one expanded neighbour row at a time
     b.partials = (double *)P(32 * dblocks);
     b.dstats = (double *)P(32);
     return L.total;
@@ -297,31 +288,34 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
         return APBF_OK;
     e = timed(s, st, APBF_STAGE_NEIGHBORS, [&] {
         cudaMemsetAsync(b.counters, 0, 8 * (2 + 256), st);
-        return launch_neighbors(sc, b, st, s->grid_iter, false);
+        return launch_neighbors(sc, b, st);
     });
     if (e != cudaSuccess)
         return cuda_fail(s, e, "neighbors");
     if (stop_stage == APBF_STAGE_NEIGHBORS)
         return APBF_OK;
-    if ((e = timed(s, st, APBF_STAGE_LEVELS, [&] { return launch_levels(sc, b, st); })) != cudaSuccess)
-        return cuda_fail(s, e, "levels");
+    if (dtc && sc.K > 1) {
+        if ((e = timed(s, st, APBF_STAGE_LEVELS, [&] { return launch_levels(sc, b, st); })) != cudaSuccess)
+            return cuda_fail(s, e, "levels");
+    }
     if (stop_stage == APBF_STAGE_LEVELS)
         return APBF_OK;
     for (uint32_t l = 1; l <= sc.n_max; ++l) {
-        e = timed(s, st, APBF_STAGE_LAMBDA, [&] { return launch_lambda(sc, b, st, l, s->grid_iter); });
+        const bool dense = l <= sc.n_min;
+        e = timed(s, st, APBF_STAGE_LAMBDA, [&] { return launch_lambda(sc, b, st, l, dense, s->grid_iter); });
         if (e != cudaSuccess)
             return cuda_fail(s, e, "lambda");
         s->cur_buf = 1;
         if (stop_stage == APBF_STAGE_LAMBDA && stop_iter == l)
             return APBF_OK;
-        e = timed(s, st, APBF_STAGE_DELTAP, [&] { return launch_deltap(sc, b, st, l, s->grid_iter); });
+        e = timed(s, st, APBF_STAGE_DELTAP, [&] { return launch_deltap(sc, b, st, l, dense, s->grid_iter); });
         if (e != cudaSuccess)
             return cuda_fail(s, e, "deltap");
         s->cur_buf = 0;
         if (stop_stage == APBF_STAGE_DELTAP && stop_iter == l)
             return APBF_OK;
     }
-    if ((e = timed(s, st, APBF_STAGE_FINALIZE, [&] { return launch_finalize(sc, b, st, s->grid_iter); })) != cudaSuccess)
+    if ((e = timed(s, st, APBF_STAGE_FINALIZE, [&] { return launch_finalize(sc, b, st); })) != cudaSuccess)
         return cuda_fail(s, e, "finalize");
     return APBF_OK;
 }
@@ -348,10 +342,6 @@ apbf_status check_device_errors(apbf_scene *s)
     if (*h & kErrNeighborOverflow)
         return fail(s, APBF_ERR_NEIGHBOR_OVERFLOW,
                     "a particle had more neighbours than max_neighbors (" + std::to_string(s->sc.max_nbr) + ")");
-    if (*h & kErrRunOverflow)
-        return fail(s, APBF_ERR_NEIGHBOR_OVERFLOW, "more than 2048 particles in 18 consecutive cells of one grid row");
-    if (*h & kErrTimeout)
-        return fail(s, APBF_ERR_TIMEOUT, "a bounded wait for staged tile copies gave up");
     return APBF_OK;
 }
 
@@ -646,8 +636,8 @@ APBF_API apbf_status apbf_density_stats(apbf_scene *s, double stats[4])
     APBF_CUDA(s, launch_scan(s->sc, bb, q));
     APBF_CUDA(s, launch_scatter(s->sc, bb, q));
     APBF_CUDA(s, launch_reorder(s->sc, bb, q, true));
-    APBF_CUDA(s, launch_neighbors(s->sc, bb, q, s->grid_iter, true));
-    APBF_CUDA(s, launch_density(s->sc, bb, q, s->grid_iter, &nb));
+    APBF_CUDA(s, launch_neighbors(s->sc, bb, q));
+    APBF_CUDA(s, launch_density(s->sc, bb, q, &nb));
     double *h = (double *)s->pinned_small + 8;
     APBF_CUDA(s, cudaMemcpyAsync(h, s->b.dstats, 32, cudaMemcpyDeviceToHost, q));
     if ((st = check_device_errors(s)) != APBF_OK)
@@ -676,15 +666,22 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     APBF_CUDA(s, cudaMemcpy(c.data(), s->b.counters, 8 * kCounterSlots, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(lc.data(), s->b.lvl_count, 4 * 258, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(dr, s->b.drange, 8, cudaMemcpyDeviceToHost));
+    const bool partitioned = sc.lod_mode == APBF_LOD_DTC && sc.K > 1;
     info->neighbor_pairs = c[0];
     for (uint32_t l = 0; l < 256; ++l) {
-        const uint32_t a = l <= sc.n_max ? lc[l] : 0u;
+        uint32_t a = 0;
+        if (l <= sc.n_max)
+            a = partitioned ? lc[l] : sc.n;
         info->active_count[l] = a;
         if (l >= 1)
             info->particle_iterations += a;
     }
-    for (uint32_t bin = 0; bin < sc.K; ++bin)
-        info->lambda_pairs += c[2 + bin] * (unsigned long long)(sc.n_max - bin);
+    if (partitioned) {
+        for (uint32_t bin = 0; bin < sc.K; ++bin)
+            info->lambda_pairs += c[2 + bin] * (unsigned long long)(sc.n_max - bin);
+    } else {
+        info->lambda_pairs = c[0] * (unsigned long long)sc.n_max;
+    }
     if (sc.lod_mode == APBF_LOD_DTC) {
         if (s->dyn.auto_range) {
             info->d_range[0] = dr[0];
@@ -821,21 +818,8 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
     case APBF_DBG_XPRED: src = b.xs32; size = 16 * n; break;
     case APBF_DBG_LEVEL: src = b.lvl_s; size = n; break;
     case APBF_DBG_NBR_COUNT: src = b.nbr_cnt; size = n; break;
-    case APBF_DBG_NBR: {
-        size = 4 * (size_t)sc.max_nbr * n;
-        if (bytes != size || (size && !host))
-            return fail(s, APBF_ERR_INVALID_ARG, "debug_read size mismatch: field needs " + std::to_string(size) + " bytes");
-        for (uint32_t k = 0; k < sc.max_nbr && n; ++k) {
-            APBF_CUDA(s, launch_debug_neighbors(sc, b, s->stream, k));
-            APBF_CUDA(s, cudaMemcpyAsync((char *)host + 4 * (size_t)k * n, b.dbg_nbr, 4 * n, cudaMemcpyDeviceToHost,
-                                         s->stream));
-        }
-        APBF_CUDA(s, cudaStreamSynchronize(s->stream));
-        return check_device_errors(s);
-    }
-    case APBF_DBG_ACTIVE: src = b.tile_list; size = 4 * (size_t)sc.ntiles; break;
-    case APBF_DBG_TILE_LEVEL: src = b.tile_lvl; size = sc.ntiles; break;
-    case APBF_DBG_TILE_COUNT: src = b.tile_count; size = 4 * ((size_t)sc.n_max + 2); break;
+    case APBF_DBG_NBR: src = b.nbr; size = 4 * (size_t)sc.max_nbr * n; break;
+    case APBF_DBG_ACTIVE: src = b.act; size = 4 * n; break;
     case APBF_DBG_LEVEL_COUNT: src = b.lvl_count; size = 4 * ((size_t)sc.n_max + 2); break;
     case APBF_DBG_LAMBDA:
         APBF_CUDA(s, launch_debug_lambda(sc, b, cur, s->stream));

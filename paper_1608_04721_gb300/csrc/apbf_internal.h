@@ -13,27 +13,14 @@
 namespace apbf {
 
 constexpr uint32_t kDefaultMaxNeighbors = 128;
-constexpr uint32_t kSlotBits = 27;   // debug neighbour entry: slot (27 bits) | cell offset code (5 bits)
+constexpr uint32_t kSlotBits = 27;  // neighbour entry: slot (27 bits) | cell offset code (5 bits)
 constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
 constexpr int kBlock = 256;          // threads per block of the per-particle kernels
 constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
-constexpr int kPartBlock = 1024;     // elements per block of the level partitions
-
-// Solver tiles: kTileX consecutive cells of one grid row. A tile's halo is 9
-// contiguous runs of the sorted particle arrays (rows y-1..y+1, z-1..z+1,
-// cells x0-1..x1), staged into shared memory when it holds <= kTileCap records.
-constexpr int kTileX = 16;
-constexpr int kTileThreads = 128;
-constexpr uint32_t kTileCap = 2560;  // 40 KB of float4 records
-// Neighbour entry (16 bits): cell offset code (dx+1) + 3(dy+1) + 9(dz+1) in
-// the high 5 bits, offset of the neighbour within its halo run in the low 11.
-constexpr uint32_t kOffBits = 11;
-constexpr uint32_t kOffMask = (1u << kOffBits) - 1u;
+constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
 
 // Device error word bits.
 constexpr uint32_t kErrNeighborOverflow = 1u;
-constexpr uint32_t kErrRunOverflow = 2u;   // a halo run longer than 2^11 particles
-constexpr uint32_t kErrTimeout = 4u;       // a bounded wait for staged copies gave up
 
 // Step constants, fixed for a scene's lifetime (passed by value as kernel
 // arguments and therefore baked into the captured step graph).
@@ -64,11 +51,8 @@ struct StepConst {
     float c_xsph;       // c (m / rho0) * 315/(64 pi h^9)
     uint32_t n_min, n_max, K, lod_mode;
     uint32_t max_nbr;
-    uint32_t part_blocks;    // ceil(n / kPartBlock)
-    float rho0;              // rest density as given (FP32)
-    uint32_t tiles_per_row;  // ceil(nx / kTileX)
-    uint32_t ntiles;         // tiles_per_row * ny * nz
-    uint32_t tile_blocks;    // ceil(ntiles / kPartBlock)
+    uint32_t level_tiles;
+    float rho0;         // rest density as given (FP32)
 };
 
 // Per-step values that callers change between steps (device copy read by kernels).
@@ -90,11 +74,9 @@ struct Buffers {
     float4 *recA, *recB, *xs32, *xt;
     uint32_t *id_s, *cell_s;
     uint8_t *lvl_s, *nbr_cnt;
-    uint16_t *nbr;                 // max_nbr x n neighbour entries (see kOffBits)
+    uint32_t *nbr;
     float *rho;
-    uint32_t *lvl_hist, *lvl_off, *lvl_count;      // particle level histogram -> |P_l|
-    uint8_t *tile_lvl;                              // max level of each tile (0: empty)
-    uint32_t *tile_hist, *tile_off, *tile_list, *tile_count;  // tiles by level, highest first
+    uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
     unsigned long long *counters;  // [0] pairs, [1] lambda pairs
     uint32_t *drange;              // float bits of d_min, d_max
     uint32_t *err;
@@ -102,7 +84,6 @@ struct Buffers {
     float *stage_f;                // 3n floats readback staging
     uint8_t *stage_u8;             // n bytes readback staging
     float4 *dbg4;                  // n float4 debug staging
-    uint32_t *dbg_nbr;             // max_nbr x n expanded neighbour entries (debug)
     double *partials;              // diagnostic partial sums
     double *dstats;                // 4 doubles
 };
@@ -153,25 +134,24 @@ struct apbf_scene {
 
 namespace apbf {
 
-// Kernel launchers (kernels.cu: grid stages; solver.cu: tile-staged stages).
-// Each returns cudaGetLastError().
-int occupancy(const void *fn, int block);
+// Kernel launchers (kernels.cu). Each returns cudaGetLastError().
 cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
 cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense,
+                          int grid);
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense,
+                          int grid);
+cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what);
-cudaError_t launch_density_final(const StepConst &sc, const Buffers &b, cudaStream_t s, int nblocks);
+cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks);
 cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);
 cudaError_t launch_debug_lambda(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);
-cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, int sms, bool diag);
-cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
-cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, int sms);
-cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, int sms);
-cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s, int sms);
-cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int sms, int *nblocks);
-cudaError_t launch_debug_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t k);
-int tile_grid(int sms);
+cudaError_t launch_fixed_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
+int iteration_grid(int sms);
 
 }  // namespace apbf

@@ -21,10 +21,202 @@
 // domain (a 10 m basin has an FP32 spacing of ~1e-6 m).
 #include "apbf_internal.h"
 
-#include "device_common.cuh"
-
 namespace apbf {
 namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ float3 predict_position(float4 x, float4 v, const StepConst &sc, const DynParams *dyn)
+{
+    // Fig. 7 lines 1-4 in FP32, rounded after every operation (no FMA):
+    // v' = v + dt g, x* = x + dt v', then the box clamp.
+    float vx = __fadd_rn(v.x, __fmul_rn(sc.dt, sc.g[0]));
+    float vy = __fadd_rn(v.y, __fmul_rn(sc.dt, sc.g[1]));
+    float vz = __fadd_rn(v.z, __fmul_rn(sc.dt, sc.g[2]));
+    float px = __fadd_rn(x.x, __fmul_rn(sc.dt, vx));
+    float py = __fadd_rn(x.y, __fmul_rn(sc.dt, vy));
+    float pz = __fadd_rn(x.z, __fmul_rn(sc.dt, vz));
+    px = fminf(fmaxf(px, dyn->box_lo[0]), dyn->box_hi[0]);
+    py = fminf(fmaxf(py, dyn->box_lo[1]), dyn->box_hi[1]);
+    pz = fminf(fmaxf(pz, dyn->box_lo[2]), dyn->box_hi[2]);
+    return make_float3(px, py, pz);
+}
+
+__device__ __forceinline__ int cell_axis(float p, float lo, float inv_h, int dim)
+{
+    float t = __fmul_rn(__fsub_rn(p, lo), inv_h);
+    int c = (int)floorf(t);
+    return min(max(c, 0), dim - 1);
+}
+
+__device__ __forceinline__ int3 cell_of(float3 p, const StepConst &sc)
+{
+    return make_int3(cell_axis(p.x, sc.glo[0], sc.inv_h, sc.nx), cell_axis(p.y, sc.glo[1], sc.inv_h, sc.ny),
+                     cell_axis(p.z, sc.glo[2], sc.inv_h, sc.nz));
+}
+
+__device__ __forceinline__ uint32_t pack_cell(int3 c) { return (uint32_t)c.x | ((uint32_t)c.y << 11) | ((uint32_t)c.z << 22); }
+
+__device__ __forceinline__ int3 unpack_cell(uint32_t v)
+{
+    return make_int3((int)(v & 2047u), (int)((v >> 11) & 2047u), (int)(v >> 22));
+}
+
+__device__ __forceinline__ float3 cell_origin(int3 c, const StepConst &sc)
+{
+    return make_float3((float)(sc.m[0] + c.x) * sc.q, (float)(sc.m[1] + c.y) * sc.q, (float)(sc.m[2] + c.z) * sc.q);
+}
+
+__device__ __forceinline__ float camera_distance(float4 x, const DynParams *dyn)
+{
+    float dx = __fsub_rn(x.x, dyn->eye[0]);
+    float dy = __fsub_rn(x.y, dyn->eye[1]);
+    float dz = __fsub_rn(x.z, dyn->eye[2]);
+    float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+    return __fsqrt_rn(d2);
+}
+
+// Sec. 4.1 / Eq. 8: linear interpolation of the distance range onto the level
+// range, near -> n_max, as K equal-width bins (FP32).
+__device__ __forceinline__ uint32_t lod_level(float d, float dmin, float dmax, const StepConst &sc)
+{
+    float span = __fsub_rn(dmax, dmin);
+    float t = 0.0f;
+    if (span > 0.0f)
+        t = __fdiv_rn(__fsub_rn(d, dmin), span);
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    int b = (int)floorf(__fmul_rn(t, (float)sc.K));
+    b = min(b, (int)sc.K - 1);
+    return sc.n_max - (uint32_t)b;
+}
+
+// Cell-origin difference o_i - o_j = -(offset) q for the 27 neighbour cells.
+__device__ __forceinline__ void fill_dtab(float4 *dtab, float q)
+{
+    if (threadIdx.x < 27) {
+        int c = threadIdx.x;
+        float ox = (float)(c % 3 - 1), oy = (float)((c / 3) % 3 - 1), oz = (float)(c / 9 - 1);
+        dtab[c] = make_float4(-ox * q, -oy * q, -oz * q, 0.0f);
+    }
+}
+
+// Neighbour batch depth and the minimum resident blocks per SM the solver
+// kernels are compiled for (register budget); tuned on the GB300.
+#ifndef APBF_UNROLL
+#define APBF_UNROLL 4
+#endif
+#ifndef APBF_SOLVER_MIN_BLOCKS
+#define APBF_SOLVER_MIN_BLOCKS 6
+#endif
+constexpr uint32_t kNoEntry = 0xffffffffu;  // code 31: never a valid neighbour entry
+constexpr int kUnroll = APBF_UNROLL;
+
+// Visit the neighbour entries of one particle in batches of kUnroll: the
+// batch's entries are loaded first, then its records, then f runs on each,
+// so a thread has kUnroll independent gathers in flight. Entries are read
+// once per pass (streaming hint, they should not displace the records that
+// neighbouring threads reuse from L1).
+template <typename F>
+__device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ e_ptr, size_t stride, uint32_t nn,
+                                                  const float4 *__restrict__ rec, F &&f)
+{
+    for (uint32_t k = 0; k < nn; k += kUnroll) {
+        uint32_t e[kUnroll];
+        float4 r[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            e[u] = (k + u < nn) ? __ldcs(e_ptr + (size_t)(k + u) * stride) : kNoEntry;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            r[u] = (e[u] != kNoEntry) ? __ldg(&rec[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (e[u] != kNoEntry)
+                f(e[u], r[u]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_minf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Block-wide sum of a u32 (any multiple-of-32 block size <= 1024), result in every thread.
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sh32)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0)
+        sh32[w] = v;
+    __syncthreads();
+    uint32_t t = (lane < nw) ? sh32[lane] : 0u;
+    t = warp_sum(t);
+    return t;
+}
+
+// Block-wide exclusive scan of a u32; returns the exclusive prefix, *total the sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t *sh32, uint32_t *total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o)
+            inc += y;
+    }
+    __syncthreads();
+    if (lane == 31)
+        sh32[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = (lane < nw) ? sh32[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        if (lane < nw)
+            sh32[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t warp_prefix = (w > 0) ? sh32[w - 1] : 0u;
+    *total = sh32[nw - 1];
+    return warp_prefix + inc - v;
+}
 
 // ------------------------------------------------------------- a1: range
 
@@ -197,6 +389,336 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
     }
 }
 
+// ----------------------------------------------- neighbour lists (l. 5-6)
+
+__global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b)
+{
+    __shared__ uint32_t sh[32];
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t cnt = 0;
+    if (p < sc.n) {
+        const float4 xi = b.xs32[p];
+        const int3 c = unpack_cell(b.cell_s[p]);
+        const size_t n = sc.n;
+        // the cells x-1..x+1 of one row (y+dy, z+dz) are contiguous in sorted order
+        const int xl = max(c.x - 1, 0), xr = min(c.x + 1, sc.nx - 1);
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int cz = c.z + dz;
+            if (cz < 0 || cz >= sc.nz)
+                continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int cy = c.y + dy;
+                if (cy < 0 || cy >= sc.ny)
+                    continue;
+                const uint32_t row = ((uint32_t)cz * (uint32_t)sc.ny + (uint32_t)cy) * (uint32_t)sc.nx;
+                const uint32_t j0 = b.start[row + xl], jm = b.start[row + c.x], jp = b.start[row + c.x + 1],
+                               j1 = b.start[row + xr + 1];
+                const uint32_t code_row = (uint32_t)(3 * (dy + 1) + 9 * (dz + 1));
+                for (uint32_t j = j0; j < j1; j += kUnroll) {
+                    float4 xj[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u)
+                        xj[u] = (j + u < j1) ? b.xs32[j + u] : xi;
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const uint32_t q = j + u;
+                        if (q >= j1 || q == p)
+                            continue;
+                        // FP32 predicate, rounded after every operation
+                        const float dx = __fsub_rn(xi.x, xj[u].x);
+                        const float dy2 = __fsub_rn(xi.y, xj[u].y);
+                        const float dz2 = __fsub_rn(xi.z, xj[u].z);
+                        float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy2, dy2));
+                        r2 = __fadd_rn(r2, __fmul_rn(dz2, dz2));
+                        if (r2 < sc.h2) {
+                            const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
+                            if (cnt < sc.max_nbr)
+                                b.nbr[(size_t)cnt * n + p] = q | ((code_row + dxc) << kSlotBits);
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+        }
+        if (cnt > sc.max_nbr) {
+            atomicOr(b.err, kErrNeighborOverflow);
+            cnt = sc.max_nbr;
+        }
+        b.nbr_cnt[p] = (uint8_t)cnt;
+    }
+    uint32_t tot = block_sum_u32(cnt, sh);
+    if (threadIdx.x == 0 && tot)
+        atomicAdd(&b.counters[0], (unsigned long long)tot);
+}
+
+// ---------------------------------------- a7: active sets by stable partition
+// Particles are partitioned by level, highest first, stable in sorted-slot
+// order within a level. P_l is then the prefix of act of length |P_l|.
+
+__global__ void __launch_bounds__(kLevelTile) level_hist_kernel(StepConst sc, Buffers b)
+{
+    extern __shared__ uint32_t sh[];  // K counts, K pair sums
+    const uint32_t K = sc.K;
+    for (uint32_t k = threadIdx.x; k < 2 * K; k += blockDim.x)
+        sh[k] = 0u;
+    __syncthreads();
+    uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
+    if (p < sc.n) {
+        uint32_t bin = sc.n_max - b.lvl_s[p];
+        atomicAdd(&sh[bin], 1u);
+        atomicAdd(&sh[K + bin], (uint32_t)b.nbr_cnt[p]);
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x) {
+        b.lvl_hist[(size_t)k * sc.level_tiles + blockIdx.x] = sh[k];
+        if (sh[K + k])
+            atomicAdd(&b.counters[2 + k], (unsigned long long)sh[K + k]);
+    }
+}
+
+__global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers b)
+{
+    __shared__ uint32_t sh[32];
+    const uint32_t E = sc.K * sc.level_tiles;
+    const uint32_t chunk = (E + blockDim.x - 1) / blockDim.x;
+    const uint32_t e0 = min(E, threadIdx.x * chunk), e1 = min(E, e0 + chunk);
+    uint32_t s = 0;
+    for (uint32_t e = e0; e < e1; ++e)
+        s += b.lvl_hist[e];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan_u32(s, sh, &total);
+    for (uint32_t e = e0; e < e1; ++e) {
+        uint32_t v = b.lvl_hist[e];
+        b.lvl_off[e] = run;
+        run += v;
+    }
+    __syncthreads();
+    for (uint32_t l = threadIdx.x; l <= sc.n_max + 1; l += blockDim.x) {
+        uint32_t c;
+        if (l > sc.n_max)
+            c = 0;
+        else if (l <= sc.n_min)
+            c = sc.n;
+        else {
+            uint32_t bin_end = sc.n_max - l + 1;  // bins 0..n_max-l hold levels >= l
+            c = (bin_end >= sc.K) ? sc.n : b.lvl_off[(size_t)bin_end * sc.level_tiles];
+        }
+        b.lvl_count[l] = c;
+    }
+}
+
+__global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc, Buffers b)
+{
+    extern __shared__ uint32_t wc[];  // 32 warps x K
+    const uint32_t K = sc.K;
+    for (uint32_t k = threadIdx.x; k < 32 * K; k += blockDim.x)
+        wc[k] = 0u;
+    __syncthreads();
+    uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
+    bool valid = p < sc.n;
+    uint32_t bin = valid ? (sc.n_max - b.lvl_s[p]) : 0xffffffffu;
+    unsigned peers = __match_any_sync(kFull, bin);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int leader = __ffs(peers) - 1;
+    uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    if (valid && lane == leader)
+        wc[w * K + bin] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (valid) {
+        uint32_t pos = b.lvl_off[(size_t)bin * sc.level_tiles + blockIdx.x] + rank;
+        for (int v = 0; v < w; ++v)
+            pos += wc[v * K + bin];
+        b.act[pos] = p;
+    }
+}
+
+// ---------------------------------------------------------- a8: lambda pass
+// Iteration l, threads over P_{l-1}: particles of P_l compute rho and lambda
+// (Eq. 4-6) from A and write (position, lambda) to B; particles that finished
+// in iteration l-1 copy their final position into B and keep their lambda
+// there, so inactive neighbours enter Eq. 7 with their last lambda.
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) lambda_kernel(StepConst sc, const float4 *__restrict__ A,
+                                                        float4 *__restrict__ B, float *__restrict__ rho_out,
+                                                        const uint32_t *__restrict__ act,
+                                                        const uint32_t *__restrict__ nbr,
+                                                        const uint8_t *__restrict__ nbr_cnt,
+                                                        const uint32_t *__restrict__ lvl_count, uint32_t l)
+{
+    __shared__ float4 dtab[27];
+    fill_dtab(dtab, sc.q);
+    __syncthreads();
+    const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
+    const uint32_t cnt_prev = DENSE ? sc.n : lvl_count[l - 1];
+    const size_t n = sc.n;
+    // grid-stride: at any moment the whole grid works on one compact window of
+    // the (cell-sorted) work list, which keeps the gathers' working set in L2
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_prev; t += gridDim.x * blockDim.x) {
+        const uint32_t p = DENSE ? t : act[t];
+        const float4 ai = A[p];
+        if (!DENSE && t >= cnt_l) {
+            B[p] = make_float4(ai.x, ai.y, ai.z, B[p].w);
+            continue;
+        }
+        const uint32_t nn = nbr_cnt[p];
+        float racc = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, s2 = 0.0f;
+        for_each_neighbor(nbr + p, n, nn, A, [&](uint32_t e, const float4 &aj) {
+            const float4 o = dtab[e >> kSlotBits];
+            const float dx = (ai.x - aj.x) + o.x;
+            const float dy = (ai.y - aj.y) + o.y;
+            const float dz = (ai.z - aj.z) + o.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2) {
+                const float u = sc.h2 - r2;
+                racc += u * u * u;
+                if (r2 > 0.0f) {
+                    const float ir = rsqrtf(r2);
+                    const float hr = sc.h - r2 * ir;
+                    const float gw = hr * hr * ir;  // |grad W| / (45/(pi h^6)) / r
+                    gx += gw * dx;
+                    gy += gw * dy;
+                    gz += gw * dz;
+                    s2 += gw * gw * r2;
+                }
+            }
+        });
+        const float rho = sc.mass_poly6 * (sc.h6 + racc);
+        const float C = rho * sc.inv_rho0 - 1.0f;
+        const float denom = sc.c_lam * (gx * gx + gy * gy + gz * gz + s2) + sc.eps;
+        const float lam = -C / denom;
+        B[p] = make_float4(ai.x, ai.y, ai.z, lam);
+        rho_out[p] = rho;
+    }
+}
+
+// ------------------------------------------- a9: position correction pass
+// Iteration l, threads over P_l: Eq. 7 with the tensile term from B, box
+// contact, Jacobi update written to A.
+
+template <int NPOW>
+__device__ __forceinline__ float powi(float x, uint32_t n)
+{
+    if (NPOW == 4) {
+        float x2 = x * x;
+        return x2 * x2;
+    }
+    float r = 1.0f;
+    for (uint32_t e = 0; e < n; ++e)
+        r *= x;
+    return r;
+}
+
+template <bool DENSE, int NPOW>
+__global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) deltap_kernel(StepConst sc, const float4 *__restrict__ B,
+                                                        float4 *__restrict__ A, const uint32_t *__restrict__ act,
+                                                        const uint32_t *__restrict__ nbr,
+                                                        const uint8_t *__restrict__ nbr_cnt,
+                                                        const uint32_t *__restrict__ cell_s,
+                                                        const uint32_t *__restrict__ lvl_count,
+                                                        const DynParams *__restrict__ dyn, uint32_t l)
+{
+    __shared__ float4 dtab[27];
+    fill_dtab(dtab, sc.q);
+    __syncthreads();
+    const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
+    const size_t n = sc.n;
+    const float blo0 = dyn->box_lo[0], blo1 = dyn->box_lo[1], blo2 = dyn->box_lo[2];
+    const float bhi0 = dyn->box_hi[0], bhi1 = dyn->box_hi[1], bhi2 = dyn->box_hi[2];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_l; t += gridDim.x * blockDim.x) {
+        const uint32_t p = DENSE ? t : act[t];
+        const float4 bi = B[p];
+        const uint32_t nn = nbr_cnt[p];
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        for_each_neighbor(nbr + p, n, nn, B, [&](uint32_t e, const float4 &bj) {
+            const float4 o = dtab[e >> kSlotBits];
+            const float dx = (bi.x - bj.x) + o.x;
+            const float dy = (bi.y - bj.y) + o.y;
+            const float dz = (bi.z - bj.z) + o.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2 && r2 > 0.0f) {
+                const float ir = rsqrtf(r2);
+                const float hr = sc.h - r2 * ir;
+                const float gw = hr * hr * ir;
+                const float u = (sc.h2 - r2) * sc.inv_wdq;  // W(r) / W(dq) = u^3
+                const float scorr = sc.neg_k * powi<NPOW>(u * u * u, sc.scorr_n);
+                const float f = (bi.w + bj.w + scorr) * gw;
+                ax += f * dx;
+                ay += f * dy;
+                az += f * dz;
+            }
+        });
+        // new position, clamped to the box expressed relative to the cell origin
+        const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
+        float px = bi.x + sc.c_dp * ax;
+        float py = bi.y + sc.c_dp * ay;
+        float pz = bi.z + sc.c_dp * az;
+        px = fminf(fmaxf(px, blo0 - og.x), bhi0 - og.x);
+        py = fminf(fmaxf(py, blo1 - og.y), bhi1 - og.y);
+        pz = fminf(fmaxf(pz, blo2 - og.z), bhi2 - og.z);
+        A[p] = make_float4(px, py, pz, bi.w);
+    }
+}
+
+// ------------------------------------------ a10: velocity, XSPH, commit
+
+__global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers b)
+{
+    __shared__ float4 dtab[27];
+    fill_dtab(dtab, sc.q);
+    __syncthreads();
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sc.n)
+        return;
+    const size_t n = sc.n;
+    const float4 af = b.recA[p];
+    const float4 x0 = b.xt[p];
+    const float vx = (af.x - x0.x) * sc.inv_dt;
+    const float vy = (af.y - x0.y) * sc.inv_dt;
+    const float vz = (af.z - x0.z) * sc.inv_dt;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    const uint32_t nn = b.nbr_cnt[p];
+    const uint32_t *e_ptr = b.nbr + p;
+    for (uint32_t k = 0; k < nn; k += kUnroll) {
+        uint32_t e[kUnroll];
+        float4 aj[kUnroll], xj[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            e[u] = (k + u < nn) ? __ldcs(e_ptr + (size_t)(k + u) * n) : kNoEntry;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const bool ok = e[u] != kNoEntry;
+            aj[u] = ok ? __ldg(&b.recA[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            xj[u] = ok ? __ldg(&b.xt[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (e[u] == kNoEntry)
+                continue;
+            const float4 o = dtab[e[u] >> kSlotBits];
+            const float dx = (af.x - aj[u].x) + o.x;
+            const float dy = (af.y - aj[u].y) + o.y;
+            const float dz = (af.z - aj[u].z) + o.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2) {
+                const float w = sc.h2 - r2;
+                const float W = w * w * w;
+                sx += ((aj[u].x - xj[u].x) * sc.inv_dt - vx) * W;
+                sy += ((aj[u].y - xj[u].y) * sc.inv_dt - vy) * W;
+                sz += ((aj[u].z - xj[u].z) * sc.inv_dt - vz) * W;
+            }
+        }
+    }
+    const float3 og = cell_origin(unpack_cell(b.cell_s[p]), sc);
+    const DynParams *dyn = b.dyn;
+    float px = fminf(fmaxf(og.x + af.x, dyn->box_lo[0]), dyn->box_hi[0]);
+    float py = fminf(fmaxf(og.y + af.y, dyn->box_lo[1]), dyn->box_hi[1]);
+    float pz = fminf(fmaxf(og.z + af.z, dyn->box_lo[2]), dyn->box_hi[2]);
+    b.state_x[p] = make_float4(px, py, pz, 0.0f);
+    b.state_v[p] = make_float4(vx + sc.c_xsph * sx, vy + sc.c_xsph * sy, vz + sc.c_xsph * sz, 0.0f);
+    b.state_id[p] = b.id_s[p];
+}
+
 // ------------------------------------------------------- readback helpers
 
 __global__ void __launch_bounds__(kBlock) unpermute_kernel(StepConst sc, Buffers b, uint32_t what)
@@ -214,6 +736,60 @@ __global__ void __launch_bounds__(kBlock) unpermute_kernel(StepConst sc, Buffers
         b.stage_u8[id] = b.lvl_s[p];
     } else {
         b.stage_f[id] = b.rho[p];
+    }
+}
+
+// density diagnostic (Fig. 9): rho at the current positions, FP64 partial sums
+__global__ void __launch_bounds__(kBlock) density_kernel(StepConst sc, Buffers b, double rho0)
+{
+    __shared__ double sh[4][kBlock / 32];
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    double ea = 0.0, em = 0.0, es = 0.0, ep = 0.0;
+    if (p < sc.n) {
+        const size_t n = sc.n;
+        const float4 xi = b.xs32[p];
+        float racc = 0.0f;
+        const uint32_t nn = b.nbr_cnt[p];
+        for (uint32_t k = 0; k < nn; ++k) {
+            const uint32_t j = b.nbr[(size_t)k * n + p] & kSlotMask;
+            const float4 xj = b.xs32[j];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < sc.h2) {
+                const float u = sc.h2 - r2;
+                racc += u * u * u;
+            }
+        }
+        const double e = (double)(sc.mass_poly6 * (sc.h6 + racc)) / rho0 - 1.0;
+        ea = fabs(e);
+        em = fabs(e);
+        es = e;
+        ep = e > 0.0 ? e : 0.0;
+    }
+    ea = warp_sum(ea);
+    es = warp_sum(es);
+    ep = warp_sum(ep);
+    em = warp_max(em);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][w] = ea;
+        sh[1][w] = em;
+        sh[2][w] = es;
+        sh[3][w] = ep;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, m = 0, s = 0, q = 0;
+        for (int v = 0; v < kBlock / 32; ++v) {
+            a += sh[0][v];
+            m = fmax(m, sh[1][v]);
+            s += sh[2][v];
+            q += sh[3][v];
+        }
+        b.partials[4 * (size_t)blockIdx.x + 0] = a;
+        b.partials[4 * (size_t)blockIdx.x + 1] = m;
+        b.partials[4 * (size_t)blockIdx.x + 2] = s;
+        b.partials[4 * (size_t)blockIdx.x + 3] = q;
     }
 }
 
@@ -259,12 +835,8 @@ __global__ void __launch_bounds__(kBlock) debug_lambda_kernel(StepConst sc, Buff
 
 inline unsigned blocks_for(uint32_t n, int bs) { return (unsigned)((n + (uint32_t)bs - 1) / (uint32_t)bs); }
 
-}  // namespace
-
-// ------------------------------------------------------------- launchers
-
-// Resident blocks per SM of a kernel launched with `block` threads (cached per function).
-int occupancy(const void *fn, int block)
+// Resident blocks of kBlock threads per SM for a kernel (cached per function).
+int occupancy(const void *fn)
 {
     static const void *keys[16];
     static int vals[16];
@@ -272,7 +844,7 @@ int occupancy(const void *fn, int block)
         if (keys[k] == fn)
             return vals[k];
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 4;
     }
@@ -285,6 +857,9 @@ int occupancy(const void *fn, int block)
     return occ;
 }
 
+}  // namespace
+
+// ------------------------------------------------------------- launchers
 
 cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
@@ -322,6 +897,65 @@ cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s
     return cudaGetLastError();
 }
 
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        neighbors_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    level_hist_kernel<<<sc.level_tiles, kLevelTile, 2 * sc.K * sizeof(uint32_t), s>>>(sc, b);
+    level_scan_kernel<<<1, 1024, 0, s>>>(sc, b);
+    level_scatter_kernel<<<sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s>>>(sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms)
+{
+    const int grid = sms * occupancy(dense ? (const void *)lambda_kernel<true> : (const void *)lambda_kernel<false>);
+    if (!sc.n)
+        return cudaGetLastError();
+    if (dense)
+        lambda_kernel<true><<<grid, kBlock, 0, s>>>(sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_count, l);
+    else
+        lambda_kernel<false><<<grid, kBlock, 0, s>>>(sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_count, l);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    const bool p4 = sc.scorr_n == 4;
+    const void *fn = dense ? (p4 ? (const void *)deltap_kernel<true, 4> : (const void *)deltap_kernel<true, -1>)
+                           : (p4 ? (const void *)deltap_kernel<false, 4> : (const void *)deltap_kernel<false, -1>);
+    const int grid = sms * occupancy(fn);
+#define APBF_DP(D, P)                                                                                          \
+    deltap_kernel<D, P><<<grid, kBlock, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s, b.lvl_count, \
+                                                b.dyn, l)
+    if (dense && p4)
+        APBF_DP(true, 4);
+    else if (dense)
+        APBF_DP(true, -1);
+    else if (p4)
+        APBF_DP(false, 4);
+    else
+        APBF_DP(false, -1);
+#undef APBF_DP
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        finalize_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what)
 {
     if (sc.n)
@@ -329,9 +963,13 @@ cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_density_final(const StepConst &sc, const Buffers &b, cudaStream_t s, int nblocks)
+cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks)
 {
-    density_final_kernel<<<1, 32, 0, s>>>(b.partials, nblocks, sc.n, b.dstats);
+    int nb = (int)blocks_for(sc.n, kBlock);
+    *nblocks = nb;
+    if (sc.n)
+        density_kernel<<<nb, kBlock, 0, s>>>(sc, b, (double)sc.rho0);
+    density_final_kernel<<<1, 32, 0, s>>>(b.partials, nb, sc.n, b.dstats);
     return cudaGetLastError();
 }
 
@@ -349,5 +987,6 @@ cudaError_t launch_debug_lambda(const StepConst &sc, const Buffers &b, const flo
     return cudaGetLastError();
 }
 
+int iteration_grid(int sms) { return sms; }
 
 }  // namespace apbf

@@ -82,20 +82,12 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
         off = np.stack([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], 1)
         assert np.array_equal(cells[got] - cells[q], off), q
     lvl = st.level_presort[st.order]
-    # a7: |P_l| and the tiles (16 cells of a grid row) ordered by their highest level
-    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
-    lc = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_COUNT).astype(np.int64)
-    assert np.array_equal(lc, st.active_count)
-    tpr = (int(dims[0]) + apbf.TILE_X - 1) // apbf.TILE_X
-    ntiles = tpr * int(dims[1]) * int(dims[2])
-    tile_of = (cells[:, 2] * dims[1] + cells[:, 1]) * tpr + cells[:, 0] // apbf.TILE_X
-    tl = np.zeros(ntiles, np.int64)
-    np.maximum.at(tl, tile_of, lvl)
-    assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_TILE_LEVEL).astype(np.int64), tl)
-    assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_ACTIVE).astype(np.int64),
-                          np.lexsort((np.arange(ntiles), -tl)))
-    tc = apbf.apbf_debug_read(scene, apbf.APBF_DBG_TILE_COUNT).astype(np.int64)
-    assert np.array_equal(tc, [(tl >= l).sum() for l in range(n_max + 2)])
+    if cfg.lod_mode == scenes.LOD_DTC and p.n_max > p.n_min:
+        apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
+        lc = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_COUNT).astype(np.int64)
+        assert np.array_equal(lc, st.active_count)
+        act = apbf.apbf_debug_read(scene, apbf.APBF_DBG_ACTIVE).astype(np.int64)
+        assert np.array_equal(act, np.lexsort((np.arange(n), -lvl)))
     # a8-a9 per iteration
     h = float(p.h)
     for l in range(1, (n_max if iters else 1) + 1):
