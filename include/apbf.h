@@ -183,6 +183,45 @@ APBF_API const char *apbf_last_error(const apbf_scene *scene);
 /* Release the scene and the memory it allocated (NULL-safe). Synchronises. */
 APBF_API void apbf_destroy_scene(apbf_scene *scene);
 
+/* ------------------------------------------- allocation-free diagnostic */
+
+/* Limits of apbf_density_stats_static's built-in scratch memory. */
+#define APBF_STATIC_MAX_PARTICLES 65536u
+#define APBF_STATIC_MAX_CELLS 262144u
+
+/*
+ * The density-error statistics of apbf_density_stats, computed for positions
+ * the caller already holds in device memory, without allocating any device
+ * memory. (The paper has no counterpart: this is a convenience of the
+ * library.) It is meant for callers that must not allocate GPU memory while
+ * they run -- a game or renderer frame loop where cudaMalloc/cudaFree would
+ * synchronise the device and stall the frame, a plug-in confined to its host
+ * application's memory budget, or code with no allocator to hand to the
+ * library.
+ *
+ *  pos        device, 3n floats (x, y, z per particle, any particle order).
+ *  n          particles, at most APBF_STATIC_MAX_PARTICLES.
+ *  h, mass, rho0, grid_lo, grid_hi (host, 3 floats each)
+ *             as in apbf_scene_desc; the grid of cells of size h must have at
+ *             most APBF_STATIC_MAX_CELLS cells. Positions outside the grid are
+ *             counted in its boundary cells.
+ *  stats      device, 4 doubles: {mean |rho/rho0-1|, max |rho/rho0-1|,
+ *             mean (rho/rho0-1), mean max(0, rho/rho0-1)}, written
+ *             asynchronously on cuda_stream (NULL = the legacy default stream).
+ * Larger n or grids return APBF_ERR_INVALID_ARG with a message in
+ * apbf_last_error(NULL). The call makes no cudaMalloc, cudaFree or other
+ * allocating call: all scratch (about 3.9 MB) is one static device array that
+ * every GPU loading this library keeps until the process exits. The first call
+ * on each device looks up that array's device address; make that first call
+ * before capturing any stream. All calls share the one array and it keeps the
+ * previous call's contents (the call clears what must start at zero), so calls
+ * that overlap on the GPU -- on different streams, or from several host
+ * threads -- race and must be serialised by the caller.
+ */
+APBF_API apbf_status apbf_density_stats_static(const float *pos, uint32_t n, float h, float mass, float rho0,
+                                               const float grid_lo[3], const float grid_hi[3], double *stats,
+                                               void *cuda_stream);
+
 /* ---------------------------------------------------------------- timing */
 
 /* Stage identifiers (timing and debug). */

@@ -75,8 +75,10 @@ EXPORTS = [
     "apbf_status_string", "apbf_rest_density", "apbf_scene_bytes", "apbf_create_scene", "apbf_set_camera",
     "apbf_set_box", "apbf_step", "apbf_read_state", "apbf_density_stats", "apbf_get_step_info", "apbf_sync",
     "apbf_last_error", "apbf_destroy_scene", "apbf_set_timing", "apbf_timing_report", "apbf_debug_step_to",
-    "apbf_debug_read", "apbf_debug_dims",
+    "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static",
 ]
+APBF_STATIC_MAX_PARTICLES = 65536
+APBF_STATIC_MAX_CELLS = 262144
 
 _lib = None
 
@@ -124,6 +126,8 @@ def lib():
         L.apbf_debug_step_to.argtypes = [V, C.c_uint32, C.c_uint32]
         L.apbf_debug_read.argtypes = [V, C.c_uint32, V, C.c_size_t]
         L.apbf_debug_dims.argtypes = [V, P(C.c_int32), P(C.c_uint32), P(C.c_uint32)]
+        L.apbf_density_stats_static.argtypes = [V, C.c_uint32, C.c_float, C.c_float, C.c_float, P(C.c_float),
+                                                P(C.c_float), V, V]
         for f in EXPORTS:
             if f not in ("apbf_status_string", "apbf_last_error", "apbf_destroy_scene"):
                 getattr(L, f).restype = C.c_int
@@ -366,3 +370,25 @@ def apbf_debug_read(scene: Scene, field: int) -> np.ndarray:
     _check(lib().apbf_debug_read(scene.handle, field, C.c_void_p(a.ctypes.data if a.size else 0), a.nbytes),
            "apbf_debug_read", scene)
     return a
+
+
+def apbf_density_stats_static(pos_dev, n: int, h: float, mass: float, rho0: float, grid_lo, grid_hi, stats_dev,
+                              stream=None):
+    """Allocation-free density statistics of device positions (see the C
+    header). pos_dev and stats_dev are device pointers (ints) or CUDA tensors
+    (float32 of 3n values, float64 of 4 values); stream as in apbf_create_scene."""
+    def ptr(x):
+        return x.data_ptr() if hasattr(x, "data_ptr") else int(x)
+    if stream is None:
+        try:
+            import torch
+            stream_ptr = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        except Exception:
+            stream_ptr = 0
+    else:
+        stream_ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    lo = (C.c_float * 3)(*[float(v) for v in grid_lo])
+    hi = (C.c_float * 3)(*[float(v) for v in grid_hi])
+    _check(lib().apbf_density_stats_static(C.c_void_p(ptr(pos_dev)), n, h, mass, rho0, lo, hi,
+                                           C.c_void_p(ptr(stats_dev)), C.c_void_p(stream_ptr)),
+           "apbf_density_stats_static")

@@ -377,6 +377,11 @@ apbf_status build_graph(apbf_scene *s)
 
 }  // namespace
 
+namespace apbf {
+// Message returned by apbf_last_error(NULL) for calls that have no scene.
+void set_last_error_message(const std::string &m) { g_create_error = m; }
+}  // namespace apbf
+
 extern "C" {
 
 APBF_API const char *apbf_status_string(apbf_status st)
