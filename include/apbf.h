@@ -144,6 +144,27 @@ APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes
 APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *desc, void *cuda_stream, void *device_arena,
                                        size_t arena_bytes, apbf_scene **out);
 
+/*
+ * Batches: several independent scenes stepped together, each stage of the
+ * step one launch over all of them (their particles and grids concatenated).
+ * A scene inside a batch evolves bit-identically to the same scene created
+ * alone. Every scene's description must agree with scene 0 in everything but
+ * n, pos, vel, grid_lo/hi and box_lo/hi (APBF_ERR_INVALID_ARG otherwise);
+ * count <= 65535 and the total particle count < 2^27.
+ *  descs  host, count descriptions (copied, as for apbf_create_scene).
+ * On a batch, apbf_set_camera / apbf_set_box set every scene (the _at forms
+ * set one); apbf_read_state returns all particles, scene after scene, each
+ * scene's particles in its own id order; apbf_density_stats and
+ * apbf_get_step_info aggregate over all scenes (d_range: scene 0's).
+ * apbf_create_scene(d, ...) is apbf_create_batch(d, 1, ...).
+ */
+APBF_API apbf_status apbf_batch_bytes(const apbf_scene_desc *descs, uint32_t count, size_t *bytes);
+APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t count, void *cuda_stream,
+                                       void *device_arena, size_t arena_bytes, apbf_scene **out);
+APBF_API apbf_status apbf_set_camera_at(apbf_scene *scene, uint32_t index, const float eye[3], const float dir[3],
+                                        float d_near, float d_far);
+APBF_API apbf_status apbf_set_box_at(apbf_scene *scene, uint32_t index, const float lo[3], const float hi[3]);
+
 /* Camera of the DTC model (Sec. 4.1), used from the next apbf_step on.
  *  eye, dir  host, 3 floats; dir is stored for view-dependent models and must be finite.
  *  d_near < d_far: user-defined distance range; otherwise the range is the
@@ -268,7 +289,7 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint3
 #define APBF_DBG_LAMBDA 11u       /* float[n] lambda after the stage, sorted */
 #define APBF_DBG_RHO 12u          /* float[n] density of the last lambda pass, sorted */
 #define APBF_DBG_XSTAR 13u        /* float4[n] current x* (absolute FP32), sorted */
-#define APBF_DBG_DRANGE 14u       /* float[2] LOD distance range */
+#define APBF_DBG_DRANGE 14u       /* float[2*scenes] LOD distance ranges: the minima, then the maxima */
 
 /* Copy a debug field (see APBF_DBG_*) to host memory of `bytes` bytes
  * (must equal the field's size). Synchronises. */

@@ -75,7 +75,8 @@ EXPORTS = [
     "apbf_status_string", "apbf_rest_density", "apbf_scene_bytes", "apbf_create_scene", "apbf_set_camera",
     "apbf_set_box", "apbf_step", "apbf_read_state", "apbf_density_stats", "apbf_get_step_info", "apbf_sync",
     "apbf_last_error", "apbf_destroy_scene", "apbf_set_timing", "apbf_timing_report", "apbf_debug_step_to",
-    "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static",
+    "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
+    "apbf_set_camera_at", "apbf_set_box_at",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -126,6 +127,10 @@ def lib():
         L.apbf_debug_step_to.argtypes = [V, C.c_uint32, C.c_uint32]
         L.apbf_debug_read.argtypes = [V, C.c_uint32, V, C.c_size_t]
         L.apbf_debug_dims.argtypes = [V, P(C.c_int32), P(C.c_uint32), P(C.c_uint32)]
+        L.apbf_batch_bytes.argtypes = [P(apbf_scene_desc), C.c_uint32, P(C.c_size_t)]
+        L.apbf_create_batch.argtypes = [P(apbf_scene_desc), C.c_uint32, V, V, C.c_size_t, P(V)]
+        L.apbf_set_camera_at.argtypes = [V, C.c_uint32, P(C.c_float), P(C.c_float), C.c_float, C.c_float]
+        L.apbf_set_box_at.argtypes = [V, C.c_uint32, P(C.c_float), P(C.c_float)]
         L.apbf_density_stats_static.argtypes = [V, C.c_uint32, C.c_float, C.c_float, C.c_float, P(C.c_float),
                                                 P(C.c_float), V, V]
         for f in EXPORTS:
@@ -146,13 +151,18 @@ def _fptr(a):
 
 
 class Scene:
-    """Handle of a created scene; keeps the arena and inputs alive."""
+    """Handle of a created scene or batch; keeps the arena and inputs alive."""
 
-    def __init__(self, handle, n, desc, keep):
+    def __init__(self, handle, n, desc, keep, counts=None):
         self.handle = handle
         self.n = n
         self.desc = desc
         self._keep = keep
+        self.counts = [n] if counts is None else list(counts)  # particles per scene
+
+    @property
+    def scenes(self) -> int:
+        return len(self.counts)
 
     def __del__(self):
         try:
@@ -212,6 +222,77 @@ def apbf_scene_bytes(desc) -> int:
     out = C.c_size_t()
     _check(lib().apbf_scene_bytes(C.byref(d), C.byref(out)), "apbf_scene_bytes")
     return out.value
+
+
+def _stream_and_arena(nbytes_fn, stream, device_arena):
+    torch = None
+    try:
+        import torch as _torch
+        torch = _torch if _torch.cuda.is_available() else None
+    except Exception:
+        torch = None
+    if stream is None:
+        stream_ptr = torch.cuda.current_stream().cuda_stream if torch is not None else 0
+    elif hasattr(stream, "cuda_stream"):
+        stream_ptr = stream.cuda_stream
+    else:
+        stream_ptr = int(stream)
+    arena_ptr, arena_bytes, arena_keep = None, 0, None
+    if isinstance(device_arena, str) and device_arena == "torch":
+        if torch is not None:
+            nbytes = nbytes_fn()
+            arena_keep = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            arena_ptr = (arena_keep.data_ptr() + 255) // 256 * 256
+            arena_bytes = nbytes
+    elif device_arena is None:
+        pass
+    elif hasattr(device_arena, "data_ptr"):
+        arena_keep = device_arena
+        arena_ptr = device_arena.data_ptr()
+        arena_bytes = device_arena.numel() * device_arena.element_size()
+    else:
+        arena_ptr, arena_bytes = int(device_arena[0]), int(device_arena[1])
+    return stream_ptr, arena_ptr, arena_bytes, arena_keep
+
+
+def apbf_batch_bytes(descs) -> int:
+    arr, _ = _desc_array(descs)
+    out = C.c_size_t()
+    _check(lib().apbf_batch_bytes(arr, len(arr), C.byref(out)), "apbf_batch_bytes")
+    return out.value
+
+
+def _desc_array(descs):
+    items = [d[0] if isinstance(d, tuple) else d for d in descs]
+    keep = [d[1] for d in descs if isinstance(d, tuple)]
+    arr = (apbf_scene_desc * len(items))(*items)
+    return arr, keep
+
+
+def apbf_create_batch(descs, stream=None, device_arena="torch") -> Scene:
+    """descs: a list of apbf_scene_desc (or make_desc pairs); other arguments
+    as in apbf_create_scene."""
+    arr, keep = _desc_array(descs)
+    stream_ptr, arena_ptr, arena_bytes, arena_keep = _stream_and_arena(lambda: apbf_batch_bytes(descs), stream,
+                                                                       device_arena)
+    h = C.c_void_p()
+    _check(lib().apbf_create_batch(arr, len(arr), C.c_void_p(stream_ptr), C.c_void_p(arena_ptr), arena_bytes,
+                                   C.byref(h)), "apbf_create_batch")
+    counts = [int(d.n) for d in arr]
+    return Scene(h, sum(counts), arr[0], (keep, arena_keep, arr), counts)
+
+
+def apbf_set_camera_at(scene: Scene, index: int, eye, direction=(1.0, 0.0, 0.0), d_near: float = 0.0,
+                       d_far: float = 0.0):
+    e = (C.c_float * 3)(*[float(v) for v in eye])
+    d = (C.c_float * 3)(*[float(v) for v in direction])
+    _check(lib().apbf_set_camera_at(scene.handle, index, e, d, d_near, d_far), "apbf_set_camera_at", scene)
+
+
+def apbf_set_box_at(scene: Scene, index: int, lo, hi):
+    a = (C.c_float * 3)(*[float(v) for v in lo])
+    b = (C.c_float * 3)(*[float(v) for v in hi])
+    _check(lib().apbf_set_box_at(scene.handle, index, a, b), "apbf_set_box_at", scene)
 
 
 def apbf_create_scene(desc, stream=None, device_arena="torch") -> Scene:
@@ -363,7 +444,7 @@ def apbf_debug_read(scene: Scene, field: int) -> np.ndarray:
         APBF_DBG_NBR: ((mx, n), np.uint32), APBF_DBG_ACTIVE: ((n,), np.uint32),
         APBF_DBG_LEVEL_COUNT: ((n_max + 2,), np.uint32), APBF_DBG_LAMBDA: ((n,), np.float32),
         APBF_DBG_RHO: ((n,), np.float32), APBF_DBG_XSTAR: ((n, 4), np.float32),
-        APBF_DBG_DRANGE: ((2,), np.float32),
+        APBF_DBG_DRANGE: ((2 * scene.scenes,), np.float32),
     }
     shape, dt = shapes[field]
     a = np.empty(shape, dt)

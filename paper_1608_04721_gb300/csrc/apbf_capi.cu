@@ -155,6 +155,65 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.max_nbr = d->max_neighbors ? d->max_neighbors : kDefaultMaxNeighbors;
     sc.level_tiles = (d->n + kLevelTile - 1) / kLevelTile;
     sc.rho0 = d->rho0;
+    sc.scenes = 1;
+    st = APBF_OK;
+    return "";
+}
+
+// Validation and derived constants of a batch: every scene is validated on
+// its own; the physics (everything but particles, grid and box) must match
+// scene 0; the scenes' particles and cells are concatenated.
+std::string derive_batch(const apbf_scene_desc *descs, uint32_t count, StepConst &sc, std::vector<SceneGeom> &geo,
+                         apbf_status &st)
+{
+    st = APBF_ERR_INVALID_ARG;
+    if (!descs || count == 0)
+        return "descs is NULL or count is 0";
+    if (count > 65535)
+        return "at most 65535 scenes per batch";
+    geo.assign(count, SceneGeom{});
+    uint64_t n_total = 0, c_total = 0;
+    for (uint32_t k = 0; k < count; ++k) {
+        StepConst sk;
+        std::string m = derive(descs + k, sk, st);
+        if (st != APBF_OK)
+            return "scene " + std::to_string(k) + ": " + m;
+        st = APBF_ERR_INVALID_ARG;
+        if (k == 0) {
+            sc = sk;
+        } else {
+            const apbf_scene_desc &a = descs[0], &d = descs[k];
+            bool same = a.h == d.h && a.dt == d.dt && a.mass == d.mass && a.rho0 == d.rho0 && a.eps == d.eps &&
+                        a.scorr_k == d.scorr_k && a.scorr_dq == d.scorr_dq && a.scorr_n == d.scorr_n &&
+                        a.xsph_c == d.xsph_c && a.n_min == d.n_min && a.n_max == d.n_max && a.lod_mode == d.lod_mode &&
+                        a.stabil_s == d.stabil_s && a.max_neighbors == d.max_neighbors && a.flags == d.flags;
+            for (int ax = 0; ax < 3; ++ax)
+                same = same && a.gravity[ax] == d.gravity[ax];
+            if (!same)
+                return "scene " + std::to_string(k) + " differs from scene 0 in a physics parameter";
+        }
+        SceneGeom &g = geo[k];
+        for (int ax = 0; ax < 3; ++ax) {
+            g.glo[ax] = sk.glo[ax];
+            g.m[ax] = sk.m[ax];
+        }
+        g.nx = sk.nx;
+        g.ny = sk.ny;
+        g.nz = sk.nz;
+        g.cell_base = (uint32_t)c_total;
+        g.p0 = (uint32_t)n_total;
+        g.n = sk.n;
+        n_total += sk.n;
+        c_total += sk.ncell;
+    }
+    if (n_total >= (1ull << kSlotBits))
+        return "the batch holds 2^27 particles or more";
+    if (c_total >= (1ull << 31))
+        return "the batch's grids hold too many cells";
+    sc.n = (uint32_t)n_total;
+    sc.ncell = (uint32_t)c_total;
+    sc.scenes = count;
+    sc.level_tiles = (sc.n + kLevelTile - 1) / kLevelTile;
     st = APBF_OK;
     return "";
 }
@@ -207,9 +266,11 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.lvl_off = (uint32_t *)P(4 * lvl_e);
     b.lvl_count = (uint32_t *)P(4 * 258);
     b.counters = (unsigned long long *)P(8 * kCounterSlots);
-    b.drange = (uint32_t *)P(8);
+    b.drange = (uint32_t *)P(8 * (size_t)sc.scenes);
     b.err = (uint32_t *)P(4);
-    b.dyn = (DynParams *)P(sizeof(DynParams));
+    b.dyn = (DynParams *)P(sizeof(DynParams) * (size_t)sc.scenes);
+    b.geo = (const SceneGeom *)P(sizeof(SceneGeom) * (size_t)sc.scenes);
+    b.sid = (const uint16_t *)P(2 * n);
     b.stage_f = (float *)P(12 * n);
     b.stage_u8 = (uint8_t *)P(n);
     b.dbg4 = (float4 *)P(16 * n);
@@ -260,8 +321,8 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
     cudaError_t e;
     if (dtc) {  // always captured; unused when the camera gives a distance range
         e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
-            cudaMemsetAsync(b.drange, 0x7f, 4, st);  // 0x7f7f7f7f = 3.4e38f
-            cudaMemsetAsync(b.drange + 1, 0, 4, st);
+            cudaMemsetAsync(b.drange, 0x7f, 4 * (size_t)sc.scenes, st);  // 0x7f7f7f7f = 3.4e38f
+            cudaMemsetAsync(b.drange + sc.scenes, 0, 4 * (size_t)sc.scenes, st);
             return launch_lod_range(sc, b, st);
         });
         if (e != cudaSuccess)
@@ -327,8 +388,10 @@ apbf_status upload_dyn(apbf_scene *s)
     int k = s->dyn_slot;
     s->dyn_slot = (s->dyn_slot + 1) % 16;
     APBF_CUDA(s, cudaEventSynchronize(s->dyn_ev[k]));  // the previous copy out of this slot is done
-    s->dyn_pinned[k] = s->dyn;
-    APBF_CUDA(s, cudaMemcpyAsync(s->b.dyn, &s->dyn_pinned[k], sizeof(DynParams), cudaMemcpyHostToDevice, s->stream));
+    const size_t cnt = s->dyn.size();
+    std::memcpy(s->dyn_pinned + k * cnt, s->dyn.data(), sizeof(DynParams) * cnt);
+    APBF_CUDA(s, cudaMemcpyAsync(s->b.dyn, s->dyn_pinned + k * cnt, sizeof(DynParams) * cnt, cudaMemcpyHostToDevice,
+                                 s->stream));
     APBF_CUDA(s, cudaEventRecord(s->dyn_ev[k], s->stream));
     s->dyn_dirty = false;
     return APBF_OK;
@@ -420,13 +483,14 @@ APBF_API apbf_status apbf_rest_density(float h, float mass, float spacing, doubl
     return APBF_OK;
 }
 
-APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes)
+APBF_API apbf_status apbf_batch_bytes(const apbf_scene_desc *descs, uint32_t count, size_t *bytes)
 {
     if (!bytes)
-        return APBF_ERR_INVALID_ARG;
+        return fail(nullptr, APBF_ERR_INVALID_ARG, "bytes is NULL");
     StepConst sc;
+    std::vector<SceneGeom> geo;
     apbf_status st;
-    std::string m = derive(desc, sc, st);
+    std::string m = derive_batch(descs, count, sc, geo, st);
     if (st != APBF_OK)
         return fail(nullptr, st, m);
     Buffers b;
@@ -434,24 +498,35 @@ APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes
     return APBF_OK;
 }
 
-APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stream, void *device_arena,
-                                       size_t arena_bytes, apbf_scene **out)
+APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes)
+{
+    return apbf_batch_bytes(desc, 1, bytes);
+}
+
+APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t count, void *cuda_stream,
+                                       void *device_arena, size_t arena_bytes, apbf_scene **out)
 {
     if (!out)
         return fail(nullptr, APBF_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     StepConst sc;
+    std::vector<SceneGeom> geo;
     apbf_status st;
-    std::string m = derive(d, sc, st);
+    std::string m = derive_batch(descs, count, sc, geo, st);
     if (st != APBF_OK)
         return fail(nullptr, st, m);
-    for (uint32_t i = 0; i < 3 * d->n; ++i)
-        if (!std::isfinite(d->pos[i]) || (d->vel && !std::isfinite(d->vel[i])))
-            return fail(nullptr, APBF_ERR_INVALID_ARG, "positions and velocities must be finite");
-    for (uint32_t i = 0; i < d->n; ++i)
-        for (int a = 0; a < 3; ++a)
-            if (!(d->pos[3 * i + a] >= d->grid_lo[a] && d->pos[3 * i + a] <= d->grid_hi[a]))
-                return fail(nullptr, APBF_ERR_INVALID_ARG, "particle " + std::to_string(i) + " lies outside the grid");
+    for (uint32_t k = 0; k < count; ++k) {
+        const apbf_scene_desc *d = descs + k;
+        const std::string who = count > 1 ? "scene " + std::to_string(k) + ": " : "";
+        for (uint32_t i = 0; i < 3 * d->n; ++i)
+            if (!std::isfinite(d->pos[i]) || (d->vel && !std::isfinite(d->vel[i])))
+                return fail(nullptr, APBF_ERR_INVALID_ARG, who + "positions and velocities must be finite");
+        for (uint32_t i = 0; i < d->n; ++i)
+            for (int a = 0; a < 3; ++a)
+                if (!(d->pos[3 * i + a] >= d->grid_lo[a] && d->pos[3 * i + a] <= d->grid_hi[a]))
+                    return fail(nullptr, APBF_ERR_INVALID_ARG,
+                                who + "particle " + std::to_string(i) + " lies outside the grid");
+    }
     if (device_arena && ((uintptr_t)device_arena % kAlign))
         return fail(nullptr, APBF_ERR_INVALID_ARG, "device_arena must be 256-byte aligned");
 
@@ -459,9 +534,17 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
     if (!s)
         return fail(nullptr, APBF_ERR_OUT_OF_MEMORY, "host allocation failed");
     s->sc = sc;
-    for (int a = 0; a < 3; ++a)
-        s->grid_hi[a] = d->grid_hi[a];
-    s->flags = d->flags;
+    s->geo = geo;
+    s->grid_hi3.resize(3 * (size_t)count);
+    s->dyn.assign(count, DynParams{});
+    for (uint32_t k = 0; k < count; ++k)
+        for (int a = 0; a < 3; ++a) {
+            s->grid_hi3[3 * k + a] = descs[k].grid_hi[a];
+            s->dyn[k].box_lo[a] = descs[k].box_lo[a];
+            s->dyn[k].box_hi[a] = descs[k].box_hi[a];
+            s->dyn[k].auto_range = 1;
+        }
+    s->flags = descs[0].flags;
     s->stream = (cudaStream_t)cuda_stream;
     auto bail = [&](apbf_status code, const std::string &msg) {
         g_create_error = msg;
@@ -475,7 +558,7 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
     size_t need = carve(sc, nullptr, s->b);
     if (device_arena) {
         if (arena_bytes < need)
-            return bail(APBF_ERR_OUT_OF_MEMORY, "device_arena is smaller than apbf_scene_bytes()");
+            return bail(APBF_ERR_OUT_OF_MEMORY, "device_arena is smaller than apbf_batch_bytes()");
         s->arena = device_arena;
         s->arena_bytes = arena_bytes;
     } else {
@@ -493,7 +576,8 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
     const size_t n = sc.n;
 
     if ((e = cudaHostAlloc(&s->pinned_small, 4096, cudaHostAllocDefault)) != cudaSuccess ||
-        (e = cudaHostAlloc((void **)&s->dyn_pinned, 16 * sizeof(DynParams), cudaHostAllocDefault)) != cudaSuccess)
+        (e = cudaHostAlloc((void **)&s->dyn_pinned, 16 * sizeof(DynParams) * (size_t)count, cudaHostAllocDefault)) !=
+            cudaSuccess)
         return bail(APBF_ERR_CUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
     for (int k = 0; k < 16; ++k)
         if ((e = cudaEventCreateWithFlags(&s->dyn_ev[k], cudaEventDisableTiming)) != cudaSuccess)
@@ -501,29 +585,33 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
     if ((e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(APBF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
 
-    // initial state, particle-id order
+    // initial state: the scenes' particles concatenated, each in its id order;
+    // global id = scene's first slot + id within the scene
     std::vector<float4> hx(n ? n : 1), hv(n ? n : 1);
     std::vector<uint32_t> hid(n ? n : 1);
-    for (size_t i = 0; i < n; ++i) {
-        hx[i] = make_float4(d->pos[3 * i], d->pos[3 * i + 1], d->pos[3 * i + 2], 0.0f);
-        hv[i] = d->vel ? make_float4(d->vel[3 * i], d->vel[3 * i + 1], d->vel[3 * i + 2], 0.0f)
-                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        hid[i] = (uint32_t)i;
+    std::vector<uint16_t> hsid(n ? n : 1);
+    for (uint32_t k = 0; k < count; ++k) {
+        const apbf_scene_desc *d = descs + k;
+        for (size_t i = 0; i < d->n; ++i) {
+            const size_t g = geo[k].p0 + i;
+            hx[g] = make_float4(d->pos[3 * i], d->pos[3 * i + 1], d->pos[3 * i + 2], 0.0f);
+            hv[g] = d->vel ? make_float4(d->vel[3 * i], d->vel[3 * i + 1], d->vel[3 * i + 2], 0.0f)
+                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            hid[g] = (uint32_t)g;
+            hsid[g] = (uint16_t)k;
+        }
     }
     std::vector<uint32_t> lc(258, 0u);
     for (uint32_t l = 0; l <= sc.n_max; ++l)
         lc[l] = sc.n;  // every particle is active in every iteration until a partition says otherwise
-    s->dyn = DynParams{};
-    for (int a = 0; a < 3; ++a) {
-        s->dyn.box_lo[a] = d->box_lo[a];
-        s->dyn.box_hi[a] = d->box_hi[a];
-    }
-    s->dyn.auto_range = 1;
     cudaStream_t st0 = s->stream;
     if ((e = cudaMemsetAsync(s->arena, 0, need, st0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b.state_x, hx.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b.state_v, hv.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b.state_id, hid.data(), 4 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void *)b.sid, hsid.data(), 2 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void *)b.geo, geo.data(), sizeof(SceneGeom) * count, cudaMemcpyHostToDevice, st0)) !=
+            cudaSuccess ||
         (e = cudaMemcpyAsync(b.lvl_count, lc.data(), 4 * 258, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st0)) != cudaSuccess)
         return bail(APBF_ERR_CUDA, std::string("initial upload: ") + cudaGetErrorString(e));
@@ -533,38 +621,76 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
     return APBF_OK;
 }
 
-APBF_API apbf_status apbf_set_camera(apbf_scene *s, const float eye[3], const float dir[3], float d_near, float d_far)
+APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stream, void *device_arena,
+                                       size_t arena_bytes, apbf_scene **out)
+{
+    return apbf_create_batch(d, 1, cuda_stream, device_arena, arena_bytes, out);
+}
+
+namespace {
+apbf_status set_camera_range(apbf_scene *s, uint32_t k0, uint32_t k1, const float eye[3], const float dir[3],
+                             float d_near, float d_far)
 {
     apbf_status st = enter(s);
     if (st != APBF_OK)
         return st;
     if (!eye || !dir || !finite3(eye) || !finite3(dir) || !std::isfinite(d_near) || !std::isfinite(d_far))
         return fail(s, APBF_ERR_INVALID_ARG, "camera values must be finite and non-NULL");
-    for (int a = 0; a < 3; ++a)
-        s->dyn.eye[a] = eye[a];
-    s->dyn.d_near = d_near;
-    s->dyn.d_far = d_far;
-    s->dyn.auto_range = (d_near < d_far) ? 0u : 1u;
+    if (k0 >= s->sc.scenes)
+        return fail(s, APBF_ERR_INVALID_ARG, "scene index out of range");
+    for (uint32_t k = k0; k < k1; ++k) {
+        for (int a = 0; a < 3; ++a)
+            s->dyn[k].eye[a] = eye[a];
+        s->dyn[k].d_near = d_near;
+        s->dyn[k].d_far = d_far;
+        s->dyn[k].auto_range = (d_near < d_far) ? 0u : 1u;
+    }
     s->dyn_dirty = true;
     return APBF_OK;
 }
 
-APBF_API apbf_status apbf_set_box(apbf_scene *s, const float lo[3], const float hi[3])
+apbf_status set_box_range(apbf_scene *s, uint32_t k0, uint32_t k1, const float lo[3], const float hi[3])
 {
     apbf_status st = enter(s);
     if (st != APBF_OK)
         return st;
     if (!lo || !hi || !finite3(lo) || !finite3(hi))
         return fail(s, APBF_ERR_INVALID_ARG, "box bounds must be finite and non-NULL");
-    for (int a = 0; a < 3; ++a)
-        if (!(s->sc.glo[a] <= lo[a] && lo[a] < hi[a] && hi[a] <= s->grid_hi[a]))
-            return fail(s, APBF_ERR_INVALID_ARG, "need grid_lo <= lo < hi <= grid_hi on every axis");
-    for (int a = 0; a < 3; ++a) {
-        s->dyn.box_lo[a] = lo[a];
-        s->dyn.box_hi[a] = hi[a];
-    }
+    if (k0 >= s->sc.scenes)
+        return fail(s, APBF_ERR_INVALID_ARG, "scene index out of range");
+    for (uint32_t k = k0; k < k1; ++k)
+        for (int a = 0; a < 3; ++a)
+            if (!(s->geo[k].glo[a] <= lo[a] && lo[a] < hi[a] && hi[a] <= s->grid_hi3[3 * k + a]))
+                return fail(s, APBF_ERR_INVALID_ARG, "need grid_lo <= lo < hi <= grid_hi on every axis");
+    for (uint32_t k = k0; k < k1; ++k)
+        for (int a = 0; a < 3; ++a) {
+            s->dyn[k].box_lo[a] = lo[a];
+            s->dyn[k].box_hi[a] = hi[a];
+        }
     s->dyn_dirty = true;
     return APBF_OK;
+}
+}  // namespace
+
+APBF_API apbf_status apbf_set_camera(apbf_scene *s, const float eye[3], const float dir[3], float d_near, float d_far)
+{
+    return s ? set_camera_range(s, 0, s->sc.scenes, eye, dir, d_near, d_far) : APBF_ERR_INVALID_ARG;
+}
+
+APBF_API apbf_status apbf_set_camera_at(apbf_scene *s, uint32_t index, const float eye[3], const float dir[3],
+                                        float d_near, float d_far)
+{
+    return s ? set_camera_range(s, index, index + 1, eye, dir, d_near, d_far) : APBF_ERR_INVALID_ARG;
+}
+
+APBF_API apbf_status apbf_set_box(apbf_scene *s, const float lo[3], const float hi[3])
+{
+    return s ? set_box_range(s, 0, s->sc.scenes, lo, hi) : APBF_ERR_INVALID_ARG;
+}
+
+APBF_API apbf_status apbf_set_box_at(apbf_scene *s, uint32_t index, const float lo[3], const float hi[3])
+{
+    return s ? set_box_range(s, index, index + 1, lo, hi) : APBF_ERR_INVALID_ARG;
 }
 
 APBF_API apbf_status apbf_step(apbf_scene *s, uint32_t nsteps)
@@ -670,7 +796,8 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     float dr[2];
     APBF_CUDA(s, cudaMemcpy(c.data(), s->b.counters, 8 * kCounterSlots, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(lc.data(), s->b.lvl_count, 4 * 258, cudaMemcpyDeviceToHost));
-    APBF_CUDA(s, cudaMemcpy(dr, s->b.drange, 8, cudaMemcpyDeviceToHost));
+    APBF_CUDA(s, cudaMemcpy(&dr[0], s->b.drange, 4, cudaMemcpyDeviceToHost));
+    APBF_CUDA(s, cudaMemcpy(&dr[1], s->b.drange + sc.scenes, 4, cudaMemcpyDeviceToHost));
     const bool partitioned = sc.lod_mode == APBF_LOD_DTC && sc.K > 1;
     info->neighbor_pairs = c[0];
     for (uint32_t l = 0; l < 256; ++l) {
@@ -688,12 +815,12 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
         info->lambda_pairs = c[0] * (unsigned long long)sc.n_max;
     }
     if (sc.lod_mode == APBF_LOD_DTC) {
-        if (s->dyn.auto_range) {
+        if (s->dyn[0].auto_range) {
             info->d_range[0] = dr[0];
             info->d_range[1] = dr[1];
         } else {
-            info->d_range[0] = s->dyn.d_near;
-            info->d_range[1] = s->dyn.d_far;
+            info->d_range[0] = s->dyn[0].d_near;
+            info->d_range[1] = s->dyn[0].d_far;
         }
     }
     return APBF_OK;
@@ -837,7 +964,7 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
         src = b.dbg4;
         size = 16 * n;
         break;
-    case APBF_DBG_DRANGE: src = b.drange; size = 8; break;
+    case APBF_DBG_DRANGE: src = b.drange; size = 8 * (size_t)sc.scenes; break;
     default: return fail(s, APBF_ERR_INVALID_ARG, "unknown debug field");
     }
     if (bytes != size || (size && !host))

@@ -53,9 +53,24 @@ struct StepConst {
     uint32_t max_nbr;
     uint32_t level_tiles;
     float rho0;         // rest density as given (FP32)
+    uint32_t scenes;    // scenes in the batch (1: the fields glo, nx.., m above describe it)
 };
 
-// Per-step values that callers change between steps (device copy read by kernels).
+// Geometry of one scene of a batch (device table, one entry per scene). The
+// scenes' particles and cells are concatenated: scene s owns particle slots
+// p0 .. p0+n-1 (in every order the step uses, because cell keys are
+// scene-major) and cell keys cell_base .. cell_base + nx*ny*nz - 1.
+struct SceneGeom {
+    float glo[3];
+    int32_t nx, ny, nz;
+    uint32_t cell_base;
+    int32_t m[3];  // local-origin lattice offsets (see StepConst::q)
+    uint32_t p0, n;
+    uint32_t pad;
+};
+
+// Per-step values that callers change between steps (device copy read by kernels,
+// one per scene).
 struct DynParams {
     float box_lo[4];
     float box_hi[4];
@@ -78,9 +93,11 @@ struct Buffers {
     float *rho;
     uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
     unsigned long long *counters;  // [0] pairs, [1] lambda pairs
-    uint32_t *drange;              // float bits of d_min, d_max
+    uint32_t *drange;              // float bits of d_min (scenes entries), then d_max (scenes entries)
+    const SceneGeom *geo;          // per scene
+    const uint16_t *sid;           // scene of each particle slot (constant)
     uint32_t *err;
-    DynParams *dyn;
+    DynParams *dyn;                // per scene
     float *stage_f;                // 3n floats readback staging
     uint8_t *stage_u8;             // n bytes readback staging
     float4 *dbg4;                  // n float4 debug staging
@@ -98,7 +115,7 @@ struct TimedLaunch {
 struct apbf_scene {
     int device = 0;
     apbf::StepConst sc{};
-    float grid_hi[3] = {};
+    std::vector<apbf::SceneGeom> geo;  // host copy of the per-scene geometry
     apbf::Buffers b{};
     cudaStream_t stream = nullptr;
     void *arena = nullptr;
@@ -107,10 +124,11 @@ struct apbf_scene {
     uint32_t flags = 0;
     int sms = 0;
     int grid_iter = 0;  // persistent grid of the iteration kernels
-    // dynamic parameters
-    apbf::DynParams dyn{};
+    // dynamic parameters, one per scene
+    std::vector<apbf::DynParams> dyn;
+    std::vector<float> grid_hi3;             // per scene static grid upper bounds (3 each)
     bool dyn_dirty = true;
-    apbf::DynParams *dyn_pinned = nullptr;  // ring of pinned upload slots
+    apbf::DynParams *dyn_pinned = nullptr;  // ring of 16 pinned upload slots of `scenes` entries
     cudaEvent_t dyn_ev[16] = {};
     int dyn_slot = 0;
     // graph

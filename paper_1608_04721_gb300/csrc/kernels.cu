@@ -51,12 +51,6 @@ __device__ __forceinline__ int cell_axis(float p, float lo, float inv_h, int dim
     return min(max(c, 0), dim - 1);
 }
 
-__device__ __forceinline__ int3 cell_of(float3 p, const StepConst &sc)
-{
-    return make_int3(cell_axis(p.x, sc.glo[0], sc.inv_h, sc.nx), cell_axis(p.y, sc.glo[1], sc.inv_h, sc.ny),
-                     cell_axis(p.z, sc.glo[2], sc.inv_h, sc.nz));
-}
-
 __device__ __forceinline__ uint32_t pack_cell(int3 c) { return (uint32_t)c.x | ((uint32_t)c.y << 11) | ((uint32_t)c.z << 22); }
 
 __device__ __forceinline__ int3 unpack_cell(uint32_t v)
@@ -218,47 +212,125 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_
     return warp_prefix + inc - v;
 }
 
+// ------------------------------------------------- per-scene geometry
+// A batch concatenates independent scenes; a particle slot's scene is
+// constant (cell keys are scene-major, so every order the step uses keeps
+// each scene's particles in its own slot range). With one scene (BATCH =
+// false) the geometry comes from the kernel constants.
+
+struct Geo {
+    float glo[3];
+    int nx, ny, nz;
+    uint32_t cell_base;
+    int m[3];
+};
+
+template <bool BATCH>
+__device__ __forceinline__ uint32_t scene_of(const Buffers &b, uint32_t i)
+{
+    return BATCH ? (uint32_t)__ldg(&b.sid[i]) : 0u;
+}
+
+template <bool BATCH>
+__device__ __forceinline__ Geo geo_of(const StepConst &sc, const Buffers &b, uint32_t s)
+{
+    Geo g;
+    if (BATCH) {
+        const SceneGeom *t = b.geo + s;
+        g.glo[0] = __ldg(&t->glo[0]);
+        g.glo[1] = __ldg(&t->glo[1]);
+        g.glo[2] = __ldg(&t->glo[2]);
+        g.nx = __ldg(&t->nx);
+        g.ny = __ldg(&t->ny);
+        g.nz = __ldg(&t->nz);
+        g.cell_base = __ldg(&t->cell_base);
+        g.m[0] = __ldg(&t->m[0]);
+        g.m[1] = __ldg(&t->m[1]);
+        g.m[2] = __ldg(&t->m[2]);
+    } else {
+        g.glo[0] = sc.glo[0];
+        g.glo[1] = sc.glo[1];
+        g.glo[2] = sc.glo[2];
+        g.nx = sc.nx;
+        g.ny = sc.ny;
+        g.nz = sc.nz;
+        g.cell_base = 0u;
+        g.m[0] = sc.m[0];
+        g.m[1] = sc.m[1];
+        g.m[2] = sc.m[2];
+    }
+    return g;
+}
+
+__device__ __forceinline__ int3 cell_in(float3 p, const Geo &g, float inv_h)
+{
+    return make_int3(cell_axis(p.x, g.glo[0], inv_h, g.nx), cell_axis(p.y, g.glo[1], inv_h, g.ny),
+                     cell_axis(p.z, g.glo[2], inv_h, g.nz));
+}
+
+__device__ __forceinline__ uint32_t key_in(int3 c, const Geo &g)
+{
+    return g.cell_base + ((uint32_t)c.z * (uint32_t)g.ny + (uint32_t)c.y) * (uint32_t)g.nx + (uint32_t)c.x;
+}
+
+__device__ __forceinline__ float3 origin_in(int3 c, const Geo &g, float q)
+{
+    return make_float3((float)(g.m[0] + c.x) * q, (float)(g.m[1] + c.y) * q, (float)(g.m[2] + c.z) * q);
+}
+
 // ------------------------------------------------------------- a1: range
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers b)
 {
     __shared__ float smin[kBlock / 32], smax[kBlock / 32];
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < sc.n;
+    const uint32_t s = valid ? scene_of<BATCH>(b, i) : 0u;
     float dmin = 3.0e38f, dmax = 0.0f;
-    if (i < sc.n) {
-        float d = camera_distance(b.state_x[i], b.dyn);
+    if (valid) {
+        const float d = camera_distance(b.state_x[i], b.dyn + s);
         dmin = d;
         dmax = d;
     }
-    dmin = warp_minf(dmin);
-    dmax = warp_maxf(dmax);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        smin[w] = dmin;
-        smax[w] = dmax;
-    }
-    __syncthreads();
-    if (w == 0) {
-        dmin = lane < kBlock / 32 ? smin[lane] : 3.0e38f;
-        dmax = lane < kBlock / 32 ? smax[lane] : 0.0f;
+    // distances are >= 0, so their bit patterns order like the values
+    const uint32_t s_first = scene_of<BATCH>(b, blockIdx.x * blockDim.x);
+    if (__syncthreads_and(!valid || s == s_first)) {
+        // the whole block lies in one scene: one atomic pair per block
         dmin = warp_minf(dmin);
         dmax = warp_maxf(dmax);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
         if (lane == 0) {
-            // distances are >= 0, so their bit patterns order like the values
-            atomicMin(&b.drange[0], __float_as_uint(dmin));
-            atomicMax(&b.drange[1], __float_as_uint(dmax));
+            smin[w] = dmin;
+            smax[w] = dmax;
         }
+        __syncthreads();
+        if (w == 0) {
+            dmin = warp_minf(lane < kBlock / 32 ? smin[lane] : 3.0e38f);
+            dmax = warp_maxf(lane < kBlock / 32 ? smax[lane] : 0.0f);
+            if (lane == 0) {
+                atomicMin(&b.drange[s_first], __float_as_uint(dmin));
+                atomicMax(&b.drange[sc.scenes + s_first], __float_as_uint(dmax));
+            }
+        }
+    } else if (valid) {
+        atomicMin(&b.drange[s], __float_as_uint(dmin));
+        atomicMax(&b.drange[sc.scenes + s], __float_as_uint(dmax));
     }
 }
 
 // ------------------------------------- a1-a4: level, predict, hash, count
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buffers b, int diag)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = i < sc.n;
     uint32_t key = 0xffffffffu;
     if (valid) {
+        const uint32_t s = scene_of<BATCH>(b, i);
+        const Geo g = geo_of<BATCH>(sc, b, s);
+        const DynParams *dyn = b.dyn + s;
         float4 x = b.state_x[i];
         float3 p;
         if (diag) {
@@ -266,19 +338,17 @@ __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buff
         } else {
             uint32_t lv = sc.n_max;
             if (sc.lod_mode == APBF_LOD_DTC) {
-                const DynParams *dyn = b.dyn;
                 float dmin = dyn->d_near, dmax = dyn->d_far;
                 if (dyn->auto_range) {
-                    dmin = __uint_as_float(b.drange[0]);
-                    dmax = __uint_as_float(b.drange[1]);
+                    dmin = __uint_as_float(b.drange[s]);
+                    dmax = __uint_as_float(b.drange[sc.scenes + s]);
                 }
                 lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
             }
             b.lvl[i] = (uint8_t)lv;
-            p = predict_position(x, b.state_v[i], sc, b.dyn);
+            p = predict_position(x, b.state_v[i], sc, dyn);
         }
-        int3 c = cell_of(p, sc);
-        key = ((uint32_t)c.z * (uint32_t)sc.ny + (uint32_t)c.y) * (uint32_t)sc.nx + (uint32_t)c.x;
+        key = key_in(cell_in(p, g, sc.inv_h), g);
         b.key[i] = key;
     }
     // warp-aggregated histogram: one atomic per distinct cell in the warp
@@ -361,6 +431,7 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(StepConst sc, Buffers b
 
 // ------------------------------------------ a4/a5: stable rank + reorder
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b, int diag)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,13 +446,15 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
     for (uint32_t j = s0; j < s1; ++j)
         r += (b.tmp[j] < id) ? 1u : 0u;
     uint32_t p = s0 + r;
+    const uint32_t s = scene_of<BATCH>(b, i);
+    const Geo g = geo_of<BATCH>(sc, b, s);
     float4 x = b.state_x[i];
-    float3 xp = diag ? make_float3(x.x, x.y, x.z) : predict_position(x, b.state_v[i], sc, b.dyn);
-    int3 c = cell_of(xp, sc);
+    float3 xp = diag ? make_float3(x.x, x.y, x.z) : predict_position(x, b.state_v[i], sc, b.dyn + s);
+    int3 c = cell_in(xp, g, sc.inv_h);
     b.xs32[p] = make_float4(xp.x, xp.y, xp.z, 0.0f);
     b.cell_s[p] = pack_cell(c);
     if (!diag) {
-        float3 o = cell_origin(c, sc);
+        float3 o = origin_in(c, g, sc.q);
         b.recA[p] = make_float4(__fsub_rn(xp.x, o.x), __fsub_rn(xp.y, o.y), __fsub_rn(xp.z, o.z), 0.0f);
         b.xt[p] = make_float4(__fsub_rn(x.x, o.x), __fsub_rn(x.y, o.y), __fsub_rn(x.z, o.z), 0.0f);
         b.id_s[p] = id;
@@ -391,26 +464,28 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
 
 // ----------------------------------------------- neighbour lists (l. 5-6)
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b)
 {
     __shared__ uint32_t sh[32];
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
     if (p < sc.n) {
+        const Geo g = geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p));
         const float4 xi = b.xs32[p];
         const int3 c = unpack_cell(b.cell_s[p]);
         const size_t n = sc.n;
         // the cells x-1..x+1 of one row (y+dy, z+dz) are contiguous in sorted order
-        const int xl = max(c.x - 1, 0), xr = min(c.x + 1, sc.nx - 1);
+        const int xl = max(c.x - 1, 0), xr = min(c.x + 1, g.nx - 1);
         for (int dz = -1; dz <= 1; ++dz) {
             const int cz = c.z + dz;
-            if (cz < 0 || cz >= sc.nz)
+            if (cz < 0 || cz >= g.nz)
                 continue;
             for (int dy = -1; dy <= 1; ++dy) {
                 const int cy = c.y + dy;
-                if (cy < 0 || cy >= sc.ny)
+                if (cy < 0 || cy >= g.ny)
                     continue;
-                const uint32_t row = ((uint32_t)cz * (uint32_t)sc.ny + (uint32_t)cy) * (uint32_t)sc.nx;
+                const uint32_t row = g.cell_base + ((uint32_t)cz * (uint32_t)g.ny + (uint32_t)cy) * (uint32_t)g.nx;
                 const uint32_t j0 = b.start[row + xl], jm = b.start[row + c.x], jp = b.start[row + c.x + 1],
                                j1 = b.start[row + xr + 1];
                 const uint32_t code_row = (uint32_t)(3 * (dy + 1) + 9 * (dz + 1));
@@ -609,14 +684,14 @@ __device__ __forceinline__ float powi(float x, uint32_t n)
     return r;
 }
 
-template <bool DENSE, int NPOW>
+template <bool DENSE, int NPOW, bool BATCH>
 __global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) deltap_kernel(StepConst sc, const float4 *__restrict__ B,
                                                         float4 *__restrict__ A, const uint32_t *__restrict__ act,
                                                         const uint32_t *__restrict__ nbr,
                                                         const uint8_t *__restrict__ nbr_cnt,
                                                         const uint32_t *__restrict__ cell_s,
                                                         const uint32_t *__restrict__ lvl_count,
-                                                        const DynParams *__restrict__ dyn, uint32_t l)
+                                                        const DynParams *__restrict__ dyn, Buffers b, uint32_t l)
 {
     __shared__ float4 dtab[27];
     fill_dtab(dtab, sc.q);
@@ -649,19 +724,30 @@ __global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) deltap_kernel(
             }
         });
         // new position, clamped to the box expressed relative to the cell origin
-        const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
         float px = bi.x + sc.c_dp * ax;
         float py = bi.y + sc.c_dp * ay;
         float pz = bi.z + sc.c_dp * az;
-        px = fminf(fmaxf(px, blo0 - og.x), bhi0 - og.x);
-        py = fminf(fmaxf(py, blo1 - og.y), bhi1 - og.y);
-        pz = fminf(fmaxf(pz, blo2 - og.z), bhi2 - og.z);
+        if (BATCH) {
+            const uint32_t s = scene_of<true>(b, p);
+            const Geo g = geo_of<true>(sc, b, s);
+            const DynParams *d = dyn + s;
+            const float3 og = origin_in(unpack_cell(cell_s[p]), g, sc.q);
+            px = fminf(fmaxf(px, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
+            py = fminf(fmaxf(py, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
+            pz = fminf(fmaxf(pz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
+        } else {
+            const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
+            px = fminf(fmaxf(px, blo0 - og.x), bhi0 - og.x);
+            py = fminf(fmaxf(py, blo1 - og.y), bhi1 - og.y);
+            pz = fminf(fmaxf(pz, blo2 - og.z), bhi2 - og.z);
+        }
         A[p] = make_float4(px, py, pz, bi.w);
     }
 }
 
 // ------------------------------------------ a10: velocity, XSPH, commit
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers b)
 {
     __shared__ float4 dtab[27];
@@ -709,8 +795,9 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
             }
         }
     }
-    const float3 og = cell_origin(unpack_cell(b.cell_s[p]), sc);
-    const DynParams *dyn = b.dyn;
+    const uint32_t s = scene_of<BATCH>(b, p);
+    const float3 og = origin_in(unpack_cell(b.cell_s[p]), geo_of<BATCH>(sc, b, s), sc.q);
+    const DynParams *dyn = b.dyn + s;
     float px = fminf(fmaxf(og.x + af.x, dyn->box_lo[0]), dyn->box_hi[0]);
     float py = fminf(fmaxf(og.y + af.y, dyn->box_lo[1]), dyn->box_hi[1]);
     float pz = fminf(fmaxf(og.z + af.z, dyn->box_lo[2]), dyn->box_hi[2]);
@@ -816,13 +903,14 @@ __global__ void __launch_bounds__(32) density_final_kernel(const double *__restr
     }
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) debug_xstar_kernel(StepConst sc, Buffers b, const float4 *__restrict__ rec)
 {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= sc.n)
         return;
     const float4 r = rec[p];
-    const float3 og = cell_origin(unpack_cell(b.cell_s[p]), sc);
+    const float3 og = origin_in(unpack_cell(b.cell_s[p]), geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p)), sc.q);
     b.dbg4[p] = make_float4(og.x + r.x, og.y + r.y, og.z + r.z, 0.0f);
 }
 
@@ -864,14 +952,15 @@ int occupancy(const void *fn)
 cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (sc.n)
-        lod_range_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+        (sc.scenes > 1 ? lod_range_kernel<true> : lod_range_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
 {
     if (sc.n)
-        predict_hash_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, diag ? 1 : 0);
+        (sc.scenes > 1 ? predict_hash_kernel<true> : predict_hash_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0,
+                                                                                   s>>>(sc, b, diag ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -893,14 +982,16 @@ cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s
 cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
 {
     if (sc.n)
-        reorder_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, diag ? 1 : 0);
+        (sc.scenes > 1 ? reorder_kernel<true> : reorder_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
+            sc, b, diag ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (sc.n)
-        neighbors_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+        (sc.scenes > 1 ? neighbors_kernel<true> : neighbors_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
+            sc, b);
     return cudaGetLastError();
 }
 
@@ -930,21 +1021,26 @@ cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s,
 {
     if (!sc.n)
         return cudaGetLastError();
-    const bool p4 = sc.scorr_n == 4;
-    const void *fn = dense ? (p4 ? (const void *)deltap_kernel<true, 4> : (const void *)deltap_kernel<true, -1>)
-                           : (p4 ? (const void *)deltap_kernel<false, 4> : (const void *)deltap_kernel<false, -1>);
-    const int grid = sms * occupancy(fn);
-#define APBF_DP(D, P)                                                                                          \
-    deltap_kernel<D, P><<<grid, kBlock, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s, b.lvl_count, \
-                                                b.dyn, l)
-    if (dense && p4)
-        APBF_DP(true, 4);
-    else if (dense)
-        APBF_DP(true, -1);
-    else if (p4)
-        APBF_DP(false, 4);
-    else
-        APBF_DP(false, -1);
+    const bool p4 = sc.scorr_n == 4, batch = sc.scenes > 1;
+    const void *fns[8] = {(const void *)deltap_kernel<false, -1, false>, (const void *)deltap_kernel<false, -1, true>,
+                          (const void *)deltap_kernel<false, 4, false>,  (const void *)deltap_kernel<false, 4, true>,
+                          (const void *)deltap_kernel<true, -1, false>,  (const void *)deltap_kernel<true, -1, true>,
+                          (const void *)deltap_kernel<true, 4, false>,   (const void *)deltap_kernel<true, 4, true>};
+    const int k = (dense ? 4 : 0) + (p4 ? 2 : 0) + (batch ? 1 : 0);
+    const int grid = sms * occupancy(fns[k]);
+#define APBF_DP(D, P, BT)                                                                                      \
+    deltap_kernel<D, P, BT><<<grid, kBlock, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s,   \
+                                                    b.lvl_count, b.dyn, b, l)
+    switch (k) {
+    case 0: APBF_DP(false, -1, false); break;
+    case 1: APBF_DP(false, -1, true); break;
+    case 2: APBF_DP(false, 4, false); break;
+    case 3: APBF_DP(false, 4, true); break;
+    case 4: APBF_DP(true, -1, false); break;
+    case 5: APBF_DP(true, -1, true); break;
+    case 6: APBF_DP(true, 4, false); break;
+    default: APBF_DP(true, 4, true); break;
+    }
 #undef APBF_DP
     return cudaGetLastError();
 }
@@ -952,7 +1048,8 @@ cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s,
 cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (sc.n)
-        finalize_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
+        (sc.scenes > 1 ? finalize_kernel<true> : finalize_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
+            sc, b);
     return cudaGetLastError();
 }
 
@@ -976,7 +1073,8 @@ cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s
 cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s)
 {
     if (sc.n)
-        debug_xstar_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, rec);
+        (sc.scenes > 1 ? debug_xstar_kernel<true> : debug_xstar_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0,
+                                                                                 s>>>(sc, b, rec);
     return cudaGetLastError();
 }
 

@@ -128,6 +128,31 @@ def config_ocean_1m(lod_mode: int = LOD_DTC, n_min: int = 3, n_max: int = 15) ->
                        camera="spline", wall="oscillate_xlo")
 
 
+def config_batch_256(count: int = 256, seed: int = 1608_04721, n_lo: int = 2048, n_hi: int = 65536,
+                     n_min: int = 4, n_max: int = 8, steps: int = 100):
+    """Independent dam-break scenes for batched stepping: particle counts
+    log-uniform in [n_lo, n_hi], block aspect ratio (x : y) uniform in 1..4
+    with depth z = y, the block in the low-x half of a box twice its length
+    and 1.5 times its height, a camera 3 m outside the box's x = 0 wall at a
+    random height; N_i in n_min..n_max from the distance to the camera."""
+    u = uniform01(seed, 2, 4 * count).reshape(count, 4)
+    out = []
+    for k in range(count):
+        n_target = math.exp(math.log(n_lo) + u[k, 0] * (math.log(n_hi) - math.log(n_lo)))
+        aspect = 1.0 + 3.0 * u[k, 1]
+        ny = max(2, int(round((n_target / aspect) ** (1.0 / 3.0))))
+        nx = max(2, int(round(aspect * ny)))
+        nz = ny
+        s = 0.05
+        bx, by, bz = nx * s, ny * s, nz * s
+        box_hi = (round(2.0 * bx + 0.1, 2), round(by + 0.1, 2), round(1.5 * bz + 0.1, 2))
+        eye = (-3.0, 0.5 * box_hi[1], float(0.2 + u[k, 2] * box_hi[2]))
+        out.append(SceneConfig(name=f"batch_{k:03d}", lattice=(nx, ny, nz), spacing=s, block_lo=(0.0, 0.0, 0.0),
+                               box_lo=(0.0, 0.0, 0.0), box_hi=box_hi, n_min=n_min, n_max=n_max, lod_mode=LOD_DTC,
+                               steps=steps, seed=seed + 7919 * (k + 1), camera="fixed", eye=eye))
+    return out
+
+
 CONFIGS = {
     "dam_break_4k": config_dam_break_4k,
     "dam_break_131k": config_dam_break_131k,

@@ -25,7 +25,7 @@ def _declared():
 
 def test_exports_every_declared_symbol():
     names = _declared()
-    assert len(names) == 19
+    assert len(names) == 23
     out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout
     exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
@@ -106,3 +106,17 @@ def test_non_finite_or_outside_positions_are_rejected():
 def test_status_strings():
     assert apbf.apbf_status_string(0) == "ok"
     assert "overflow" in apbf.apbf_status_string(apbf.APBF_ERR_NEIGHBOR_OVERFLOW)
+
+
+def test_batch_validation_on_the_host():
+    cfg = scenes.config_dam_break_4k().replace(lattice=(4, 4, 4))
+    x, v = scenes.make_scene(cfg)
+    a = apbf.desc_from_config(cfg, x, v, 8078.2)
+    b = apbf.desc_from_config(cfg, x, v, 8078.2, eps=50.0)
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_create_batch([a, b], stream=0, device_arena=None)
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG and "scene 1" in apbf.apbf_last_error()
+    c = apbf.desc_from_config(cfg.replace(box_hi=(2.0, 1.6, 1.6)), x, v, 8078.2)
+    assert apbf.apbf_batch_bytes([a, c]) > apbf.apbf_batch_bytes([a])
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_create_batch([], stream=0, device_arena=None)
