@@ -267,6 +267,31 @@ APBF_API apbf_status apbf_set_timing(apbf_scene *scene, int enable);
  * the last report; then reset the counters. */
 APBF_API apbf_status apbf_timing_report(apbf_scene *scene, double *ms, uint64_t *launches);
 
+/* ------------------------------------------------------------- tuning */
+
+/* Result of apbf_autotune: the chosen configuration and every trial. */
+typedef struct apbf_tune_result {
+    uint32_t block;          /* threads per block of the solver passes (128 or 256) */
+    float mask_threshold;    /* masked (all particles) instead of compacted when |P_l| >= threshold * n */
+    double ms_per_step;      /* the chosen configuration's trial time */
+    uint32_t tried;          /* trials below */
+    uint32_t blocks[16];
+    float thresholds[16];
+    double ms[16];
+} apbf_tune_result;
+
+/* Set the solver passes' launch configuration: block = 128 or 256 threads;
+ * iterations with a shrinking active set run over all particles (masked)
+ * instead of the compacted list when |P_l| >= mask_threshold * n (a
+ * threshold above 1 means always compacted). Results do not depend on it. */
+APBF_API apbf_status apbf_set_tuning(apbf_scene *scene, uint32_t block, float mask_threshold);
+
+/* Time every configuration (2 blocks x 5 thresholds) over trial_steps steps
+ * each (1..1000, after 2 warm-up steps) from the current state, restore the
+ * state, and keep the fastest. out (host) receives the choice and the trials.
+ * Synchronises; the state and the results of later steps are unchanged. */
+APBF_API apbf_status apbf_autotune(apbf_scene *scene, uint32_t trial_steps, apbf_tune_result *out);
+
 /* ----------------------------------------------------- test-only exports */
 
 /* Run one fresh step of the current state up to and including a stage

@@ -71,12 +71,24 @@ class apbf_step_info(C.Structure):
     ]
 
 
+class apbf_tune_result(C.Structure):
+    _fields_ = [
+        ("block", C.c_uint32),
+        ("mask_threshold", C.c_float),
+        ("ms_per_step", C.c_double),
+        ("tried", C.c_uint32),
+        ("blocks", C.c_uint32 * 16),
+        ("thresholds", C.c_float * 16),
+        ("ms", C.c_double * 16),
+    ]
+
+
 EXPORTS = [
     "apbf_status_string", "apbf_rest_density", "apbf_scene_bytes", "apbf_create_scene", "apbf_set_camera",
     "apbf_set_box", "apbf_step", "apbf_read_state", "apbf_density_stats", "apbf_get_step_info", "apbf_sync",
     "apbf_last_error", "apbf_destroy_scene", "apbf_set_timing", "apbf_timing_report", "apbf_debug_step_to",
     "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
-    "apbf_set_camera_at", "apbf_set_box_at",
+    "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -131,6 +143,8 @@ def lib():
         L.apbf_create_batch.argtypes = [P(apbf_scene_desc), C.c_uint32, V, V, C.c_size_t, P(V)]
         L.apbf_set_camera_at.argtypes = [V, C.c_uint32, P(C.c_float), P(C.c_float), C.c_float, C.c_float]
         L.apbf_set_box_at.argtypes = [V, C.c_uint32, P(C.c_float), P(C.c_float)]
+        L.apbf_set_tuning.argtypes = [V, C.c_uint32, C.c_float]
+        L.apbf_autotune.argtypes = [V, C.c_uint32, P(apbf_tune_result)]
         L.apbf_density_stats_static.argtypes = [V, C.c_uint32, C.c_float, C.c_float, C.c_float, P(C.c_float),
                                                 P(C.c_float), V, V]
         for f in EXPORTS:
@@ -473,3 +487,15 @@ def apbf_density_stats_static(pos_dev, n: int, h: float, mass: float, rho0: floa
     _check(lib().apbf_density_stats_static(C.c_void_p(ptr(pos_dev)), n, h, mass, rho0, lo, hi,
                                            C.c_void_p(ptr(stats_dev)), C.c_void_p(stream_ptr)),
            "apbf_density_stats_static")
+
+
+def apbf_set_tuning(scene: Scene, block: int, mask_threshold: float):
+    _check(lib().apbf_set_tuning(scene.handle, block, mask_threshold), "apbf_set_tuning", scene)
+
+
+def apbf_autotune(scene: Scene, trial_steps: int = 5) -> dict:
+    r = apbf_tune_result()
+    _check(lib().apbf_autotune(scene.handle, trial_steps, C.byref(r)), "apbf_autotune", scene)
+    trials = [(int(r.blocks[k]), float(r.thresholds[k]), float(r.ms[k])) for k in range(r.tried)]
+    return dict(block=int(r.block), mask_threshold=float(r.mask_threshold), ms_per_step=float(r.ms_per_step),
+                trials=trials)

@@ -271,6 +271,9 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.dyn = (DynParams *)P(sizeof(DynParams) * (size_t)sc.scenes);
     b.geo = (const SceneGeom *)P(sizeof(SceneGeom) * (size_t)sc.scenes);
     b.sid = (const uint16_t *)P(2 * n);
+    b.snap_x = (float4 *)P(16 * n);
+    b.snap_v = (float4 *)P(16 * n);
+    b.snap_id = (uint32_t *)P(4 * n);
     b.stage_f = (float *)P(12 * n);
     b.stage_u8 = (uint8_t *)P(n);
     b.dbg4 = (float4 *)P(16 * n);
@@ -363,13 +366,13 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
         return APBF_OK;
     for (uint32_t l = 1; l <= sc.n_max; ++l) {
         const bool dense = l <= sc.n_min;
-        e = timed(s, st, APBF_STAGE_LAMBDA, [&] { return launch_lambda(sc, b, st, l, dense, s->grid_iter); });
+        e = timed(s, st, APBF_STAGE_LAMBDA, [&] { return launch_lambda(sc, b, st, l, dense, s->grid_iter, s->tune); });
         if (e != cudaSuccess)
             return cuda_fail(s, e, "lambda");
         s->cur_buf = 1;
         if (stop_stage == APBF_STAGE_LAMBDA && stop_iter == l)
             return APBF_OK;
-        e = timed(s, st, APBF_STAGE_DELTAP, [&] { return launch_deltap(sc, b, st, l, dense, s->grid_iter); });
+        e = timed(s, st, APBF_STAGE_DELTAP, [&] { return launch_deltap(sc, b, st, l, dense, s->grid_iter, s->tune); });
         if (e != cudaSuccess)
             return cuda_fail(s, e, "deltap");
         s->cur_buf = 0;
@@ -904,6 +907,113 @@ APBF_API apbf_status apbf_timing_report(apbf_scene *s, double *ms, uint64_t *lau
         s->stage_launches[k] = 0;
     }
     return APBF_OK;
+}
+
+namespace {
+void drop_graph(apbf_scene *s)
+{
+    if (s->gexec)
+        cudaGraphExecDestroy(s->gexec);
+    if (s->graph)
+        cudaGraphDestroy(s->graph);
+    s->gexec = nullptr;
+    s->graph = nullptr;
+}
+
+apbf_status copy_state(apbf_scene *s, bool to_snapshot)
+{
+    const Buffers &b = s->b;
+    const size_t n = s->sc.n;
+    float4 *x0 = to_snapshot ? b.snap_x : b.state_x, *x1 = to_snapshot ? b.state_x : b.snap_x;
+    float4 *v0 = to_snapshot ? b.snap_v : b.state_v, *v1 = to_snapshot ? b.state_v : b.snap_v;
+    uint32_t *i0 = to_snapshot ? b.snap_id : b.state_id, *i1 = to_snapshot ? b.state_id : b.snap_id;
+    APBF_CUDA(s, cudaMemcpyAsync(x0, x1, 16 * n, cudaMemcpyDeviceToDevice, s->stream));
+    APBF_CUDA(s, cudaMemcpyAsync(v0, v1, 16 * n, cudaMemcpyDeviceToDevice, s->stream));
+    APBF_CUDA(s, cudaMemcpyAsync(i0, i1, 4 * n, cudaMemcpyDeviceToDevice, s->stream));
+    return APBF_OK;
+}
+}  // namespace
+
+APBF_API apbf_status apbf_set_tuning(apbf_scene *s, uint32_t block, float mask_threshold)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if ((block != 128 && block != 256) || !(mask_threshold >= 0.0f) || !std::isfinite(mask_threshold))
+        return fail(s, APBF_ERR_INVALID_ARG, "block must be 128 or 256 and mask_threshold finite and >= 0");
+    s->tune.block = (int)block;
+    s->tune.mask_threshold = mask_threshold;
+    drop_graph(s);
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_autotune(apbf_scene *s, uint32_t trial_steps, apbf_tune_result *out)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!out || trial_steps == 0 || trial_steps > 1000)
+        return fail(s, APBF_ERR_INVALID_ARG, "out is NULL or trial_steps not in 1..1000");
+    std::memset(out, 0, sizeof(*out));
+    out->block = (uint32_t)s->tune.block;
+    out->mask_threshold = s->tune.mask_threshold;
+    if (s->sc.n == 0)
+        return APBF_OK;
+    const uint32_t blocks[2] = {256, 128};
+    const float thresholds[5] = {2.0f, 0.9f, 0.75f, 0.5f, 0.0f};
+    if ((st = upload_dyn(s)) != APBF_OK)
+        return st;
+    if ((st = copy_state(s, true)) != APBF_OK)
+        return st;
+    cudaEvent_t e0 = get_event(s), e1 = get_event(s);
+    const bool timing = s->timing;
+    s->timing = false;
+    double best = 1e300;
+    Tune best_t = s->tune;
+    uint32_t k = 0;
+    for (uint32_t bi = 0; bi < 2; ++bi)
+        for (uint32_t ti = 0; ti < 5; ++ti, ++k) {
+            s->tune.block = (int)blocks[bi];
+            s->tune.mask_threshold = thresholds[ti];
+            if ((st = copy_state(s, false)) != APBF_OK)
+                break;
+            for (uint32_t w = 0; w < 2 && st == APBF_OK; ++w)
+                st = enqueue_step(s, s->stream, kStageAll, 0);
+            if (st != APBF_OK)
+                break;
+            APBF_CUDA(s, cudaEventRecord(e0, s->stream));
+            for (uint32_t w = 0; w < trial_steps && st == APBF_OK; ++w)
+                st = enqueue_step(s, s->stream, kStageAll, 0);
+            if (st != APBF_OK)
+                break;
+            APBF_CUDA(s, cudaEventRecord(e1, s->stream));
+            APBF_CUDA(s, cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            APBF_CUDA(s, cudaEventElapsedTime(&ms, e0, e1));
+            const double per = (double)ms / trial_steps;
+            out->ms[k] = per;
+            out->blocks[k] = blocks[bi];
+            out->thresholds[k] = thresholds[ti];
+            if (per < best) {
+                best = per;
+                best_t = s->tune;
+            }
+        }
+    s->timing = timing;
+    s->ev_pool.push_back(e0);
+    s->ev_pool.push_back(e1);
+    if (st != APBF_OK)
+        return st;
+    out->tried = k;
+    if ((st = copy_state(s, false)) != APBF_OK)
+        return st;
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->tune = best_t;
+    drop_graph(s);
+    out->block = (uint32_t)best_t.block;
+    out->mask_threshold = best_t.mask_threshold;
+    out->ms_per_step = best;
+    return check_device_errors(s);
 }
 
 APBF_API apbf_status apbf_debug_step_to(apbf_scene *s, uint32_t stage, uint32_t iteration)

@@ -98,11 +98,19 @@ struct Buffers {
     const uint16_t *sid;           // scene of each particle slot (constant)
     uint32_t *err;
     DynParams *dyn;                // per scene
+    float4 *snap_x, *snap_v;       // state snapshot for the autotuner
+    uint32_t *snap_id;
     float *stage_f;                // 3n floats readback staging
     uint8_t *stage_u8;             // n bytes readback staging
     float4 *dbg4;                  // n float4 debug staging
     double *partials;              // diagnostic partial sums
     double *dstats;                // 4 doubles
+};
+
+// Launch configuration of the solver passes, picked per scene by the autotuner.
+struct Tune {
+    int block = 256;              // threads per block of the lambda / delta-p kernels (128 or 256)
+    float mask_threshold = 2.0f;  // iterate masked over all particles when |P_l| >= threshold * n
 };
 
 struct TimedLaunch {
@@ -124,6 +132,7 @@ struct apbf_scene {
     uint32_t flags = 0;
     int sms = 0;
     int grid_iter = 0;  // persistent grid of the iteration kernels
+    apbf::Tune tune;
     // dynamic parameters, one per scene
     std::vector<apbf::DynParams> dyn;
     std::vector<float> grid_hi3;             // per scene static grid upper bounds (3 each)
@@ -160,10 +169,10 @@ cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s
 cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
 cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
-cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense,
-                          int grid);
-cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense,
-                          int grid);
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
+                          const Tune &tune);
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
+                          const Tune &tune);
 cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what);
 cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks);

@@ -613,26 +613,40 @@ __global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc,
 // in iteration l-1 copy their final position into B and keep their lambda
 // there, so inactive neighbours enter Eq. 7 with their last lambda.
 
-template <bool DENSE>
-__global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) lambda_kernel(StepConst sc, const float4 *__restrict__ A,
-                                                        float4 *__restrict__ B, float *__restrict__ rho_out,
-                                                        const uint32_t *__restrict__ act,
-                                                        const uint32_t *__restrict__ nbr,
-                                                        const uint8_t *__restrict__ nbr_cnt,
-                                                        const uint32_t *__restrict__ lvl_count, uint32_t l)
+// Work-list modes of an iteration with a shrinking active set: compacted
+// (threads over the level-ordered list act, |P_l| of them) or masked
+// (threads over all particles, inactive ones skip). The kernel picks masked
+// when |P_l| >= mask_thr * n; the threshold is tuned per scene. Both modes do
+// identical arithmetic per particle, so the choice never changes a result.
+template <bool DENSE, int BS>
+__global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_kernel(
+    StepConst sc, const float4 *__restrict__ A, float4 *__restrict__ B, float *__restrict__ rho_out,
+    const uint32_t *__restrict__ act, const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt,
+    const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr)
 {
     __shared__ float4 dtab[27];
     fill_dtab(dtab, sc.q);
     __syncthreads();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
     const uint32_t cnt_prev = DENSE ? sc.n : lvl_count[l - 1];
+    const bool masked = !DENSE && (float)cnt_l >= mask_thr * (float)sc.n;
+    const uint32_t work = masked ? sc.n : cnt_prev;
     const size_t n = sc.n;
     // grid-stride: at any moment the whole grid works on one compact window of
     // the (cell-sorted) work list, which keeps the gathers' working set in L2
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_prev; t += gridDim.x * blockDim.x) {
-        const uint32_t p = DENSE ? t : act[t];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
+        const uint32_t p = (DENSE || masked) ? t : act[t];
+        bool finished_last = false;  // finished in iteration l-1: keep position and lambda in B
+        if (masked) {
+            const uint32_t lv = lvl_s[p];
+            if (lv + 1 < l)
+                continue;
+            finished_last = lv < l;
+        } else if (!DENSE) {
+            finished_last = t >= cnt_l;
+        }
         const float4 ai = A[p];
-        if (!DENSE && t >= cnt_l) {
+        if (finished_last) {
             B[p] = make_float4(ai.x, ai.y, ai.z, B[p].w);
             continue;
         }
@@ -684,24 +698,25 @@ __device__ __forceinline__ float powi(float x, uint32_t n)
     return r;
 }
 
-template <bool DENSE, int NPOW, bool BATCH>
-__global__ void __launch_bounds__(kBlock, APBF_SOLVER_MIN_BLOCKS) deltap_kernel(StepConst sc, const float4 *__restrict__ B,
-                                                        float4 *__restrict__ A, const uint32_t *__restrict__ act,
-                                                        const uint32_t *__restrict__ nbr,
-                                                        const uint8_t *__restrict__ nbr_cnt,
-                                                        const uint32_t *__restrict__ cell_s,
-                                                        const uint32_t *__restrict__ lvl_count,
-                                                        const DynParams *__restrict__ dyn, Buffers b, uint32_t l)
+template <bool DENSE, int NPOW, bool BATCH, int BS>
+__global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_kernel(
+    StepConst sc, const float4 *__restrict__ B, float4 *__restrict__ A, const uint32_t *__restrict__ act,
+    const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt, const uint32_t *__restrict__ cell_s,
+    const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr)
 {
     __shared__ float4 dtab[27];
     fill_dtab(dtab, sc.q);
     __syncthreads();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
+    const bool masked = !DENSE && (float)cnt_l >= mask_thr * (float)sc.n;
+    const uint32_t work = masked ? sc.n : cnt_l;
     const size_t n = sc.n;
     const float blo0 = dyn->box_lo[0], blo1 = dyn->box_lo[1], blo2 = dyn->box_lo[2];
     const float bhi0 = dyn->box_hi[0], bhi1 = dyn->box_hi[1], bhi2 = dyn->box_hi[2];
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt_l; t += gridDim.x * blockDim.x) {
-        const uint32_t p = DENSE ? t : act[t];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
+        const uint32_t p = (DENSE || masked) ? t : act[t];
+        if (masked && b.lvl_s[p] < l)
+            continue;
         const float4 bi = B[p];
         const uint32_t nn = nbr_cnt[p];
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
@@ -924,7 +939,7 @@ __global__ void __launch_bounds__(kBlock) debug_lambda_kernel(StepConst sc, Buff
 inline unsigned blocks_for(uint32_t n, int bs) { return (unsigned)((n + (uint32_t)bs - 1) / (uint32_t)bs); }
 
 // Resident blocks of kBlock threads per SM for a kernel (cached per function).
-int occupancy(const void *fn)
+int occupancy(const void *fn, int block = kBlock)
 {
     static const void *keys[16];
     static int vals[16];
@@ -932,7 +947,7 @@ int occupancy(const void *fn)
         if (keys[k] == fn)
             return vals[k];
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, 0) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, 0) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 4;
     }
@@ -1005,44 +1020,62 @@ cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms)
+template <int BS>
+cudaError_t launch_lambda_bs(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
+                             float thr)
 {
-    const int grid = sms * occupancy(dense ? (const void *)lambda_kernel<true> : (const void *)lambda_kernel<false>);
-    if (!sc.n)
-        return cudaGetLastError();
     if (dense)
-        lambda_kernel<true><<<grid, kBlock, 0, s>>>(sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_count, l);
+        lambda_kernel<true, BS><<<sms * occupancy((const void *)lambda_kernel<true, BS>, BS), BS, 0, s>>>(
+            sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr);
     else
-        lambda_kernel<false><<<grid, kBlock, 0, s>>>(sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_count, l);
+        lambda_kernel<false, BS><<<sms * occupancy((const void *)lambda_kernel<false, BS>, BS), BS, 0, s>>>(
+            sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms)
+cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
+                          const Tune &tune)
 {
     if (!sc.n)
         return cudaGetLastError();
-    const bool p4 = sc.scorr_n == 4, batch = sc.scenes > 1;
-    const void *fns[8] = {(const void *)deltap_kernel<false, -1, false>, (const void *)deltap_kernel<false, -1, true>,
-                          (const void *)deltap_kernel<false, 4, false>,  (const void *)deltap_kernel<false, 4, true>,
-                          (const void *)deltap_kernel<true, -1, false>,  (const void *)deltap_kernel<true, -1, true>,
-                          (const void *)deltap_kernel<true, 4, false>,   (const void *)deltap_kernel<true, 4, true>};
-    const int k = (dense ? 4 : 0) + (p4 ? 2 : 0) + (batch ? 1 : 0);
-    const int grid = sms * occupancy(fns[k]);
-#define APBF_DP(D, P, BT)                                                                                      \
-    deltap_kernel<D, P, BT><<<grid, kBlock, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s,   \
-                                                    b.lvl_count, b.dyn, b, l)
-    switch (k) {
-    case 0: APBF_DP(false, -1, false); break;
-    case 1: APBF_DP(false, -1, true); break;
-    case 2: APBF_DP(false, 4, false); break;
-    case 3: APBF_DP(false, 4, true); break;
-    case 4: APBF_DP(true, -1, false); break;
-    case 5: APBF_DP(true, -1, true); break;
-    case 6: APBF_DP(true, 4, false); break;
-    default: APBF_DP(true, 4, true); break;
-    }
-#undef APBF_DP
+    return tune.block == 128 ? launch_lambda_bs<128>(sc, b, s, l, dense, sms, tune.mask_threshold)
+                             : launch_lambda_bs<256>(sc, b, s, l, dense, sms, tune.mask_threshold);
+}
+
+template <bool DENSE, int NPOW, bool BATCH, int BS>
+cudaError_t launch_deltap_t(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, int sms, float thr)
+{
+    const int grid = sms * occupancy((const void *)deltap_kernel<DENSE, NPOW, BATCH, BS>, BS);
+    deltap_kernel<DENSE, NPOW, BATCH, BS><<<grid, BS, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s,
+                                                              b.lvl_count, b.dyn, b, l, thr);
     return cudaGetLastError();
+}
+
+template <int BS>
+cudaError_t launch_deltap_bs(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
+                             float thr)
+{
+    const bool p4 = sc.scorr_n == 4, batch = sc.scenes > 1;
+    const int k = (dense ? 4 : 0) + (p4 ? 2 : 0) + (batch ? 1 : 0);
+    switch (k) {
+    case 0: return launch_deltap_t<false, -1, false, BS>(sc, b, s, l, sms, thr);
+    case 1: return launch_deltap_t<false, -1, true, BS>(sc, b, s, l, sms, thr);
+    case 2: return launch_deltap_t<false, 4, false, BS>(sc, b, s, l, sms, thr);
+    case 3: return launch_deltap_t<false, 4, true, BS>(sc, b, s, l, sms, thr);
+    case 4: return launch_deltap_t<true, -1, false, BS>(sc, b, s, l, sms, thr);
+    case 5: return launch_deltap_t<true, -1, true, BS>(sc, b, s, l, sms, thr);
+    case 6: return launch_deltap_t<true, 4, false, BS>(sc, b, s, l, sms, thr);
+    default: return launch_deltap_t<true, 4, true, BS>(sc, b, s, l, sms, thr);
+    }
+}
+
+cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
+                          const Tune &tune)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    return tune.block == 128 ? launch_deltap_bs<128>(sc, b, s, l, dense, sms, tune.mask_threshold)
+                             : launch_deltap_bs<256>(sc, b, s, l, dense, sms, tune.mask_threshold);
 }
 
 cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s)

@@ -135,3 +135,29 @@ def test_batch_graph_replay_equals_eager_and_density_aggregates():
     e_all = np.concatenate(rhos) / np.float32(r0) - 1.0
     ref = [np.abs(e_all).mean(), np.abs(e_all).max(), e_all.mean(), np.maximum(e_all, 0).mean()]
     assert np.allclose(stats, ref, rtol=1e-5, atol=1e-6), (stats, ref)
+
+
+def test_tuning_choices_do_not_change_results_and_autotune_restores_the_state():
+    cfg = scenes.config_dam_break_131k(n_min=3, n_max=9).replace(lattice=(40, 24, 16))
+    x, v = scenes.make_scene(cfg)
+    r0 = rest_density(cfg)
+    ref = None
+    for block, thr in ((256, 2.0), (128, 2.0), (256, 0.0), (128, 0.6), (256, 0.85)):
+        s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+        apbf.apbf_set_camera(s, cfg.eye)
+        apbf.apbf_set_tuning(s, block, thr)
+        apbf.apbf_step(s, 4)
+        got = apbf.apbf_read_state(s, pos=True, vel=True, rho=True)
+        if ref is None:
+            ref = got
+        for f in ref:
+            assert np.array_equal(got[f], ref[f]), (block, thr, f)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    apbf.apbf_set_camera(s, cfg.eye)
+    res = apbf.apbf_autotune(s, 2)
+    assert len(res["trials"]) == 10 and res["block"] in (128, 256)
+    assert res["ms_per_step"] == min(t[2] for t in res["trials"])
+    apbf.apbf_step(s, 4)
+    got = apbf.apbf_read_state(s, pos=True, vel=True, rho=True)
+    for f in ref:
+        assert np.array_equal(got[f], ref[f]), f
