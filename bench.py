@@ -204,7 +204,7 @@ def timed_run(apbf, torch, scene, cfg, warmup, steps, first_step=0):
     return evs[0].elapsed_time(evs[-1]), per, s
 
 
-def stage_profile(apbf, scene, cfg, first_step, steps):
+def stage_profile(apbf, scene, cfg, first_step, steps, drive_fn=None):
     """Per-stage CUDA-event times over `steps` eager steps, plus the neighbour
     pairs each step's solver passes visited."""
     apbf.apbf_set_timing(scene, True)
@@ -216,7 +216,7 @@ def stage_profile(apbf, scene, cfg, first_step, steps):
     ln_tot = np.zeros(len(STAGE_NAMES))
     s = first_step
     for _ in range(steps):
-        drive(apbf, scene, cfg, s)
+        (drive_fn or drive)(apbf, scene, cfg, s)
         apbf.apbf_step(scene, 1)
         info = apbf.apbf_get_step_info(scene)
         pairs += info["lambda_pairs"]
@@ -271,14 +271,170 @@ def cpu_baseline(cfg, n_full, budget_s=20.0):
             "sample_seconds": dt}
 
 
+def tune_summary(res):
+    return {"block": res["block"], "mask_threshold": res["mask_threshold"], "trial_ms": res["ms_per_step"],
+            "candidates": len(res["trials"])}
+
+
+def run_batch(args, apbf, torch, d):
+    """Batched multi-scene stepping: 256 independent dam breaks (sizes
+    log-uniform in 2048..65536 particles, N_i in 4..8 by camera distance)
+    stepped as one batch, one launch per stage over all scenes, against the
+    same scenes stepped one at a time (one scene, one graph, per call).
+    Each rank steps its own batch (seeded by rank): weak scaling, no
+    collective on the data path."""
+    cfgs = scenes.config_batch_256(seed=1608_04721 + 7 * d.rank)
+    c0 = cfgs[0]
+    rho0 = float(np.float32(apbf.apbf_rest_density(c0.h, c0.mass, c0.spacing)))
+    descs = []
+    for c in cfgs:
+        x, v = scenes.make_scene(c)
+        descs.append(apbf.desc_from_config(c, x, v, rho0))
+    n_total = sum(c.n for c in cfgs)
+    batch = apbf.apbf_create_batch(descs)
+    for k, c in enumerate(cfgs):
+        apbf.apbf_set_camera_at(batch, k, c.eye)
+    tuning = "defaults (block 256, compacted levels)"
+    if not args.no_autotune:
+        tuning = tune_summary(apbf.apbf_autotune(batch, 4))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def time_steps(step_fn, warmup, steps):
+        for _ in range(warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        d.barrier()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for k in range(steps):
+            step_fn()
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        d.barrier()
+        return evs[0].elapsed_time(evs[-1]), [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    tot, per = time_steps(lambda: apbf.apbf_step(batch, 1), args.warmup, args.steps)
+    ms_step = d.max(tot / args.steps)
+    density = apbf.apbf_density_stats(batch)
+    # one at a time: the same scenes, each its own scene object and graph, same tuning
+    singles = []
+    for k, c in enumerate(cfgs):
+        s = apbf.apbf_create_scene(descs[k])
+        apbf.apbf_set_camera(s, c.eye)
+        if isinstance(tuning, dict):
+            apbf.apbf_set_tuning(s, tuning["block"], tuning["mask_threshold"])
+        singles.append(s)
+
+    def step_all():
+        for s in singles:
+            apbf.apbf_step(s, 1)
+
+    single_steps = max(3, min(args.steps, 100))
+    stot, sper = time_steps(step_all, args.warmup, single_steps)
+    single_ms = d.max(stot / single_steps)
+    for s in singles:
+        apbf.apbf_destroy_scene(s)
+    # end to end: step, then read every scene's positions into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host_pos = torch.empty((n_total, 3), dtype=torch.float32, pin_memory=True).numpy()
+        e2e_steps = max(3, min(args.steps, 100))
+        for _ in range(args.warmup):
+            apbf.apbf_step(batch, 1)
+            apbf.apbf_read_state(batch, pos=host_pos, vel=False)
+        d.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            apbf.apbf_step(batch, 1)
+            apbf.apbf_read_state(batch, pos=host_pos, vel=False)
+        e2e_ms = d.max((time.perf_counter() - t0) * 1e3 / e2e_steps)
+        e2e = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 12 * n_total + 4,
+               "what": "per step: apbf_step of the batch, apbf_read_state of all positions of all scenes into "
+                       "pinned host memory (synchronising); cameras and walls are fixed, so nothing is uploaded"}
+    clock_info = clocks.stop()
+    ms_st, ln_st, pairs, nbr_pairs, iters, _ = stage_profile(apbf, batch, c0, 0, args.profile_steps,
+                                                             drive_fn=lambda *a: None)
+    stage_ms = {STAGE_NAMES[k]: float(ms_st[k] / args.profile_steps) for k in range(len(STAGE_NAMES))}
+    top = max(("lambda", "deltap"), key=lambda k: stage_ms[k])
+    k_top = STAGE_NAMES.index(top)
+    launches = max(1.0, float(ln_st[k_top]))
+    avg_launch_s = ms_st[k_top] / launches * 1e-3
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR[top] * pairs / launches / avg_launch_s / 1e12
+    roofline = {"bound": "alu", "kernel": f"{top}_kernel", "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": read_traffic(f"{top}_kernel", "apbf_batch_256"),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+                "flops_per_pair": FLOPS_PER_PAIR[top], "pairs_per_launch": pairs / launches,
+                "avg_launch_us": avg_launch_s * 1e6}
+    per_step_iters = iters / args.profile_steps
+    line = {
+        "metric": "batched APBF ms/step for 256 independent scenes vs one at a time", "value": ms_step,
+        "unit": UNIT, "n_gpus": d.ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "apbf_batch_256", "scenes": len(cfgs), "particles": n_total,
+                   "particles_per_scene": f"log-uniform {min(c.n for c in cfgs)}..{max(c.n for c in cfgs)}",
+                   "n_range": f"{c0.n_min}..{c0.n_max}", "lod": "distance to camera, automatic range per scene",
+                   "parallelism": f"one batch per rank x{d.ws}" if d.ws > 1 else "single GPU",
+                   "l2": "no flush: each step touches > 1 GB (> 129 MB L2)",
+                   "launch": "one captured CUDA graph per batch step", "tuning": tuning},
+        "p50_ms": metrics.percentile(per, 50), "p99_ms": metrics.percentile(per, 99),
+        "one_at_a_time": {"ms_per_step": single_ms, "p50_ms": metrics.percentile(sper, 50),
+                          "p99_ms": metrics.percentile(sper, 99), "steps": single_steps,
+                          "speedup_of_batch": single_ms / ms_step,
+                          "gpu_launches_per_step": len(cfgs) * kernels_per_step(c0)},
+        "particle_iterations_per_step": per_step_iters,
+        "particle_iterations_per_s": d.sum(per_step_iters / (ms_step * 1e-3)),
+        "neighbor_pairs_per_step": nbr_pairs / args.profile_steps,
+        "density": {"batch": [float(v) for v in density],
+                    "fields": ["mean|rho/rho0-1|", "max|rho/rho0-1|", "mean(rho/rho0-1)", "mean max(0,rho/rho0-1)"]},
+        "roofline": roofline, "stage_ms_per_step": stage_ms, "e2e": e2e,
+        "gpu_launches": kernels_per_step(c0) * args.steps, "clocks": clock_info,
+    }
+    if d.rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(cfgs, rho0)
+    apbf.apbf_destroy_scene(batch)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+def batch_cpu_baseline(cfgs, rho0, budget_s=20.0):
+    """The oracle, single-threaded, stepping the batch's scenes in order until
+    the budget is spent; the per-particle time scaled to the whole batch."""
+    import oracle
+
+    t_used, n_used, done = 0.0, 0, 0
+    for c in sorted(cfgs, key=lambda c: c.n):
+        x, v = scenes.make_scene(c)
+        p = oracle.make_params(c, rho0=rho0, eye=c.eye)
+        t0 = time.perf_counter()
+        oracle.step(p, x, v)
+        t_used += time.perf_counter() - t0
+        n_used += c.n
+        done += 1
+        if t_used > budget_s:
+            break
+    n_total = sum(c.n for c in cfgs)
+    scale = n_total / n_used
+    return {"value": t_used * 1e3 * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle step of the {done} smallest of the {len(cfgs)} scenes ({n_used} of {n_total} "
+                      f"particles), time x {scale:.3g}", "sample_seconds": t_used}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle, timed on the host cores, on this arm's
     workload; each step is a bounded sample (the bottom lattice layers of the
     same scene), the per-step time scaled by particles."""
     ws, rank, _ = dist_env()
-    cfg = workload(args.workload, "apbf")
     if rank != 0:
         return 0
+    if args.workload == "batch_256":
+        return run_reference_batch(args, ws)
+    cfg = workload(args.workload, "apbf")
     import oracle
 
     rho0 = float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
@@ -322,13 +478,63 @@ def run_reference(args):
     return 0
 
 
+def run_reference_batch(args, ws):
+    """Reference arm for the batch: each step, the oracle steps the smallest
+    scenes of the batch that fit the per-step budget, the time scaled by
+    particles to the whole batch."""
+    import oracle
+
+    cfgs = sorted(scenes.config_batch_256(), key=lambda c: c.n)
+    c0 = cfgs[0]
+    rho0 = float(np.float32(oracle.rest_density(c0.h, c0.mass, c0.spacing)))
+    budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "150")) / max(1, args.steps + args.warmup)
+    states = []
+    t_cal = 0.0
+    for c in cfgs:   # calibrate: one step per scene until the per-step budget is reached
+        x, v = scenes.make_scene(c)
+        p = oracle.make_params(c, rho0=rho0, eye=c.eye)
+        t0 = time.perf_counter()
+        oracle.step(p, x, v)
+        t_cal += time.perf_counter() - t0
+        states.append([c, p, x, v, np.arange(c.n, dtype=np.int32)])
+        if t_cal > budget:
+            break
+    n_total = sum(c.n for c in cfgs)
+    n_used = sum(st[0].n for st in states)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for st in states:
+            out = oracle.step(st[1], st[2], st[3], st[4])
+            st[2], st[3], st[4] = out.x, out.v, out.ids
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt * 1e3 * n_total / n_used)
+    value = float(np.mean(times))
+    sample = (f"each step: one oracle step of each of the {len(states)} smallest of the {len(cfgs)} scenes "
+              f"({n_used} of {n_total} particles), time x {n_total / n_used:.3g}")
+    line = {"impl": "reference", "metric": "batched APBF ms/step for 256 independent scenes vs one at a time",
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "apbf_batch_256", "scenes": len(cfgs), "particles": n_total,
+                       "n_range": f"{c0.n_min}..{c0.n_max}", "lod": "distance to camera"},
+            "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ocean_1m", choices=["ocean_1m", "dam_break_131k", "dam_break_4k"])
+    ap.add_argument("--workload", default="ocean_1m",
+                    choices=["ocean_1m", "dam_break_131k", "dam_break_4k", "batch_256"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pbf", action="store_true")
@@ -347,12 +553,22 @@ def main():
     torch.cuda.set_device(d.local)
     build.build()
     apbf.lib()
+    if args.workload == "batch_256":
+        return run_batch(args, apbf, torch, d)
     cfg = workload(args.workload, "apbf")
     pbf_cfg = workload(args.workload, "pbf")
     rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))
 
     scene = make_scene(apbf, cfg, rho0)
     pbf = None if args.no_pbf else make_scene(apbf, pbf_cfg, rho0)
+    tuning = {}
+    if not args.no_autotune:
+        # trial steps run on a snapshot that the tuner restores, so the timed trajectory is unchanged
+        drive(apbf, scene, cfg, 0)
+        tuning["apbf"] = tune_summary(apbf.apbf_autotune(scene, 4))
+        if pbf is not None:
+            drive(apbf, pbf, pbf_cfg, 0)
+            tuning["pbf_nmax"] = tune_summary(apbf.apbf_autotune(pbf, 4))
     torch.cuda.synchronize()
 
     clocks = ClockSampler(torch.cuda.current_device())
@@ -426,7 +642,8 @@ def main():
                    "lod": "distance to camera, automatic range", "pbf_n": pbf_cfg.n_max,
                    "parallelism": f"replicas x{d.ws}" if d.ws > 1 else "single GPU",
                    "l2": "no flush: each step touches ~0.3 GB (> 129 MB L2)",
-                   "launch": "captured CUDA graph per step"},
+                   "launch": "captured CUDA graph per step",
+                   "tuning": tuning or "defaults (block 256, compacted levels)"},
         "p50_ms": metrics.percentile(per, 50), "p99_ms": metrics.percentile(per, 99),
         "particle_iterations_per_step": particle_iters_per_step,
         "particle_iterations_per_s": d.sum(particle_iters_per_step / (ms_step * 1e-3)),

@@ -129,12 +129,14 @@ def config_ocean_1m(lod_mode: int = LOD_DTC, n_min: int = 3, n_max: int = 15) ->
 
 
 def config_batch_256(count: int = 256, seed: int = 1608_04721, n_lo: int = 2048, n_hi: int = 65536,
-                     n_min: int = 4, n_max: int = 8, steps: int = 100):
+                     n_min: int = 4, n_max: int = 8, steps: int = 100, dt: float = 0.0016):
     """Independent dam-break scenes for batched stepping: particle counts
     log-uniform in [n_lo, n_hi], block aspect ratio (x : y) uniform in 1..4
     with depth z = y, the block in the low-x half of a box twice its length
     and 1.5 times its height, a camera 3 m outside the box's x = 0 wall at a
-    random height; N_i in n_min..n_max from the distance to the camera."""
+    random height; N_i in n_min..n_max from the distance to the camera.
+    The time step is the paper's 0.0016 s (Sec. 7): at 1/60 s the tallest
+    columns (about 1.75 m) collapse within 50 steps at 4..8 iterations."""
     u = uniform01(seed, 2, 4 * count).reshape(count, 4)
     out = []
     for k in range(count):
@@ -149,7 +151,7 @@ def config_batch_256(count: int = 256, seed: int = 1608_04721, n_lo: int = 2048,
         eye = (-3.0, 0.5 * box_hi[1], float(0.2 + u[k, 2] * box_hi[2]))
         out.append(SceneConfig(name=f"batch_{k:03d}", lattice=(nx, ny, nz), spacing=s, block_lo=(0.0, 0.0, 0.0),
                                box_lo=(0.0, 0.0, 0.0), box_hi=box_hi, n_min=n_min, n_max=n_max, lod_mode=LOD_DTC,
-                               steps=steps, seed=seed + 7919 * (k + 1), camera="fixed", eye=eye))
+                               steps=steps, seed=seed + 7919 * (k + 1), camera="fixed", eye=eye, dt=dt))
     return out
 
 
