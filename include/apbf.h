@@ -292,6 +292,97 @@ APBF_API apbf_status apbf_set_tuning(apbf_scene *scene, uint32_t block, float ma
  * Synchronises; the state and the results of later steps are unchanged. */
 APBF_API apbf_status apbf_autotune(apbf_scene *scene, uint32_t trial_steps, apbf_tune_result *out);
 
+/* ------------------------------------------------------------- serving */
+
+/*
+ * A server steps many independent scenes that arrive and leave over time (the
+ * paper's real-time setting, Sec. 1 and Sec. 7, with one simulation per client
+ * instead of one per application). Requests wait in a FIFO queue and are
+ * admitted, in arrival order, into one resident device pool while the pool's
+ * particle, cell and scene capacities have room; a request that does not fit
+ * waits (no later request overtakes it). Each apbf_server_tick() advances every
+ * resident scene by one step of Fig. 7, all of them in one batched step (one
+ * launch per stage). A scene leaves the pool at the first tick after its last
+ * step, when its final state is copied to the caller's buffers. A scene's
+ * result is bit-identical to the same scene stepped alone with
+ * apbf_create_scene / apbf_set_camera(eye, auto range) / apbf_step(steps).
+ * Every request must agree with the server's physics description in
+ * everything but n, pos, vel, grid_lo/hi and box_lo/hi. Calls on one server
+ * are not thread-safe. A device error of the pool (neighbour-list overflow,
+ * CUDA error) fails every resident request and sticks to the server.
+ */
+typedef struct apbf_server apbf_server;
+
+typedef struct apbf_server_desc {
+    const apbf_scene_desc *physics; /* host: h, dt, mass, rho0, eps, s_corr, XSPH, gravity, n_min/n_max,
+                                       lod_mode, max_neighbors, flags shared by every request (its n, pos,
+                                       vel, grid and box are ignored) */
+    uint32_t max_particles;         /* resident particle capacity (< 2^27); 0 = the most that budget_bytes holds */
+    uint32_t max_cells;             /* resident grid-cell capacity (< 2^31); 0 = 4 x max_particles */
+    uint32_t max_scenes;            /* resident scenes (<= 65535); 0 = 4096 */
+    size_t budget_bytes;            /* device bytes the pool may use; 0 = no limit (max_particles required) */
+} apbf_server_desc;
+
+typedef struct apbf_request {
+    const apbf_scene_desc *scene;   /* host; n >= 1, pos, vel (may be NULL), grid, box copied at submit */
+    float eye[3];                   /* DTC camera position (automatic distance range, Sec. 4.1) */
+    uint32_t steps;                 /* steps to run, >= 1 */
+    float *pos_out, *vel_out;       /* host, 3n floats each in particle-id order, or NULL; written by the tick
+                                       that retires the request; the caller keeps them valid until then */
+} apbf_request;
+
+typedef struct apbf_tick_info {
+    uint64_t tick;                  /* index of this tick (0, 1, ...) */
+    uint32_t resident_scenes;       /* scenes stepped by this tick */
+    uint32_t resident_particles;    /* their particles */
+    uint32_t admitted;              /* requests admitted by this tick */
+    uint32_t completed;             /* requests retired (results written) by this tick */
+    uint32_t queued;                /* requests still waiting */
+    uint32_t pad;
+    double prev_step_ms;            /* device time of the previous tick's step (0 if it stepped nothing) */
+} apbf_tick_info;
+
+#define APBF_REQ_QUEUED 0u
+#define APBF_REQ_RESIDENT 1u
+#define APBF_REQ_DONE 2u
+#define APBF_REQ_FAILED 3u
+
+typedef struct apbf_request_info {
+    uint32_t state;                 /* APBF_REQ_* */
+    uint32_t steps_done;
+    uint32_t n, steps;
+    uint64_t submit_tick, admit_tick, done_tick; /* tick counter at submit, admission, retirement */
+} apbf_request_info;
+
+/* Pool bytes and resolved capacities of a description (host-only, no GPU);
+ * each output may be NULL. APBF_ERR_OUT_OF_MEMORY if the capacities exceed
+ * budget_bytes. */
+APBF_API apbf_status apbf_server_bytes(const apbf_server_desc *desc, size_t *bytes, uint32_t *max_particles,
+                                       uint32_t *max_cells);
+
+/* Create a server on the current device; its pool is allocated (cudaMalloc)
+ * once, here. cuda_stream as in apbf_create_scene. */
+APBF_API apbf_status apbf_server_create(const apbf_server_desc *desc, void *cuda_stream, apbf_server **out);
+
+/* Queue a request (validated and copied; APBF_ERR_INVALID_ARG if it could never
+ * fit the pool alone). ticket (host) receives its id. Does not touch the GPU. */
+APBF_API apbf_status apbf_server_submit(apbf_server *server, const apbf_request *req, uint64_t *ticket);
+
+/* One tick: wait for the previous tick's step, retire the scenes it finished
+ * (results to their buffers), close the pool's gaps, admit queued requests,
+ * and enqueue one step of every resident scene (returns before it finishes).
+ * info (host, may be NULL) receives the tick's counts. */
+APBF_API apbf_status apbf_server_tick(apbf_server *server, apbf_tick_info *info);
+
+/* State of a request (host output). */
+APBF_API apbf_status apbf_server_query(apbf_server *server, uint64_t ticket, apbf_request_info *info);
+
+/* Last error message of the server (or of the last failed create when NULL). */
+APBF_API const char *apbf_server_last_error(const apbf_server *server);
+
+/* Release the server (NULL-safe); synchronises. Unfinished requests are dropped. */
+APBF_API void apbf_server_destroy(apbf_server *server);
+
 /* ----------------------------------------------------- test-only exports */
 
 /* Run one fresh step of the current state up to and including a stage

@@ -83,12 +83,61 @@ class apbf_tune_result(C.Structure):
     ]
 
 
+class apbf_server_desc(C.Structure):
+    _fields_ = [
+        ("physics", C.POINTER(apbf_scene_desc)),
+        ("max_particles", C.c_uint32),
+        ("max_cells", C.c_uint32),
+        ("max_scenes", C.c_uint32),
+        ("budget_bytes", C.c_size_t),
+    ]
+
+
+class apbf_request(C.Structure):
+    _fields_ = [
+        ("scene", C.POINTER(apbf_scene_desc)),
+        ("eye", C.c_float * 3),
+        ("steps", C.c_uint32),
+        ("pos_out", C.POINTER(C.c_float)),
+        ("vel_out", C.POINTER(C.c_float)),
+    ]
+
+
+class apbf_tick_info(C.Structure):
+    _fields_ = [
+        ("tick", C.c_uint64),
+        ("resident_scenes", C.c_uint32),
+        ("resident_particles", C.c_uint32),
+        ("admitted", C.c_uint32),
+        ("completed", C.c_uint32),
+        ("queued", C.c_uint32),
+        ("pad", C.c_uint32),
+        ("prev_step_ms", C.c_double),
+    ]
+
+
+class apbf_request_info(C.Structure):
+    _fields_ = [
+        ("state", C.c_uint32),
+        ("steps_done", C.c_uint32),
+        ("n", C.c_uint32),
+        ("steps", C.c_uint32),
+        ("submit_tick", C.c_uint64),
+        ("admit_tick", C.c_uint64),
+        ("done_tick", C.c_uint64),
+    ]
+
+
+APBF_REQ_QUEUED, APBF_REQ_RESIDENT, APBF_REQ_DONE, APBF_REQ_FAILED = 0, 1, 2, 3
+
 EXPORTS = [
     "apbf_status_string", "apbf_rest_density", "apbf_scene_bytes", "apbf_create_scene", "apbf_set_camera",
     "apbf_set_box", "apbf_step", "apbf_read_state", "apbf_density_stats", "apbf_get_step_info", "apbf_sync",
     "apbf_last_error", "apbf_destroy_scene", "apbf_set_timing", "apbf_timing_report", "apbf_debug_step_to",
     "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
-    "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune",
+    "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune", "apbf_server_bytes",
+    "apbf_server_create", "apbf_server_submit", "apbf_server_tick", "apbf_server_query", "apbf_server_last_error",
+    "apbf_server_destroy",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -147,8 +196,18 @@ def lib():
         L.apbf_autotune.argtypes = [V, C.c_uint32, P(apbf_tune_result)]
         L.apbf_density_stats_static.argtypes = [V, C.c_uint32, C.c_float, C.c_float, C.c_float, P(C.c_float),
                                                 P(C.c_float), V, V]
+        L.apbf_server_bytes.argtypes = [P(apbf_server_desc), P(C.c_size_t), P(C.c_uint32), P(C.c_uint32)]
+        L.apbf_server_create.argtypes = [P(apbf_server_desc), V, P(V)]
+        L.apbf_server_submit.argtypes = [V, P(apbf_request), P(C.c_uint64)]
+        L.apbf_server_tick.argtypes = [V, P(apbf_tick_info)]
+        L.apbf_server_query.argtypes = [V, C.c_uint64, P(apbf_request_info)]
+        L.apbf_server_last_error.restype = C.c_char_p
+        L.apbf_server_last_error.argtypes = [V]
+        L.apbf_server_destroy.restype = None
+        L.apbf_server_destroy.argtypes = [V]
         for f in EXPORTS:
-            if f not in ("apbf_status_string", "apbf_last_error", "apbf_destroy_scene"):
+            if f not in ("apbf_status_string", "apbf_last_error", "apbf_destroy_scene", "apbf_server_last_error",
+                         "apbf_server_destroy"):
                 getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -499,3 +558,104 @@ def apbf_autotune(scene: Scene, trial_steps: int = 5) -> dict:
     trials = [(int(r.blocks[k]), float(r.thresholds[k]), float(r.ms[k])) for k in range(r.tried)]
     return dict(block=int(r.block), mask_threshold=float(r.mask_threshold), ms_per_step=float(r.ms_per_step),
                 trials=trials)
+
+
+# ---------------------------------------------------------------- serving
+
+
+class Server:
+    """Handle of an apbf_server; keeps submitted requests' output buffers alive
+    until they are retired."""
+
+    def __init__(self, handle, physics_keep, max_particles, max_cells):
+        self.handle = handle
+        self._physics_keep = physics_keep
+        self._outputs = {}
+        self.max_particles = max_particles
+        self.max_cells = max_cells
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().apbf_server_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _server_check(st: int, where: str, server=None):
+    if st != APBF_OK:
+        h = server.handle if server is not None else None
+        raise ApbfError(st, where, lib().apbf_server_last_error(h).decode())
+
+
+def _server_desc(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0):
+    phys = physics[0] if isinstance(physics, tuple) else physics
+    d = apbf_server_desc()
+    d.physics = C.pointer(phys)
+    d.max_particles, d.max_cells, d.max_scenes, d.budget_bytes = max_particles, max_cells, max_scenes, budget_bytes
+    return d, phys
+
+
+def apbf_server_bytes(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0):
+    """(pool bytes, particle capacity, cell capacity) of a server description."""
+    d, _ = _server_desc(physics, max_particles, max_cells, max_scenes, budget_bytes)
+    nb, npart, ncell = C.c_size_t(), C.c_uint32(), C.c_uint32()
+    _server_check(lib().apbf_server_bytes(C.byref(d), C.byref(nb), C.byref(npart), C.byref(ncell)),
+                  "apbf_server_bytes")
+    return nb.value, npart.value, ncell.value
+
+
+def apbf_server_create(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0, stream=None) -> Server:
+    d, phys = _server_desc(physics, max_particles, max_cells, max_scenes, budget_bytes)
+    _, npart, ncell = apbf_server_bytes(physics, max_particles, max_cells, max_scenes, budget_bytes)
+    stream_ptr, _, _, _ = _stream_and_arena(lambda: 0, stream, None)
+    h = C.c_void_p()
+    _server_check(lib().apbf_server_create(C.byref(d), C.c_void_p(stream_ptr), C.byref(h)), "apbf_server_create")
+    return Server(h, phys, npart, ncell)
+
+
+def apbf_server_submit(server: Server, desc, eye, steps: int, want_pos=True, want_vel=False) -> int:
+    """Queue a scene (a make_desc / desc_from_config pair or an apbf_scene_desc);
+    returns its ticket. Results: apbf_server_result(server, ticket) once done."""
+    d = desc[0] if isinstance(desc, tuple) else desc
+    n = int(d.n)
+    pos = np.empty((n, 3), np.float32) if want_pos else None
+    vel = np.empty((n, 3), np.float32) if want_vel else None
+    r = apbf_request()
+    r.scene = C.pointer(d)
+    r.eye[:] = [float(e) for e in eye]
+    r.steps = steps
+    r.pos_out = _fptr(pos)
+    r.vel_out = _fptr(vel)
+    t = C.c_uint64()
+    _server_check(lib().apbf_server_submit(server.handle, C.byref(r), C.byref(t)), "apbf_server_submit", server)
+    server._outputs[t.value] = (pos, vel)
+    return t.value
+
+
+def apbf_server_tick(server: Server) -> dict:
+    info = apbf_tick_info()
+    _server_check(lib().apbf_server_tick(server.handle, C.byref(info)), "apbf_server_tick", server)
+    return {f: getattr(info, f) for f, _ in apbf_tick_info._fields_ if f != "pad"}
+
+
+def apbf_server_query(server: Server, ticket: int) -> dict:
+    info = apbf_request_info()
+    _server_check(lib().apbf_server_query(server.handle, ticket, C.byref(info)), "apbf_server_query", server)
+    return {f: getattr(info, f) for f, _ in apbf_request_info._fields_}
+
+
+def apbf_server_result(server: Server, ticket: int):
+    """(pos, vel) arrays of a finished request (None where not requested); the
+    server stops holding them."""
+    q = apbf_server_query(server, ticket)
+    if q["state"] != APBF_REQ_DONE:
+        raise ApbfError(APBF_ERR_BAD_STATE, "apbf_server_result", f"request {ticket} is not done (state {q['state']})")
+    return server._outputs.pop(ticket)
+
+
+def apbf_server_destroy(server: Server):
+    if server.handle:
+        lib().apbf_server_destroy(server.handle)
+        server.handle = None

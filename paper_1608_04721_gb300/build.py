@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libapbf.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["kernels.cu", "apbf_capi.cu", "density_static.cu"]
+SOURCES = ["kernels.cu", "apbf_capi.cu", "density_static.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off,-fvisibility=hidden",
               "-I", INCLUDE, "-I", CSRC]

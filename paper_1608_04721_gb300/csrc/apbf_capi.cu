@@ -47,6 +47,9 @@ apbf_status cuda_fail(apbf_scene *s, cudaError_t e, const char *where)
 
 bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
+}  // namespace
+
+namespace apbf {
 // Derived constants of a description; returns an error message or "".
 std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
 {
@@ -160,6 +163,19 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     return "";
 }
 
+bool same_physics(const apbf_scene_desc &a, const apbf_scene_desc &d)
+{
+    bool same = a.h == d.h && a.dt == d.dt && a.mass == d.mass && a.rho0 == d.rho0 && a.eps == d.eps &&
+                a.scorr_k == d.scorr_k && a.scorr_dq == d.scorr_dq && a.scorr_n == d.scorr_n &&
+                a.xsph_c == d.xsph_c && a.n_min == d.n_min && a.n_max == d.n_max && a.lod_mode == d.lod_mode &&
+                a.stabil_s == d.stabil_s && a.max_neighbors == d.max_neighbors && a.flags == d.flags;
+    for (int ax = 0; ax < 3; ++ax)
+        same = same && a.gravity[ax] == d.gravity[ax];
+    return same;
+}
+}  // namespace apbf
+
+namespace {
 // Validation and derived constants of a batch: every scene is validated on
 // its own; the physics (everything but particles, grid and box) must match
 // scene 0; the scenes' particles and cells are concatenated.
@@ -182,14 +198,7 @@ std::string derive_batch(const apbf_scene_desc *descs, uint32_t count, StepConst
         if (k == 0) {
             sc = sk;
         } else {
-            const apbf_scene_desc &a = descs[0], &d = descs[k];
-            bool same = a.h == d.h && a.dt == d.dt && a.mass == d.mass && a.rho0 == d.rho0 && a.eps == d.eps &&
-                        a.scorr_k == d.scorr_k && a.scorr_dq == d.scorr_dq && a.scorr_n == d.scorr_n &&
-                        a.xsph_c == d.xsph_c && a.n_min == d.n_min && a.n_max == d.n_max && a.lod_mode == d.lod_mode &&
-                        a.stabil_s == d.stabil_s && a.max_neighbors == d.max_neighbors && a.flags == d.flags;
-            for (int ax = 0; ax < 3; ++ax)
-                same = same && a.gravity[ax] == d.gravity[ax];
-            if (!same)
+            if (!same_physics(descs[0], descs[k]))
                 return "scene " + std::to_string(k) + " differs from scene 0 in a physics parameter";
         }
         SceneGeom &g = geo[k];
@@ -231,6 +240,9 @@ struct Layout {
     }
 };
 
+}  // namespace
+
+namespace apbf {
 // Carves the arena; with base == nullptr only measures.
 size_t carve(const StepConst &sc, char *base, Buffers &b)
 {
@@ -281,6 +293,9 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.dstats = (double *)P(32);
     return L.total;
 }
+}  // namespace apbf
+
+namespace {
 
 cudaEvent_t get_event(apbf_scene *s)
 {
@@ -391,10 +406,10 @@ apbf_status upload_dyn(apbf_scene *s)
     int k = s->dyn_slot;
     s->dyn_slot = (s->dyn_slot + 1) % 16;
     APBF_CUDA(s, cudaEventSynchronize(s->dyn_ev[k]));  // the previous copy out of this slot is done
-    const size_t cnt = s->dyn.size();
-    std::memcpy(s->dyn_pinned + k * cnt, s->dyn.data(), sizeof(DynParams) * cnt);
-    APBF_CUDA(s, cudaMemcpyAsync(s->b.dyn, s->dyn_pinned + k * cnt, sizeof(DynParams) * cnt, cudaMemcpyHostToDevice,
-                                 s->stream));
+    const size_t cnt = s->dyn.size();  // <= dyn_cap, the stride of the ring's slots
+    std::memcpy(s->dyn_pinned + k * s->dyn_cap, s->dyn.data(), sizeof(DynParams) * cnt);
+    APBF_CUDA(s, cudaMemcpyAsync(s->b.dyn, s->dyn_pinned + k * s->dyn_cap, sizeof(DynParams) * cnt,
+                                 cudaMemcpyHostToDevice, s->stream));
     APBF_CUDA(s, cudaEventRecord(s->dyn_ev[k], s->stream));
     s->dyn_dirty = false;
     return APBF_OK;
@@ -506,6 +521,74 @@ APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes
     return apbf_batch_bytes(desc, 1, bytes);
 }
 
+}  // extern "C"
+
+namespace apbf {
+// A scene object whose arena is carved for `cap` (particles, cells, scenes of
+// the largest membership it will hold), zeroed on its stream; nothing is
+// uploaded and no geometry is set.
+apbf_status alloc_scene(const StepConst &cap, uint32_t flags, void *cuda_stream, void *device_arena,
+                        size_t arena_bytes, apbf_scene **out, std::string &msg)
+{
+    *out = nullptr;
+    if (device_arena && ((uintptr_t)device_arena % kAlign)) {
+        msg = "device_arena must be 256-byte aligned";
+        return APBF_ERR_INVALID_ARG;
+    }
+    apbf_scene *s = new (std::nothrow) apbf_scene();
+    if (!s) {
+        msg = "host allocation failed";
+        return APBF_ERR_OUT_OF_MEMORY;
+    }
+    s->sc = cap;
+    s->dyn_cap = cap.scenes;
+    s->flags = flags;
+    s->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](apbf_status code, const std::string &m) {
+        msg = m;
+        apbf_destroy_scene(s);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    const size_t need = carve(cap, nullptr, s->b);
+    if (device_arena) {
+        if (arena_bytes < need)
+            return bail(APBF_ERR_OUT_OF_MEMORY, "device_arena is smaller than the bytes the scene needs");
+        s->arena = device_arena;
+        s->arena_bytes = arena_bytes;
+    } else {
+        e = cudaMalloc(&s->arena, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->arena = nullptr;
+            return bail(APBF_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        s->own_arena = true;
+        s->arena_bytes = need;
+    }
+    carve(cap, (char *)s->arena, s->b);
+    if ((e = cudaHostAlloc(&s->pinned_small, 4096, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaHostAlloc((void **)&s->dyn_pinned, 16 * sizeof(DynParams) * (size_t)cap.scenes,
+                           cudaHostAllocDefault)) != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 16; ++k)
+        if ((e = cudaEventCreateWithFlags(&s->dyn_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(APBF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    if ((e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    if ((e = cudaMemsetAsync(s->arena, 0, need, s->stream)) != cudaSuccess)
+        return bail(APBF_ERR_CUDA, std::string("arena memset: ") + cudaGetErrorString(e));
+    s->grid_iter = s->sms > 0 ? s->sms : 1;  // the launchers scale by each kernel's occupancy
+    *out = s;
+    return APBF_OK;
+}
+}  // namespace apbf
+
+extern "C" {
+
 APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t count, void *cuda_stream,
                                        void *device_arena, size_t arena_bytes, apbf_scene **out)
 {
@@ -530,13 +613,11 @@ APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t co
                     return fail(nullptr, APBF_ERR_INVALID_ARG,
                                 who + "particle " + std::to_string(i) + " lies outside the grid");
     }
-    if (device_arena && ((uintptr_t)device_arena % kAlign))
-        return fail(nullptr, APBF_ERR_INVALID_ARG, "device_arena must be 256-byte aligned");
-
-    apbf_scene *s = new (std::nothrow) apbf_scene();
-    if (!s)
-        return fail(nullptr, APBF_ERR_OUT_OF_MEMORY, "host allocation failed");
-    s->sc = sc;
+    apbf_scene *s = nullptr;
+    std::string amsg;
+    st = alloc_scene(sc, descs[0].flags, cuda_stream, device_arena, arena_bytes, &s, amsg);
+    if (st != APBF_OK)
+        return fail(nullptr, st, amsg);
     s->geo = geo;
     s->grid_hi3.resize(3 * (size_t)count);
     s->dyn.assign(count, DynParams{});
@@ -547,46 +628,14 @@ APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t co
             s->dyn[k].box_hi[a] = descs[k].box_hi[a];
             s->dyn[k].auto_range = 1;
         }
-    s->flags = descs[0].flags;
-    s->stream = (cudaStream_t)cuda_stream;
     auto bail = [&](apbf_status code, const std::string &msg) {
         g_create_error = msg;
         apbf_destroy_scene(s);
         return code;
     };
-    cudaError_t e = cudaGetDevice(&s->device);
-    if (e != cudaSuccess)
-        return bail(APBF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
-    size_t need = carve(sc, nullptr, s->b);
-    if (device_arena) {
-        if (arena_bytes < need)
-            return bail(APBF_ERR_OUT_OF_MEMORY, "device_arena is smaller than apbf_batch_bytes()");
-        s->arena = device_arena;
-        s->arena_bytes = arena_bytes;
-    } else {
-        e = cudaMalloc(&s->arena, need);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            s->arena = nullptr;
-            return bail(APBF_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        }
-        s->own_arena = true;
-        s->arena_bytes = need;
-    }
-    carve(sc, (char *)s->arena, s->b);
+    cudaError_t e;
     const Buffers &b = s->b;
     const size_t n = sc.n;
-
-    if ((e = cudaHostAlloc(&s->pinned_small, 4096, cudaHostAllocDefault)) != cudaSuccess ||
-        (e = cudaHostAlloc((void **)&s->dyn_pinned, 16 * sizeof(DynParams) * (size_t)count, cudaHostAllocDefault)) !=
-            cudaSuccess)
-        return bail(APBF_ERR_CUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
-    for (int k = 0; k < 16; ++k)
-        if ((e = cudaEventCreateWithFlags(&s->dyn_ev[k], cudaEventDisableTiming)) != cudaSuccess)
-            return bail(APBF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
-    if ((e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(APBF_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
 
     // initial state: the scenes' particles concatenated, each in its id order;
     // global id = scene's first slot + id within the scene
@@ -608,8 +657,7 @@ APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t co
     for (uint32_t l = 0; l <= sc.n_max; ++l)
         lc[l] = sc.n;  // every particle is active in every iteration until a partition says otherwise
     cudaStream_t st0 = s->stream;
-    if ((e = cudaMemsetAsync(s->arena, 0, need, st0)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(b.state_x, hx.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(b.state_x, hx.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b.state_v, hv.data(), 16 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b.state_id, hid.data(), 4 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
         (e = cudaMemcpyAsync((void *)b.sid, hsid.data(), 2 * n, cudaMemcpyHostToDevice, st0)) != cudaSuccess ||
@@ -619,7 +667,6 @@ APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t co
         (e = cudaStreamSynchronize(st0)) != cudaSuccess)
         return bail(APBF_ERR_CUDA, std::string("initial upload: ") + cudaGetErrorString(e));
     s->dyn_dirty = true;
-    s->grid_iter = s->sms > 0 ? s->sms : 1;  // the launchers scale by each kernel's occupancy
     *out = s;
     return APBF_OK;
 }
@@ -909,7 +956,9 @@ APBF_API apbf_status apbf_timing_report(apbf_scene *s, double *ms, uint64_t *lau
     return APBF_OK;
 }
 
-namespace {
+}  // extern "C"
+
+namespace apbf {
 void drop_graph(apbf_scene *s)
 {
     if (s->gexec)
@@ -919,7 +968,10 @@ void drop_graph(apbf_scene *s)
     s->gexec = nullptr;
     s->graph = nullptr;
 }
+}  // namespace apbf
 
+extern "C" {
+namespace {
 apbf_status copy_state(apbf_scene *s, bool to_snapshot)
 {
     const Buffers &b = s->b;

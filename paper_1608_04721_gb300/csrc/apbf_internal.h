@@ -137,7 +137,8 @@ struct apbf_scene {
     std::vector<apbf::DynParams> dyn;
     std::vector<float> grid_hi3;             // per scene static grid upper bounds (3 each)
     bool dyn_dirty = true;
-    apbf::DynParams *dyn_pinned = nullptr;  // ring of 16 pinned upload slots of `scenes` entries
+    apbf::DynParams *dyn_pinned = nullptr;  // ring of 16 pinned upload slots of dyn_cap entries each
+    uint32_t dyn_cap = 1;                   // scenes the arena was carved for
     cudaEvent_t dyn_ev[16] = {};
     int dyn_slot = 0;
     // graph
@@ -180,5 +181,14 @@ cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const floa
 cudaError_t launch_debug_lambda(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);
 cudaError_t launch_fixed_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
 int iteration_grid(int sms);
+
+// Host helpers shared by the scene / batch entry points and the server (apbf_capi.cu).
+std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st);
+bool same_physics(const apbf_scene_desc &a, const apbf_scene_desc &d);
+size_t carve(const StepConst &sc, char *base, Buffers &b);
+apbf_status alloc_scene(const StepConst &cap, uint32_t flags, void *cuda_stream, void *device_arena,
+                        size_t arena_bytes, apbf_scene **out, std::string &msg);
+void drop_graph(apbf_scene *s);
+void set_last_error_message(const std::string &m);
 
 }  // namespace apbf

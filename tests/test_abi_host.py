@@ -25,7 +25,7 @@ def _declared():
 
 def test_exports_every_declared_symbol():
     names = _declared()
-    assert len(names) == 25
+    assert len(names) == 32
     out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout
     exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
@@ -120,3 +120,39 @@ def test_batch_validation_on_the_host():
     assert apbf.apbf_batch_bytes([a, c]) > apbf.apbf_batch_bytes([a])
     with pytest.raises(apbf.ApbfError):
         apbf.apbf_create_batch([], stream=0, device_arena=None)
+
+
+def test_server_capacity_from_budget():
+    phys = _desc()
+    b_small, n_small, c_small = apbf.apbf_server_bytes(phys, budget_bytes=1 << 30)
+    b_big, n_big, c_big = apbf.apbf_server_bytes(phys, budget_bytes=150 * 10**9)
+    # the largest particle capacity that fits: one more particle no longer fits
+    assert b_small <= 1 << 30 and n_small > 0 and c_small == 4 * n_small
+    over, _, _ = apbf.apbf_server_bytes(phys, max_particles=n_small + 1)
+    assert over > 1 << 30
+    # 150 GB holds more than the 27-bit slot space: the capacity stops at 2^27 - 1
+    assert n_big == (1 << 27) - 1 and b_big <= 150 * 10**9
+    # explicit capacities; bytes grow with each of them
+    b1, n1, c1 = apbf.apbf_server_bytes(phys, max_particles=100000, max_cells=50000, max_scenes=16)
+    assert (n1, c1) == (100000, 50000)
+    assert apbf.apbf_server_bytes(phys, max_particles=200000, max_cells=50000, max_scenes=16)[0] > b1
+    assert apbf.apbf_server_bytes(phys, max_particles=100000, max_cells=90000, max_scenes=16)[0] > b1
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(), apbf.APBF_ERR_INVALID_ARG),                                   # neither capacity nor budget
+    (dict(budget_bytes=1000), apbf.APBF_ERR_OUT_OF_MEMORY),                # not even one particle
+    (dict(max_particles=1 << 27), apbf.APBF_ERR_INVALID_ARG),              # beyond the slot space
+    (dict(max_particles=1000, max_scenes=70000), apbf.APBF_ERR_INVALID_ARG),
+    (dict(max_particles=10**7, budget_bytes=10**6), apbf.APBF_ERR_OUT_OF_MEMORY),
+])
+def test_server_bytes_rejects(kw, status):
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_server_bytes(_desc(), **kw)
+    assert e.value.status == status
+
+
+def test_server_bytes_rejects_bad_physics():
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_server_bytes(_desc(h=0.0), max_particles=1000)
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG

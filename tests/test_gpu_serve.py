@@ -1,0 +1,130 @@
+"""Serving loop: scenes arrive over time, queue for room in the resident pool,
+are stepped together one step per tick and leave when done. Each scene's
+result must be bit-identical to the same scene stepped alone, whatever else
+shared the pool with it, wherever it sat in the pool, and whether it ran
+alone (the single-scene kernels) or in a batch."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_04721_gb300 import apbf, build, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    apbf.lib()
+
+
+def _configs(count, seed):
+    cfgs = scenes.config_batch_256(count=count, seed=seed, n_lo=400, n_hi=4000, n_min=3, n_max=7)
+    out = []
+    for k, c in enumerate(cfgs):
+        if k % 3 == 2:  # a grid away from the origin
+            c = c.replace(block_lo=(0.5, -1.0, 0.3), box_lo=(0.5, -1.0, 0.3),
+                          box_hi=(c.box_hi[0] + 0.5, c.box_hi[1] - 1.0, c.box_hi[2] + 0.3),
+                          eye=(c.eye[0] + 0.5, c.eye[1] - 1.0, c.eye[2]))
+        out.append(c)
+    return out
+
+
+def _alone(desc, eye, steps):
+    s = apbf.apbf_create_scene(desc)
+    apbf.apbf_set_camera(s, eye)
+    apbf.apbf_step(s, steps)
+    st = apbf.apbf_read_state(s, pos=True, vel=True)
+    apbf.apbf_destroy_scene(s)
+    return st["pos"], st["vel"]
+
+
+def test_each_scene_matches_itself_alone_bitwise():
+    cfgs = _configs(9, 31)
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    descs = [apbf.desc_from_config(c, *scenes.make_scene(c), r0) for c in cfgs]
+    steps = [6, 3, 9, 4, 7, 2, 5, 8, 3]
+    arrive = [0, 3, 3, 4, 6, 6, 7, 12, 12]   # scene 0 runs alone for three ticks
+    largest = max(c.n for c in cfgs)
+    srv = apbf.apbf_server_create(descs[0], max_particles=int(2.2 * largest), max_cells=4 * 10**6, max_scenes=8)
+    tickets = {}
+    log = []
+    tick = 0
+    while True:
+        for k in range(len(cfgs)):
+            if arrive[k] == tick:
+                tickets[k] = apbf.apbf_server_submit(srv, descs[k], cfgs[k].eye, steps[k], want_pos=True,
+                                                     want_vel=True)
+        info = apbf.apbf_server_tick(srv)
+        log.append(info)
+        tick += 1
+        if len(tickets) == len(cfgs) and info["resident_scenes"] == 0 and info["queued"] == 0:
+            break
+        assert tick < 200
+    assert any(i["queued"] > 0 for i in log), "the capacity never made a request wait"
+    assert any(i["resident_scenes"] == 1 for i in log) and max(i["resident_scenes"] for i in log) >= 3
+    assert sum(i["admitted"] for i in log) == len(cfgs) == sum(i["completed"] for i in log)
+    for k in range(len(cfgs)):
+        q = apbf.apbf_server_query(srv, tickets[k])
+        assert q["state"] == apbf.APBF_REQ_DONE and q["steps_done"] == steps[k]
+        assert q["done_tick"] - q["admit_tick"] == steps[k]
+        pos, vel = apbf.apbf_server_result(srv, tickets[k])
+        ref_pos, ref_vel = _alone(descs[k], cfgs[k].eye, steps[k])
+        assert np.array_equal(pos, ref_pos), k
+        assert np.array_equal(vel, ref_vel), k
+    # FIFO: no request was admitted before one that arrived earlier
+    adm = [apbf.apbf_server_query(srv, tickets[k])["admit_tick"] for k in range(len(cfgs))]
+    order = sorted(range(len(cfgs)), key=lambda k: (arrive[k], k))
+    assert all(adm[a] <= adm[b] for a, b in zip(order, order[1:]))
+    apbf.apbf_server_destroy(srv)
+
+
+def test_one_scene_after_another_reuses_the_pool():
+    cfgs = _configs(3, 5)
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    descs = [apbf.desc_from_config(c, *scenes.make_scene(c), r0) for c in cfgs]
+    srv = apbf.apbf_server_create(descs[0], max_particles=max(c.n for c in cfgs), max_cells=4 * 10**6,
+                                  max_scenes=1)
+    t = [apbf.apbf_server_submit(srv, descs[k], cfgs[k].eye, 4 + k) for k in range(3)]
+    for _ in range(40):
+        info = apbf.apbf_server_tick(srv)
+        assert info["resident_scenes"] <= 1
+        if info["resident_scenes"] == 0 and info["queued"] == 0:
+            break
+    for k in range(3):
+        pos, _ = apbf.apbf_server_result(srv, t[k])
+        assert np.array_equal(pos, _alone(descs[k], cfgs[k].eye, 4 + k)[0]), k
+    apbf.apbf_server_destroy(srv)
+
+
+def test_server_rejects_what_can_never_run():
+    cfgs = _configs(2, 9)
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    d0 = apbf.desc_from_config(cfgs[0], *scenes.make_scene(cfgs[0]), r0)
+    srv = apbf.apbf_server_create(d0, max_particles=cfgs[0].n, max_cells=4 * 10**6, max_scenes=4)
+    # more particles than the pool holds
+    big = cfgs[0].replace(lattice=(cfgs[0].lattice[0] + 2,) + tuple(cfgs[0].lattice[1:]))
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_server_submit(srv, apbf.desc_from_config(big, *scenes.make_scene(big), r0), big.eye, 3)
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    # other physics
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_server_submit(srv, apbf.desc_from_config(cfgs[0], *scenes.make_scene(cfgs[0]), r0, dt=0.001),
+                                cfgs[0].eye, 3)
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_server_submit(srv, d0, cfgs[0].eye, 0)
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_server_query(srv, 12345)
+    # the server still works after rejected calls
+    t = apbf.apbf_server_submit(srv, d0, cfgs[0].eye, 2)
+    assert apbf.apbf_server_query(srv, t)["state"] == apbf.APBF_REQ_QUEUED
+    for _ in range(4):
+        apbf.apbf_server_tick(srv)
+    assert apbf.apbf_server_query(srv, t)["state"] == apbf.APBF_REQ_DONE
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_server_result(srv, 777)
+    apbf.apbf_server_destroy(srv)
