@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -402,6 +403,151 @@ def run_batch(args, apbf, torch, d):
     return 0
 
 
+SERVE_METRIC = "served APBF particle-steps/s, Poisson arrivals, budget-sized pool; queueing and latency"
+
+
+def run_serve(args, apbf, torch, d):
+    """Served scenes: Poisson arrivals (200/s) of dam breaks with 4096..262144
+    particles for 30..300 steps each (N_i in 5..10), admitted in arrival order
+    into one pool sized from an HBM budget, every resident scene stepped once
+    per tick. Runs for the arrival window on the wall clock; reports
+    throughput, queueing and latency. Each rank serves its own arrivals."""
+    temps = scenes.config_serve_templates()
+    arrivals = scenes.serve_arrivals(seconds=args.serve_seconds, templates=len(temps), seed=1608_04721 + 11 * d.rank)
+    c0 = temps[0]
+    rho0 = float(np.float32(apbf.apbf_rest_density(c0.h, c0.mass, c0.spacing)))
+    # the templates start at rest: no velocity arrays, so queued requests hold positions only
+    descs = [apbf.desc_from_config(c, scenes.make_scene(c)[0], None, rho0) for c in temps]
+    budget = int(args.serve_budget_gb * 1e9)
+    pool_bytes, cap_n, cap_c = apbf.apbf_server_bytes(descs[0], max_particles=args.serve_max_particles,
+                                                      budget_bytes=budget)
+    srv = apbf.apbf_server_create(descs[0], max_particles=args.serve_max_particles, budget_bytes=budget)
+    # warm-up: a few ticks of a few scenes (graph capture, first launches), then drain
+    for k in range(args.warmup):
+        apbf.apbf_server_submit(srv, descs[k % len(descs)], temps[k % len(temps)].eye, 3, want_pos=False)
+    while True:
+        info = apbf.apbf_server_tick(srv)
+        if info["resident_scenes"] == 0 and info["queued"] == 0:
+            break
+    torch.cuda.synchronize()
+    d.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    tick_start, infos, reqs = [], [], []
+    ai = 0
+    t0 = time.perf_counter()
+    first_tick = None
+    h2d = d2h = 0
+    idle = True
+    while True:
+        now = time.perf_counter() - t0
+        if now >= args.serve_seconds:
+            break
+        if idle and (ai >= len(arrivals) or arrivals[ai][0] > now):
+            # nothing resident or queued: wait for the next arrival instead of ticking empty
+            time.sleep(min(args.serve_seconds, arrivals[ai][0] if ai < len(arrivals) else args.serve_seconds) - now)
+            continue
+        while ai < len(arrivals) and arrivals[ai][0] <= now:
+            ta, k, steps = arrivals[ai]
+            tk = apbf.apbf_server_submit(srv, descs[k], temps[k].eye, steps, want_pos=True, want_vel=False)
+            reqs.append((tk, ta, k, steps))
+            ai += 1
+        tick_start.append(now)
+        info = apbf.apbf_server_tick(srv)
+        if first_tick is None:
+            first_tick = info["tick"]
+        infos.append(info)
+        idle = info["resident_scenes"] == 0 and info["queued"] == 0
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    d.barrier()
+    clock_info = clocks.stop()
+    stepped = [i["resident_particles"] for i in infos if i["resident_scenes"] > 0]
+    timeline = []
+    for sec in range(int(math.ceil(args.serve_seconds))):
+        ks = [k for k, t in enumerate(tick_start) if sec <= t < sec + 1]
+        if ks:
+            timeline.append([sec, len(ks), int(sum(infos[k]["resident_particles"] for k in ks)),
+                             int(max(infos[k]["resident_particles"] for k in ks)),
+                             int(max(infos[k]["resident_scenes"] for k in ks)), int(infos[ks[-1]]["queued"])])
+    step_ms = [infos[k + 1]["prev_step_ms"] for k in range(len(infos) - 1) if infos[k]["resident_scenes"] > 0]
+    particle_steps = float(sum(stepped))
+    waits, lat, done, adm = [], [], 0, 0
+    for tk, ta, k, steps in reqs:
+        q = apbf.apbf_server_query(srv, tk)
+        if q["state"] in (apbf.APBF_REQ_RESIDENT, apbf.APBF_REQ_DONE):
+            adm += 1
+            waits.append(tick_start[q["admit_tick"] - first_tick] - ta)
+            h2d += 24 * temps[k].n
+        if q["state"] == apbf.APBF_REQ_DONE:
+            done += 1
+            lat.append(tick_start[q["done_tick"] - first_tick] - ta)
+            d2h += 12 * temps[k].n
+            srv._outputs.pop(tk, None)
+    offered = sum(temps[k].n * steps for _, k, steps in arrivals) / args.serve_seconds
+    value = d.sum(particle_steps / elapsed)
+    ticks = len(stepped)
+    line = {
+        "metric": SERVE_METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": d.ws,
+        "steps": ticks, "warmup": args.warmup, "ms_per_step": metrics.percentile(step_ms, 50) if step_ms else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "apbf_serve", "arrivals_per_s": 200.0, "seconds": args.serve_seconds,
+                   "particles_per_scene": "log-uniform 4096..262144 (64 seeded templates)",
+                   "steps_per_scene": "uniform 30..300", "n_range": f"{c0.n_min}..{c0.n_max}",
+                   "budget_gb": args.serve_budget_gb, "pool_gb": pool_bytes / 1e9,
+                   "capacity_particles": cap_n, "capacity_cells": cap_c,
+                   "admission": "FIFO while particles, cells and scenes fit the pool",
+                   "l2": "no flush: resident state far above 129 MB", "launch": "one captured graph per membership"},
+        "offered_particle_steps_per_s": offered,
+        "timeline": {"fields": ["second", "ticks", "particle_steps", "resident_particles_max", "resident_scenes_max",
+                                "queued_at_end"], "rows": timeline},
+        "ticks": ticks, "step_ms_p50": metrics.percentile(step_ms, 50) if step_ms else None,
+        "step_ms_p99": metrics.percentile(step_ms, 99) if step_ms else None,
+        "resident_particles_mean": float(np.mean(stepped)) if stepped else 0.0,
+        "resident_particles_max": int(max(stepped)) if stepped else 0,
+        "resident_scenes_max": int(max(i["resident_scenes"] for i in infos)) if infos else 0,
+        "requests": {"submitted": len(reqs), "admitted": adm, "completed": done,
+                     "queued_at_end": infos[-1]["queued"] if infos else 0,
+                     "queue_wait_s_p50": metrics.percentile(waits, 50) if waits else None,
+                     "queue_wait_s_p99": metrics.percentile(waits, 99) if waits else None,
+                     "latency_s_p50": metrics.percentile(lat, 50) if lat else None,
+                     "latency_s_p99": metrics.percentile(lat, 99) if lat else None},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d / max(1, ticks),
+                "d2h_bytes_per_step": d2h / max(1, ticks),
+                "what": "wall clock of the serving loop: host submit, admission uploads, ticks, result readback"},
+        "roofline": None,
+        "gpu_launches": ticks * kernels_per_step(c0),
+        "clocks": clock_info,
+    }
+    if d.rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = serve_cpu_baseline(temps, rho0)
+    apbf.apbf_server_destroy(srv)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+def serve_cpu_baseline(temps, rho0, budget_s=20.0):
+    """The oracle, single-threaded: particle-steps/s over one step of each of
+    the smallest serving templates until the budget is spent."""
+    import oracle
+
+    t_used, n_used, done = 0.0, 0, 0
+    for c in sorted(temps, key=lambda c: c.n):
+        x, v = scenes.make_scene(c)
+        p = oracle.make_params(c, rho0=rho0, eye=c.eye)
+        t0 = time.perf_counter()
+        oracle.step(p, x, v)
+        t_used += time.perf_counter() - t0
+        n_used += c.n
+        done += 1
+        if t_used > budget_s:
+            break
+    return {"value": n_used / t_used, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one oracle step of each of the {done} smallest of {len(temps)} serving templates "
+                      f"({n_used} particles)", "sample_seconds": t_used}
+
+
 def batch_cpu_baseline(cfgs, rho0, budget_s=20.0):
     """The oracle, single-threaded, stepping the batch's scenes in order until
     the budget is spent; the per-particle time scaled to the whole batch."""
@@ -434,6 +580,8 @@ def run_reference(args):
         return 0
     if args.workload == "batch_256":
         return run_reference_batch(args, ws)
+    if args.workload == "serve":
+        return run_reference_serve(args, ws)
     cfg = workload(args.workload, "apbf")
     import oracle
 
@@ -474,6 +622,48 @@ def run_reference(args):
             "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_serve(args, ws):
+    """Reference arm for the served workload: the oracle's particle-steps/s,
+    each step one oracle step of the smallest serving templates that fit the
+    per-step budget."""
+    import oracle
+
+    temps = sorted(scenes.config_serve_templates(), key=lambda c: c.n)
+    c0 = temps[0]
+    rho0 = float(np.float32(oracle.rest_density(c0.h, c0.mass, c0.spacing)))
+    budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "150")) / max(1, args.steps + args.warmup)
+    states, t_cal = [], 0.0
+    for c in temps:
+        x, v = scenes.make_scene(c)
+        p = oracle.make_params(c, rho0=rho0, eye=c.eye)
+        t0 = time.perf_counter()
+        oracle.step(p, x, v)
+        t_cal += time.perf_counter() - t0
+        states.append([c, p, x, v, np.arange(c.n, dtype=np.int32)])
+        if t_cal > budget:
+            break
+    n_used = sum(st[0].n for st in states)
+    rates = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for st in states:
+            out = oracle.step(st[1], st[2], st[3], st[4])
+            st[2], st[3], st[4] = out.x, out.v, out.ids
+        if s >= args.warmup:
+            rates.append(n_used / (time.perf_counter() - t0))
+    value = float(np.mean(rates))
+    sample = f"each step: one oracle step of each of the {len(states)} smallest serving templates ({n_used} particles)"
+    line = {"impl": "reference", "metric": SERVE_METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "apbf_serve", "n_range": f"{c0.n_min}..{c0.n_max}"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -533,7 +723,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ocean_1m",
-                    choices=["ocean_1m", "dam_break_131k", "dam_break_4k", "batch_256"])
+                    choices=["ocean_1m", "dam_break_131k", "dam_break_4k", "batch_256", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-max-particles", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -555,6 +748,8 @@ def main():
     apbf.lib()
     if args.workload == "batch_256":
         return run_batch(args, apbf, torch, d)
+    if args.workload == "serve":
+        return run_serve(args, apbf, torch, d)
     cfg = workload(args.workload, "apbf")
     pbf_cfg = workload(args.workload, "pbf")
     rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))

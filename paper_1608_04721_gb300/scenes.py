@@ -155,6 +155,31 @@ def config_batch_256(count: int = 256, seed: int = 1608_04721, n_lo: int = 2048,
     return out
 
 
+def serve_arrivals(rate: float = 200.0, seconds: float = 60.0, templates: int = 64, seed: int = 1608_04721,
+                   steps_lo: int = 30, steps_hi: int = 300):
+    """Arrival schedule of a served workload: a Poisson process of the given
+    rate (exponential gaps from seeded uniforms) over `seconds`; each arrival
+    names a scene template (uniform over `templates`) and a step count
+    (uniform integer in steps_lo..steps_hi). Returns a list of
+    (arrival time in s, template index, steps)."""
+    expected = int(rate * seconds * 1.5) + 64
+    u = uniform01(seed, 3, 3 * expected).reshape(expected, 3)
+    out = []
+    t = 0.0
+    for k in range(expected):
+        t += -math.log(1.0 - u[k, 0]) / rate
+        if t >= seconds:
+            break
+        out.append((t, int(u[k, 1] * templates), steps_lo + int(u[k, 2] * (steps_hi - steps_lo + 1))))
+    return out
+
+
+def config_serve_templates(count: int = 64, seed: int = 1608_04721 + 5):
+    """Scene templates of the served workload: the batch generator's dam
+    breaks with 4096..262144 particles (log-uniform) and N_i in 5..10."""
+    return config_batch_256(count=count, seed=seed, n_lo=4096, n_hi=262144, n_min=5, n_max=10)
+
+
 CONFIGS = {
     "dam_break_4k": config_dam_break_4k,
     "dam_break_131k": config_dam_break_131k,
