@@ -18,9 +18,34 @@ from . import build as _build
 
 ORC_LOD_FIXED = 0
 ORC_LOD_DTC = 1
+ORC_LOD_DTVS = 2
+DEPTH_EMPTY_BITS = 0x7F7F7F7F
 ORC_LAMBDA_STALE = 0
 ORC_LAMBDA_ZERO = 1
 ORC_LAMBDA_RECOMPUTE = 2
+
+
+class OrcView(C.Structure):
+    _fields_ = [
+        ("width", C.c_int32), ("height", C.c_int32),
+        ("tan_half_fov", C.c_float),
+        ("dir", C.c_float * 3),
+        ("up", C.c_float * 3),
+        ("radius", C.c_float),
+        ("brute_force", C.c_int32),
+    ]
+
+
+def make_view(width: int, height: int, tan_half_fov: float, direction, up=(0.0, 0.0, 1.0), radius: float = 0.025,
+              brute_force: bool = False) -> OrcView:
+    v = OrcView()
+    v.width, v.height = int(width), int(height)
+    v.tan_half_fov = float(tan_half_fov)
+    v.dir[:] = [float(a) for a in direction]
+    v.up[:] = [float(a) for a in up]
+    v.radius = float(radius)
+    v.brute_force = int(bool(brute_force))
+    return v
 
 
 class OrcParams(C.Structure):
@@ -35,6 +60,7 @@ class OrcParams(C.Structure):
         ("eye", C.c_float * 3),
         ("d_near", C.c_float), ("d_far", C.c_float),
         ("lambda_mode", C.c_int32), ("lod_rounding", C.c_int32),
+        ("view", OrcView),
     ]
 
 
@@ -96,9 +122,13 @@ def lib():
                                P(OrcRecord)]
         L.orc_density_stats.argtypes = [P(OrcParams), C.c_int32, P(C.c_float), P(C.c_double),
                                         P(C.c_double)]
+        L.orc_view_basis.argtypes = [P(OrcView), P(C.c_float), P(C.c_float), P(C.c_float)]
+        L.orc_pixel_ray.argtypes = [P(OrcView), C.c_int32, C.c_int32, P(C.c_float)]
+        L.orc_depth_image.argtypes = [P(OrcParams), C.c_int32, P(C.c_float), P(C.c_float)]
+        L.orc_dtvs_distance.argtypes = [P(OrcParams), C.c_int32, P(C.c_float), P(C.c_float), P(C.c_float)]
         for f in ("orc_grid_dims", "orc_lod_levels", "orc_predict", "orc_cell_keys", "orc_counting_sort",
                   "orc_neighbors", "orc_constraint", "orc_delta_p", "orc_xsph", "orc_step",
-                  "orc_density_stats"):
+                  "orc_density_stats", "orc_view_basis", "orc_pixel_ray", "orc_depth_image", "orc_dtvs_distance"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -122,7 +152,7 @@ def _ptr(a: Optional[np.ndarray], ctype):
 
 def make_params(cfg=None, *, rho0: float, box_lo=None, box_hi=None, eye=(0.0, 0.0, 0.0),
                 d_near: float = 0.0, d_far: float = 0.0, lambda_mode: int = ORC_LAMBDA_STALE,
-                lod_rounding: int = 0, **over) -> OrcParams:
+                lod_rounding: int = 0, view: Optional[OrcView] = None, **over) -> OrcParams:
     """Parameters from a scenes.SceneConfig (or keyword overrides)."""
     vals = {}
     if cfg is not None:
@@ -151,6 +181,8 @@ def make_params(cfg=None, *, rho0: float, box_lo=None, box_hi=None, eye=(0.0, 0.
     p.d_far = float(d_far)
     p.lambda_mode = int(lambda_mode)
     p.lod_rounding = int(lod_rounding)
+    if view is not None:
+        p.view = view
     return p
 
 
@@ -187,6 +219,37 @@ def lod_levels(p: OrcParams, x: np.ndarray):
     _check(lib().orc_lod_levels(C.byref(p), n, _ptr(x, C.c_float), _ptr(lv, C.c_int32),
                                 _ptr(rng, C.c_float)), "orc_lod_levels")
     return lv, rng
+
+
+def view_basis(v: OrcView):
+    f, r, u = (np.zeros(3, np.float32) for _ in range(3))
+    _check(lib().orc_view_basis(C.byref(v), _ptr(f, C.c_float), _ptr(r, C.c_float), _ptr(u, C.c_float)),
+           "orc_view_basis")
+    return f, r, u
+
+
+def pixel_ray(v: OrcView, px: int, py: int) -> np.ndarray:
+    ray = np.zeros(3, np.float32)
+    _check(lib().orc_pixel_ray(C.byref(v), px, py, _ptr(ray, C.c_float)), "orc_pixel_ray")
+    return ray
+
+
+def depth_image(p: OrcParams, x: np.ndarray) -> np.ndarray:
+    """(height, width) float32 depth image; empty pixels hold the float with bits 0x7f7f7f7f."""
+    x = np.ascontiguousarray(x, np.float32)
+    d = np.zeros((p.view.height, p.view.width), np.float32)
+    _check(lib().orc_depth_image(C.byref(p), x.shape[0], _ptr(x, C.c_float), _ptr(d, C.c_float)),
+           "orc_depth_image")
+    return d
+
+
+def dtvs_distance(p: OrcParams, x: np.ndarray, depth: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32)
+    depth = np.ascontiguousarray(depth, np.float32)
+    out = np.zeros(x.shape[0], np.float32)
+    _check(lib().orc_dtvs_distance(C.byref(p), x.shape[0], _ptr(x, C.c_float), _ptr(depth, C.c_float),
+                                   _ptr(out, C.c_float)), "orc_dtvs_distance")
+    return out
 
 
 def predict(p: OrcParams, x: np.ndarray, v: np.ndarray) -> np.ndarray:

@@ -100,6 +100,192 @@ int orc_grid_dims(const orc_params *p, int32_t dims[3])
 /* Distance to camera (Sec. 4.1), linear interpolation between the distance
    range and the level range (Sec. 4.1): near -> n_max, far -> n_min, with
    K = n_max - n_min + 1 bins of equal width over the range. */
+
+/* ---------------------------------------------------------------- DTVS */
+
+static float dot3(const float a[3], const float b[3])
+{
+    float s = a[0] * b[0] + a[1] * b[1];
+    s = s + a[2] * b[2];
+    return s;
+}
+
+static int normalize3(float v[3])
+{
+    float n = sqrtf(dot3(v, v));
+    if (!(n > 0.0f))
+        return -1;
+    v[0] = v[0] / n;
+    v[1] = v[1] / n;
+    v[2] = v[2] / n;
+    return 0;
+}
+
+static void cross3(const float a[3], const float b[3], float c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static float depth_empty(void)
+{
+    uint32_t u = 0x7f7f7f7fu;
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
+
+int orc_view_basis(const orc_view *v, float f[3], float r[3], float u[3])
+{
+    if (!v)
+        return -1;
+    for (int a = 0; a < 3; ++a)
+        f[a] = v->dir[a];
+    if (normalize3(f))
+        return -1;
+    cross3(f, v->up, r);
+    if (normalize3(r))
+        return -1;
+    cross3(r, f, u);
+    return 0;
+}
+
+/* The image plane at unit distance spans [-ax, ax] x [-ay, ay]. */
+static void half_extents(const orc_view *v, float *ax, float *ay)
+{
+    *ax = v->tan_half_fov * ((float)v->width / (float)v->height);
+    *ay = v->tan_half_fov;
+}
+
+int orc_pixel_ray(const orc_view *v, int32_t px, int32_t py, float ray[3])
+{
+    float f[3], r[3], u[3], ax, ay;
+    if (orc_view_basis(v, f, r, u))
+        return -1;
+    half_extents(v, &ax, &ay);
+    float sx = ((float)(2 * px + 1) / (float)v->width - 1.0f) * ax;
+    float sy = (1.0f - (float)(2 * py + 1) / (float)v->height) * ay;
+    for (int a = 0; a < 3; ++a) {
+        float c = f[a] + sx * r[a];
+        ray[a] = c + sy * u[a];
+    }
+    return normalize3(ray);
+}
+
+static int view_ok(const orc_view *v)
+{
+    return v->width >= 1 && v->height >= 1 && v->tan_half_fov > 0.0f && v->radius > 0.0f;
+}
+
+int orc_depth_image(const orc_params *p, int32_t n, const float *x, float *depth)
+{
+    if (!p || n < 0 || (n > 0 && !x) || !depth || !view_ok(&p->view))
+        return -1;
+    const orc_view *v = &p->view;
+    const int32_t W = v->width, H = v->height;
+    float f[3], r[3], u[3], ax, ay;
+    if (orc_view_basis(v, f, r, u))
+        return -1;
+    half_extents(v, &ax, &ay);
+    float *rays = (float *)malloc(sizeof(float) * 3 * (size_t)W * (size_t)H);
+    if (!rays)
+        return -3;
+    for (int32_t py = 0; py < H; ++py)
+        for (int32_t px = 0; px < W; ++px) {
+            orc_pixel_ray(v, px, py, rays + 3 * ((size_t)py * W + px));
+            depth[(size_t)py * W + px] = depth_empty();
+        }
+    const float r2 = v->radius * v->radius;
+    for (int32_t i = 0; i < n; ++i) {
+        float rel[3] = {x[3 * i + 0] - p->eye[0], x[3 * i + 1] - p->eye[1], x[3 * i + 2] - p->eye[2]};
+        float cc = dot3(rel, rel) - r2;
+        if (!(cc > 0.0f))
+            continue; /* the eye is inside this sphere: it is not rendered */
+        /* pixels to test: all, or a box around the projections of the 8
+           corners of the sphere's bounding cube, widened by one pixel (a
+           conservative cull that does not change the image) */
+        int32_t x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
+        if (!v->brute_force) {
+            float fx_lo = INFINITY, fx_hi = -INFINITY, fy_lo = INFINITY, fy_hi = -INFINITY;
+            int behind = 0;
+            for (int c = 0; c < 8; ++c) {
+                float q[3] = {rel[0] + ((c & 1) ? v->radius : -v->radius), rel[1] + ((c & 2) ? v->radius : -v->radius),
+                              rel[2] + ((c & 4) ? v->radius : -v->radius)};
+                float zc = dot3(q, f);
+                if (!(zc > 0.0f)) {
+                    behind = 1;
+                    break;
+                }
+                float fx = ((dot3(q, r) / zc) / ax + 1.0f) * (0.5f * (float)W);
+                float fy = (1.0f - (dot3(q, u) / zc) / ay) * (0.5f * (float)H);
+                fx_lo = fminf(fx_lo, fx);
+                fx_hi = fmaxf(fx_hi, fx);
+                fy_lo = fminf(fy_lo, fy);
+                fy_hi = fmaxf(fy_hi, fy);
+            }
+            if (!behind) {
+                if (fx_hi < -1.0f || fy_hi < -1.0f || fx_lo > (float)W + 1.0f || fy_lo > (float)H + 1.0f)
+                    continue; /* entirely outside the image */
+                x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) - 1;
+                x1 = (int32_t)floorf(fminf(fx_hi, (float)W + 1.0f)) + 1;
+                y0 = (int32_t)floorf(fmaxf(fy_lo, -1.0f)) - 1;
+                y1 = (int32_t)floorf(fminf(fy_hi, (float)H + 1.0f)) + 1;
+                x0 = x0 < 0 ? 0 : x0;
+                y0 = y0 < 0 ? 0 : y0;
+                x1 = x1 > W - 1 ? W - 1 : x1;
+                y1 = y1 > H - 1 ? H - 1 : y1;
+            }
+        }
+        for (int32_t py = y0; py <= y1; ++py)
+            for (int32_t px = x0; px <= x1; ++px) {
+                const float *ray = rays + 3 * ((size_t)py * W + px);
+                float b = dot3(ray, rel); /* distance along the ray to the centre's foot point */
+                if (!(b > 0.0f))
+                    continue;
+                /* squared half chord r^2 - |rel - b ray|^2: the perpendicular
+                   offset is formed first, which keeps the difference well conditioned */
+                float w[3] = {rel[0] - b * ray[0], rel[1] - b * ray[1], rel[2] - b * ray[2]};
+                float disc = r2 - dot3(w, w);
+                if (!(disc >= 0.0f))
+                    continue;
+                float t = b - sqrtf(disc);
+                float *dp = depth + (size_t)py * W + px;
+                if (t < *dp)
+                    *dp = t;
+            }
+    }
+    free(rays);
+    return 0;
+}
+
+int orc_dtvs_distance(const orc_params *p, int32_t n, const float *x, const float *depth, float *dist)
+{
+    if (!p || n < 0 || (n > 0 && (!x || !dist)) || !depth || !view_ok(&p->view))
+        return -1;
+    const orc_view *v = &p->view;
+    float f[3], r[3], u[3], ax, ay;
+    if (orc_view_basis(v, f, r, u))
+        return -1;
+    half_extents(v, &ax, &ay);
+    for (int32_t i = 0; i < n; ++i) {
+        float rel[3] = {x[3 * i + 0] - p->eye[0], x[3 * i + 1] - p->eye[1], x[3 * i + 2] - p->eye[2]};
+        float zc = dot3(rel, f);
+        dist[i] = -1.0f;
+        if (!(zc > 0.0f))
+            continue;
+        float fx = ((dot3(rel, r) / zc) / ax + 1.0f) * (0.5f * (float)v->width);
+        float fy = (1.0f - (dot3(rel, u) / zc) / ay) * (0.5f * (float)v->height);
+        if (!(fx >= 0.0f && fx < (float)v->width && fy >= 0.0f && fy < (float)v->height))
+            continue;
+        int32_t px = (int32_t)floorf(fx), py = (int32_t)floorf(fy);
+        float front = sqrtf(dot3(rel, rel)) - v->radius;
+        float d = front - depth[(size_t)py * v->width + px];
+        dist[i] = d > 0.0f ? d : 0.0f;
+    }
+    return 0;
+}
+
 int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *level, float range[2])
 {
     if (!p || n < 0 || (n > 0 && (!x || !level)))
@@ -115,36 +301,64 @@ int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *leve
         }
         return 0;
     }
-    if (p->lod_mode != ORC_LOD_DTC)
+    if (p->lod_mode != ORC_LOD_DTC && p->lod_mode != ORC_LOD_DTVS)
         return -1;
     float *d = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
     if (!d)
         return -3;
-    for (int32_t i = 0; i < n; ++i) {
-        float dx = x[3 * i + 0] - p->eye[0];
-        float dy = x[3 * i + 1] - p->eye[1];
-        float dz = x[3 * i + 2] - p->eye[2];
-        float d2 = dx * dx + dy * dy;
-        d2 = d2 + dz * dz;
-        d[i] = sqrtf(d2);
+    if (p->lod_mode == ORC_LOD_DTC) {
+        for (int32_t i = 0; i < n; ++i) {
+            float dx = x[3 * i + 0] - p->eye[0];
+            float dy = x[3 * i + 1] - p->eye[1];
+            float dz = x[3 * i + 2] - p->eye[2];
+            float d2 = dx * dx + dy * dy;
+            d2 = d2 + dz * dz;
+            d[i] = sqrtf(d2);
+        }
+    } else {
+        if (!view_ok(&p->view)) {
+            free(d);
+            return -1;
+        }
+        float *depth = (float *)malloc(sizeof(float) * (size_t)p->view.width * (size_t)p->view.height);
+        if (!depth) {
+            free(d);
+            return -3;
+        }
+        int rc = orc_depth_image(p, n, x, depth);
+        if (rc == 0)
+            rc = orc_dtvs_distance(p, n, x, depth, d);
+        free(depth);
+        if (rc) {
+            free(d);
+            return rc;
+        }
     }
     int automatic = !(p->d_near < p->d_far);
     float dmin = p->d_near, dmax = p->d_far;
     if (automatic) {
+        int32_t seen = 0;
         dmin = INFINITY;
         dmax = 0.0f;
         for (int32_t i = 0; i < n; ++i) {
+            if (d[i] < 0.0f)
+                continue; /* DTVS: outside the view */
+            ++seen;
             if (d[i] < dmin)
                 dmin = d[i];
             if (d[i] > dmax)
                 dmax = d[i];
         }
-        if (n == 0)
+        if (seen == 0)
             dmin = dmax = 0.0f;
     }
     int32_t K = p->n_max - p->n_min + 1;
     float span = dmax - dmin;
     for (int32_t i = 0; i < n; ++i) {
+        if (d[i] < 0.0f) {
+            level[i] = p->n_min;
+            continue;
+        }
         float t = 0.0f;
         if (span > 0.0f) {
             float num = d[i] - dmin;

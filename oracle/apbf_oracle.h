@@ -29,10 +29,24 @@ extern "C" {
 
 #define ORC_LOD_FIXED 0
 #define ORC_LOD_DTC 1
+#define ORC_LOD_DTVS 2
 
 #define ORC_LAMBDA_STALE 0     /* inactive neighbours keep their last lambda */
 #define ORC_LAMBDA_ZERO 1      /* inactive neighbours contribute lambda = 0 */
 #define ORC_LAMBDA_RECOMPUTE 2 /* lambda recomputed for every particle each iteration */
+
+/* Camera image of the DTVS model (Sec. 4.1, Sec. 6): a pinhole camera at
+   orc_params.eye looking along dir, world up `up`, vertical half-angle with
+   tangent tan_half_fov, width x height pixels (row 0 at the top); particles
+   are rendered as spheres of the given radius. */
+typedef struct orc_view {
+    int32_t width, height;
+    float tan_half_fov;
+    float dir[3];
+    float up[3];
+    float radius;
+    int32_t brute_force; /* 1: test every pixel against every sphere (no bounding box) */
+} orc_view;
 
 typedef struct orc_params {
     /* Scene values exactly as the solver receives them (FP32). */
@@ -46,6 +60,7 @@ typedef struct orc_params {
     float d_near, d_far;          /* d_near >= d_far: automatic range */
     int32_t lambda_mode;          /* ORC_LAMBDA_* */
     int32_t lod_rounding;         /* 0: equal-width bins, 1: rounded interpolation */
+    orc_view view;                /* DTVS only */
 } orc_params;
 
 typedef struct orc_record {
@@ -84,7 +99,27 @@ double orc_rest_density(double h, double mass, double spacing);
 /* Grid cells per axis: floor((hi - lo) * inv_h) + 1 in FP32, inv_h = 1/h in FP32. */
 int orc_grid_dims(const orc_params *p, int32_t dims[3]);
 
-/* Sec. 4.1 DTC model + Eq. 8: per-particle level from the camera distance. */
+/* DTVS camera basis: forward f = dir/|dir|, right r = (f x up)/|f x up|,
+   image up u = r x f (FP32). Returns -1 when dir or f x up is zero. */
+int orc_view_basis(const orc_view *v, float f[3], float r[3], float u[3]);
+
+/* Unit direction of the camera ray through the centre of pixel (px, py) (FP32). */
+int orc_pixel_ray(const orc_view *v, int32_t px, int32_t py, float ray[3]);
+
+/* Depth image of the particles rendered as spheres (Sec. 6): per pixel the
+   smallest distance along the pixel's ray to a sphere it hits, or the value
+   with bit pattern 0x7f7f7f7f (3.4e38) where it hits none. width*height floats. */
+int orc_depth_image(const orc_params *p, int32_t n, const float *x, float *depth);
+
+/* DTVS distance (Sec. 4.1): for a particle whose centre projects into the
+   image, max(0, (|x - eye| - radius) - depth at that pixel), the distance
+   behind the visible surface along its camera ray; -1 for particles outside
+   the view. */
+int orc_dtvs_distance(const orc_params *p, int32_t n, const float *x, const float *depth, float *dist);
+
+/* Sec. 4.1 DTC / DTVS model + Eq. 8: per-particle level from the camera
+   distance (DTC) or the distance behind the visible surface (DTVS;
+   particles outside the view get n_min and do not enter the automatic range). */
 int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *level, float range[2]);
 
 /* Fig. 7 lines 1-4 plus the box clamp, FP32. */

@@ -11,6 +11,7 @@ import pytest
 
 import oracle as O
 from oracle import build as B
+import tests.test_oracle_dtvs_pins as dtvs
 import tests.test_oracle_pins as pins
 
 MUTATIONS = [
@@ -45,6 +46,25 @@ MUTATIONS = [
      "            if (lvl[s] >= l) {\n                xs[3 * s + 0] += dp[3 * s + 0];",
      "            if (lvl[s] + 1 >= l) {\n                xs[3 * s + 0] += dp[3 * s + 0];",
      lambda: pins.test_active_sets_nested_and_finished_particles_fixed(O.rest_density(0.1, 1.0, 0.05))),
+    ("DTVS depth at the sphere's exit instead of its entry",
+     "float t = b - sqrtf(disc);", "float t = b + sqrtf(disc);",
+     lambda: dtvs.test_depth_of_one_sphere_is_the_closed_form(0)),
+    ("DTVS image rows counted from the bottom",
+     "float sy = (1.0f - (float)(2 * py + 1) / (float)v->height) * ay;",
+     "float sy = ((float)(2 * py + 1) / (float)v->height - 1.0f) * ay;",
+     dtvs.test_pixel_rays_are_pinhole_rays),
+    ("DTVS depth keeps the last sphere drawn, not the nearest",
+     "if (t < *dp)", "if (t == t)",
+     dtvs.test_depth_keeps_the_nearest_sphere_in_any_order),
+    ("DTVS distance measured from the centre instead of the front surface",
+     "float front = sqrtf(dot3(rel, rel)) - v->radius;", "float front = sqrtf(dot3(rel, rel));",
+     dtvs.test_distance_to_the_visible_surface_along_a_ray),
+    ("DTVS particles outside the view enter the automatic range",
+     "            if (d[i] < 0.0f)\n                continue; /* DTVS: outside the view */\n", "",
+     dtvs.test_dtvs_levels_of_a_wall_with_particles_behind_it),
+    ("DTVS cull box without its one-pixel margin",
+     "x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) - 1;", "x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) + 1;",
+     lambda: dtvs.test_bounding_box_cull_equals_every_pixel(0)),
 ]
 
 

@@ -19,6 +19,9 @@ result, or brute force. What pins each oracle function:
   orc_counting_sort    equals a stable argsort; cell starts = searchsorted
   orc_lod_levels       end points, monotonicity, equal-width bins, constant
                        level when n_min = n_max
+  orc_view_basis, orc_pixel_ray, orc_depth_image, orc_dtvs_distance and the
+                       DTVS levels: tests/test_oracle_dtvs_pins.py (pinhole and
+                       sphere geometry in float64, occlusion, culling = brute force)
   orc_predict/orc_step isolated particle in free fall (closed form); clamp
                        keeps the box; APBF with every N_i = N_max is PBF;
                        nested active sets; finished particles stay fixed;
