@@ -250,6 +250,8 @@ int orc_depth_image(const orc_params *p, int32_t n, const float *x, float *depth
                 if (!(disc >= 0.0f))
                     continue;
                 float t = b - sqrtf(disc);
+                if (!(t > 0.0f))
+                    continue; /* the image holds distances in front of the camera */
                 float *dp = depth + (size_t)py * W + px;
                 if (t < *dp)
                     *dp = t;

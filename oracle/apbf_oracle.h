@@ -107,8 +107,9 @@ int orc_view_basis(const orc_view *v, float f[3], float r[3], float u[3]);
 int orc_pixel_ray(const orc_view *v, int32_t px, int32_t py, float ray[3]);
 
 /* Depth image of the particles rendered as spheres (Sec. 6): per pixel the
-   smallest distance along the pixel's ray to a sphere it hits, or the value
-   with bit pattern 0x7f7f7f7f (3.4e38) where it hits none. width*height floats. */
+   smallest positive distance along the pixel's ray to the surface of a sphere
+   it enters, or the value with bit pattern 0x7f7f7f7f (3.4e38) where it
+   enters none. width*height floats. */
 int orc_depth_image(const orc_params *p, int32_t n, const float *x, float *depth);
 
 /* DTVS distance (Sec. 4.1): for a particle whose centre projects into the
