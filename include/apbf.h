@@ -10,7 +10,8 @@
  * (Eq. 4-7, lines 12-23) in which particle i is active only in iterations
  * 1..N_i (Eq. 9-11), and the velocity/position update (lines 24-27). N_i is
  * the particle's level of detail (Eq. 8) from its distance to the camera
- * (Sec. 4.1, DTC model).
+ * (Sec. 4.1, DTC model) or from its distance behind the visible surface of
+ * the particles rendered as spheres (Sec. 4.1 and Sec. 6, DTVS model).
  *
  * Conventions for every entry point:
  *  - Returns apbf_status; nothing aborts, throws or exits.
@@ -55,7 +56,7 @@ typedef enum apbf_status {
 /* Level-of-detail models (Sec. 4.1). */
 #define APBF_LOD_FIXED 0u /* plain PBF: every particle runs n_max iterations */
 #define APBF_LOD_DTC 1u   /* distance to camera (Sec. 4.1) */
-#define APBF_LOD_DTVS 2u  /* distance to the visible surface: reserved, APBF_ERR_NOT_SUPPORTED */
+#define APBF_LOD_DTVS 2u  /* distance to the visible surface (Sec. 4.1, Sec. 6); single scenes, see apbf_set_view */
 
 /* apbf_scene_desc.flags */
 #define APBF_FLAG_NO_GRAPH 1u /* issue the step's kernels one by one instead of replaying a CUDA graph */
@@ -82,7 +83,8 @@ typedef enum apbf_status {
  *  xsph_c       XSPH viscosity, v_i += c sum_j (m/rho0) (v_j - v_i) W_ij.
  *  gravity      external acceleration f_ext (Fig. 7 line 2).
  *  n_min, n_max iteration range, 1 <= n_min <= n_max <= 255 (Eq. 8: levels 1..N_l).
- *  lod_mode     APBF_LOD_FIXED or APBF_LOD_DTC.
+ *  lod_mode     APBF_LOD_FIXED, APBF_LOD_DTC or APBF_LOD_DTVS (not in batches or servers:
+ *               APBF_ERR_NOT_SUPPORTED).
  *  stabil_iters, stabil_s
  *               pre-stabilisation (Fig. 7 lines 7-11) of the set of Eq. 11 for
  *               l = S. Only S <= 1 (empty set) is supported; S > 1 returns
@@ -171,6 +173,32 @@ APBF_API apbf_status apbf_set_box_at(apbf_scene *scene, uint32_t index, const fl
  *  min/max camera distance over the scene at the start of each step (Sec. 4.1). */
 APBF_API apbf_status apbf_set_camera(apbf_scene *scene, const float eye[3], const float dir[3], float d_near,
                                      float d_far);
+
+/*
+ * Camera image of the DTVS model (Sec. 4.1, Sec. 6), used from the next step
+ * on; a DTVS scene must have one before it steps (APBF_ERR_BAD_STATE
+ * otherwise); other scenes reject it (APBF_ERR_INVALID_ARG). The camera is a
+ * pinhole at apbf_set_camera's eye looking along its dir: forward f =
+ * dir/|dir|, right r = (f x up)/|f x up|, image up u = r x f; the image has
+ * width x height pixels, row 0 at the top, and spans tan_half_fov (the
+ * tangent of half the vertical field of view) vertically and tan_half_fov *
+ * width/height horizontally at unit distance. Each step:
+ *  1. every particle is rendered as a sphere of `radius` around its position:
+ *     per pixel, the smallest positive distance along the ray through the
+ *     pixel centre at which the ray enters a sphere (spheres containing the
+ *     eye are not rendered);
+ *  2. a particle whose centre projects into the image gets d = max(0,
+ *     (|x - eye| - radius) - depth at that pixel), its distance behind the
+ *     visible surface along its camera ray; visible particles get 0;
+ *  3. N_i follows from d as for DTC (linear interpolation between the
+ *     distance range, automatic over the particles in view, or the camera's
+ *     d_near..d_far, and n_max..n_min); particles outside the view get n_min.
+ * All of steps 1-3 is FP32 with every operation rounded (no contraction).
+ *  width, height  1..16384 each, width * height <= 2^26.
+ *  up             host, 3 floats, finite, not parallel to the camera's dir.
+ * The image (20 bytes per pixel) is device memory the scene allocates here. */
+APBF_API apbf_status apbf_set_view(apbf_scene *scene, uint32_t width, uint32_t height, float tan_half_fov,
+                                   const float up[3], float radius);
 
 /* Move the collision box (e.g. an oscillating wall) from the next step on.
  * lo, hi: host, 3 floats, grid_lo <= lo < hi <= grid_hi. */
@@ -406,6 +434,9 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint3
 #define APBF_DBG_RHO 12u          /* float[n] density of the last lambda pass, sorted */
 #define APBF_DBG_XSTAR 13u        /* float4[n] current x* (absolute FP32), sorted */
 #define APBF_DBG_DRANGE 14u       /* float[2*scenes] LOD distance ranges: the minima, then the maxima */
+#define APBF_DBG_DEPTH 15u        /* float[width*height] DTVS depth image (0x7f7f7f7f bits: empty) */
+#define APBF_DBG_LOD_DISTANCE 16u /* float[n] DTVS distance behind the visible surface, pre-sort
+                                     (state) order; -1 outside the view */
 
 /* Copy a debug field (see APBF_DBG_*) to host memory of `bytes` bytes
  * (must equal the field's size). Synchronises. */

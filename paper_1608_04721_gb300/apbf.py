@@ -39,7 +39,8 @@ APBF_STAGE_COUNT = 10
 
 (APBF_DBG_KEYS, APBF_DBG_STATE_IDS, APBF_DBG_LEVEL_PRESORT, APBF_DBG_SORTED_IDS, APBF_DBG_CELL_START,
  APBF_DBG_XPRED, APBF_DBG_LEVEL, APBF_DBG_NBR_COUNT, APBF_DBG_NBR, APBF_DBG_ACTIVE, APBF_DBG_LEVEL_COUNT,
- APBF_DBG_LAMBDA, APBF_DBG_RHO, APBF_DBG_XSTAR, APBF_DBG_DRANGE) = range(15)
+ APBF_DBG_LAMBDA, APBF_DBG_RHO, APBF_DBG_XSTAR, APBF_DBG_DRANGE, APBF_DBG_DEPTH,
+ APBF_DBG_LOD_DISTANCE) = range(17)
 
 
 class apbf_scene_desc(C.Structure):
@@ -137,7 +138,7 @@ EXPORTS = [
     "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
     "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune", "apbf_server_bytes",
     "apbf_server_create", "apbf_server_submit", "apbf_server_tick", "apbf_server_query", "apbf_server_last_error",
-    "apbf_server_destroy",
+    "apbf_server_destroy", "apbf_set_view",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -196,6 +197,7 @@ def lib():
         L.apbf_autotune.argtypes = [V, C.c_uint32, P(apbf_tune_result)]
         L.apbf_density_stats_static.argtypes = [V, C.c_uint32, C.c_float, C.c_float, C.c_float, P(C.c_float),
                                                 P(C.c_float), V, V]
+        L.apbf_set_view.argtypes = [V, C.c_uint32, C.c_uint32, C.c_float, P(C.c_float), C.c_float]
         L.apbf_server_bytes.argtypes = [P(apbf_server_desc), P(C.c_size_t), P(C.c_uint32), P(C.c_uint32)]
         L.apbf_server_create.argtypes = [P(apbf_server_desc), V, P(V)]
         L.apbf_server_submit.argtypes = [V, P(apbf_request), P(C.c_uint64)]
@@ -518,6 +520,8 @@ def apbf_debug_read(scene: Scene, field: int) -> np.ndarray:
         APBF_DBG_LEVEL_COUNT: ((n_max + 2,), np.uint32), APBF_DBG_LAMBDA: ((n,), np.float32),
         APBF_DBG_RHO: ((n,), np.float32), APBF_DBG_XSTAR: ((n, 4), np.float32),
         APBF_DBG_DRANGE: ((2 * scene.scenes,), np.float32),
+        APBF_DBG_DEPTH: ((getattr(scene, "view", (0, 0))[1], getattr(scene, "view", (0, 0))[0]), np.float32),
+        APBF_DBG_LOD_DISTANCE: ((n,), np.float32),
     }
     shape, dt = shapes[field]
     a = np.empty(shape, dt)
@@ -659,3 +663,11 @@ def apbf_server_destroy(server: Server):
     if server.handle:
         lib().apbf_server_destroy(server.handle)
         server.handle = None
+
+
+def apbf_set_view(scene: Scene, width: int, height: int, tan_half_fov: float, up=(0.0, 0.0, 1.0),
+                  radius: float = 0.025):
+    """Camera image of the DTVS model (see include/apbf.h)."""
+    u = (C.c_float * 3)(*[float(a) for a in up])
+    _check(lib().apbf_set_view(scene.handle, width, height, tan_half_fov, u, radius), "apbf_set_view", scene)
+    scene.view = (int(width), int(height))

@@ -76,11 +76,7 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
         return "xsph_c and gravity must be finite";
     if (d->n_min < 1 || d->n_max < d->n_min || d->n_max > 255)
         return "need 1 <= n_min <= n_max <= 255";
-    if (d->lod_mode == APBF_LOD_DTVS) {
-        st = APBF_ERR_NOT_SUPPORTED;
-        return "the DTVS adaption model is not built";
-    }
-    if (d->lod_mode != APBF_LOD_FIXED && d->lod_mode != APBF_LOD_DTC)
+    if (d->lod_mode != APBF_LOD_FIXED && d->lod_mode != APBF_LOD_DTC && d->lod_mode != APBF_LOD_DTVS)
         return "unknown lod_mode";
     if (d->stabil_s > 1) {
         st = APBF_ERR_NOT_SUPPORTED;
@@ -187,6 +183,10 @@ std::string derive_batch(const apbf_scene_desc *descs, uint32_t count, StepConst
         return "descs is NULL or count is 0";
     if (count > 65535)
         return "at most 65535 scenes per batch";
+    if (count > 1 && descs[0].lod_mode == APBF_LOD_DTVS) {
+        st = APBF_ERR_NOT_SUPPORTED;
+        return "the DTVS model renders one camera image per scene; batches of DTVS scenes are not built";
+    }
     geo.assign(count, SceneGeom{});
     uint64_t n_total = 0, c_total = 0;
     for (uint32_t k = 0; k < count; ++k) {
@@ -273,6 +273,7 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.nbr_cnt = (uint8_t *)P(n);
     b.nbr = (uint32_t *)P(4 * (size_t)sc.max_nbr * n);
     b.rho = (float *)P(4 * n);
+    b.lodd = (float *)P(4 * n);
     b.act = (uint32_t *)P(4 * n);
     b.lvl_hist = (uint32_t *)P(4 * lvl_e);
     b.lvl_off = (uint32_t *)P(4 * lvl_e);
@@ -336,7 +337,19 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
     const StepConst &sc = s->sc;
     const Buffers &b = s->b;
     const bool dtc = sc.lod_mode == APBF_LOD_DTC;
+    const bool dtvs = sc.lod_mode == APBF_LOD_DTVS;
     cudaError_t e;
+    if (dtvs && (!s->view_set || !s->view.depth || !s->view.ray))
+        return fail(s, APBF_ERR_BAD_STATE, "a DTVS scene needs apbf_set_view before it steps");
+    if (dtvs) {  // depth image, distances behind the visible surface and their range
+        e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
+            cudaMemsetAsync(b.drange, 0x7f, 4, st);
+            cudaMemsetAsync(b.drange + 1, 0, 4, st);
+            return launch_dtvs(sc, b, s->view, st);
+        });
+        if (e != cudaSuccess)
+            return cuda_fail(s, e, "dtvs");
+    }
     if (dtc) {  // always captured; unused when the camera gives a distance range
         e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
             cudaMemsetAsync(b.drange, 0x7f, 4 * (size_t)sc.scenes, st);  // 0x7f7f7f7f = 3.4e38f
@@ -373,7 +386,7 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
         return cuda_fail(s, e, "neighbors");
     if (stop_stage == APBF_STAGE_NEIGHBORS)
         return APBF_OK;
-    if (dtc && sc.K > 1) {
+    if ((dtc || dtvs) && sc.K > 1) {
         if ((e = timed(s, st, APBF_STAGE_LEVELS, [&] { return launch_levels(sc, b, st); })) != cudaSuccess)
             return cuda_fail(s, e, "levels");
     }
@@ -626,6 +639,7 @@ APBF_API apbf_status apbf_create_batch(const apbf_scene_desc *descs, uint32_t co
             s->grid_hi3[3 * k + a] = descs[k].grid_hi[a];
             s->dyn[k].box_lo[a] = descs[k].box_lo[a];
             s->dyn[k].box_hi[a] = descs[k].box_hi[a];
+            s->dyn[k].dir[a] = a == 0 ? 1.0f : 0.0f;
             s->dyn[k].auto_range = 1;
         }
     auto bail = [&](apbf_status code, const std::string &msg) {
@@ -678,6 +692,18 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *d, void *cuda_stre
 }
 
 namespace {
+// The DTVS camera basis needs dir != 0 and dir x up != 0 (checked in FP64).
+bool view_axes_ok(const float dir[3], const float *up)
+{
+    const double d0 = dir[0], d1 = dir[1], d2 = dir[2];
+    if (d0 * d0 + d1 * d1 + d2 * d2 == 0.0)
+        return false;
+    if (!up)
+        return true;
+    const double c0 = d1 * up[2] - d2 * up[1], c1 = d2 * up[0] - d0 * up[2], c2 = d0 * up[1] - d1 * up[0];
+    return c0 * c0 + c1 * c1 + c2 * c2 > 1e-24 * (d0 * d0 + d1 * d1 + d2 * d2);
+}
+
 apbf_status set_camera_range(apbf_scene *s, uint32_t k0, uint32_t k1, const float eye[3], const float dir[3],
                              float d_near, float d_far)
 {
@@ -688,9 +714,13 @@ apbf_status set_camera_range(apbf_scene *s, uint32_t k0, uint32_t k1, const floa
         return fail(s, APBF_ERR_INVALID_ARG, "camera values must be finite and non-NULL");
     if (k0 >= s->sc.scenes)
         return fail(s, APBF_ERR_INVALID_ARG, "scene index out of range");
+    if (s->sc.lod_mode == APBF_LOD_DTVS && !view_axes_ok(dir, s->view_set ? s->view.up : nullptr))
+        return fail(s, APBF_ERR_INVALID_ARG, "dir must be non-zero and not parallel to the view's up vector");
     for (uint32_t k = k0; k < k1; ++k) {
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a) {
             s->dyn[k].eye[a] = eye[a];
+            s->dyn[k].dir[a] = dir[a];
+        }
         s->dyn[k].d_near = d_near;
         s->dyn[k].d_far = d_far;
         s->dyn[k].auto_range = (d_near < d_far) ? 0u : 1u;
@@ -743,6 +773,49 @@ APBF_API apbf_status apbf_set_box_at(apbf_scene *s, uint32_t index, const float 
     return s ? set_box_range(s, index, index + 1, lo, hi) : APBF_ERR_INVALID_ARG;
 }
 
+APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t height, float tan_half_fov,
+                                   const float up[3], float radius)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (s->sc.lod_mode != APBF_LOD_DTVS)
+        return fail(s, APBF_ERR_INVALID_ARG, "the scene's lod_mode is not APBF_LOD_DTVS");
+    if (width < 1 || height < 1 || width > 16384 || height > 16384 || (uint64_t)width * height > (1ull << 26))
+        return fail(s, APBF_ERR_INVALID_ARG, "need 1 <= width, height <= 16384 and width*height <= 2^26");
+    if (!(tan_half_fov > 0.0f) || !(tan_half_fov < 1.0e4f) || !(radius > 0.0f) || !std::isfinite(radius))
+        return fail(s, APBF_ERR_INVALID_ARG, "need 0 < tan_half_fov < 1e4 and a finite radius > 0");
+    if (!up || !finite3(up) || !view_axes_ok(s->dyn[0].dir, up))
+        return fail(s, APBF_ERR_INVALID_ARG, "up must be finite and not parallel to the camera direction");
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));  // the previous image may still be in use
+    const size_t pix = (size_t)width * height;
+    if (!s->view_set || (size_t)s->view.W * s->view.H != pix) {
+        if (s->view.depth)
+            cudaFree(s->view.depth);
+        if (s->view.ray)
+            cudaFree(s->view.ray);
+        s->view.depth = nullptr;
+        s->view.ray = nullptr;
+        s->view_set = false;
+        cudaError_t e = cudaMalloc(&s->view.depth, 4 * pix);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->view.ray, 16 * pix);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(s, APBF_ERR_OUT_OF_MEMORY, std::string("view image: ") + cudaGetErrorString(e));
+        }
+    }
+    s->view.W = width;
+    s->view.H = height;
+    s->view.tan_half = tan_half_fov;
+    for (int a = 0; a < 3; ++a)
+        s->view.up[a] = up[a];
+    s->view.radius = radius;
+    s->view_set = true;
+    drop_graph(s);
+    return APBF_OK;
+}
+
 APBF_API apbf_status apbf_step(apbf_scene *s, uint32_t nsteps)
 {
     apbf_status st = enter(s);
@@ -752,6 +825,8 @@ APBF_API apbf_status apbf_step(apbf_scene *s, uint32_t nsteps)
         s->stepped = true;
         return APBF_OK;
     }
+    if (s->sc.lod_mode == APBF_LOD_DTVS && !s->view_set)
+        return fail(s, APBF_ERR_BAD_STATE, "a DTVS scene needs apbf_set_view before it steps");
     const bool eager = s->timing || (s->flags & APBF_FLAG_NO_GRAPH);
     for (uint32_t k = 0; k < nsteps; ++k) {
         if ((st = upload_dyn(s)) != APBF_OK)
@@ -848,7 +923,7 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     APBF_CUDA(s, cudaMemcpy(lc.data(), s->b.lvl_count, 4 * 258, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(&dr[0], s->b.drange, 4, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(&dr[1], s->b.drange + sc.scenes, 4, cudaMemcpyDeviceToHost));
-    const bool partitioned = sc.lod_mode == APBF_LOD_DTC && sc.K > 1;
+    const bool partitioned = sc.lod_mode != APBF_LOD_FIXED && sc.K > 1;
     info->neighbor_pairs = c[0];
     for (uint32_t l = 0; l < 256; ++l) {
         uint32_t a = 0;
@@ -864,7 +939,7 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     } else {
         info->lambda_pairs = c[0] * (unsigned long long)sc.n_max;
     }
-    if (sc.lod_mode == APBF_LOD_DTC) {
+    if (sc.lod_mode != APBF_LOD_FIXED) {
         if (s->dyn[0].auto_range) {
             info->d_range[0] = dr[0];
             info->d_range[1] = dr[1];
@@ -918,6 +993,10 @@ APBF_API void apbf_destroy_scene(apbf_scene *s)
         cudaFreeHost(s->pinned_small);
     if (s->own_arena && s->arena)
         cudaFree(s->arena);
+    if (s->view.depth)
+        cudaFree(s->view.depth);
+    if (s->view.ray)
+        cudaFree(s->view.ray);
     delete s;
 }
 
@@ -1006,6 +1085,8 @@ APBF_API apbf_status apbf_autotune(apbf_scene *s, uint32_t trial_steps, apbf_tun
         return st;
     if (!out || trial_steps == 0 || trial_steps > 1000)
         return fail(s, APBF_ERR_INVALID_ARG, "out is NULL or trial_steps not in 1..1000");
+    if (s->sc.lod_mode == APBF_LOD_DTVS && !s->view_set)
+        return fail(s, APBF_ERR_BAD_STATE, "a DTVS scene needs apbf_set_view before it steps");
     std::memset(out, 0, sizeof(*out));
     out->block = (uint32_t)s->tune.block;
     out->mask_threshold = s->tune.mask_threshold;
@@ -1077,6 +1158,8 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *s, uint32_t stage, uint32_t 
         return fail(s, APBF_ERR_INVALID_ARG, "unknown stage");
     if ((stage == APBF_STAGE_LAMBDA || stage == APBF_STAGE_DELTAP) && (iteration < 1 || iteration > s->sc.n_max))
         return fail(s, APBF_ERR_INVALID_ARG, "iteration must be in 1..n_max");
+    if (s->sc.lod_mode == APBF_LOD_DTVS && !s->view_set)
+        return fail(s, APBF_ERR_BAD_STATE, "a DTVS scene needs apbf_set_view before it steps");
     if (s->sc.n == 0)
         return APBF_OK;
     if ((st = upload_dyn(s)) != APBF_OK)
@@ -1127,6 +1210,11 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
         size = 16 * n;
         break;
     case APBF_DBG_DRANGE: src = b.drange; size = 8 * (size_t)sc.scenes; break;
+    case APBF_DBG_DEPTH:
+        src = s->view.depth;
+        size = s->view_set ? 4 * (size_t)s->view.W * s->view.H : 0;
+        break;
+    case APBF_DBG_LOD_DISTANCE: src = b.lodd; size = 4 * n; break;
     default: return fail(s, APBF_ERR_INVALID_ARG, "unknown debug field");
     }
     if (bytes != size || (size && !host))

@@ -75,9 +75,21 @@ struct DynParams {
     float box_lo[4];
     float box_hi[4];
     float eye[4];
+    float dir[4];  // viewing direction (DTVS)
     float d_near, d_far;
     uint32_t auto_range;
     uint32_t pad;
+};
+
+// Camera image of the DTVS model (Sec. 4.1, Sec. 6), fixed between
+// apbf_set_view calls (passed by value, so it is part of the captured step).
+struct ViewConst {
+    uint32_t W = 0, H = 0;
+    float tan_half = 0.0f;  // tan of half the vertical field of view
+    float up[3] = {0.0f, 0.0f, 1.0f};
+    float radius = 0.0f;    // sphere radius of the rendered particles
+    uint32_t *depth = nullptr;  // W*H float bits, row 0 at the top
+    float4 *ray = nullptr;      // W*H unit pixel rays of the current camera
 };
 
 struct Buffers {
@@ -91,6 +103,7 @@ struct Buffers {
     uint8_t *lvl_s, *nbr_cnt;
     uint32_t *nbr;
     float *rho;
+    float *lodd;                   // DTVS distance behind the visible surface, state order (-1: outside the view)
     uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
     unsigned long long *counters;  // [0] pairs, [1] lambda pairs
     uint32_t *drange;              // float bits of d_min (scenes entries), then d_max (scenes entries)
@@ -133,6 +146,8 @@ struct apbf_scene {
     int sms = 0;
     int grid_iter = 0;  // persistent grid of the iteration kernels
     apbf::Tune tune;
+    apbf::ViewConst view;  // DTVS camera image (single scenes)
+    bool view_set = false;
     // dynamic parameters, one per scene
     std::vector<apbf::DynParams> dyn;
     std::vector<float> grid_hi3;             // per scene static grid upper bounds (3 each)
@@ -175,6 +190,7 @@ cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s,
 cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
                           const Tune &tune);
 cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, cudaStream_t s);
 cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what);
 cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks);
 cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);

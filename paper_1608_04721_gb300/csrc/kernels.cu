@@ -319,6 +319,200 @@ __global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers
     }
 }
 
+// ------------------------------------------------- a1: DTVS (Sec. 4.1, Sec. 6)
+// Depth image of the particles rendered as spheres, then each particle's
+// distance behind the visible surface along its camera ray. Every value that
+// decides a level is FP32 with explicit rounding (no contraction): the camera
+// basis, the pixel rays, the sphere entry distances, the projection of the
+// particle onto its pixel and the distance.
+
+__device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0, float b1, float b2)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));
+}
+
+__device__ __forceinline__ void normalize3_rn(float &x, float &y, float &z)
+{
+    const float n = __fsqrt_rn(dot3_rn(x, y, z, x, y, z));
+    x = __fdiv_rn(x, n);
+    y = __fdiv_rn(y, n);
+    z = __fdiv_rn(z, n);
+}
+
+// forward f = dir/|dir|, right r = (f x up)/|f x up|, image up u = r x f
+struct Basis {
+    float f[3], r[3], u[3];
+    float ax, ay;  // half extents of the image plane at unit distance
+};
+
+__device__ __forceinline__ Basis view_basis(const ViewConst &v, const DynParams *dyn)
+{
+    Basis B;
+    float f0 = dyn->dir[0], f1 = dyn->dir[1], f2 = dyn->dir[2];
+    normalize3_rn(f0, f1, f2);
+    float r0 = __fsub_rn(__fmul_rn(f1, v.up[2]), __fmul_rn(f2, v.up[1]));
+    float r1 = __fsub_rn(__fmul_rn(f2, v.up[0]), __fmul_rn(f0, v.up[2]));
+    float r2 = __fsub_rn(__fmul_rn(f0, v.up[1]), __fmul_rn(f1, v.up[0]));
+    normalize3_rn(r0, r1, r2);
+    B.f[0] = f0;
+    B.f[1] = f1;
+    B.f[2] = f2;
+    B.r[0] = r0;
+    B.r[1] = r1;
+    B.r[2] = r2;
+    B.u[0] = __fsub_rn(__fmul_rn(r1, f2), __fmul_rn(r2, f1));
+    B.u[1] = __fsub_rn(__fmul_rn(r2, f0), __fmul_rn(r0, f2));
+    B.u[2] = __fsub_rn(__fmul_rn(r0, f1), __fmul_rn(r1, f0));
+    B.ax = __fmul_rn(v.tan_half, __fdiv_rn((float)v.W, (float)v.H));
+    B.ay = v.tan_half;
+    return B;
+}
+
+// Image coordinates (pixels, row 0 at the top) of a point relative to the eye
+// with depth zc > 0 along f.
+__device__ __forceinline__ float2 image_xy(const Basis &B, const ViewConst &v, float q0, float q1, float q2, float zc)
+{
+    const float qx = __fdiv_rn(__fdiv_rn(dot3_rn(q0, q1, q2, B.r[0], B.r[1], B.r[2]), zc), B.ax);
+    const float qy = __fdiv_rn(__fdiv_rn(dot3_rn(q0, q1, q2, B.u[0], B.u[1], B.u[2]), zc), B.ay);
+    return make_float2(__fmul_rn(__fadd_rn(qx, 1.0f), __fmul_rn(0.5f, (float)v.W)),
+                       __fmul_rn(__fsub_rn(1.0f, qy), __fmul_rn(0.5f, (float)v.H)));
+}
+
+// Pixel rays of the current camera; clears the depth image.
+__global__ void __launch_bounds__(kBlock) view_rays_kernel(ViewConst v, const DynParams *__restrict__ dyn)
+{
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= v.W * v.H)
+        return;
+    const Basis B = view_basis(v, dyn);
+    const uint32_t px = p % v.W, py = p / v.W;
+    const float sx = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * px + 1), (float)v.W), 1.0f), B.ax);
+    const float sy = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn((float)(2 * py + 1), (float)v.H)), B.ay);
+    float d[3];
+    for (int a = 0; a < 3; ++a)
+        d[a] = __fadd_rn(__fadd_rn(B.f[a], __fmul_rn(sx, B.r[a])), __fmul_rn(sy, B.u[a]));
+    normalize3_rn(d[0], d[1], d[2]);
+    v.ray[p] = make_float4(d[0], d[1], d[2], 0.0f);
+    v.depth[p] = 0x7f7f7f7fu;
+}
+
+// One particle per thread: the sphere's entry distance along every pixel ray
+// of its screen box, kept as the minimum per pixel. Positive floats order
+// like their bit patterns, so an unsigned atomicMin keeps the nearest; a
+// plain read first skips pixels already holding something nearer (the value
+// only decreases, so the skip never changes the result).
+__global__ void __launch_bounds__(kBlock) splat_kernel(StepConst sc, Buffers b, ViewConst v)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n)
+        return;
+    const DynParams *dyn = b.dyn;
+    const Basis B = view_basis(v, dyn);
+    const float4 x = b.state_x[i];
+    const float rel0 = __fsub_rn(x.x, dyn->eye[0]), rel1 = __fsub_rn(x.y, dyn->eye[1]),
+                rel2 = __fsub_rn(x.z, dyn->eye[2]);
+    const float rad = v.radius, r2 = __fmul_rn(v.radius, v.radius);
+    const float cc = __fsub_rn(dot3_rn(rel0, rel1, rel2, rel0, rel1, rel2), r2);
+    if (!(cc > 0.0f))
+        return;  // the eye is inside this sphere
+    const int W = (int)v.W, H = (int)v.H;
+    int x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
+    {
+        // screen box of the sphere's bounding cube, widened by one pixel
+        float fx_lo = 3.0e38f, fx_hi = -3.0e38f, fy_lo = 3.0e38f, fy_hi = -3.0e38f;
+        bool behind = false;
+        for (int c = 0; c < 8; ++c) {
+            const float q0 = __fadd_rn(rel0, (c & 1) ? rad : -rad);
+            const float q1 = __fadd_rn(rel1, (c & 2) ? rad : -rad);
+            const float q2 = __fadd_rn(rel2, (c & 4) ? rad : -rad);
+            const float zc = dot3_rn(q0, q1, q2, B.f[0], B.f[1], B.f[2]);
+            if (!(zc > 0.0f)) {
+                behind = true;
+                break;
+            }
+            const float2 xy = image_xy(B, v, q0, q1, q2, zc);
+            fx_lo = fminf(fx_lo, xy.x);
+            fx_hi = fmaxf(fx_hi, xy.x);
+            fy_lo = fminf(fy_lo, xy.y);
+            fy_hi = fmaxf(fy_hi, xy.y);
+        }
+        if (!behind) {
+            if (fx_hi < -1.0f || fy_hi < -1.0f || fx_lo > (float)W + 1.0f || fy_lo > (float)H + 1.0f)
+                return;  // entirely outside the image
+            x0 = max((int)floorf(fmaxf(fx_lo, -1.0f)) - 1, 0);
+            x1 = min((int)floorf(fminf(fx_hi, (float)W + 1.0f)) + 1, W - 1);
+            y0 = max((int)floorf(fmaxf(fy_lo, -1.0f)) - 1, 0);
+            y1 = min((int)floorf(fminf(fy_hi, (float)H + 1.0f)) + 1, H - 1);
+        }
+    }
+    for (int py = y0; py <= y1; ++py)
+        for (int px = x0; px <= x1; ++px) {
+            const uint32_t p = (uint32_t)py * v.W + (uint32_t)px;
+            const float4 ray = __ldg(&v.ray[p]);
+            const float bb = dot3_rn(ray.x, ray.y, ray.z, rel0, rel1, rel2);
+            if (!(bb > 0.0f))
+                continue;
+            const float w0 = __fsub_rn(rel0, __fmul_rn(bb, ray.x));
+            const float w1 = __fsub_rn(rel1, __fmul_rn(bb, ray.y));
+            const float w2 = __fsub_rn(rel2, __fmul_rn(bb, ray.z));
+            const float disc = __fsub_rn(r2, dot3_rn(w0, w1, w2, w0, w1, w2));
+            if (!(disc >= 0.0f))
+                continue;
+            const float t = __fsub_rn(bb, __fsqrt_rn(disc));
+            if (!(t > 0.0f))
+                continue;
+            const uint32_t tb = __float_as_uint(t);
+            if (tb < *(volatile uint32_t *)&v.depth[p])
+                atomicMin(&v.depth[p], tb);
+        }
+}
+
+// Distance of each particle behind the visible surface (-1 outside the view)
+// and the min/max over the particles in view.
+__global__ void __launch_bounds__(kBlock) dtvs_distance_kernel(StepConst sc, Buffers b, ViewConst v)
+{
+    __shared__ float smin[kBlock / 32], smax[kBlock / 32];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    float dmin = 3.0e38f, dmax = 0.0f;
+    if (i < sc.n) {
+        const DynParams *dyn = b.dyn;
+        const Basis B = view_basis(v, dyn);
+        const float4 x = b.state_x[i];
+        const float rel0 = __fsub_rn(x.x, dyn->eye[0]), rel1 = __fsub_rn(x.y, dyn->eye[1]),
+                    rel2 = __fsub_rn(x.z, dyn->eye[2]);
+        float d = -1.0f;
+        const float zc = dot3_rn(rel0, rel1, rel2, B.f[0], B.f[1], B.f[2]);
+        if (zc > 0.0f) {
+            const float2 xy = image_xy(B, v, rel0, rel1, rel2, zc);
+            if (xy.x >= 0.0f && xy.x < (float)v.W && xy.y >= 0.0f && xy.y < (float)v.H) {
+                const uint32_t p = (uint32_t)floorf(xy.y) * v.W + (uint32_t)floorf(xy.x);
+                const float front = __fsub_rn(__fsqrt_rn(dot3_rn(rel0, rel1, rel2, rel0, rel1, rel2)), v.radius);
+                const float g = __fsub_rn(front, __uint_as_float(v.depth[p]));
+                d = g > 0.0f ? g : 0.0f;
+                dmin = d;
+                dmax = d;
+            }
+        }
+        b.lodd[i] = d;
+    }
+    dmin = warp_minf(dmin);
+    dmax = warp_maxf(dmax);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        smin[w] = dmin;
+        smax[w] = dmax;
+    }
+    __syncthreads();
+    if (w == 0) {
+        dmin = warp_minf(lane < kBlock / 32 ? smin[lane] : 3.0e38f);
+        dmax = warp_maxf(lane < kBlock / 32 ? smax[lane] : 0.0f);
+        if (lane == 0 && dmin <= dmax) {
+            atomicMin(&b.drange[0], __float_as_uint(dmin));
+            atomicMax(&b.drange[1], __float_as_uint(dmax));
+        }
+    }
+}
+
 // ------------------------------------- a1-a4: level, predict, hash, count
 
 template <bool BATCH>
@@ -337,13 +531,18 @@ __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buff
             p = make_float3(x.x, x.y, x.z);
         } else {
             uint32_t lv = sc.n_max;
-            if (sc.lod_mode == APBF_LOD_DTC) {
+            if (sc.lod_mode != APBF_LOD_FIXED) {
                 float dmin = dyn->d_near, dmax = dyn->d_far;
                 if (dyn->auto_range) {
                     dmin = __uint_as_float(b.drange[s]);
                     dmax = __uint_as_float(b.drange[sc.scenes + s]);
                 }
-                lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
+                if (sc.lod_mode == APBF_LOD_DTC) {
+                    lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
+                } else {  // DTVS: outside the view -> n_min
+                    const float d = b.lodd[i];
+                    lv = d < 0.0f ? sc.n_min : lod_level(d, dmin, dmax, sc);
+                }
             }
             b.lvl[i] = (uint8_t)lv;
             p = predict_position(x, b.state_v[i], sc, dyn);
@@ -1083,6 +1282,17 @@ cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t 
     if (sc.n)
         (sc.scenes > 1 ? finalize_kernel<true> : finalize_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
             sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, cudaStream_t s)
+{
+    const uint32_t pix = v.W * v.H;
+    view_rays_kernel<<<blocks_for(pix, kBlock), kBlock, 0, s>>>(v, b.dyn);
+    if (sc.n) {
+        splat_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v);
+        dtvs_distance_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v);
+    }
     return cudaGetLastError();
 }
 

@@ -135,6 +135,10 @@ std::string resolve(const apbf_server_desc *d, StepConst &phys, StepConst &cap, 
     std::string m = derive(&p, phys, st);
     if (st != APBF_OK)
         return "physics: " + m;
+    if (p.lod_mode == APBF_LOD_DTVS) {
+        st = APBF_ERR_NOT_SUPPORTED;
+        return "the server steps batches; DTVS scenes are single scenes";
+    }
     st = APBF_ERR_INVALID_ARG;
     const uint32_t scenes = d->max_scenes ? d->max_scenes : 4096u;
     if (scenes > 65535u)
@@ -268,6 +272,7 @@ apbf_status relayout(apbf_server *sv)
             s->dyn[k].box_lo[a] = r->desc.box_lo[a];
             s->dyn[k].box_hi[a] = r->desc.box_hi[a];
             s->dyn[k].eye[a] = r->eye[a];
+            s->dyn[k].dir[a] = a == 0 ? 1.0f : 0.0f;
         }
         g.nx = r->geo.nx;
         g.ny = r->geo.ny;

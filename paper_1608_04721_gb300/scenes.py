@@ -32,6 +32,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 LOD_FIXED = 0
 LOD_DTC = 1
+LOD_DTVS = 2
 
 
 def splitmix64(counter: np.ndarray) -> np.ndarray:

@@ -25,7 +25,7 @@ def _declared():
 
 def test_exports_every_declared_symbol():
     names = _declared()
-    assert len(names) == 32
+    assert len(names) == 33
     out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout
     exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
@@ -75,7 +75,6 @@ def test_scene_bytes_scale_with_particles():
     (dict(n_min=0), apbf.APBF_ERR_INVALID_ARG),
     (dict(n_min=5, n_max=4), apbf.APBF_ERR_INVALID_ARG),
     (dict(n_max=256), apbf.APBF_ERR_INVALID_ARG),
-    (dict(lod_mode=apbf.APBF_LOD_DTVS), apbf.APBF_ERR_NOT_SUPPORTED),
     (dict(lod_mode=9), apbf.APBF_ERR_INVALID_ARG),
     (dict(stabil_s=3, stabil_iters=2), apbf.APBF_ERR_NOT_SUPPORTED),
     (dict(max_neighbors=300), apbf.APBF_ERR_INVALID_ARG),

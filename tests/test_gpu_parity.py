@@ -82,7 +82,7 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
         off = np.stack([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], 1)
         assert np.array_equal(cells[got] - cells[q], off), q
     lvl = st.level_presort[st.order]
-    if cfg.lod_mode == scenes.LOD_DTC and p.n_max > p.n_min:
+    if cfg.lod_mode in (scenes.LOD_DTC, scenes.LOD_DTVS) and p.n_max > p.n_min:
         apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
         lc = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_COUNT).astype(np.int64)
         assert np.array_equal(lc, st.active_count)
