@@ -46,6 +46,9 @@ STAGE_NAMES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors"
                "finalize"]
 
 
+DTVS_VIEW = (1280, 720, math.tan(math.radians(30.0)), (0.0, 0.0, 1.0))  # width, height, tan(fov_y/2), up
+
+
 def workload(name: str, lod: str):
     if name == "ocean_1m":
         cfg = scenes.config_ocean_1m()
@@ -58,6 +61,8 @@ def workload(name: str, lod: str):
         raise SystemExit(f"unknown workload {name}")
     if lod == "pbf":
         cfg = cfg.replace(lod_mode=scenes.LOD_FIXED, n_min=cfg.n_max)
+    elif lod == "dtvs":
+        cfg = cfg.replace(lod_mode=scenes.LOD_DTVS)
     return cfg
 
 
@@ -171,7 +176,12 @@ def kernels_per_step(cfg) -> int:
 
 def make_scene(apbf, cfg, rho0, stream=None):
     x, v = scenes.make_scene(cfg)
-    return apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, rho0), stream=stream)
+    s = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, rho0), stream=stream)
+    if cfg.lod_mode == scenes.LOD_DTVS:
+        W, H, t, up = DTVS_VIEW
+        drive(apbf, s, cfg, 0)
+        apbf.apbf_set_view(s, W, H, t, up, 0.5 * cfg.spacing)
+    return s
 
 
 def drive(apbf, scene, cfg, step):
@@ -731,6 +741,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pbf", action="store_true")
+    ap.add_argument("--no-dtvs", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -754,8 +765,10 @@ def main():
     pbf_cfg = workload(args.workload, "pbf")
     rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))
 
+    dtvs_cfg = workload(args.workload, "dtvs")
     scene = make_scene(apbf, cfg, rho0)
     pbf = None if args.no_pbf else make_scene(apbf, pbf_cfg, rho0)
+    dtvs = None if args.no_dtvs else make_scene(apbf, dtvs_cfg, rho0)
     tuning = {}
     if not args.no_autotune:
         # trial steps run on a snapshot that the tuner restores, so the timed trajectory is unchanged
@@ -764,6 +777,9 @@ def main():
         if pbf is not None:
             drive(apbf, pbf, pbf_cfg, 0)
             tuning["pbf_nmax"] = tune_summary(apbf.apbf_autotune(pbf, 4))
+        if dtvs is not None:
+            drive(apbf, dtvs, dtvs_cfg, 0)
+            tuning["apbf_dtvs"] = tune_summary(apbf.apbf_autotune(dtvs, 4))
     torch.cuda.synchronize()
 
     clocks = ClockSampler(torch.cuda.current_device())
@@ -786,6 +802,23 @@ def main():
         pbf_line = {"ms_per_step": pbf_ms, "p50_ms": metrics.percentile(pper, 50),
                     "p99_ms": metrics.percentile(pper, 99), "n": pbf_cfg.n_max,
                     "density": [float(v) for v in pbf_density]}
+    # ---- APBF with the DTVS model on identical inputs and drivers
+    dtvs_line = None
+    if dtvs is not None:
+        d.barrier()
+        dtot, dper, ds_next = timed_run(apbf, torch, dtvs, dtvs_cfg, args.warmup, args.steps)
+        d.barrier()
+        dtvs_ms = d.max(dtot / args.steps)
+        dtvs_density = apbf.apbf_density_stats(dtvs)
+        dms, _, _, _, diters, _ = stage_profile(apbf, dtvs, dtvs_cfg, ds_next, min(args.profile_steps, 20))
+        nprof = min(args.profile_steps, 20)
+        dtvs_line = {"ms_per_step": dtvs_ms, "p50_ms": metrics.percentile(dper, 50),
+                     "p99_ms": metrics.percentile(dper, 99),
+                     "view": {"width": DTVS_VIEW[0], "height": DTVS_VIEW[1], "fov_y_deg": 60.0,
+                              "radius": 0.5 * dtvs_cfg.spacing},
+                     "lod_stage_ms": float(dms[0] / nprof),
+                     "particle_iterations_per_step": diters / nprof,
+                     "density": [float(v) for v in dtvs_density]}
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -847,6 +880,9 @@ def main():
                     "fields": ["mean|rho/rho0-1|", "max|rho/rho0-1|", "mean(rho/rho0-1)", "mean max(0,rho/rho0-1)"]},
         "pbf_nmax": pbf_line,
         "improvement": metrics.improvement(pbf_line["ms_per_step"], ms_step) if pbf_line else None,
+        "apbf_dtvs": dtvs_line,
+        "improvement_dtvs": (metrics.improvement(pbf_line["ms_per_step"], dtvs_line["ms_per_step"])
+                             if pbf_line and dtvs_line else None),
         "roofline": roofline,
         "stage_ms_per_step": stage_ms,
         "e2e": e2e,
@@ -861,6 +897,8 @@ def main():
     apbf.apbf_destroy_scene(scene)
     if pbf is not None:
         apbf.apbf_destroy_scene(pbf)
+    if dtvs is not None:
+        apbf.apbf_destroy_scene(dtvs)
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.close()

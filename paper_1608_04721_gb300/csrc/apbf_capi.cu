@@ -345,7 +345,7 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
         e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
             cudaMemsetAsync(b.drange, 0x7f, 4, st);
             cudaMemsetAsync(b.drange + 1, 0, 4, st);
-            return launch_dtvs(sc, b, s->view, st);
+            return launch_dtvs(sc, b, s->view, s->sms, st);
         });
         if (e != cudaSuccess)
             return cuda_fail(s, e, "dtvs");
@@ -788,23 +788,48 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     if (!up || !finite3(up) || !view_axes_ok(s->dyn[0].dir, up))
         return fail(s, APBF_ERR_INVALID_ARG, "up must be finite and not parallel to the camera direction");
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));  // the previous image may still be in use
+    // one allocation: depth, rays, tile counters, starts and lists, the big-sphere list
     const size_t pix = (size_t)width * height;
-    if (!s->view_set || (size_t)s->view.W * s->view.H != pix) {
-        if (s->view.depth)
-            cudaFree(s->view.depth);
-        if (s->view.ray)
-            cudaFree(s->view.ray);
-        s->view.depth = nullptr;
-        s->view.ray = nullptr;
+    const uint32_t tx = (width + kTilePx - 1) / kTilePx, ty = (height + kTilePx - 1) / kTilePx;
+    const size_t tiles = (size_t)tx * ty, n = s->sc.n;
+    const size_t cap = (size_t)kSplatListPerParticle * n + 65536;
+    size_t off[12], total = 0;
+    const size_t sizes[12] = {4 * pix, 16 * pix, 4 * tiles, 4 * tiles, 4 * (tiles + 1), 4 * cap, 4 * n, 4,
+                              4 * (tiles + 1), 8, n, 8 * n};
+    for (int k = 0; k < 12; ++k) {
+        off[k] = total;
+        total = align_up(total + (sizes[k] ? sizes[k] : 1));
+    }
+    if (!s->view.alloc || s->view.alloc_bytes < total) {
+        if (s->view.alloc)
+            cudaFree(s->view.alloc);
+        s->view.alloc = nullptr;
+        s->view.alloc_bytes = 0;
         s->view_set = false;
-        cudaError_t e = cudaMalloc(&s->view.depth, 4 * pix);
-        if (e == cudaSuccess)
-            e = cudaMalloc(&s->view.ray, 16 * pix);
+        cudaError_t e = cudaMalloc(&s->view.alloc, total);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            s->view.alloc = nullptr;
             return fail(s, APBF_ERR_OUT_OF_MEMORY, std::string("view image: ") + cudaGetErrorString(e));
         }
+        s->view.alloc_bytes = total;
     }
+    char *base = (char *)s->view.alloc;
+    s->view.depth = (uint32_t *)(base + off[0]);
+    s->view.ray = (float4 *)(base + off[1]);
+    s->view.tile_cnt = (uint32_t *)(base + off[2]);
+    s->view.tile_fill = (uint32_t *)(base + off[3]);
+    s->view.tile_start = (uint32_t *)(base + off[4]);
+    s->view.tile_list = (uint32_t *)(base + off[5]);
+    s->view.big = (uint32_t *)(base + off[6]);
+    s->view.big_cnt = (uint32_t *)(base + off[7]);
+    s->view.chunk_start = (uint32_t *)(base + off[8]);
+    s->view.list_used = (unsigned long long *)(base + off[9]);
+    s->view.accepted = (uint8_t *)(base + off[10]);
+    s->view.box = (uint2 *)(base + off[11]);
+    s->view.list_cap = (uint32_t)cap;
+    s->view.tiles_x = tx;
+    s->view.tiles_y = ty;
     s->view.W = width;
     s->view.H = height;
     s->view.tan_half = tan_half_fov;
@@ -993,10 +1018,8 @@ APBF_API void apbf_destroy_scene(apbf_scene *s)
         cudaFreeHost(s->pinned_small);
     if (s->own_arena && s->arena)
         cudaFree(s->arena);
-    if (s->view.depth)
-        cudaFree(s->view.depth);
-    if (s->view.ray)
-        cudaFree(s->view.ray);
+    if (s->view.alloc)
+        cudaFree(s->view.alloc);
     delete s;
 }
 

@@ -18,6 +18,10 @@ constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
 constexpr int kBlock = 256;          // threads per block of the per-particle kernels
 constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
 constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
+constexpr int kTilePx = 16;          // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
+constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles are rasterised one block each
+constexpr uint32_t kSplatChunk = 1024;     // list entries per work chunk of the tile rasteriser
+constexpr uint32_t kSplatListPerParticle = 16;  // tile-list capacity: 16 entries per particle + 65536
 
 // Device error word bits.
 constexpr uint32_t kErrNeighborOverflow = 1u;
@@ -90,6 +94,21 @@ struct ViewConst {
     float radius = 0.0f;    // sphere radius of the rendered particles
     uint32_t *depth = nullptr;  // W*H float bits, row 0 at the top
     float4 *ray = nullptr;      // W*H unit pixel rays of the current camera
+    // binning of the rendered spheres into kTilePx x kTilePx pixel tiles
+    uint32_t tiles_x = 0, tiles_y = 0;
+    uint32_t *tile_cnt = nullptr;    // spheres per tile
+    uint32_t *tile_fill = nullptr;   // fill counters of the scatter pass
+    uint32_t *tile_start = nullptr;  // tiles + 1 list offsets
+    uint32_t *chunk_start = nullptr; // tiles + 1 offsets of the tiles' kSplatChunk-entry work chunks
+    uint32_t *tile_list = nullptr;   // list_cap particle indices
+    uint32_t list_cap = 0;
+    unsigned long long *list_used = nullptr;  // entries reserved this step (64-bit: rejected reservations count too)
+    uint8_t *accepted = nullptr;     // n: the sphere is in the tile lists
+    uint2 *box = nullptr;            // n: screen box of an accepted sphere (x0 | x1 << 16, y0 | y1 << 16)
+    uint32_t *big = nullptr;         // n: spheres rasterised one block each
+    uint32_t *big_cnt = nullptr;
+    void *alloc = nullptr;           // the one device allocation holding all of the above
+    size_t alloc_bytes = 0;
 };
 
 struct Buffers {
@@ -190,7 +209,7 @@ cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s,
 cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
                           const Tune &tune);
 cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s);
-cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, cudaStream_t s);
+cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, int sms, cudaStream_t s);
 cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what);
 cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks);
 cudaError_t launch_debug_xstar(const StepConst &sc, const Buffers &b, const float4 *rec, cudaStream_t s);

@@ -378,10 +378,18 @@ __device__ __forceinline__ float2 image_xy(const Basis &B, const ViewConst &v, f
                        __fmul_rn(__fsub_rn(1.0f, qy), __fmul_rn(0.5f, (float)v.H)));
 }
 
-// Pixel rays of the current camera; clears the depth image.
+// Pixel rays of the current camera; clears the depth image and the binning counters.
 __global__ void __launch_bounds__(kBlock) view_rays_kernel(ViewConst v, const DynParams *__restrict__ dyn)
 {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < v.tiles_x * v.tiles_y) {
+        v.tile_cnt[p] = 0u;
+        v.tile_fill[p] = 0u;
+    }
+    if (p == 0) {
+        *v.big_cnt = 0u;
+        *v.list_used = 0ull;
+    }
     if (p >= v.W * v.H)
         return;
     const Basis B = view_basis(v, dyn);
@@ -396,75 +404,269 @@ __global__ void __launch_bounds__(kBlock) view_rays_kernel(ViewConst v, const Dy
     v.depth[p] = 0x7f7f7f7fu;
 }
 
-// One particle per thread: the sphere's entry distance along every pixel ray
-// of its screen box, kept as the minimum per pixel. Positive floats order
-// like their bit patterns, so an unsigned atomicMin keeps the nearest; a
-// plain read first skips pixels already holding something nearer (the value
-// only decreases, so the skip never changes the result).
-__global__ void __launch_bounds__(kBlock) splat_kernel(StepConst sc, Buffers b, ViewConst v)
+// Screen box of a particle's sphere: the pixels around the projections of the
+// 8 corners of its bounding cube, widened by one pixel (conservative: every
+// pixel whose ray enters the sphere is inside). Returns 0 when the sphere is
+// not rendered (the eye is inside it) or lies entirely outside the image, 1
+// for a box, 2 when a corner is not in front of the camera (then the box is
+// the whole image).
+struct SplatBox {
+    float rel0, rel1, rel2, cc;
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ int splat_box(const Basis &B, const ViewConst &v, const DynParams *dyn, float4 x,
+                                         SplatBox &o)
+{
+    o.rel0 = __fsub_rn(x.x, dyn->eye[0]);
+    o.rel1 = __fsub_rn(x.y, dyn->eye[1]);
+    o.rel2 = __fsub_rn(x.z, dyn->eye[2]);
+    const float rad = v.radius, r2 = __fmul_rn(v.radius, v.radius);
+    const float len2 = dot3_rn(o.rel0, o.rel1, o.rel2, o.rel0, o.rel1, o.rel2);
+    o.cc = __fsub_rn(len2, r2);
+    if (!(o.cc > 0.0f))
+        return 0;
+    {
+        // frustum cull: every pixel ray lies within the angle gamma of f (the
+        // image corner), and a ray entering the sphere lies within its angular
+        // radius beta of rel, so a sphere whose direction is further than
+        // gamma + beta (+ 0.01 rad for rounding) from f is entered by no pixel
+        // ray. This also drops every sphere behind the camera.
+        const float len = sqrtf(len2);
+        const float zc = dot3_rn(o.rel0, o.rel1, o.rel2, B.f[0], B.f[1], B.f[2]);
+        const float theta = acosf(fminf(fmaxf(zc / len, -1.0f), 1.0f));
+        const float beta = asinf(fminf(rad / len, 1.0f));
+        const float gamma = atanf(sqrtf(B.ax * B.ax + B.ay * B.ay));
+        if (theta > beta + gamma + 0.01f)
+            return 0;
+    }
+    const int W = (int)v.W, H = (int)v.H;
+    o.x0 = 0;
+    o.x1 = W - 1;
+    o.y0 = 0;
+    o.y1 = H - 1;
+    float fx_lo = 3.0e38f, fx_hi = -3.0e38f, fy_lo = 3.0e38f, fy_hi = -3.0e38f;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        const float q0 = __fadd_rn(o.rel0, (c & 1) ? rad : -rad);
+        const float q1 = __fadd_rn(o.rel1, (c & 2) ? rad : -rad);
+        const float q2 = __fadd_rn(o.rel2, (c & 4) ? rad : -rad);
+        const float zc = dot3_rn(q0, q1, q2, B.f[0], B.f[1], B.f[2]);
+        if (!(zc > 0.0f))
+            return 2;
+        const float2 xy = image_xy(B, v, q0, q1, q2, zc);
+        fx_lo = fminf(fx_lo, xy.x);
+        fx_hi = fmaxf(fx_hi, xy.x);
+        fy_lo = fminf(fy_lo, xy.y);
+        fy_hi = fmaxf(fy_hi, xy.y);
+    }
+    if (fx_hi < -1.0f || fy_hi < -1.0f || fx_lo > (float)W + 1.0f || fy_lo > (float)H + 1.0f)
+        return 0;
+    o.x0 = max((int)floorf(fmaxf(fx_lo, -1.0f)) - 1, 0);
+    o.x1 = min((int)floorf(fminf(fx_hi, (float)W + 1.0f)) + 1, W - 1);
+    o.y0 = max((int)floorf(fmaxf(fy_lo, -1.0f)) - 1, 0);
+    o.y1 = min((int)floorf(fminf(fy_hi, (float)H + 1.0f)) + 1, H - 1);
+    return (o.x0 <= o.x1 && o.y0 <= o.y1) ? 1 : 0;
+}
+
+// Entry distance of the ray into the sphere at rel (FP32, every operation
+// rounded), as float bits; 0x7f7f7f7f when it does not enter in front of the eye.
+__device__ __forceinline__ uint32_t entry_bits(float4 ray, float rel0, float rel1, float rel2, float r2)
+{
+    const float bb = dot3_rn(ray.x, ray.y, ray.z, rel0, rel1, rel2);
+    if (!(bb > 0.0f))
+        return 0x7f7f7f7fu;
+    const float w0 = __fsub_rn(rel0, __fmul_rn(bb, ray.x));
+    const float w1 = __fsub_rn(rel1, __fmul_rn(bb, ray.y));
+    const float w2 = __fsub_rn(rel2, __fmul_rn(bb, ray.z));
+    const float disc = __fsub_rn(r2, dot3_rn(w0, w1, w2, w0, w1, w2));
+    if (!(disc >= 0.0f))
+        return 0x7f7f7f7fu;
+    const float t = __fsub_rn(bb, __fsqrt_rn(disc));
+    return t > 0.0f ? __float_as_uint(t) : 0x7f7f7f7fu;
+}
+
+// Binning of the spheres into kTilePx x kTilePx pixel tiles. Pass 0 reserves
+// room in the tile lists (capacity v.list_cap entries) for each sphere's
+// tiles and counts them per tile; a sphere that crosses the camera plane,
+// covers more than kMaxSplatTiles tiles or finds the lists full is listed as
+// "big" instead. Pass 1 writes the tile lists of the spheres pass 0 accepted.
+// Positive floats order like their bit patterns, so the depth is a minimum
+// over unsigned integers: it depends neither on list order nor on which
+// spheres took which path.
+__global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers b, ViewConst v, int pass)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc.n)
-        return;
-    const DynParams *dyn = b.dyn;
-    const Basis B = view_basis(v, dyn);
-    const float4 x = b.state_x[i];
-    const float rel0 = __fsub_rn(x.x, dyn->eye[0]), rel1 = __fsub_rn(x.y, dyn->eye[1]),
-                rel2 = __fsub_rn(x.z, dyn->eye[2]);
-    const float rad = v.radius, r2 = __fmul_rn(v.radius, v.radius);
-    const float cc = __fsub_rn(dot3_rn(rel0, rel1, rel2, rel0, rel1, rel2), r2);
-    if (!(cc > 0.0f))
-        return;  // the eye is inside this sphere
-    const int W = (int)v.W, H = (int)v.H;
-    int x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
-    {
-        // screen box of the sphere's bounding cube, widened by one pixel
-        float fx_lo = 3.0e38f, fx_hi = -3.0e38f, fy_lo = 3.0e38f, fy_hi = -3.0e38f;
-        bool behind = false;
-        for (int c = 0; c < 8; ++c) {
-            const float q0 = __fadd_rn(rel0, (c & 1) ? rad : -rad);
-            const float q1 = __fadd_rn(rel1, (c & 2) ? rad : -rad);
-            const float q2 = __fadd_rn(rel2, (c & 4) ? rad : -rad);
-            const float zc = dot3_rn(q0, q1, q2, B.f[0], B.f[1], B.f[2]);
-            if (!(zc > 0.0f)) {
-                behind = true;
-                break;
+    const bool valid = i < sc.n;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    if (pass == 1) {
+        if (!valid || !v.accepted[i])
+            return;
+        const uint2 bx = v.box[i];
+        x0 = (int)(bx.x & 0xffffu);
+        x1 = (int)(bx.x >> 16);
+        y0 = (int)(bx.y & 0xffffu);
+        y1 = (int)(bx.y >> 16);
+    } else {
+        int kind = 0;
+        uint32_t nt = 0;
+        if (valid) {
+            const Basis B = view_basis(v, b.dyn);
+            SplatBox o;
+            kind = splat_box(B, v, b.dyn, b.state_x[i], o);
+            v.accepted[i] = 0;
+            if (kind == 1) {
+                x0 = o.x0;
+                x1 = o.x1;
+                y0 = o.y0;
+                y1 = o.y1;
+                nt = (uint32_t)((x1 / kTilePx - x0 / kTilePx + 1) * (y1 / kTilePx - y0 / kTilePx + 1));
+                if (nt > kMaxSplatTiles) {
+                    kind = 2;
+                    nt = 0;
+                }
             }
-            const float2 xy = image_xy(B, v, q0, q1, q2, zc);
-            fx_lo = fminf(fx_lo, xy.x);
-            fx_hi = fmaxf(fx_hi, xy.x);
-            fy_lo = fminf(fy_lo, xy.y);
-            fy_hi = fmaxf(fy_hi, xy.y);
         }
-        if (!behind) {
-            if (fx_hi < -1.0f || fy_hi < -1.0f || fx_lo > (float)W + 1.0f || fy_lo > (float)H + 1.0f)
-                return;  // entirely outside the image
-            x0 = max((int)floorf(fmaxf(fx_lo, -1.0f)) - 1, 0);
-            x1 = min((int)floorf(fminf(fx_hi, (float)W + 1.0f)) + 1, W - 1);
-            y0 = max((int)floorf(fmaxf(fy_lo, -1.0f)) - 1, 0);
-            y1 = min((int)floorf(fminf(fy_hi, (float)H + 1.0f)) + 1, H - 1);
+        // one reservation per warp: the lanes' tile counts, prefix-summed
+        uint32_t incl = nt;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o)
+                incl += y;
         }
+        const uint32_t wsum = __shfl_sync(kFull, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && wsum)
+            base = atomicAdd(v.list_used, (unsigned long long)wsum);
+        base = __shfl_sync(kFull, base, 31);
+        if (!valid || kind == 0)
+            return;
+        if (kind == 2 || base + incl > (unsigned long long)v.list_cap) {
+            v.big[atomicAdd(v.big_cnt, 1u)] = i;  // whole-image sphere, too many tiles, or the lists are full
+            return;
+        }
+        v.accepted[i] = 1;
+        v.box[i] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
     }
-    for (int py = y0; py <= y1; ++py)
-        for (int px = x0; px <= x1; ++px) {
-            const uint32_t p = (uint32_t)py * v.W + (uint32_t)px;
-            const float4 ray = __ldg(&v.ray[p]);
-            const float bb = dot3_rn(ray.x, ray.y, ray.z, rel0, rel1, rel2);
-            if (!(bb > 0.0f))
-                continue;
-            const float w0 = __fsub_rn(rel0, __fmul_rn(bb, ray.x));
-            const float w1 = __fsub_rn(rel1, __fmul_rn(bb, ray.y));
-            const float w2 = __fsub_rn(rel2, __fmul_rn(bb, ray.z));
-            const float disc = __fsub_rn(r2, dot3_rn(w0, w1, w2, w0, w1, w2));
-            if (!(disc >= 0.0f))
-                continue;
-            const float t = __fsub_rn(bb, __fsqrt_rn(disc));
-            if (!(t > 0.0f))
-                continue;
-            const uint32_t tb = __float_as_uint(t);
+    const int tx0 = x0 / kTilePx, tx1 = x1 / kTilePx, ty0 = y0 / kTilePx, ty1 = y1 / kTilePx;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const uint32_t t = (uint32_t)ty * v.tiles_x + (uint32_t)tx;
+            if (pass == 0)
+                atomicAdd(&v.tile_cnt[t], 1u);
+            else
+                v.tile_list[v.tile_start[t] + atomicAdd(&v.tile_fill[t], 1u)] = i;
+        }
+}
+
+// Exclusive scans of the tile counts into tile_start and of the tiles'
+// kSplatChunk-entry work chunks into chunk_start (tiles + 1 entries each), one block.
+__global__ void __launch_bounds__(1024) splat_tile_scan_kernel(ViewConst v)
+{
+    __shared__ uint32_t sh32[32];
+    const uint32_t T = v.tiles_x * v.tiles_y;
+    const uint32_t per = (T + blockDim.x - 1) / blockDim.x;
+    const uint32_t a = threadIdx.x * per, e = min(a + per, T);
+    uint32_t sum = 0, chunks = 0;
+    for (uint32_t k = a; k < e; ++k) {
+        sum += v.tile_cnt[k];
+        chunks += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+    }
+    uint32_t total, ctotal;
+    uint32_t run = block_exclusive_scan_u32(sum, sh32, &total);
+    uint32_t crun = block_exclusive_scan_u32(chunks, sh32, &ctotal);
+    for (uint32_t k = a; k < e; ++k) {
+        v.tile_start[k] = run;
+        v.chunk_start[k] = crun;
+        run += v.tile_cnt[k];
+        crun += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+    }
+    if (threadIdx.x == 0) {
+        v.tile_start[T] = total;
+        v.chunk_start[T] = ctotal;
+    }
+}
+
+// Spheres covering many tiles: one block each, its threads over the box's
+// pixels, nearest kept with an atomic minimum (a plain read first skips
+// pixels that already hold something nearer; values only decrease).
+__global__ void __launch_bounds__(kBlock) splat_big_kernel(StepConst sc, Buffers b, ViewConst v)
+{
+    const uint32_t nb = *v.big_cnt;
+    const Basis B = view_basis(v, b.dyn);
+    const float r2 = __fmul_rn(v.radius, v.radius);
+    for (uint32_t k = blockIdx.x; k < nb; k += gridDim.x) {
+        SplatBox o;
+        if (splat_box(B, v, b.dyn, b.state_x[v.big[k]], o) == 0)
+            continue;
+        const uint32_t bw = (uint32_t)(o.x1 - o.x0 + 1), area = bw * (uint32_t)(o.y1 - o.y0 + 1);
+        for (uint32_t q = threadIdx.x; q < area; q += blockDim.x) {
+            const uint32_t p = (uint32_t)(o.y0 + (int)(q / bw)) * v.W + (uint32_t)(o.x0 + (int)(q % bw));
+            const uint32_t tb = entry_bits(__ldg(&v.ray[p]), o.rel0, o.rel1, o.rel2, r2);
             if (tb < *(volatile uint32_t *)&v.depth[p])
                 atomicMin(&v.depth[p], tb);
         }
+    }
+}
+
+// Persistent blocks over work chunks (up to kSplatChunk list entries of one
+// tile): one thread per pixel of the chunk's tile, the spheres staged in
+// shared memory kTilePx^2 at a time with their screen boxes, the nearest
+// entry along the thread's ray kept in a register (a sphere is tested only
+// at pixels inside its conservative box), then merged into the image with an
+// atomic minimum (several chunks of a crowded tile may finish in any order).
+__global__ void __launch_bounds__(kTilePx *kTilePx) splat_tile_kernel(StepConst sc, Buffers b, ViewConst v)
+{
+    __shared__ float4 sp[kTilePx * kTilePx];
+    __shared__ uint2 sbox[kTilePx * kTilePx];
+    const uint32_t T = v.tiles_x * v.tiles_y;
+    const uint32_t nwork = v.chunk_start[T];
+    const float r2 = __fmul_rn(v.radius, v.radius);
+    const DynParams *dyn = b.dyn;
+    const float e0 = dyn->eye[0], e1 = dyn->eye[1], e2 = dyn->eye[2];
+    for (uint32_t w = blockIdx.x; w < nwork; w += gridDim.x) {
+        uint32_t lo = 0, hi = T;  // the tile whose chunks hold w: chunk_start[lo] <= w < chunk_start[lo + 1]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (v.chunk_start[mid] <= w)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint32_t tile = lo;
+        const uint32_t beg = v.tile_start[tile] + (w - v.chunk_start[tile]) * kSplatChunk;
+        const uint32_t end = min(beg + kSplatChunk, v.tile_start[tile + 1]);
+        const uint32_t px = (tile % v.tiles_x) * kTilePx + (threadIdx.x % kTilePx);
+        const uint32_t py = (tile / v.tiles_x) * kTilePx + (threadIdx.x / kTilePx);
+        const bool inside = px < v.W && py < v.H;
+        const uint32_t p = py * v.W + px;
+        const float4 ray = inside ? v.ray[p] : make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+        uint32_t best = 0x7f7f7f7fu;
+        for (uint32_t c = beg; c < end; c += kTilePx * kTilePx) {
+            const uint32_t k = c + threadIdx.x;
+            if (k < end) {
+                const uint32_t i = v.tile_list[k];
+                const float4 x = b.state_x[i];
+                sp[threadIdx.x] = make_float4(__fsub_rn(x.x, e0), __fsub_rn(x.y, e1), __fsub_rn(x.z, e2), 0.0f);
+                sbox[threadIdx.x] = v.box[i];
+            }
+            __syncthreads();
+            const uint32_t m = min((uint32_t)(kTilePx * kTilePx), end - c);
+            if (inside)
+                for (uint32_t j = 0; j < m; ++j) {
+                    const uint2 bx = sbox[j];
+                    if (px < (bx.x & 0xffffu) || px > (bx.x >> 16) || py < (bx.y & 0xffffu) || py > (bx.y >> 16))
+                        continue;
+                    const float4 q = sp[j];
+                    best = min(best, entry_bits(ray, q.x, q.y, q.z, r2));
+                }
+            __syncthreads();
+        }
+        if (inside && best < *(volatile uint32_t *)&v.depth[p])
+            atomicMin(&v.depth[p], best);
+    }
 }
 
 // Distance of each particle behind the visible surface (-1 outside the view)
@@ -1285,12 +1487,16 @@ cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, cudaStream_t s)
+cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, int sms, cudaStream_t s)
 {
-    const uint32_t pix = v.W * v.H;
-    view_rays_kernel<<<blocks_for(pix, kBlock), kBlock, 0, s>>>(v, b.dyn);
+    const uint32_t pix = v.W * v.H, tiles = v.tiles_x * v.tiles_y;
+    view_rays_kernel<<<blocks_for(pix > tiles ? pix : tiles, kBlock), kBlock, 0, s>>>(v, b.dyn);
     if (sc.n) {
-        splat_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v);
+        splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 0);
+        splat_tile_scan_kernel<<<1, 1024, 0, s>>>(v);
+        splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 1);
+        splat_big_kernel<<<(unsigned)(sms > 0 ? 2 * sms : 1), kBlock, 0, s>>>(sc, b, v);
+        splat_tile_kernel<<<(unsigned)(sms > 0 ? 8 * sms : 1), kTilePx * kTilePx, 0, s>>>(sc, b, v);
         dtvs_distance_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v);
     }
     return cudaGetLastError();

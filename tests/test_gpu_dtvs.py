@@ -74,6 +74,10 @@ CASES = {
                                 (64, 64, 0.8, (0, 0, 1), 0.03)),
     # narrow view: most particles outside the image
     "narrow_view_5200": lambda: (_dam(), (-1.5, 0.5, 0.3), (1.0, 0.0, 0.0), (32, 24, 0.05, (0, 0, 1), 0.025)),
+    # large spheres close to the camera: their tiles exhaust the tile-list capacity
+    # (16 per particle + 65536), so many spheres take the one-block-per-sphere path
+    "huge_spheres_1000": lambda: (_dam((10, 10, 10), 2, 6), (-0.35, 0.25, 0.3), (1.0, 0.05, -0.1),
+                                  (512, 512, 0.9, (0, 0, 1), 0.2)),
     # a single pixel
     "one_pixel_1000": lambda: (_dam((10, 10, 10), 1, 4), (-1.0, 0.25, 0.25), (1.0, 0.0, 0.0),
                                (1, 1, 0.4, (0, 0, 1), 0.025)),
