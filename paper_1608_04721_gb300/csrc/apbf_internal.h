@@ -18,7 +18,7 @@ constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
 constexpr int kBlock = 256;          // threads per block of the per-particle kernels
 constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
 constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
-constexpr int kTilePx = 16;          // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
+constexpr int kTilePx = 8;           // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
 constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles are rasterised one block each
 constexpr uint32_t kSplatChunk = 1024;     // list entries per work chunk of the tile rasteriser
 constexpr uint32_t kSplatListPerParticle = 16;  // tile-list capacity: 16 entries per particle + 65536

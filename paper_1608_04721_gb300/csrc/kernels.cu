@@ -1496,7 +1496,7 @@ cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &
         splat_tile_scan_kernel<<<1, 1024, 0, s>>>(v);
         splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 1);
         splat_big_kernel<<<(unsigned)(sms > 0 ? 2 * sms : 1), kBlock, 0, s>>>(sc, b, v);
-        splat_tile_kernel<<<(unsigned)(sms > 0 ? 8 * sms : 1), kTilePx * kTilePx, 0, s>>>(sc, b, v);
+        splat_tile_kernel<<<(unsigned)(sms > 0 ? 32 * sms : 1), kTilePx * kTilePx, 0, s>>>(sc, b, v);
         dtvs_distance_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v);
     }
     return cudaGetLastError();
