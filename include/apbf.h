@@ -196,8 +196,8 @@ APBF_API apbf_status apbf_set_camera(apbf_scene *scene, const float eye[3], cons
  * All of steps 1-3 is FP32 with every operation rounded (no contraction).
  *  width, height  1..16384 each, width * height <= 2^26.
  *  up             host, 3 floats, finite, not parallel to the camera's dir.
- * The image and its rasterisation lists (20 bytes per pixel, 16 per 16 x 16
- * tile, 77 per particle) are device memory the scene allocates here. */
+ * The image and its rasterisation lists (20 bytes per pixel, 20 per 8 x 8
+ * tile, 81 per particle) are device memory the scene allocates here. */
 APBF_API apbf_status apbf_set_view(apbf_scene *scene, uint32_t width, uint32_t height, float tan_half_fov,
                                    const float up[3], float radius);
 

@@ -793,10 +793,10 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     const uint32_t tx = (width + kTilePx - 1) / kTilePx, ty = (height + kTilePx - 1) / kTilePx;
     const size_t tiles = (size_t)tx * ty, n = s->sc.n;
     const size_t cap = (size_t)kSplatListPerParticle * n + 65536;
-    size_t off[12], total = 0;
-    const size_t sizes[12] = {4 * pix, 16 * pix, 4 * tiles, 4 * tiles, 4 * (tiles + 1), 4 * cap, 4 * n, 4,
-                              4 * (tiles + 1), 8, n, 8 * n};
-    for (int k = 0; k < 12; ++k) {
+    size_t off[14], total = 0;
+    const size_t sizes[14] = {4 * pix, 16 * pix, 4 * tiles, 4 * tiles, 4 * (tiles + 1), 4 * cap, 4 * n, 4,
+                              4 * (tiles + 1), 8, n, 8 * n, 4 * n, 4 * tiles};
+    for (int k = 0; k < 14; ++k) {
         off[k] = total;
         total = align_up(total + (sizes[k] ? sizes[k] : 1));
     }
@@ -827,6 +827,8 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     s->view.list_used = (unsigned long long *)(base + off[9]);
     s->view.accepted = (uint8_t *)(base + off[10]);
     s->view.box = (uint2 *)(base + off[11]);
+    s->view.near = (float *)(base + off[12]);
+    s->view.tile_max = (uint32_t *)(base + off[13]);
     s->view.list_cap = (uint32_t)cap;
     s->view.tiles_x = tx;
     s->view.tiles_y = ty;

@@ -19,9 +19,11 @@ constexpr int kBlock = 256;          // threads per block of the per-particle ke
 constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
 constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
 constexpr int kTilePx = 8;           // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
-constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles are rasterised one block each
+constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles take the big-sphere path
+constexpr int kBigBlockPx = 64;            // image blocks of the big-sphere path
 constexpr uint32_t kSplatChunk = 1024;     // list entries per work chunk of the tile rasteriser
 constexpr uint32_t kSplatListPerParticle = 16;  // tile-list capacity: 16 entries per particle + 65536
+constexpr uint8_t kFrontNeighbors = 28;    // phase-0 spheres: fewer neighbours than this in the last step
 
 // Device error word bits.
 constexpr uint32_t kErrNeighborOverflow = 1u;
@@ -105,6 +107,8 @@ struct ViewConst {
     unsigned long long *list_used = nullptr;  // entries reserved this step (64-bit: rejected reservations count too)
     uint8_t *accepted = nullptr;     // n: the sphere is in the tile lists
     uint2 *box = nullptr;            // n: screen box of an accepted sphere (x0 | x1 << 16, y0 | y1 << 16)
+    float *near = nullptr;           // n: lower bound of the sphere's entry distances
+    uint32_t *tile_max = nullptr;    // tiles: farthest depth bits of the phase-0 image
     uint32_t *big = nullptr;         // n: spheres rasterised one block each
     uint32_t *big_cnt = nullptr;
     void *alloc = nullptr;           // the one device allocation holding all of the above

@@ -412,6 +412,7 @@ __global__ void __launch_bounds__(kBlock) view_rays_kernel(ViewConst v, const Dy
 // the whole image).
 struct SplatBox {
     float rel0, rel1, rel2, cc;
+    float near;  // a lower bound of every FP32 entry distance into the sphere
     int x0, x1, y0, y1;
 };
 
@@ -433,6 +434,9 @@ __device__ __forceinline__ int splat_box(const Basis &B, const ViewConst &v, con
         // gamma + beta (+ 0.01 rad for rounding) from f is entered by no pixel
         // ray. This also drops every sphere behind the camera.
         const float len = sqrtf(len2);
+        // no ray enters the sphere closer than len - r; 4e-6 len (32 units in
+        // the last place) covers the rounding of the FP32 entry distance there
+        o.near = (len - rad) - 4.0e-6f * len;
         const float zc = dot3_rn(o.rel0, o.rel1, o.rel2, B.f[0], B.f[1], B.f[2]);
         const float theta = acosf(fminf(fmaxf(zc / len, -1.0f), 1.0f));
         const float beta = asinf(fminf(rad / len, 1.0f));
@@ -486,44 +490,88 @@ __device__ __forceinline__ uint32_t entry_bits(float4 ray, float rel0, float rel
     return t > 0.0f ? __float_as_uint(t) : 0x7f7f7f7fu;
 }
 
-// Binning of the spheres into kTilePx x kTilePx pixel tiles. Pass 0 reserves
-// room in the tile lists (capacity v.list_cap entries) for each sphere's
-// tiles and counts them per tile; a sphere that crosses the camera plane,
-// covers more than kMaxSplatTiles tiles or finds the lists full is listed as
-// "big" instead. Pass 1 writes the tile lists of the spheres pass 0 accepted.
-// Positive floats order like their bit patterns, so the depth is a minimum
-// over unsigned integers: it depends neither on list order nor on which
-// spheres took which path.
-__global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers b, ViewConst v, int pass)
+// Binning of the spheres into kTilePx x kTilePx pixel tiles, in two phases.
+// Phase 0 takes the spheres of particles that had fewer than kFrontNeighbors
+// neighbours in the previous step (the fluid's surfaces, which hide most of
+// the rest); phase 1 takes the others, after tile_max holds each tile's
+// farthest depth of the phase-0 image, and lists a sphere only in the tiles
+// where it can still come out in front (its nearest possible entry is
+// nearer than that tile's farthest depth: otherwise it can lower no pixel
+// of the tile). Pass 0 of a phase reserves room in the tile lists (capacity
+// v.list_cap entries) for each sphere's tiles and counts them per tile; a
+// sphere that crosses the camera plane, covers more than kMaxSplatTiles
+// tiles or finds the lists full is listed as "big" instead. Pass 1 writes
+// the tile lists of the spheres pass 0 accepted. Positive floats order like
+// their bit patterns, so the depth is a minimum over unsigned integers: it
+// depends neither on list order nor on which spheres took which path, and a
+// sphere that can lower no pixel may be left out.
+__device__ __forceinline__ bool tile_open(const ViewConst &v, int phase, uint32_t t, float near)
+{
+    return phase == 0 || near < __uint_as_float(v.tile_max[t]);
+}
+
+__global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers b, ViewConst v, int pass, int phase)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < sc.n;
+    const bool member = valid && ((b.nbr_cnt[i] < kFrontNeighbors) == (phase == 0));
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    float near = 0.0f;
     if (pass == 1) {
-        if (!valid || !v.accepted[i])
+        const bool mine = member && v.accepted[i];
+        if (mine) {
+            const uint2 bx = v.box[i];
+            x0 = (int)(bx.x & 0xffffu);
+            x1 = (int)(bx.x >> 16);
+            y0 = (int)(bx.y & 0xffffu);
+            y1 = (int)(bx.y >> 16);
+            near = v.near[i];
+        }
+        const int tx0 = x0 / kTilePx, tx1 = x1 / kTilePx, ty0 = y0 / kTilePx, ty1 = y1 / kTilePx;
+        const int tw = tx1 - tx0 + 1, ntb = mine ? tw * (ty1 - ty0 + 1) : 0;
+        // spheres over many tiles: the warp writes their entries together, one
+        // tile per lane (each entry's slot comes from an atomic on its tile)
+        unsigned wide = __ballot_sync(kFull, ntb > 32);
+        const int lane = threadIdx.x & 31;
+        while (wide) {
+            const int src = __ffs(wide) - 1;
+            wide &= wide - 1;
+            const int sx0 = __shfl_sync(kFull, tx0, src), sy0 = __shfl_sync(kFull, ty0, src);
+            const int sw = __shfl_sync(kFull, tw, src), sn = __shfl_sync(kFull, ntb, src);
+            const float snear = __shfl_sync(kFull, near, src);
+            const uint32_t si = __shfl_sync(kFull, i, src);
+            for (int q = lane; q < sn; q += 32) {
+                const uint32_t t = (uint32_t)(sy0 + q / sw) * v.tiles_x + (uint32_t)(sx0 + q % sw);
+                if (tile_open(v, phase, t, snear))
+                    v.tile_list[v.tile_start[t] + atomicAdd(&v.tile_fill[t], 1u)] = si;
+            }
+        }
+        if (ntb == 0 || ntb > 32)
             return;
-        const uint2 bx = v.box[i];
-        x0 = (int)(bx.x & 0xffffu);
-        x1 = (int)(bx.x >> 16);
-        y0 = (int)(bx.y & 0xffffu);
-        y1 = (int)(bx.y >> 16);
     } else {
         int kind = 0;
         uint32_t nt = 0;
-        if (valid) {
+        if (valid)
+            v.accepted[i] = 0;
+        if (member) {
             const Basis B = view_basis(v, b.dyn);
             SplatBox o;
             kind = splat_box(B, v, b.dyn, b.state_x[i], o);
-            v.accepted[i] = 0;
             if (kind == 1) {
                 x0 = o.x0;
                 x1 = o.x1;
                 y0 = o.y0;
                 y1 = o.y1;
-                nt = (uint32_t)((x1 / kTilePx - x0 / kTilePx + 1) * (y1 / kTilePx - y0 / kTilePx + 1));
-                if (nt > kMaxSplatTiles) {
+                near = o.near;
+                const int tx0 = x0 / kTilePx, tx1 = x1 / kTilePx, ty0 = y0 / kTilePx, ty1 = y1 / kTilePx;
+                if ((uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1)) > kMaxSplatTiles) {
                     kind = 2;
-                    nt = 0;
+                } else {
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx)
+                            nt += tile_open(v, phase, (uint32_t)ty * v.tiles_x + (uint32_t)tx, near) ? 1u : 0u;
+                    if (nt == 0)
+                        kind = 0;  // hidden in every tile it covers
                 }
             }
         }
@@ -541,7 +589,7 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
         if (lane == 31 && wsum)
             base = atomicAdd(v.list_used, (unsigned long long)wsum);
         base = __shfl_sync(kFull, base, 31);
-        if (!valid || kind == 0)
+        if (!member || kind == 0)
             return;
         if (kind == 2 || base + incl > (unsigned long long)v.list_cap) {
             v.big[atomicAdd(v.big_cnt, 1u)] = i;  // whole-image sphere, too many tiles, or the lists are full
@@ -549,16 +597,41 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
         }
         v.accepted[i] = 1;
         v.box[i] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+        v.near[i] = near;
     }
     const int tx0 = x0 / kTilePx, tx1 = x1 / kTilePx, ty0 = y0 / kTilePx, ty1 = y1 / kTilePx;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
             const uint32_t t = (uint32_t)ty * v.tiles_x + (uint32_t)tx;
+            if (!tile_open(v, phase, t, near))
+                continue;
             if (pass == 0)
                 atomicAdd(&v.tile_cnt[t], 1u);
             else
                 v.tile_list[v.tile_start[t] + atomicAdd(&v.tile_fill[t], 1u)] = i;
         }
+}
+
+// Between the phases: each tile's farthest depth of the image so far (an
+// empty pixel makes it 3.4e38, so nothing is culled there), and the binning
+// counters reset for phase 1.
+__global__ void __launch_bounds__(kBlock) splat_tile_max_kernel(ViewConst v)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        *v.big_cnt = 0u;
+        *v.list_used = 0ull;
+    }
+    if (t >= v.tiles_x * v.tiles_y)
+        return;
+    const uint32_t ox = (t % v.tiles_x) * kTilePx, oy = (t / v.tiles_x) * kTilePx;
+    uint32_t m = 0u;
+    for (uint32_t y = oy; y < min(oy + kTilePx, v.H); ++y)
+        for (uint32_t x = ox; x < min(ox + kTilePx, v.W); ++x)
+            m = max(m, v.depth[y * v.W + x]);
+    v.tile_max[t] = m;
+    v.tile_cnt[t] = 0u;
+    v.tile_fill[t] = 0u;
 }
 
 // Exclusive scans of the tile counts into tile_start and of the tiles'
@@ -589,21 +662,33 @@ __global__ void __launch_bounds__(1024) splat_tile_scan_kernel(ViewConst v)
     }
 }
 
-// Spheres covering many tiles: one block each, its threads over the box's
-// pixels, nearest kept with an atomic minimum (a plain read first skips
-// pixels that already hold something nearer; values only decrease).
+// Spheres covering many tiles (near the eye), crossing the camera plane, or
+// left over when the tile lists are full: work items of one sphere and one
+// kBigBlockPx x kBigBlockPx block of the image, spread over a persistent
+// grid; the block's threads run over the pixels where that image block
+// meets the sphere's screen box, keeping the nearest entry with an atomic
+// minimum (a plain read first skips pixels that already hold something
+// nearer; values only decrease).
 __global__ void __launch_bounds__(kBlock) splat_big_kernel(StepConst sc, Buffers b, ViewConst v)
 {
     const uint32_t nb = *v.big_cnt;
+    const uint32_t mx = (v.W + kBigBlockPx - 1) / kBigBlockPx, my = (v.H + kBigBlockPx - 1) / kBigBlockPx;
+    const uint32_t per = mx * my;
     const Basis B = view_basis(v, b.dyn);
     const float r2 = __fmul_rn(v.radius, v.radius);
-    for (uint32_t k = blockIdx.x; k < nb; k += gridDim.x) {
+    for (unsigned long long w = blockIdx.x; w < (unsigned long long)nb * per; w += gridDim.x) {
+        const uint32_t k = (uint32_t)(w / per), j = (uint32_t)(w % per);
+        const int bx0 = (int)((j % mx) * kBigBlockPx), by0 = (int)((j / mx) * kBigBlockPx);
         SplatBox o;
         if (splat_box(B, v, b.dyn, b.state_x[v.big[k]], o) == 0)
             continue;
-        const uint32_t bw = (uint32_t)(o.x1 - o.x0 + 1), area = bw * (uint32_t)(o.y1 - o.y0 + 1);
+        const int x0 = max(o.x0, bx0), x1 = min(o.x1, bx0 + kBigBlockPx - 1);
+        const int y0 = max(o.y0, by0), y1 = min(o.y1, by0 + kBigBlockPx - 1);
+        if (x0 > x1 || y0 > y1)
+            continue;
+        const uint32_t bw = (uint32_t)(x1 - x0 + 1), area = bw * (uint32_t)(y1 - y0 + 1);
         for (uint32_t q = threadIdx.x; q < area; q += blockDim.x) {
-            const uint32_t p = (uint32_t)(o.y0 + (int)(q / bw)) * v.W + (uint32_t)(o.x0 + (int)(q % bw));
+            const uint32_t p = (uint32_t)(y0 + (int)(q / bw)) * v.W + (uint32_t)(x0 + (int)(q % bw));
             const uint32_t tb = entry_bits(__ldg(&v.ray[p]), o.rel0, o.rel1, o.rel2, r2);
             if (tb < *(volatile uint32_t *)&v.depth[p])
                 atomicMin(&v.depth[p], tb);
@@ -1492,11 +1577,15 @@ cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &
     const uint32_t pix = v.W * v.H, tiles = v.tiles_x * v.tiles_y;
     view_rays_kernel<<<blocks_for(pix > tiles ? pix : tiles, kBlock), kBlock, 0, s>>>(v, b.dyn);
     if (sc.n) {
-        splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 0);
-        splat_tile_scan_kernel<<<1, 1024, 0, s>>>(v);
-        splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 1);
-        splat_big_kernel<<<(unsigned)(sms > 0 ? 2 * sms : 1), kBlock, 0, s>>>(sc, b, v);
-        splat_tile_kernel<<<(unsigned)(sms > 0 ? 32 * sms : 1), kTilePx * kTilePx, 0, s>>>(sc, b, v);
+        for (int phase = 0; phase < 2; ++phase) {
+            if (phase == 1)
+                splat_tile_max_kernel<<<blocks_for(tiles, kBlock), kBlock, 0, s>>>(v);
+            splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 0, phase);
+            splat_tile_scan_kernel<<<1, 1024, 0, s>>>(v);
+            splat_bin_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v, 1, phase);
+            splat_big_kernel<<<(unsigned)(sms > 0 ? 4 * sms : 1), kBlock, 0, s>>>(sc, b, v);
+            splat_tile_kernel<<<(unsigned)(sms > 0 ? 32 * sms : 1), kTilePx * kTilePx, 0, s>>>(sc, b, v);
+        }
         dtvs_distance_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b, v);
     }
     return cudaGetLastError();

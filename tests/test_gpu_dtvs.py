@@ -95,6 +95,29 @@ def test_dtvs_stagewise_parity(name):
     check_final(cfg, scene, p, st)
 
 
+def test_dtvs_two_phase_render_after_steps_is_bitwise():
+    """After a few steps the renderer draws the spheres of particles with few
+    neighbours first and leaves out, tile by tile, the others that cannot come
+    out in front; the image, distances and levels must still equal the
+    oracle's for the same positions."""
+    cfg, eye, direction, view = CASES["oblique_5200"]()
+    scene, p, x, v = make(cfg, eye, direction, view)
+    apbf.apbf_step(scene, 3)
+    st = apbf.apbf_read_state(scene, pos=True, vel=True)
+    cnt = apbf.apbf_debug_read(scene, apbf.APBF_DBG_NBR_COUNT)
+    assert np.any(cnt < 28) and np.any(cnt >= 28)          # both phases have spheres
+    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_PREDICT)
+    ids = apbf.apbf_debug_read(scene, apbf.APBF_DBG_STATE_IDS).astype(np.int64)
+    xs = st["pos"][ids]                                     # positions in the scene's state order
+    depth_ref = oracle.depth_image(p, xs)
+    depth = apbf.apbf_debug_read(scene, apbf.APBF_DBG_DEPTH)
+    assert np.array_equal(depth.view(np.uint32), depth_ref.view(np.uint32))
+    dist = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LOD_DISTANCE)
+    assert np.array_equal(dist.view(np.uint32), oracle.dtvs_distance(p, xs, depth_ref).view(np.uint32))
+    lv = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_PRESORT).astype(np.int32)
+    assert np.array_equal(lv, oracle.lod_levels(p, xs)[0])
+
+
 def test_dtvs_user_distance_range():
     cfg, eye, direction, view = CASES["oblique_5200"]()
     scene, p, x, v = make(cfg, eye, direction, view, d_near=0.05, d_far=0.4)
