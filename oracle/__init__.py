@@ -48,6 +48,14 @@ def make_view(width: int, height: int, tan_half_fov: float, direction, up=(0.0, 
     return v
 
 
+ORC_MAX_OBSTACLES = 8
+ORC_OBSTACLE_SPHERE, ORC_OBSTACLE_BOX, ORC_OBSTACLE_CONE = 1, 2, 3
+
+
+class OrcObstacle(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", C.c_float * 3), ("b", C.c_float * 3)]
+
+
 class OrcParams(C.Structure):
     _fields_ = [
         ("h", C.c_float), ("dt", C.c_float), ("mass", C.c_float), ("rho0", C.c_float),
@@ -61,6 +69,9 @@ class OrcParams(C.Structure):
         ("d_near", C.c_float), ("d_far", C.c_float),
         ("lambda_mode", C.c_int32), ("lod_rounding", C.c_int32),
         ("view", OrcView),
+        ("stabil_iters", C.c_int32), ("stabil_s", C.c_int32),
+        ("n_obstacles", C.c_int32),
+        ("obstacles", OrcObstacle * ORC_MAX_OBSTACLES),
     ]
 
 
@@ -122,6 +133,8 @@ def lib():
                                P(OrcRecord)]
         L.orc_density_stats.argtypes = [P(OrcParams), C.c_int32, P(C.c_float), P(C.c_double),
                                         P(C.c_double)]
+        L.orc_obstacle_project.argtypes = [P(OrcObstacle), P(C.c_double), P(C.c_double)]
+        L.orc_obstacle_project.restype = C.c_int
         L.orc_view_basis.argtypes = [P(OrcView), P(C.c_float), P(C.c_float), P(C.c_float)]
         L.orc_pixel_ray.argtypes = [P(OrcView), C.c_int32, C.c_int32, P(C.c_float)]
         L.orc_depth_image.argtypes = [P(OrcParams), C.c_int32, P(C.c_float), P(C.c_float)]
@@ -152,7 +165,7 @@ def _ptr(a: Optional[np.ndarray], ctype):
 
 def make_params(cfg=None, *, rho0: float, box_lo=None, box_hi=None, eye=(0.0, 0.0, 0.0),
                 d_near: float = 0.0, d_far: float = 0.0, lambda_mode: int = ORC_LAMBDA_STALE,
-                lod_rounding: int = 0, view: Optional[OrcView] = None, **over) -> OrcParams:
+                lod_rounding: int = 0, view: Optional[OrcView] = None, obstacles=(), **over) -> OrcParams:
     """Parameters from a scenes.SceneConfig (or keyword overrides)."""
     vals = {}
     if cfg is not None:
@@ -183,6 +196,18 @@ def make_params(cfg=None, *, rho0: float, box_lo=None, box_hi=None, eye=(0.0, 0.
     p.lod_rounding = int(lod_rounding)
     if view is not None:
         p.view = view
+    if cfg is not None:
+        vals.setdefault("stabil_iters", getattr(cfg, "stabil_iters", 0))
+        vals.setdefault("stabil_s", getattr(cfg, "stabil_s", 1))
+        if not obstacles:
+            obstacles = getattr(cfg, "obstacles", ())
+    p.stabil_iters = int(vals.get("stabil_iters", 0))
+    p.stabil_s = int(vals.get("stabil_s", 1))
+    p.n_obstacles = len(obstacles)
+    for k, (kind, a, b) in enumerate(obstacles):
+        p.obstacles[k].kind = int(kind)
+        p.obstacles[k].a[:] = [float(t) for t in a]
+        p.obstacles[k].b[:] = [float(t) for t in b]
     return p
 
 
@@ -219,6 +244,18 @@ def lod_levels(p: OrcParams, x: np.ndarray):
     _check(lib().orc_lod_levels(C.byref(p), n, _ptr(x, C.c_float), _ptr(lv, C.c_int32),
                                 _ptr(rng, C.c_float)), "orc_lod_levels")
     return lv, rng
+
+
+def obstacle_project(kind, a, b, x):
+    """(inside, nearest surface point) of a point for one obstacle, FP64."""
+    o = OrcObstacle()
+    o.kind = int(kind)
+    o.a[:] = [float(t) for t in a]
+    o.b[:] = [float(t) for t in b]
+    xx = np.ascontiguousarray(x, np.float64)
+    q = np.zeros(3)
+    inside = lib().orc_obstacle_project(C.byref(o), _ptr(xx, C.c_double), _ptr(q, C.c_double))
+    return bool(inside), q
 
 
 def view_basis(v: OrcView):

@@ -16,8 +16,15 @@
  *  - Inactive neighbours enter Eq. 7 with their last lambda (Fig. 7 computes
  *    lambda only over P_iter while Eq. 7 sums over all neighbours).
  *  - A particle of level L takes part in iterations 1..L (Eq. 9-10).
- *  - Contacts are an axis-aligned box clamp after the prediction and after
- *    every position update.
+ *  - Contacts (Fig. 7 line 18): after every position update, a predicted
+ *    position strictly inside an obstacle moves to the nearest point of its
+ *    surface (obstacles in order), then into the box; the prediction itself is
+ *    only clamped to the box.
+ *  - Pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11) of the set of Eq. 11 for
+ *    l = S, i.e. the particles of level < S: stabil_iters times, the position
+ *    at the start of the step is moved out of the obstacles and into the box,
+ *    and the predicted position is moved by the same amount, so v = (x* - x)/dt
+ *    gains nothing from the correction.
  */
 #include "apbf_oracle.h"
 
@@ -749,6 +756,89 @@ int orc_xsph(const orc_params *p, int32_t n, const double *xs, const double *v, 
     return 0;
 }
 
+int orc_obstacle_project(const orc_obstacle *o, const double x[3], double q[3])
+{
+    q[0] = x[0];
+    q[1] = x[1];
+    q[2] = x[2];
+    if (!o)
+        return 0;
+    if (o->kind == ORC_OBSTACLE_SPHERE) {
+        double d[3] = {x[0] - o->a[0], x[1] - o->a[1], x[2] - o->a[2]};
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), R = o->b[0];
+        if (!(r < R))
+            return 0;
+        if (r == 0.0) {
+            q[2] = o->a[2] + R;
+            return 1;
+        }
+        for (int k = 0; k < 3; ++k)
+            q[k] = o->a[k] + R * d[k] / r;
+        return 1;
+    }
+    if (o->kind == ORC_OBSTACLE_BOX) {
+        double best = INFINITY, face = 0.0;
+        int axis = -1;
+        for (int k = 0; k < 3; ++k) {
+            if (!(x[k] > o->a[k] && x[k] < o->b[k]))
+                return 0;
+            double dl = x[k] - o->a[k], dh = o->b[k] - x[k];
+            if (dl < best) {
+                best = dl;
+                axis = k;
+                face = o->a[k];
+            }
+            if (dh < best) {
+                best = dh;
+                axis = k;
+                face = o->b[k];
+            }
+        }
+        q[axis] = face;
+        return 1;
+    }
+    if (o->kind == ORC_OBSTACLE_CONE) {
+        /* in the half plane (rho, z) through the axis the solid is the right
+           triangle (0, zb), (R, zb), (0, zb + H) */
+        const double R = o->b[0], H = o->b[1], zb = o->a[2];
+        double ux = x[0] - o->a[0], uy = x[1] - o->a[1];
+        double rho = sqrt(ux * ux + uy * uy), z = x[2] - zb;
+        if (!(z > 0.0 && rho / R + z / H < 1.0))
+            return 0;
+        double L = sqrt(R * R + H * H);
+        double g = (H * rho + R * z - R * H) / L; /* signed distance to the slant line, < 0 inside */
+        if (z <= -g) {
+            q[2] = zb; /* the base is nearest */
+            return 1;
+        }
+        double rho2 = rho - g * H / L, z2 = z - g * R / L;
+        if (rho > 0.0) {
+            ux /= rho;
+            uy /= rho;
+        } else {
+            ux = 1.0;
+            uy = 0.0;
+        }
+        q[0] = o->a[0] + rho2 * ux;
+        q[1] = o->a[1] + rho2 * uy;
+        q[2] = zb + z2;
+        return 1;
+    }
+    return 0;
+}
+
+static void contact_obstacles(const orc_params *p, double *x3)
+{
+    for (int32_t k = 0; k < p->n_obstacles; ++k) {
+        double q[3];
+        if (orc_obstacle_project(&p->obstacles[k], x3, q)) {
+            x3[0] = q[0];
+            x3[1] = q[1];
+            x3[2] = q[2];
+        }
+    }
+}
+
 static void clamp_box(const orc_params *p, double *x3)
 {
     for (int a = 0; a < 3; ++a) {
@@ -767,6 +857,8 @@ static int validate(const orc_params *p, int32_t n)
         return -1;
     if (p->n_min < 1 || p->n_max < p->n_min || p->scorr_n < 0)
         return -1;
+    if (p->n_obstacles < 0 || p->n_obstacles > ORC_MAX_OBSTACLES || p->stabil_iters < 0 || p->stabil_s < 0)
+        return -1;
     for (int a = 0; a < 3; ++a)
         if (!(p->grid_lo[a] <= p->box_lo[a]) || !(p->box_lo[a] < p->box_hi[a]) ||
             !(p->box_hi[a] <= p->grid_hi[a]))
@@ -774,8 +866,7 @@ static int validate(const orc_params *p, int32_t n)
     return 0;
 }
 
-/* One step of Fig. 7 (lines 1-27), pre-stabilisation off (S = 1, so the set
-   of Eq. 11 is empty). */
+/* One step of Fig. 7 (lines 1-27). */
 int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, orc_record *rec)
 {
     if (validate(p, n) != 0 || (n > 0 && (!x || !v || !id)))
@@ -800,9 +891,10 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
     double *lam = (double *)calloc(nn, sizeof(double));
     double *vel = (double *)malloc(sizeof(double) * 3 * nn);
     double *vout = (double *)malloc(sizeof(double) * 3 * nn);
+    double *x0d = (double *)malloc(sizeof(double) * 3 * nn);
     int32_t *noff = NULL, *nidx = NULL;
     if (!level0 || !xpred || !keys || !order || !start || !xs32 || !x0s || !ids || !lvl || !xs || !dp ||
-        !lam || !vel || !vout)
+        !lam || !vel || !vout || !x0d)
         goto done;
 
     /* LOD from the positions at the start of the step (Sec. 4.1, Sec. 6). */
@@ -893,9 +985,26 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
             rec->dims[a] = dims[a];
     }
 
-    /* Fig. 7 lines 12-23: N_max Jacobi iterations over the active sets P_l. */
-    for (size_t k = 0; k < 3 * (size_t)n; ++k)
+    for (size_t k = 0; k < 3 * (size_t)n; ++k) {
         xs[k] = (double)xs32[k];
+        x0d[k] = (double)x0s[k];
+    }
+    /* Fig. 7 lines 7-11: pre-stabilisation of the particles of level < S. */
+    for (int32_t s = 0; s < n; ++s) {
+        if (!(lvl[s] < p->stabil_s))
+            continue;
+        for (int32_t it = 0; it < p->stabil_iters; ++it) {
+            double q[3] = {x0d[3 * s], x0d[3 * s + 1], x0d[3 * s + 2]};
+            contact_obstacles(p, q);
+            clamp_box(p, q);
+            for (int a = 0; a < 3; ++a) {
+                double d = q[a] - x0d[3 * s + a];
+                x0d[3 * s + a] = q[a];
+                xs[3 * s + a] += d;
+            }
+        }
+    }
+    /* Fig. 7 lines 12-23: N_max Jacobi iterations over the active sets P_l. */
     for (int32_t l = 1; l <= p->n_max; ++l) {
         for (int32_t s = 0; s < n; ++s) {
             int active = lvl[s] >= l;
@@ -921,6 +1030,7 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
                 xs[3 * s + 0] += dp[3 * s + 0];
                 xs[3 * s + 1] += dp[3 * s + 1];
                 xs[3 * s + 2] += dp[3 * s + 2];
+                contact_obstacles(p, xs + 3 * s);
                 clamp_box(p, xs + 3 * s);
             }
         if (rec && rec->xs && l <= rec->rec_iters)
@@ -930,7 +1040,7 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
     /* Fig. 7 lines 24-27: v = (x* - x) / dt, XSPH smoothing, x = x*. */
     for (int32_t s = 0; s < n; ++s)
         for (int a = 0; a < 3; ++a)
-            vel[3 * s + a] = (xs[3 * s + a] - (double)x0s[3 * s + a]) / (double)p->dt;
+            vel[3 * s + a] = (xs[3 * s + a] - x0d[3 * s + a]) / (double)p->dt;
     orc_xsph(p, n, xs, vel, noff, nidx, vout);
     if (rec && rec->x_final)
         memcpy(rec->x_final, xs, sizeof(double) * 3 * (size_t)n);
@@ -958,6 +1068,7 @@ done:
     free(dp);
     free(lam);
     free(vel);
+    free(x0d);
     free(vout);
     free(noff);
     free(nidx);

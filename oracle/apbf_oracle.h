@@ -48,6 +48,20 @@ typedef struct orc_view {
     int32_t brute_force; /* 1: test every pixel against every sphere (no bounding box) */
 } orc_view;
 
+/* Rigid obstacles (Sec. 6 uses signed-distance fields; these are analytic
+   solids): a point strictly inside is moved to the nearest point of the
+   solid's surface. */
+#define ORC_MAX_OBSTACLES 8
+#define ORC_OBSTACLE_SPHERE 1 /* a = centre, b[0] = radius */
+#define ORC_OBSTACLE_BOX 2    /* a = min corner, b = max corner (a solid block) */
+#define ORC_OBSTACLE_CONE 3   /* a = centre of the base disc, axis +z, b[0] = base radius, b[1] = height */
+
+typedef struct orc_obstacle {
+    int32_t kind;
+    float a[3];
+    float b[3];
+} orc_obstacle;
+
 typedef struct orc_params {
     /* Scene values exactly as the solver receives them (FP32). */
     float h, dt, mass, rho0, eps, scorr_k, scorr_dq, xsph_c;
@@ -61,6 +75,12 @@ typedef struct orc_params {
     int32_t lambda_mode;          /* ORC_LAMBDA_* */
     int32_t lod_rounding;         /* 0: equal-width bins, 1: rounded interpolation */
     orc_view view;                /* DTVS only */
+    /* Pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11): particles of level < stabil_s
+       (the set of Eq. 11 for l = S) are moved out of the obstacles and into the box
+       stabil_iters times before the solver, current and predicted positions alike. */
+    int32_t stabil_iters, stabil_s;
+    int32_t n_obstacles;
+    orc_obstacle obstacles[ORC_MAX_OBSTACLES];
 } orc_params;
 
 typedef struct orc_record {
@@ -122,6 +142,10 @@ int orc_dtvs_distance(const orc_params *p, int32_t n, const float *x, const floa
    distance (DTC) or the distance behind the visible surface (DTVS;
    particles outside the view get n_min and do not enter the automatic range). */
 int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *level, float range[2]);
+
+/* Nearest surface point of an obstacle for a point strictly inside it (FP64);
+   returns 1 and writes q when x is inside, 0 (q = x) otherwise. */
+int orc_obstacle_project(const orc_obstacle *o, const double x[3], double q[3]);
 
 /* Fig. 7 lines 1-4 plus the box clamp, FP32. */
 int orc_predict(const orc_params *p, int32_t n, const float *x, const float *v, float *xpred);

@@ -275,7 +275,8 @@ def desc_from_config(cfg, pos, vel, rho0: float, **over):
     """apbf_scene_desc from a scenes.SceneConfig (plain field mapping)."""
     kw = dict(pos=pos, vel=vel, grid_lo=cfg.box_lo, grid_hi=cfg.box_hi, h=cfg.h, dt=cfg.dt, mass=cfg.mass,
               rho0=rho0, eps=cfg.eps, scorr_k=cfg.scorr_k, scorr_dq=cfg.scorr_dq, scorr_n=cfg.scorr_n,
-              xsph_c=cfg.xsph_c, gravity=cfg.gravity, n_min=cfg.n_min, n_max=cfg.n_max, lod_mode=cfg.lod_mode)
+              xsph_c=cfg.xsph_c, gravity=cfg.gravity, n_min=cfg.n_min, n_max=cfg.n_max, lod_mode=cfg.lod_mode,
+              stabil_iters=getattr(cfg, "stabil_iters", 0), stabil_s=getattr(cfg, "stabil_s", 1))
     kw.update(over)
     return make_desc(**kw)
 

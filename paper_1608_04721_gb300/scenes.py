@@ -90,6 +90,9 @@ class SceneConfig:
     wall_amplitude: float = 0.5
     wall_period: float = 2.0
     rho0: Optional[float] = None            # None: the caller supplies the lattice rest density
+    stabil_iters: int = 0                   # pre-stabilisation iterations (Sec. 4.3)
+    stabil_s: int = 1                       # S: particles of level < S are pre-stabilised (S <= 1: none)
+    obstacles: tuple = ()                   # ((kind, a, b), ...) analytic solids, see apbf_set_obstacles
 
     @property
     def n(self) -> int:

@@ -12,6 +12,7 @@ import pytest
 import oracle as O
 from oracle import build as B
 import tests.test_oracle_dtvs_pins as dtvs
+import tests.test_oracle_obstacle_pins as obst
 import tests.test_oracle_pins as pins
 
 MUTATIONS = [
@@ -65,6 +66,23 @@ MUTATIONS = [
     ("DTVS cull box without its one-pixel margin",
      "x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) - 1;", "x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) + 1;",
      lambda: dtvs.test_bounding_box_cull_equals_every_pixel(0)),
+    ("pre-stabilisation moves only the current position",
+     "                x0d[3 * s + a] = q[a];\n                xs[3 * s + a] += d;\n",
+     "                x0d[3 * s + a] = q[a];\n                (void)d;\n",
+     obst.test_prestabilisation_keeps_the_particles_own_velocity),
+    ("pre-stabilisation applied to the levels at or above S",
+     "if (!(lvl[s] < p->stabil_s))", "if (!(lvl[s] >= p->stabil_s))",
+     obst.test_only_levels_below_S_are_prestabilised),
+    ("cone projection along a wrongly oriented normal",
+     "double rho2 = rho - g * H / L, z2 = z - g * R / L;", "double rho2 = rho - g * R / L, z2 = z - g * H / L;",
+     lambda: obst.test_projection_is_the_nearest_surface_point(obst.CONE)),
+    ("block contacts ignore the upper faces",
+     "            if (dh < best) {", "            if (0 && dh < best) {",
+     lambda: obst.test_projection_is_the_nearest_surface_point(obst.BLOCK)),
+    ("contact response left out of the solver's position update",
+     "                contact_obstacles(p, xs + 3 * s);\n                clamp_box(p, xs + 3 * s);",
+     "                clamp_box(p, xs + 3 * s);",
+     obst.test_no_particle_ends_inside_an_obstacle_after_a_pbf_step),
 ]
 
 
