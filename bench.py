@@ -43,7 +43,7 @@ SM_MAX_MHZ = 2070.0
 # algorithmic FP32 operations per in-range neighbour pair (sqrt and divide count 1)
 FLOPS_PER_PAIR = {"lambda": 25, "deltap": 28, "finalize": 26}
 STAGE_NAMES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
-               "finalize"]
+               "finalize", "prestab"]
 
 
 DTVS_VIEW = (1280, 720, math.tan(math.radians(30.0)), (0.0, 0.0, 1.0))  # width, height, tan(fov_y/2), up

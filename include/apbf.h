@@ -86,9 +86,14 @@ typedef enum apbf_status {
  *  lod_mode     APBF_LOD_FIXED, APBF_LOD_DTC or APBF_LOD_DTVS (not in batches or servers:
  *               APBF_ERR_NOT_SUPPORTED).
  *  stabil_iters, stabil_s
- *               pre-stabilisation (Fig. 7 lines 7-11) of the set of Eq. 11 for
- *               l = S. Only S <= 1 (empty set) is supported; S > 1 returns
- *               APBF_ERR_NOT_SUPPORTED.
+ *               pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11) of the set of
+ *               Eq. 11 for l = S, i.e. the particles of level < S: before the
+ *               solver, stabil_iters times (<= 64), each such particle's
+ *               position at the start of the step is moved out of the
+ *               obstacles (apbf_set_obstacles) and into the box, and its
+ *               predicted position by the same amount, so its velocity gains
+ *               nothing from the correction. S <= 1 (empty set) turns it off;
+ *               S <= n_max.
  *  max_neighbors neighbour-list capacity per particle, 0 = 128, at most 255.
  *  flags        APBF_FLAG_*.
  */
@@ -201,6 +206,34 @@ APBF_API apbf_status apbf_set_camera(apbf_scene *scene, const float eye[3], cons
 APBF_API apbf_status apbf_set_view(apbf_scene *scene, uint32_t width, uint32_t height, float tan_half_fov,
                                    const float up[3], float radius);
 
+/*
+ * Rigid obstacles (the paper's signed-distance-field obstacles of Sec. 6, here
+ * analytic solids), used from the next step on by the contact response of
+ * Fig. 7 line 18 -- after every position update of the solver, a predicted
+ * position strictly inside an obstacle moves to the nearest point of its
+ * surface (obstacles in order), then into the box -- and by the
+ * pre-stabilisation above. The prediction itself is only clamped to the box.
+ *  index      scene of a batch (0 for a single scene).
+ *  obstacles  host, count entries (copied), count <= APBF_MAX_OBSTACLES; 0 removes them.
+ *  kind       APBF_OBSTACLE_SPHERE: a = centre, b[0] = radius > 0.
+ *             APBF_OBSTACLE_BOX: a solid block, a = min corner < b = max corner.
+ *             APBF_OBSTACLE_CONE: a capped cone, a = centre of the base disc,
+ *             axis +z, b[0] = base radius > 0, b[1] = height > 0.
+ */
+#define APBF_MAX_OBSTACLES 8u
+#define APBF_OBSTACLE_SPHERE 1u
+#define APBF_OBSTACLE_BOX 2u
+#define APBF_OBSTACLE_CONE 3u
+
+typedef struct apbf_obstacle {
+    uint32_t kind;
+    float a[3];
+    float b[3];
+} apbf_obstacle;
+
+APBF_API apbf_status apbf_set_obstacles(apbf_scene *scene, uint32_t index, const apbf_obstacle *obstacles,
+                                        uint32_t count);
+
 /* Move the collision box (e.g. an oscillating wall) from the next step on.
  * lo, hi: host, 3 floats, grid_lo <= lo < hi <= grid_hi. */
 APBF_API apbf_status apbf_set_box(apbf_scene *scene, const float lo[3], const float hi[3]);
@@ -285,7 +318,8 @@ APBF_API apbf_status apbf_density_stats_static(const float *pos, uint32_t n, flo
 #define APBF_STAGE_LAMBDA 7u     /* a8 */
 #define APBF_STAGE_DELTAP 8u     /* a9 */
 #define APBF_STAGE_FINALIZE 9u   /* a10 */
-#define APBF_STAGE_COUNT 10u
+#define APBF_STAGE_PRESTAB 10u   /* pre-stabilisation (Fig. 7 lines 7-11), between LEVELS and LAMBDA */
+#define APBF_STAGE_COUNT 11u
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing of apbf_step. While
  * enabled, steps are issued kernel by kernel (no graph replay). */

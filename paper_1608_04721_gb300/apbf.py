@@ -35,7 +35,10 @@ STAGES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "le
           "finalize"]
 (APBF_STAGE_LOD_RANGE, APBF_STAGE_PREDICT, APBF_STAGE_SCAN, APBF_STAGE_SCATTER, APBF_STAGE_REORDER,
  APBF_STAGE_NEIGHBORS, APBF_STAGE_LEVELS, APBF_STAGE_LAMBDA, APBF_STAGE_DELTAP, APBF_STAGE_FINALIZE) = range(10)
-APBF_STAGE_COUNT = 10
+APBF_STAGE_COUNT = 11
+APBF_STAGE_PRESTAB = 10
+APBF_MAX_OBSTACLES = 8
+APBF_OBSTACLE_SPHERE, APBF_OBSTACLE_BOX, APBF_OBSTACLE_CONE = 1, 2, 3
 
 (APBF_DBG_KEYS, APBF_DBG_STATE_IDS, APBF_DBG_LEVEL_PRESORT, APBF_DBG_SORTED_IDS, APBF_DBG_CELL_START,
  APBF_DBG_XPRED, APBF_DBG_LEVEL, APBF_DBG_NBR_COUNT, APBF_DBG_NBR, APBF_DBG_ACTIVE, APBF_DBG_LEVEL_COUNT,
@@ -70,6 +73,10 @@ class apbf_step_info(C.Structure):
         ("active_count", C.c_uint32 * 256),
         ("d_range", C.c_float * 2),
     ]
+
+
+class apbf_obstacle(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("a", C.c_float * 3), ("b", C.c_float * 3)]
 
 
 class apbf_tune_result(C.Structure):
@@ -138,7 +145,7 @@ EXPORTS = [
     "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
     "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune", "apbf_server_bytes",
     "apbf_server_create", "apbf_server_submit", "apbf_server_tick", "apbf_server_query", "apbf_server_last_error",
-    "apbf_server_destroy", "apbf_set_view",
+    "apbf_server_destroy", "apbf_set_view", "apbf_set_obstacles",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -197,6 +204,7 @@ def lib():
         L.apbf_autotune.argtypes = [V, C.c_uint32, P(apbf_tune_result)]
         L.apbf_density_stats_static.argtypes = [V, C.c_uint32, C.c_float, C.c_float, C.c_float, P(C.c_float),
                                                 P(C.c_float), V, V]
+        L.apbf_set_obstacles.argtypes = [V, C.c_uint32, P(apbf_obstacle), C.c_uint32]
         L.apbf_set_view.argtypes = [V, C.c_uint32, C.c_uint32, C.c_float, P(C.c_float), C.c_float]
         L.apbf_server_bytes.argtypes = [P(apbf_server_desc), P(C.c_size_t), P(C.c_uint32), P(C.c_uint32)]
         L.apbf_server_create.argtypes = [P(apbf_server_desc), V, P(V)]
@@ -672,3 +680,13 @@ def apbf_set_view(scene: Scene, width: int, height: int, tan_half_fov: float, up
     u = (C.c_float * 3)(*[float(a) for a in up])
     _check(lib().apbf_set_view(scene.handle, width, height, tan_half_fov, u, radius), "apbf_set_view", scene)
     scene.view = (int(width), int(height))
+
+
+def apbf_set_obstacles(scene: Scene, obstacles, index: int = 0):
+    """obstacles: sequence of (kind, a, b) with kind APBF_OBSTACLE_*; see include/apbf.h."""
+    arr = (apbf_obstacle * max(1, len(obstacles)))()
+    for k, (kind, a, b) in enumerate(obstacles):
+        arr[k].kind = int(kind)
+        arr[k].a[:] = [float(t) for t in a]
+        arr[k].b[:] = [float(t) for t in (list(b) + [0.0, 0.0, 0.0])[:3]]
+    _check(lib().apbf_set_obstacles(scene.handle, index, arr, len(obstacles)), "apbf_set_obstacles", scene)

@@ -78,10 +78,8 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
         return "need 1 <= n_min <= n_max <= 255";
     if (d->lod_mode != APBF_LOD_FIXED && d->lod_mode != APBF_LOD_DTC && d->lod_mode != APBF_LOD_DTVS)
         return "unknown lod_mode";
-    if (d->stabil_s > 1) {
-        st = APBF_ERR_NOT_SUPPORTED;
-        return "pre-stabilisation with S > 1 is not built (S <= 1 makes its set empty)";
-    }
+    if (d->stabil_s > d->n_max || d->stabil_iters > 64)
+        return "pre-stabilisation needs S <= n_max and stabil_iters <= 64";
     if (d->max_neighbors > 255)
         return "max_neighbors must be <= 255";
     if (d->flags & ~APBF_FLAG_NO_GRAPH)
@@ -154,6 +152,8 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.max_nbr = d->max_neighbors ? d->max_neighbors : kDefaultMaxNeighbors;
     sc.level_tiles = (d->n + kLevelTile - 1) / kLevelTile;
     sc.rho0 = d->rho0;
+    sc.stabil_s = d->stabil_s;
+    sc.stabil_iters = d->stabil_iters;
     sc.scenes = 1;
     st = APBF_OK;
     return "";
@@ -164,7 +164,8 @@ bool same_physics(const apbf_scene_desc &a, const apbf_scene_desc &d)
     bool same = a.h == d.h && a.dt == d.dt && a.mass == d.mass && a.rho0 == d.rho0 && a.eps == d.eps &&
                 a.scorr_k == d.scorr_k && a.scorr_dq == d.scorr_dq && a.scorr_n == d.scorr_n &&
                 a.xsph_c == d.xsph_c && a.n_min == d.n_min && a.n_max == d.n_max && a.lod_mode == d.lod_mode &&
-                a.stabil_s == d.stabil_s && a.max_neighbors == d.max_neighbors && a.flags == d.flags;
+                a.stabil_s == d.stabil_s && a.stabil_iters == d.stabil_iters && a.max_neighbors == d.max_neighbors &&
+                a.flags == d.flags;
     for (int ax = 0; ax < 3; ++ax)
         same = same && a.gravity[ax] == d.gravity[ax];
     return same;
@@ -391,6 +392,12 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
             return cuda_fail(s, e, "levels");
     }
     if (stop_stage == APBF_STAGE_LEVELS)
+        return APBF_OK;
+    if (sc.stabil_s > 1 && sc.stabil_iters > 0) {
+        if ((e = timed(s, st, APBF_STAGE_PRESTAB, [&] { return launch_prestab(sc, b, st); })) != cudaSuccess)
+            return cuda_fail(s, e, "prestab");
+    }
+    if (stop_stage == APBF_STAGE_PRESTAB)
         return APBF_OK;
     for (uint32_t l = 1; l <= sc.n_max; ++l) {
         const bool dense = l <= sc.n_min;
@@ -766,6 +773,47 @@ APBF_API apbf_status apbf_set_camera_at(apbf_scene *s, uint32_t index, const flo
 APBF_API apbf_status apbf_set_box(apbf_scene *s, const float lo[3], const float hi[3])
 {
     return s ? set_box_range(s, 0, s->sc.scenes, lo, hi) : APBF_ERR_INVALID_ARG;
+}
+
+APBF_API apbf_status apbf_set_obstacles(apbf_scene *s, uint32_t index, const apbf_obstacle *obstacles,
+                                        uint32_t count)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (index >= s->sc.scenes)
+        return fail(s, APBF_ERR_INVALID_ARG, "scene index out of range");
+    if (count > APBF_MAX_OBSTACLES || (count && !obstacles))
+        return fail(s, APBF_ERR_INVALID_ARG, "need count <= APBF_MAX_OBSTACLES and a non-NULL array");
+    for (uint32_t k = 0; k < count; ++k) {
+        const apbf_obstacle &o = obstacles[k];
+        if (!finite3(o.a) || !finite3(o.b))
+            return fail(s, APBF_ERR_INVALID_ARG, "obstacle values must be finite");
+        bool ok = false;
+        if (o.kind == APBF_OBSTACLE_SPHERE)
+            ok = o.b[0] > 0.0f;
+        else if (o.kind == APBF_OBSTACLE_BOX)
+            ok = o.a[0] < o.b[0] && o.a[1] < o.b[1] && o.a[2] < o.b[2];
+        else if (o.kind == APBF_OBSTACLE_CONE)
+            ok = o.b[0] > 0.0f && o.b[1] > 0.0f;
+        if (!ok)
+            return fail(s, APBF_ERR_INVALID_ARG, "obstacle " + std::to_string(k) + ": unknown kind or bad size");
+    }
+    DynParams &d = s->dyn[index];
+    d.n_obst = count;
+    for (uint32_t k = 0; k < APBF_MAX_OBSTACLES; ++k) {
+        Obstacle o{};
+        if (k < count) {
+            o.kind = obstacles[k].kind;
+            for (int a = 0; a < 3; ++a) {
+                o.a[a] = obstacles[k].a[a];
+                o.b[a] = obstacles[k].b[a];
+            }
+        }
+        d.obst[k] = o;
+    }
+    s->dyn_dirty = true;
+    return APBF_OK;
 }
 
 APBF_API apbf_status apbf_set_box_at(apbf_scene *s, uint32_t index, const float lo[3], const float hi[3])

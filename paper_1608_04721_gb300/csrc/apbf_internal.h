@@ -59,6 +59,7 @@ struct StepConst {
     uint32_t max_nbr;
     uint32_t level_tiles;
     float rho0;         // rest density as given (FP32)
+    uint32_t stabil_s, stabil_iters;  // pre-stabilisation of the levels below S (Sec. 4.3), S <= 1: off
     uint32_t scenes;    // scenes in the batch (1: the fields glo, nx.., m above describe it)
 };
 
@@ -77,6 +78,16 @@ struct SceneGeom {
 
 // Per-step values that callers change between steps (device copy read by kernels,
 // one per scene).
+// A rigid obstacle (apbf_obstacle): sphere (a = centre, b[0] = radius), solid
+// block (a = min, b = max corner) or capped cone (a = base centre, axis +z,
+// b[0] = base radius, b[1] = height).
+struct Obstacle {
+    uint32_t kind;
+    float a[3];
+    float b[3];
+    uint32_t pad;
+};
+
 struct DynParams {
     float box_lo[4];
     float box_hi[4];
@@ -84,7 +95,8 @@ struct DynParams {
     float dir[4];  // viewing direction (DTVS)
     float d_near, d_far;
     uint32_t auto_range;
-    uint32_t pad;
+    uint32_t n_obst;  // obstacles in use
+    Obstacle obst[APBF_MAX_OBSTACLES];
 };
 
 // Camera image of the DTVS model (Sec. 4.1, Sec. 6), fixed between
@@ -213,6 +225,7 @@ cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s,
 cudaError_t launch_deltap(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
                           const Tune &tune);
 cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_prestab(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_dtvs(const StepConst &sc, const Buffers &b, const ViewConst &v, int sms, cudaStream_t s);
 cudaError_t launch_unpermute(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t what);
 cudaError_t launch_density(const StepConst &sc, const Buffers &b, cudaStream_t s, int *nblocks);

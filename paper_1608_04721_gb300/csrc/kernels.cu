@@ -1093,6 +1093,121 @@ __global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc,
     }
 }
 
+// ------------------------------------------- contacts with obstacles
+// Fig. 7 line 18 with the obstacles of Sec. 6 (analytic solids): a position
+// strictly inside an obstacle moves to the nearest point of its surface.
+// Positions are relative to the particle's cell origin og; each obstacle is
+// taken relative to og as well, so the arithmetic acts at the scale of the
+// obstacle, not of the domain.
+__device__ __forceinline__ void project_obstacle(const Obstacle &o, float3 og, float &px, float &py, float &pz)
+{
+    if (o.kind == APBF_OBSTACLE_SPHERE) {
+        const float cx = o.a[0] - og.x, cy = o.a[1] - og.y, cz = o.a[2] - og.z, R = o.b[0];
+        const float dx = px - cx, dy = py - cy, dz = pz - cz;
+        const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+        if (!(r < R))
+            return;
+        if (r == 0.0f) {
+            pz = cz + R;
+            return;
+        }
+        const float k = R / r;
+        px = cx + dx * k;
+        py = cy + dy * k;
+        pz = cz + dz * k;
+    } else if (o.kind == APBF_OBSTACLE_BOX) {
+        const float lo[3] = {o.a[0] - og.x, o.a[1] - og.y, o.a[2] - og.z};
+        const float hi[3] = {o.b[0] - og.x, o.b[1] - og.y, o.b[2] - og.z};
+        float p[3] = {px, py, pz};
+        float best = 3.0e38f, face = 0.0f;
+        int axis = -1;
+        for (int k = 0; k < 3; ++k) {
+            if (!(p[k] > lo[k] && p[k] < hi[k]))
+                return;
+            const float dl = p[k] - lo[k], dh = hi[k] - p[k];
+            if (dl < best) {
+                best = dl;
+                axis = k;
+                face = lo[k];
+            }
+            if (dh < best) {
+                best = dh;
+                axis = k;
+                face = hi[k];
+            }
+        }
+        if (axis == 0)
+            px = face;
+        else if (axis == 1)
+            py = face;
+        else
+            pz = face;
+    } else if (o.kind == APBF_OBSTACLE_CONE) {
+        const float cx = o.a[0] - og.x, cy = o.a[1] - og.y, cz = o.a[2] - og.z, R = o.b[0], H = o.b[1];
+        float ux = px - cx, uy = py - cy;
+        const float z = pz - cz;
+        const float rho = sqrtf(ux * ux + uy * uy);
+        if (!(z > 0.0f && rho / R + z / H < 1.0f))
+            return;
+        const float L = sqrtf(R * R + H * H);
+        const float g = (H * rho + R * z - R * H) / L;  // signed distance to the slant line, < 0 inside
+        if (z <= -g) {
+            pz = cz;  // the base is nearest
+            return;
+        }
+        const float rho2 = rho - g * H / L, z2 = z - g * R / L;
+        if (rho > 0.0f) {
+            ux /= rho;
+            uy /= rho;
+        } else {
+            ux = 1.0f;
+            uy = 0.0f;
+        }
+        px = cx + rho2 * ux;
+        py = cy + rho2 * uy;
+        pz = cz + z2;
+    }
+}
+
+__device__ __forceinline__ void contact_obstacles(const DynParams *d, float3 og, float &px, float &py, float &pz)
+{
+    const uint32_t no = d->n_obst;
+    for (uint32_t k = 0; k < no; ++k)
+        project_obstacle(d->obst[k], og, px, py, pz);
+}
+
+// Fig. 7 lines 7-11 (Sec. 4.3): the particles of level < S are moved out of
+// the obstacles and into the box stabil_iters times, the start-of-step
+// position (xt) and the prediction (recA) by the same amount, so the
+// velocity (x* - x)/dt gains nothing from it.
+template <bool BATCH>
+__global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b)
+{
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sc.n || !(b.lvl_s[p] < sc.stabil_s))
+        return;
+    const uint32_t s = scene_of<BATCH>(b, p);
+    const Geo g = geo_of<BATCH>(sc, b, s);
+    const DynParams *d = b.dyn + s;
+    const float3 og = origin_in(unpack_cell(b.cell_s[p]), g, sc.q);
+    float4 x0 = b.xt[p], xs = b.recA[p];
+    for (uint32_t it = 0; it < sc.stabil_iters; ++it) {
+        float qx = x0.x, qy = x0.y, qz = x0.z;
+        contact_obstacles(d, og, qx, qy, qz);
+        qx = fminf(fmaxf(qx, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
+        qy = fminf(fmaxf(qy, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
+        qz = fminf(fmaxf(qz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
+        xs.x += qx - x0.x;
+        xs.y += qy - x0.y;
+        xs.z += qz - x0.z;
+        x0.x = qx;
+        x0.y = qy;
+        x0.z = qz;
+    }
+    b.xt[p] = x0;
+    b.recA[p] = xs;
+}
+
 // ---------------------------------------------------------- a8: lambda pass
 // Iteration l, threads over P_{l-1}: particles of P_l compute rho and lambda
 // (Eq. 4-6) from A and write (position, lambda) to B; particles that finished
@@ -1199,6 +1314,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
     const size_t n = sc.n;
     const float blo0 = dyn->box_lo[0], blo1 = dyn->box_lo[1], blo2 = dyn->box_lo[2];
     const float bhi0 = dyn->box_hi[0], bhi1 = dyn->box_hi[1], bhi2 = dyn->box_hi[2];
+    const uint32_t n_obst = dyn->n_obst;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
         const uint32_t p = (DENSE || masked) ? t : act[t];
         if (masked && b.lvl_s[p] < l)
@@ -1224,7 +1340,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
                 az += f * dz;
             }
         });
-        // new position, clamped to the box expressed relative to the cell origin
+        // new position; contacts: obstacles, then the box, expressed relative to the cell origin
         float px = bi.x + sc.c_dp * ax;
         float py = bi.y + sc.c_dp * ay;
         float pz = bi.z + sc.c_dp * az;
@@ -1233,11 +1349,14 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
             const Geo g = geo_of<true>(sc, b, s);
             const DynParams *d = dyn + s;
             const float3 og = origin_in(unpack_cell(cell_s[p]), g, sc.q);
+            contact_obstacles(d, og, px, py, pz);
             px = fminf(fmaxf(px, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
             py = fminf(fmaxf(py, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
             pz = fminf(fmaxf(pz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
         } else {
             const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
+            if (n_obst)
+                contact_obstacles(dyn, og, px, py, pz);
             px = fminf(fmaxf(px, blo0 - og.x), bhi0 - og.x);
             py = fminf(fmaxf(py, blo1 - og.y), bhi1 - og.y);
             pz = fminf(fmaxf(pz, blo2 - og.z), bhi2 - og.z);
@@ -1569,6 +1688,14 @@ cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t 
     if (sc.n)
         (sc.scenes > 1 ? finalize_kernel<true> : finalize_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
             sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prestab(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        (sc.scenes > 1 ? prestab_kernel<true> : prestab_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc,
+                                                                                                                    b);
     return cudaGetLastError();
 }
 

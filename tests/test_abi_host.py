@@ -25,7 +25,7 @@ def _declared():
 
 def test_exports_every_declared_symbol():
     names = _declared()
-    assert len(names) == 33
+    assert len(names) == 34
     out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout
     exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
@@ -76,7 +76,8 @@ def test_scene_bytes_scale_with_particles():
     (dict(n_min=5, n_max=4), apbf.APBF_ERR_INVALID_ARG),
     (dict(n_max=256), apbf.APBF_ERR_INVALID_ARG),
     (dict(lod_mode=9), apbf.APBF_ERR_INVALID_ARG),
-    (dict(stabil_s=3, stabil_iters=2), apbf.APBF_ERR_NOT_SUPPORTED),
+    (dict(stabil_s=9, stabil_iters=2), apbf.APBF_ERR_INVALID_ARG),
+    (dict(stabil_s=2, stabil_iters=65), apbf.APBF_ERR_INVALID_ARG),
     (dict(max_neighbors=300), apbf.APBF_ERR_INVALID_ARG),
     (dict(box_lo=(-1.0, 0.0, 0.0)), apbf.APBF_ERR_INVALID_ARG),
     (dict(scorr_dq=0.2), apbf.APBF_ERR_INVALID_ARG),
