@@ -93,10 +93,12 @@ class SceneConfig:
     stabil_iters: int = 0                   # pre-stabilisation iterations (Sec. 4.3)
     stabil_s: int = 1                       # S: particles of level < S are pre-stabilised (S <= 1: none)
     obstacles: tuple = ()                   # ((kind, a, b), ...) analytic solids, see apbf_set_obstacles
+    blocks: tuple = ()                      # more block corners: the lattice repeated at each (ids in order)
+    target: Optional[Tuple[float, float, float]] = None  # "fixed" camera looks at this point (else +x)
 
     @property
     def n(self) -> int:
-        return int(self.lattice[0] * self.lattice[1] * self.lattice[2])
+        return int(self.lattice[0] * self.lattice[1] * self.lattice[2]) * max(1, len(self.blocks))
 
     def replace(self, **kw) -> "SceneConfig":
         return dataclasses.replace(self, **kw)
@@ -130,6 +132,22 @@ def config_ocean_1m(lod_mode: int = LOD_DTC, n_min: int = 3, n_max: int = 15) ->
                        block_lo=(0.0, 0.0, 0.0), box_lo=(0.0, 0.0, 0.0), box_hi=(9.6, 6.4, 4.8),
                        n_min=n_min, n_max=n_max, lod_mode=lod_mode, steps=600, dt=0.0016,
                        camera="spline", wall="oscillate_xlo")
+
+
+def config_multi_dam_break_225k(lod_mode: int = LOD_DTC, n_min: int = 4, n_max: int = 8) -> SceneConfig:
+    """Analogue of the paper's multi dam break (Sec. 7.3): four blocks of
+    38x38x39 particles (225,264 in all) in the corners of a 6.4x6.4x3.2 m box
+    around a central cone (base radius 1.2 m, height 1.6 m), N_i in 4..8 from
+    a fixed camera above one corner looking at the centre, pre-stabilisation
+    of the levels below 6 (two iterations), time step 0.0016 s (Sec. 7)."""
+    w = 38 * 0.05
+    corners = ((0.0, 0.0, 0.0), (6.4 - w, 0.0, 0.0), (0.0, 6.4 - w, 0.0), (6.4 - w, 6.4 - w, 0.0))
+    cone = (3, (3.2, 3.2, 0.0), (1.2, 1.6, 0.0))  # APBF_OBSTACLE_CONE
+    return SceneConfig(name="apbf_multi_dam_break_225264", lattice=(38, 38, 39), spacing=0.05,
+                       block_lo=corners[0], blocks=corners, box_lo=(0.0, 0.0, 0.0), box_hi=(6.4, 6.4, 3.2),
+                       n_min=n_min, n_max=n_max, lod_mode=lod_mode, steps=300, dt=0.0016, camera="fixed",
+                       eye=(-2.0, -2.0, 3.5), target=(3.2, 3.2, 0.8), stabil_s=6, stabil_iters=2,
+                       obstacles=(cone,))
 
 
 def config_batch_256(count: int = 256, seed: int = 1608_04721, n_lo: int = 2048, n_hi: int = 65536,
@@ -188,11 +206,13 @@ CONFIGS = {
     "dam_break_4k": config_dam_break_4k,
     "dam_break_131k": config_dam_break_131k,
     "ocean_1m": config_ocean_1m,
+    "multi_dam_break_225k": config_multi_dam_break_225k,
 }
 
 
 def lattice_positions(cfg: SceneConfig) -> np.ndarray:
-    """Block lattice p = block_lo + (i + 0.5) s + U(+-jitter) per axis.
+    """Block lattice p = block_lo + (i + 0.5) s + U(+-jitter) per axis (the
+    same lattice at each corner of cfg.blocks, block after block, if given).
 
     Particle order (= particle id) is lattice order: x fastest, then y, then z.
     Three draws per particle in that order (x, y, z). Computed in float64 and
@@ -201,7 +221,8 @@ def lattice_positions(cfg: SceneConfig) -> np.ndarray:
     nx, ny, nz = cfg.lattice
     iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     idx = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
-    base = np.asarray(cfg.block_lo, np.float64)[None, :] + (idx + 0.5) * cfg.spacing
+    corners = cfg.blocks if cfg.blocks else (cfg.block_lo,)
+    base = np.concatenate([np.asarray(c, np.float64)[None, :] + (idx + 0.5) * cfg.spacing for c in corners])
     if cfg.jitter > 0.0:
         u = uniform01(cfg.seed, 0, 3 * cfg.n).reshape(cfg.n, 3)
         base = base + (2.0 * u - 1.0) * cfg.jitter
@@ -249,6 +270,9 @@ def camera_at(cfg: SceneConfig, step: int):
         d = d / max(np.linalg.norm(d), 1e-12)
         return eye.astype(np.float32), d.astype(np.float32)
     eye = np.asarray(cfg.eye, np.float32)
+    if cfg.target is not None:
+        d = np.asarray(cfg.target, np.float64) - np.asarray(cfg.eye, np.float64)
+        return eye, (d / np.linalg.norm(d)).astype(np.float32)
     return eye, np.asarray([1.0, 0.0, 0.0], np.float32)
 
 

@@ -137,3 +137,28 @@ def test_obstacle_arguments_are_validated():
     apbf.apbf_set_obstacles(scene, OBST)
     apbf.apbf_set_obstacles(scene, [])
     apbf.apbf_step(scene, 1)
+
+
+def test_one_step_parity_multi_dam_break_225k():
+    """The multi-dam-break workload (four blocks around the cone, N_i 4..8,
+    pre-stabilisation below level 6) in the launch configuration the
+    benchmark times: all integer stages, sampled neighbour sets, every
+    iteration's lambda, rho and x*, and the final state."""
+    cfg = scenes.config_multi_dam_break_225k()
+    x, v = scenes.make_scene(cfg)
+    # each block moved rigidly 0.54 m along both axes toward the cone, so that its inner bottom
+    # corner dents the cone by at most 2.8 cm, and moving toward it at 1 m/s: contacts in the first step
+    per = cfg.n // 4
+    for k, (sx, sy) in enumerate([(1, 1), (-1, 1), (1, -1), (-1, -1)]):
+        x[k * per:(k + 1) * per] += np.array([0.54 * sx, 0.54 * sy, 0.0], np.float32)
+        v[k * per:(k + 1) * per] = np.array([0.7071 * sx, 0.7071 * sy, 0.0], np.float32)
+    r0 = rest_density(cfg)
+    eye, direction = scenes.camera_at(cfg, 0)
+    scene = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    apbf.apbf_set_camera(scene, eye, direction)
+    apbf.apbf_set_obstacles(scene, cfg.obstacles)
+    p = oracle.make_params(cfg, rho0=r0, eye=eye)
+    assert _inside_any(x, cfg.obstacles) > 12
+    rng = np.random.default_rng(4)
+    st = check_stages(cfg, scene, p, x, v, sample=rng.choice(cfg.n, 3000, replace=False))
+    check_final(cfg, scene, p, st, x0=x)

@@ -110,7 +110,7 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
     return st
 
 
-def check_final(cfg, scene, p, st):
+def check_final(cfg, scene, p, st, x0=None):
     apbf.apbf_step(scene, 1)
     got = apbf.apbf_read_state(scene, pos=True, vel=True, n_iter=True)
     inv = np.argsort(st.ids)
@@ -119,7 +119,7 @@ def check_final(cfg, scene, p, st):
     verr = np.abs(got["vel"].astype(np.float64) - st.v[inv]).max()
     assert xerr <= 1e-5 * h, f"positions after the step differ by {xerr:.3g} m"
     assert verr <= 1e-5 * h / float(p.dt), f"velocities after the step differ by {verr:.3g} m/s"
-    lv, _ = oracle.lod_levels(p, scenes.make_scene(cfg)[0])
+    lv, _ = oracle.lod_levels(p, scenes.make_scene(cfg)[0] if x0 is None else x0)
     assert np.array_equal(got["n_iter"].astype(np.int32), lv)
     lo, hi = np.asarray(p.box_lo[:], np.float32), np.asarray(p.box_hi[:], np.float32)
     assert np.all(got["pos"] >= lo) and np.all(got["pos"] <= hi)
