@@ -975,23 +975,23 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                 const uint32_t j0 = b.start[row + xl], jm = b.start[row + c.x], jp = b.start[row + c.x + 1],
                                j1 = b.start[row + xr + 1];
                 const uint32_t code_row = (uint32_t)(3 * (dy + 1) + 9 * (dz + 1));
+                const bool own_row = dy == 0 && dz == 0;  // the only row that holds p itself
                 for (uint32_t j = j0; j < j1; j += kUnroll) {
                     float4 xj[kUnroll];
+                    // past the window's end: a far point, which the predicate rejects (r2 = inf)
 #pragma unroll
                     for (int u = 0; u < kUnroll; ++u)
-                        xj[u] = (j + u < j1) ? b.xs32[j + u] : xi;
+                        xj[u] = (j + u < j1) ? b.xs32[j + u] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
 #pragma unroll
                     for (int u = 0; u < kUnroll; ++u) {
                         const uint32_t q = j + u;
-                        if (q >= j1 || q == p)
-                            continue;
                         // FP32 predicate, rounded after every operation
                         const float dx = __fsub_rn(xi.x, xj[u].x);
                         const float dy2 = __fsub_rn(xi.y, xj[u].y);
                         const float dz2 = __fsub_rn(xi.z, xj[u].z);
                         float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy2, dy2));
                         r2 = __fadd_rn(r2, __fmul_rn(dz2, dz2));
-                        if (r2 < sc.h2) {
+                        if (r2 < sc.h2 && !(own_row && q == p)) {
                             const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
                             if (cnt < sc.max_nbr)
                                 b.nbr[(size_t)cnt * n + p] = q | ((code_row + dxc) << kSlotBits);
