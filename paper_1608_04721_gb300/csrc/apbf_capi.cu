@@ -272,6 +272,7 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.cell_s = (uint32_t *)P(4 * n);
     b.lvl_s = (uint8_t *)P(n);
     b.nbr_cnt = (uint8_t *)P(n);
+    b.prev_cnt = (uint8_t *)P(n);
     b.nbr = (uint32_t *)P(4 * (size_t)sc.max_nbr * n);
     b.rho = (float *)P(4 * n);
     b.lodd = (float *)P(4 * n);
@@ -379,19 +380,22 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
     s->cur_buf = 0;
     if (stop_stage == APBF_STAGE_REORDER)
         return APBF_OK;
-    e = timed(s, st, APBF_STAGE_NEIGHBORS, [&] {
-        cudaMemsetAsync(b.counters, 0, 8 * (2 + 256), st);
-        return launch_neighbors(sc, b, st);
-    });
-    if (e != cudaSuccess)
-        return cuda_fail(s, e, "neighbors");
-    if (stop_stage == APBF_STAGE_NEIGHBORS)
-        return APBF_OK;
-    if ((dtc || dtvs) && sc.K > 1) {
+    // the level partition comes first: the neighbour lists are stored by active-list position
+    const bool part = partitioned(sc);
+    if (part) {
         if ((e = timed(s, st, APBF_STAGE_LEVELS, [&] { return launch_levels(sc, b, st); })) != cudaSuccess)
             return cuda_fail(s, e, "levels");
     }
     if (stop_stage == APBF_STAGE_LEVELS)
+        return APBF_OK;
+    e = timed(s, st, APBF_STAGE_NEIGHBORS, [&] {
+        cudaMemsetAsync(b.counters, 0, 8 * (2 + 256), st);
+        return launch_neighbors(sc, b, st, part);
+    });
+    s->lists_by_slot = !part;
+    if (e != cudaSuccess)
+        return cuda_fail(s, e, "neighbors");
+    if (stop_stage == APBF_STAGE_NEIGHBORS)
         return APBF_OK;
     if (sc.stabil_s > 1 && sc.stabil_iters > 0) {
         if ((e = timed(s, st, APBF_STAGE_PRESTAB, [&] { return launch_prestab(sc, b, st); })) != cudaSuccess)
@@ -967,7 +971,8 @@ APBF_API apbf_status apbf_density_stats(apbf_scene *s, double stats[4])
     APBF_CUDA(s, launch_scan(s->sc, bb, q));
     APBF_CUDA(s, launch_scatter(s->sc, bb, q));
     APBF_CUDA(s, launch_reorder(s->sc, bb, q, true));
-    APBF_CUDA(s, launch_neighbors(s->sc, bb, q));
+    APBF_CUDA(s, launch_neighbors(s->sc, bb, q, false));  // by sorted slot, for the density kernel
+    s->lists_by_slot = true;
     APBF_CUDA(s, launch_density(s->sc, bb, q, &nb));
     double *h = (double *)s->pinned_small + 8;
     APBF_CUDA(s, cudaMemcpyAsync(h, s->b.dstats, 32, cudaMemcpyDeviceToHost, q));
@@ -1292,6 +1297,26 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
     }
     if (bytes != size || (size && !host))
         return fail(s, APBF_ERR_INVALID_ARG, "debug_read size mismatch: field needs " + std::to_string(size) + " bytes");
+    if ((field == APBF_DBG_NBR || field == APBF_DBG_NBR_COUNT) && !s->lists_by_slot && n) {
+        // stored by active-list position: report by sorted slot, as documented
+        std::vector<uint32_t> act(n);
+        APBF_CUDA(s, cudaMemcpyAsync(act.data(), b.act, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+        if (field == APBF_DBG_NBR_COUNT) {
+            std::vector<uint8_t> raw(n);
+            APBF_CUDA(s, cudaMemcpyAsync(raw.data(), b.nbr_cnt, n, cudaMemcpyDeviceToHost, s->stream));
+            APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+            for (size_t t = 0; t < n; ++t)
+                ((uint8_t *)host)[act[t]] = raw[t];
+        } else {
+            std::vector<uint32_t> raw((size_t)sc.max_nbr * n);
+            APBF_CUDA(s, cudaMemcpyAsync(raw.data(), b.nbr, 4 * raw.size(), cudaMemcpyDeviceToHost, s->stream));
+            APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+            for (size_t k = 0; k < sc.max_nbr; ++k)
+                for (size_t t = 0; t < n; ++t)
+                    ((uint32_t *)host)[k * n + act[t]] = raw[k * n + t];
+        }
+        return check_device_errors(s);
+    }
     if (size)
         APBF_CUDA(s, cudaMemcpyAsync(host, src, size, cudaMemcpyDeviceToHost, s->stream));
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));

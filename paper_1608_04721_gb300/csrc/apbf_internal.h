@@ -135,8 +135,9 @@ struct Buffers {
     uint32_t *cnt, *start, *tile_sums, *tmp;
     float4 *recA, *recB, *xs32, *xt;
     uint32_t *id_s, *cell_s;
-    uint8_t *lvl_s, *nbr_cnt;
+    uint8_t *lvl_s, *nbr_cnt;     // nbr_cnt and nbr: by list column (see partitioned())
     uint32_t *nbr;
+    uint8_t *prev_cnt;            // neighbour count of each state slot in the last step
     float *rho;
     float *lodd;                   // DTVS distance behind the visible surface, state order (-1: outside the view)
     uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
@@ -198,6 +199,7 @@ struct apbf_scene {
     // state
     bool stepped = false;
     int cur_buf = 0;  // debug: 0 = recA, 1 = recB holds the current positions
+    bool lists_by_slot = true;  // the neighbour lists were last written by sorted slot (density diagnostic)
     apbf_status sticky = APBF_OK;
     std::string msg;
     // timing
@@ -212,13 +214,19 @@ struct apbf_scene {
 
 namespace apbf {
 
+// A step partitions the particles by level (the active list act) when the LOD
+// spans more than one level; the neighbour lists are then stored by
+// active-list position (column t holds the particle act[t]), otherwise by
+// sorted slot.
+inline bool partitioned(const StepConst &sc) { return sc.lod_mode != APBF_LOD_FIXED && sc.K > 1; }
+
 // Kernel launchers (kernels.cu). Each returns cudaGetLastError().
 cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
 cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
-cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s);
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, bool part);
 cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
                           const Tune &tune);

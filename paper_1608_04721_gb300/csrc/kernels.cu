@@ -113,25 +113,27 @@ constexpr int kUnroll = APBF_UNROLL;
 // so a thread has kUnroll independent gathers in flight. Entries are read
 // once per pass (streaming hint, they should not displace the records that
 // neighbouring threads reuse from L1).
-template <typename F>
+template <int UNR = kUnroll, typename F>
 __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ e_ptr, size_t stride, uint32_t nn,
                                                   const float4 *__restrict__ rec, F &&f)
 {
-    for (uint32_t k = 0; k < nn; k += kUnroll) {
-        uint32_t e[kUnroll];
-        float4 r[kUnroll];
+    for (uint32_t k = 0; k < nn; k += UNR) {
+        uint32_t e[UNR];
+        float4 r[UNR];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
+        for (int u = 0; u < UNR; ++u)
             e[u] = (k + u < nn) ? __ldcs(e_ptr + (size_t)(k + u) * stride) : kNoEntry;
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
+        for (int u = 0; u < UNR; ++u)
             r[u] = (e[u] != kNoEntry) ? __ldg(&rec[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
+        for (int u = 0; u < UNR; ++u)
             if (e[u] != kNoEntry)
                 f(e[u], r[u]);
     }
 }
+
+
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < sc.n;
-    const bool member = valid && ((b.nbr_cnt[i] < kFrontNeighbors) == (phase == 0));
+    const bool member = valid && ((b.prev_cnt[i] < kFrontNeighbors) == (phase == 0));
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
     float near = 0.0f;
     if (pass == 1) {
@@ -950,13 +952,23 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
 
 // ----------------------------------------------- neighbour lists (l. 5-6)
 
+// With a level partition (part), thread t takes the particle at position t
+// of the active list and writes its list into column t (entry k at k*n + t):
+// every iteration then reads a contiguous prefix of columns. Without one,
+// column = sorted slot. The entries name neighbours by sorted slot either way.
 template <bool BATCH>
-__global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b)
+__global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b, int part)
 {
     __shared__ uint32_t sh[32];
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ uint32_t bins[256];  // pairs per level bin (part only)
+    if (part)
+        for (uint32_t k = threadIdx.x; k < sc.K; k += blockDim.x)
+            bins[k] = 0u;
+    __syncthreads();
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
-    if (p < sc.n) {
+    if (t < sc.n) {
+        const uint32_t p = part ? b.act[t] : t;
         const Geo g = geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p));
         const float4 xi = b.xs32[p];
         const int3 c = unpack_cell(b.cell_s[p]);
@@ -994,7 +1006,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                         if (r2 < sc.h2 && !(own_row && q == p)) {
                             const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
                             if (cnt < sc.max_nbr)
-                                b.nbr[(size_t)cnt * n + p] = q | ((code_row + dxc) << kSlotBits);
+                                b.nbr[(size_t)cnt * n + t] = q | ((code_row + dxc) << kSlotBits);
                             ++cnt;
                         }
                     }
@@ -1005,11 +1017,19 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
             atomicOr(b.err, kErrNeighborOverflow);
             cnt = sc.max_nbr;
         }
-        b.nbr_cnt[p] = (uint8_t)cnt;
+        b.nbr_cnt[t] = (uint8_t)cnt;
+        if (part && cnt)
+            atomicAdd(&bins[sc.n_max - b.lvl_s[p]], cnt);
     }
     uint32_t tot = block_sum_u32(cnt, sh);
     if (threadIdx.x == 0 && tot)
         atomicAdd(&b.counters[0], (unsigned long long)tot);
+    if (part) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < sc.K; k += blockDim.x)
+            if (bins[k])
+                atomicAdd(&b.counters[2 + k], (unsigned long long)bins[k]);
+    }
 }
 
 // ---------------------------------------- a7: active sets by stable partition
@@ -1018,23 +1038,17 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
 
 __global__ void __launch_bounds__(kLevelTile) level_hist_kernel(StepConst sc, Buffers b)
 {
-    extern __shared__ uint32_t sh[];  // K counts, K pair sums
+    extern __shared__ uint32_t sh[];  // K counts
     const uint32_t K = sc.K;
-    for (uint32_t k = threadIdx.x; k < 2 * K; k += blockDim.x)
+    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x)
         sh[k] = 0u;
     __syncthreads();
     uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
-    if (p < sc.n) {
-        uint32_t bin = sc.n_max - b.lvl_s[p];
-        atomicAdd(&sh[bin], 1u);
-        atomicAdd(&sh[K + bin], (uint32_t)b.nbr_cnt[p]);
-    }
+    if (p < sc.n)
+        atomicAdd(&sh[sc.n_max - b.lvl_s[p]], 1u);
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x) {
+    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x)
         b.lvl_hist[(size_t)k * sc.level_tiles + blockIdx.x] = sh[k];
-        if (sh[K + k])
-            atomicAdd(&b.counters[2 + k], (unsigned long long)sh[K + k]);
-    }
 }
 
 __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers b)
@@ -1209,6 +1223,46 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
 }
 
 // ---------------------------------------------------------- a8: lambda pass
+
+// Eq. 4-6 for one particle: its density over the neighbour list and lambda.
+// Every operation is an explicit rounding intrinsic, so that the compiler's
+// choice of where to fuse multiply-adds cannot differ between the kernel
+// instantiations that inline it (dense or compacted, block size, batch
+// depth UNR): a particle's result is the same bits whichever computes it.
+template <int UNR = kUnroll>
+__device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *dtab, const float4 *__restrict__ A,
+                                           const uint32_t *__restrict__ e_ptr, size_t n, uint32_t nn, const float4 &ai,
+                                           float &lam, float &rho)
+{
+    float racc = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, s2 = 0.0f;
+    for_each_neighbor<UNR>(e_ptr, n, nn, A, [&](uint32_t e, const float4 &aj) {
+        const float4 o = dtab[e >> kSlotBits];
+        const float dx = __fadd_rn(__fsub_rn(ai.x, aj.x), o.x);
+        const float dy = __fadd_rn(__fsub_rn(ai.y, aj.y), o.y);
+        const float dz = __fadd_rn(__fsub_rn(ai.z, aj.z), o.z);
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        if (r2 < sc.h2) {
+            const float u = __fsub_rn(sc.h2, r2);
+            racc = __fmaf_rn(__fmul_rn(u, u), u, racc);
+            if (r2 > 0.0f) {
+                const float ir = rsqrtf(r2);
+                const float hr = __fmaf_rn(-r2, ir, sc.h);
+                const float gw = __fmul_rn(__fmul_rn(hr, hr), ir);  // |grad W| / (45/(pi h^6)) / r
+                gx = __fmaf_rn(gw, dx, gx);
+                gy = __fmaf_rn(gw, dy, gy);
+                gz = __fmaf_rn(gw, dz, gz);
+                s2 = __fmaf_rn(__fmul_rn(gw, gw), r2, s2);
+            }
+        }
+    });
+    rho = __fmul_rn(sc.mass_poly6, __fadd_rn(sc.h6, racc));
+    const float C = __fmaf_rn(rho, sc.inv_rho0, -1.0f);
+    const float g2 = __fadd_rn(__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))), s2);
+    const float denom = __fmaf_rn(sc.c_lam, g2, sc.eps);
+    lam = __fdiv_rn(-C, denom);
+}
+
+
 // Iteration l, threads over P_{l-1}: particles of P_l compute rho and lambda
 // (Eq. 4-6) from A and write (position, lambda) to B; particles that finished
 // in iteration l-1 copy their final position into B and keep their lambda
@@ -1223,7 +1277,7 @@ template <bool DENSE, int BS>
 __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_kernel(
     StepConst sc, const float4 *__restrict__ A, float4 *__restrict__ B, float *__restrict__ rho_out,
     const uint32_t *__restrict__ act, const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt,
-    const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr)
+    const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr, int part)
 {
     __shared__ float4 dtab[27];
     fill_dtab(dtab, sc.q);
@@ -1236,7 +1290,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
     // grid-stride: at any moment the whole grid works on one compact window of
     // the (cell-sorted) work list, which keeps the gathers' working set in L2
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
-        const uint32_t p = (DENSE || masked) ? t : act[t];
+        const uint32_t p = part ? act[t] : t;  // t: list column (active-list position with a partition)
         bool finished_last = false;  // finished in iteration l-1: keep position and lambda in B
         if (masked) {
             const uint32_t lv = lvl_s[p];
@@ -1251,59 +1305,108 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
             B[p] = make_float4(ai.x, ai.y, ai.z, B[p].w);
             continue;
         }
-        const uint32_t nn = nbr_cnt[p];
-        float racc = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, s2 = 0.0f;
-        for_each_neighbor(nbr + p, n, nn, A, [&](uint32_t e, const float4 &aj) {
-            const float4 o = dtab[e >> kSlotBits];
-            const float dx = (ai.x - aj.x) + o.x;
-            const float dy = (ai.y - aj.y) + o.y;
-            const float dz = (ai.z - aj.z) + o.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < sc.h2) {
-                const float u = sc.h2 - r2;
-                racc += u * u * u;
-                if (r2 > 0.0f) {
-                    const float ir = rsqrtf(r2);
-                    const float hr = sc.h - r2 * ir;
-                    const float gw = hr * hr * ir;  // |grad W| / (45/(pi h^6)) / r
-                    gx += gw * dx;
-                    gy += gw * dy;
-                    gz += gw * dz;
-                    s2 += gw * gw * r2;
-                }
-            }
-        });
-        const float rho = sc.mass_poly6 * (sc.h6 + racc);
-        const float C = rho * sc.inv_rho0 - 1.0f;
-        const float denom = sc.c_lam * (gx * gx + gy * gy + gz * gz + s2) + sc.eps;
-        const float lam = -C / denom;
+        float lam, rho;
+        lambda_one(sc, dtab, A, nbr + t, n, nbr_cnt[t], ai, lam, rho);
         B[p] = make_float4(ai.x, ai.y, ai.z, lam);
         rho_out[p] = rho;
     }
 }
 
 // ------------------------------------------- a9: position correction pass
-// Iteration l, threads over P_l: Eq. 7 with the tensile term from B, box
-// contact, Jacobi update written to A.
 
+// x^n for the tensile term (n = 4 unrolled)
 template <int NPOW>
 __device__ __forceinline__ float powi(float x, uint32_t n)
 {
     if (NPOW == 4) {
-        float x2 = x * x;
-        return x2 * x2;
+        const float x2 = __fmul_rn(x, x);
+        return __fmul_rn(x2, x2);
     }
     float r = 1.0f;
     for (uint32_t e = 0; e < n; ++e)
-        r *= x;
+        r = __fmul_rn(r, x);
     return r;
 }
+
+// The scene's box and obstacle count read once per kernel (single scene).
+struct BoxK {
+    float lo[3], hi[3];
+    uint32_t n_obst;
+};
+
+__device__ __forceinline__ BoxK box_of(const DynParams *dyn)
+{
+    BoxK k;
+    for (int a = 0; a < 3; ++a) {
+        k.lo[a] = dyn->box_lo[a];
+        k.hi[a] = dyn->box_hi[a];
+    }
+    k.n_obst = dyn->n_obst;
+    return k;
+}
+
+// Eq. 7 for one particle and the contacts after it: the new position
+// relative to its cell origin; explicit rounding intrinsics as in lambda_one,
+// so the result does not depend on which instantiation computes it.
+template <int NPOW, bool BATCH, int UNR = kUnroll>
+__device__ __forceinline__ float3 deltap_one(const StepConst &sc, const float4 *dtab, const float4 *__restrict__ B,
+                                             const uint32_t *__restrict__ e_ptr, size_t n, uint32_t nn, const float4 &bi,
+                                             uint32_t p, const uint32_t *__restrict__ cell_s,
+                                             const DynParams *__restrict__ dyn, const Buffers &b, const BoxK &bk)
+{
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+    for_each_neighbor<UNR>(e_ptr, n, nn, B, [&](uint32_t e, const float4 &bj) {
+        const float4 o = dtab[e >> kSlotBits];
+        const float dx = __fadd_rn(__fsub_rn(bi.x, bj.x), o.x);
+        const float dy = __fadd_rn(__fsub_rn(bi.y, bj.y), o.y);
+        const float dz = __fadd_rn(__fsub_rn(bi.z, bj.z), o.z);
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        if (r2 < sc.h2 && r2 > 0.0f) {
+            const float ir = rsqrtf(r2);
+            const float hr = __fmaf_rn(-r2, ir, sc.h);
+            const float gw = __fmul_rn(__fmul_rn(hr, hr), ir);
+            const float u = __fmul_rn(__fsub_rn(sc.h2, r2), sc.inv_wdq);  // W(r) / W(dq) = u^3
+            const float scorr = __fmul_rn(sc.neg_k, powi<NPOW>(__fmul_rn(__fmul_rn(u, u), u), sc.scorr_n));
+            const float f = __fmul_rn(__fadd_rn(__fadd_rn(bi.w, bj.w), scorr), gw);
+            ax = __fmaf_rn(f, dx, ax);
+            ay = __fmaf_rn(f, dy, ay);
+            az = __fmaf_rn(f, dz, az);
+        }
+    });
+    // new position; contacts: obstacles, then the box, expressed relative to the cell origin
+    float px = __fmaf_rn(sc.c_dp, ax, bi.x);
+    float py = __fmaf_rn(sc.c_dp, ay, bi.y);
+    float pz = __fmaf_rn(sc.c_dp, az, bi.z);
+    if (BATCH) {
+        const uint32_t s = scene_of<true>(b, p);
+        const Geo g = geo_of<true>(sc, b, s);
+        const DynParams *d = dyn + s;
+        const float3 og = origin_in(unpack_cell(cell_s[p]), g, sc.q);
+        contact_obstacles(d, og, px, py, pz);
+        px = fminf(fmaxf(px, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
+        py = fminf(fmaxf(py, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
+        pz = fminf(fmaxf(pz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
+    } else {
+        const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
+        if (bk.n_obst)
+            contact_obstacles(dyn, og, px, py, pz);
+        px = fminf(fmaxf(px, bk.lo[0] - og.x), bk.hi[0] - og.x);
+        py = fminf(fmaxf(py, bk.lo[1] - og.y), bk.hi[1] - og.y);
+        pz = fminf(fmaxf(pz, bk.lo[2] - og.z), bk.hi[2] - og.z);
+    }
+    return make_float3(px, py, pz);
+}
+
+
+// Iteration l, threads over P_l: Eq. 7 with the tensile term from B, box
+// contact, Jacobi update written to A.
 
 template <bool DENSE, int NPOW, bool BATCH, int BS>
 __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_kernel(
     StepConst sc, const float4 *__restrict__ B, float4 *__restrict__ A, const uint32_t *__restrict__ act,
     const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt, const uint32_t *__restrict__ cell_s,
-    const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr)
+    const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr,
+    int part)
 {
     __shared__ float4 dtab[27];
     fill_dtab(dtab, sc.q);
@@ -1312,55 +1415,14 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
     const bool masked = !DENSE && (float)cnt_l >= mask_thr * (float)sc.n;
     const uint32_t work = masked ? sc.n : cnt_l;
     const size_t n = sc.n;
-    const float blo0 = dyn->box_lo[0], blo1 = dyn->box_lo[1], blo2 = dyn->box_lo[2];
-    const float bhi0 = dyn->box_hi[0], bhi1 = dyn->box_hi[1], bhi2 = dyn->box_hi[2];
-    const uint32_t n_obst = dyn->n_obst;
+    const BoxK bk = box_of(dyn);
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
-        const uint32_t p = (DENSE || masked) ? t : act[t];
+        const uint32_t p = part ? act[t] : t;  // t: list column (active-list position with a partition)
         if (masked && b.lvl_s[p] < l)
             continue;
         const float4 bi = B[p];
-        const uint32_t nn = nbr_cnt[p];
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        for_each_neighbor(nbr + p, n, nn, B, [&](uint32_t e, const float4 &bj) {
-            const float4 o = dtab[e >> kSlotBits];
-            const float dx = (bi.x - bj.x) + o.x;
-            const float dy = (bi.y - bj.y) + o.y;
-            const float dz = (bi.z - bj.z) + o.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < sc.h2 && r2 > 0.0f) {
-                const float ir = rsqrtf(r2);
-                const float hr = sc.h - r2 * ir;
-                const float gw = hr * hr * ir;
-                const float u = (sc.h2 - r2) * sc.inv_wdq;  // W(r) / W(dq) = u^3
-                const float scorr = sc.neg_k * powi<NPOW>(u * u * u, sc.scorr_n);
-                const float f = (bi.w + bj.w + scorr) * gw;
-                ax += f * dx;
-                ay += f * dy;
-                az += f * dz;
-            }
-        });
-        // new position; contacts: obstacles, then the box, expressed relative to the cell origin
-        float px = bi.x + sc.c_dp * ax;
-        float py = bi.y + sc.c_dp * ay;
-        float pz = bi.z + sc.c_dp * az;
-        if (BATCH) {
-            const uint32_t s = scene_of<true>(b, p);
-            const Geo g = geo_of<true>(sc, b, s);
-            const DynParams *d = dyn + s;
-            const float3 og = origin_in(unpack_cell(cell_s[p]), g, sc.q);
-            contact_obstacles(d, og, px, py, pz);
-            px = fminf(fmaxf(px, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
-            py = fminf(fmaxf(py, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
-            pz = fminf(fmaxf(pz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
-        } else {
-            const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
-            if (n_obst)
-                contact_obstacles(dyn, og, px, py, pz);
-            px = fminf(fmaxf(px, blo0 - og.x), bhi0 - og.x);
-            py = fminf(fmaxf(py, blo1 - og.y), bhi1 - og.y);
-            pz = fminf(fmaxf(pz, blo2 - og.z), bhi2 - og.z);
-        }
+        const float3 np = deltap_one<NPOW, BATCH>(sc, dtab, B, nbr + t, n, nbr_cnt[t], bi, p, cell_s, dyn, b, bk);
+        const float px = np.x, py = np.y, pz = np.z;
         A[p] = make_float4(px, py, pz, bi.w);
     }
 }
@@ -1368,14 +1430,15 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
 // ------------------------------------------ a10: velocity, XSPH, commit
 
 template <bool BATCH>
-__global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers b)
+__global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers b, int part)
 {
     __shared__ float4 dtab[27];
     fill_dtab(dtab, sc.q);
     __syncthreads();
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= sc.n)
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // list column
+    if (t >= sc.n)
         return;
+    const uint32_t p = part ? b.act[t] : t;
     const size_t n = sc.n;
     const float4 af = b.recA[p];
     const float4 x0 = b.xt[p];
@@ -1383,8 +1446,9 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
     const float vy = (af.y - x0.y) * sc.inv_dt;
     const float vz = (af.z - x0.z) * sc.inv_dt;
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-    const uint32_t nn = b.nbr_cnt[p];
-    const uint32_t *e_ptr = b.nbr + p;
+    const uint32_t nn = b.nbr_cnt[t];
+    b.prev_cnt[p] = (uint8_t)nn;  // by state slot, for the next step's depth image
+    const uint32_t *e_ptr = b.nbr + t;
     for (uint32_t k = 0; k < nn; k += kUnroll) {
         uint32_t e[kUnroll];
         float4 aj[kUnroll], xj[kUnroll];
@@ -1546,9 +1610,9 @@ inline unsigned blocks_for(uint32_t n, int bs) { return (unsigned)((n + (uint32_
 // Resident blocks of kBlock threads per SM for a kernel (cached per function).
 int occupancy(const void *fn, int block = kBlock)
 {
-    static const void *keys[16];
-    static int vals[16];
-    for (int k = 0; k < 16; ++k)
+    static const void *keys[64];
+    static int vals[64];
+    for (int k = 0; k < 64; ++k)
         if (keys[k] == fn)
             return vals[k];
     int occ = 0;
@@ -1556,7 +1620,7 @@ int occupancy(const void *fn, int block = kBlock)
         cudaGetLastError();
         occ = 4;
     }
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < 64; ++k)
         if (!keys[k]) {
             keys[k] = fn;
             vals[k] = occ;
@@ -1607,11 +1671,11 @@ cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s)
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, bool part)
 {
     if (sc.n)
         (sc.scenes > 1 ? neighbors_kernel<true> : neighbors_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
-            sc, b);
+            sc, b, part ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1619,7 +1683,7 @@ cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (!sc.n)
         return cudaGetLastError();
-    level_hist_kernel<<<sc.level_tiles, kLevelTile, 2 * sc.K * sizeof(uint32_t), s>>>(sc, b);
+    level_hist_kernel<<<sc.level_tiles, kLevelTile, sc.K * sizeof(uint32_t), s>>>(sc, b);
     level_scan_kernel<<<1, 1024, 0, s>>>(sc, b);
     level_scatter_kernel<<<sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s>>>(sc, b);
     return cudaGetLastError();
@@ -1629,12 +1693,13 @@ template <int BS>
 cudaError_t launch_lambda_bs(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
                              float thr)
 {
+    const int part = partitioned(sc) ? 1 : 0;
     if (dense)
         lambda_kernel<true, BS><<<sms * occupancy((const void *)lambda_kernel<true, BS>, BS), BS, 0, s>>>(
-            sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr);
+            sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr, part);
     else
         lambda_kernel<false, BS><<<sms * occupancy((const void *)lambda_kernel<false, BS>, BS), BS, 0, s>>>(
-            sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr);
+            sc, b.recA, b.recB, b.rho, b.act, b.nbr, b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr, part);
     return cudaGetLastError();
 }
 
@@ -1652,7 +1717,7 @@ cudaError_t launch_deltap_t(const StepConst &sc, const Buffers &b, cudaStream_t 
 {
     const int grid = sms * occupancy((const void *)deltap_kernel<DENSE, NPOW, BATCH, BS>, BS);
     deltap_kernel<DENSE, NPOW, BATCH, BS><<<grid, BS, 0, s>>>(sc, b.recB, b.recA, b.act, b.nbr, b.nbr_cnt, b.cell_s,
-                                                              b.lvl_count, b.dyn, b, l, thr);
+                                                              b.lvl_count, b.dyn, b, l, thr, partitioned(sc) ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1687,7 +1752,7 @@ cudaError_t launch_finalize(const StepConst &sc, const Buffers &b, cudaStream_t 
 {
     if (sc.n)
         (sc.scenes > 1 ? finalize_kernel<true> : finalize_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
-            sc, b);
+            sc, b, partitioned(sc) ? 1 : 0);
     return cudaGetLastError();
 }
 
