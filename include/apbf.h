@@ -392,6 +392,8 @@ typedef struct apbf_request {
     uint32_t steps;                 /* steps to run, >= 1 */
     float *pos_out, *vel_out;       /* host, 3n floats each in particle-id order, or NULL; written by the tick
                                        that retires the request; the caller keeps them valid until then */
+    const apbf_obstacle *obstacles; /* host, n_obstacles entries (copied at submit; as apbf_set_obstacles), or NULL */
+    uint32_t n_obstacles;           /* <= APBF_MAX_OBSTACLES */
 } apbf_request;
 
 typedef struct apbf_tick_info {

@@ -108,6 +108,8 @@ class apbf_request(C.Structure):
         ("steps", C.c_uint32),
         ("pos_out", C.POINTER(C.c_float)),
         ("vel_out", C.POINTER(C.c_float)),
+        ("obstacles", C.c_void_p),
+        ("n_obstacles", C.c_uint32),
     ]
 
 
@@ -628,9 +630,10 @@ def apbf_server_create(physics, max_particles=0, max_cells=0, max_scenes=0, budg
     return Server(h, phys, npart, ncell)
 
 
-def apbf_server_submit(server: Server, desc, eye, steps: int, want_pos=True, want_vel=False) -> int:
-    """Queue a scene (a make_desc / desc_from_config pair or an apbf_scene_desc);
-    returns its ticket. Results: apbf_server_result(server, ticket) once done."""
+def apbf_server_submit(server: Server, desc, eye, steps: int, want_pos=True, want_vel=False, obstacles=()) -> int:
+    """Queue a scene (a make_desc / desc_from_config pair or an apbf_scene_desc)
+    with optional obstacles ((kind, a, b), ...); returns its ticket. Results:
+    apbf_server_result(server, ticket) once done."""
     d = desc[0] if isinstance(desc, tuple) else desc
     n = int(d.n)
     pos = np.empty((n, 3), np.float32) if want_pos else None
@@ -641,6 +644,13 @@ def apbf_server_submit(server: Server, desc, eye, steps: int, want_pos=True, wan
     r.steps = steps
     r.pos_out = _fptr(pos)
     r.vel_out = _fptr(vel)
+    obs = (apbf_obstacle * max(1, len(obstacles)))()
+    for k, (kind, a, b) in enumerate(obstacles):
+        obs[k].kind = int(kind)
+        obs[k].a[:] = [float(t) for t in a]
+        obs[k].b[:] = [float(t) for t in (list(b) + [0.0, 0.0, 0.0])[:3]]
+    r.obstacles = C.cast(obs, C.c_void_p) if obstacles else None
+    r.n_obstacles = len(obstacles)
     t = C.c_uint64()
     _server_check(lib().apbf_server_submit(server.handle, C.byref(r), C.byref(t)), "apbf_server_submit", server)
     server._outputs[t.value] = (pos, vel)

@@ -33,6 +33,7 @@ struct Request {
     float eye[3] = {};
     uint32_t steps = 0, done = 0;
     float *pos_out = nullptr, *vel_out = nullptr;
+    std::vector<Obstacle> obst;  // the scene's obstacles
     uint32_t state = APBF_REQ_QUEUED;
     uint64_t submit_tick = 0, admit_tick = 0, done_tick = 0;
     uint32_t p0 = 0, cell_base = 0;  // place in the pool while resident
@@ -274,6 +275,9 @@ apbf_status relayout(apbf_server *sv)
             s->dyn[k].eye[a] = r->eye[a];
             s->dyn[k].dir[a] = a == 0 ? 1.0f : 0.0f;
         }
+        s->dyn[k].n_obst = (uint32_t)r->obst.size();
+        for (size_t o = 0; o < r->obst.size(); ++o)
+            s->dyn[k].obst[o] = r->obst[o];
         g.nx = r->geo.nx;
         g.ny = r->geo.ny;
         g.nz = r->geo.nz;
@@ -527,6 +531,30 @@ APBF_API apbf_status apbf_server_submit(apbf_server *sv, const apbf_request *req
     r->desc.vel = nullptr;
     for (int a = 0; a < 3; ++a)
         r->eye[a] = req->eye[a];
+    if (req->n_obstacles > APBF_MAX_OBSTACLES || (req->n_obstacles && !req->obstacles))
+        return sfail(sv, APBF_ERR_INVALID_ARG, "need n_obstacles <= APBF_MAX_OBSTACLES and a non-NULL array");
+    for (uint32_t k = 0; k < req->n_obstacles; ++k) {
+        const apbf_obstacle &o = req->obstacles[k];
+        bool ok = std::isfinite(o.a[0]) && std::isfinite(o.a[1]) && std::isfinite(o.a[2]) && std::isfinite(o.b[0]) &&
+                  std::isfinite(o.b[1]) && std::isfinite(o.b[2]);
+        if (o.kind == APBF_OBSTACLE_SPHERE)
+            ok = ok && o.b[0] > 0.0f;
+        else if (o.kind == APBF_OBSTACLE_BOX)
+            ok = ok && o.a[0] < o.b[0] && o.a[1] < o.b[1] && o.a[2] < o.b[2];
+        else if (o.kind == APBF_OBSTACLE_CONE)
+            ok = ok && o.b[0] > 0.0f && o.b[1] > 0.0f;
+        else
+            ok = false;
+        if (!ok)
+            return sfail(sv, APBF_ERR_INVALID_ARG, "obstacle " + std::to_string(k) + ": unknown kind or bad size");
+        Obstacle q{};
+        q.kind = o.kind;
+        for (int a = 0; a < 3; ++a) {
+            q.a[a] = o.a[a];
+            q.b[a] = o.b[a];
+        }
+        r->obst.push_back(q);
+    }
     r->steps = req->steps;
     r->pos_out = req->pos_out;
     r->vel_out = req->vel_out;

@@ -128,3 +128,36 @@ def test_server_rejects_what_can_never_run():
     with pytest.raises(apbf.ApbfError):
         apbf.apbf_server_result(srv, 777)
     apbf.apbf_server_destroy(srv)
+
+
+def test_served_scenes_with_obstacles_and_prestabilisation_match_alone():
+    cfgs = scenes.config_batch_256(count=4, seed=77, n_lo=500, n_hi=3000, n_min=2, n_max=6)
+    cfgs = [c.replace(stabil_s=4, stabil_iters=2) for c in cfgs]
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    descs = [apbf.desc_from_config(c, *scenes.make_scene(c), r0) for c in cfgs]
+    # a sphere dented into each block's far face and a cone on its top, per scene
+    obst = []
+    for c in cfgs:
+        nx, ny, nz = c.lattice
+        w, d, hgt = nx * c.spacing, ny * c.spacing, nz * c.spacing
+        obst.append([(apbf.APBF_OBSTACLE_SPHERE, (w + 0.11, 0.5 * d, 0.5 * hgt), (0.15, 0, 0)),
+                     (apbf.APBF_OBSTACLE_CONE, (0.5 * w, 0.5 * d, hgt - 0.015), (0.2, 0.3, 0))])
+    srv = apbf.apbf_server_create(descs[0], max_particles=sum(c.n for c in cfgs), max_cells=4 * 10**6, max_scenes=4)
+    steps = [5, 3, 6, 4]
+    t = [apbf.apbf_server_submit(srv, descs[k], cfgs[k].eye, steps[k], want_vel=True, obstacles=obst[k])
+         for k in range(4)]
+    for _ in range(20):
+        info = apbf.apbf_server_tick(srv)
+        if info["resident_scenes"] == 0 and info["queued"] == 0:
+            break
+    for k in range(4):
+        pos, vel = apbf.apbf_server_result(srv, t[k])
+        s = apbf.apbf_create_scene(descs[k])
+        apbf.apbf_set_camera(s, cfgs[k].eye)
+        apbf.apbf_set_obstacles(s, obst[k])
+        apbf.apbf_step(s, steps[k])
+        ref = apbf.apbf_read_state(s, pos=True, vel=True)
+        assert np.array_equal(pos, ref["pos"]) and np.array_equal(vel, ref["vel"]), k
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_server_submit(srv, descs[0], cfgs[0].eye, 2, obstacles=[(9, (0, 0, 0), (1, 1, 1))])
+    apbf.apbf_server_destroy(srv)
