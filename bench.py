@@ -319,6 +319,63 @@ def cpu_baseline(cfg, n_full, budget_s=20.0):
             "sample_seconds": dt}
 
 
+# Table 1 of the paper: frame time improvement T_PBF(N_max)/T_APBF - 1 on the GTX 680 / HD7850,
+# per scenario, for the DTC and DTVS models (the paper's GPUs and scenes, not these analogues).
+PAPER_TABLE1 = {
+    "dam_break_216k": {"pbf_n": (3, 6), "dtc": (0.63, 0.53), "dtvs": (0.70, 0.59)},
+    "double_dam_break_673k": {"pbf_n": (5, 10), "dtc": (0.70, 0.64), "dtvs": (0.77, 0.69)},
+    "multi_dam_break_225k": {"pbf_n": (4, 8), "dtc": (0.42, 0.40), "dtvs": (0.59, 0.46)},
+}
+
+
+def run_table1(args, apbf, torch, d):
+    """Analogues of the three scenarios of Table 1, each as PBF with N_min and
+    with N_max iterations, APBF with the DTC model and with the DTVS model
+    (its depth image rendered here, 1280x720), on identical inputs and
+    drivers; improvement = T_PBF(N_max) / T_APBF - 1 as in Table 1."""
+    steps = min(args.steps, 300)
+    rows = {}
+    for name in PAPER_TABLE1:
+        base = scenes.CONFIGS[name]()
+        rho0 = float(np.float32(apbf.apbf_rest_density(base.h, base.mass, base.spacing)))
+        variants = {
+            "pbf_nmin": base.replace(lod_mode=scenes.LOD_FIXED, n_min=base.n_min, n_max=base.n_min, stabil_s=1),
+            "pbf_nmax": base.replace(lod_mode=scenes.LOD_FIXED, n_min=base.n_max),
+            "apbf_dtc": base,
+            "apbf_dtvs": base.replace(lod_mode=scenes.LOD_DTVS),
+        }
+        scene_bytes = apbf.apbf_scene_bytes(apbf.desc_from_config(base, *scenes.make_scene(base), rho0))
+        flush = needs_flush(apbf, scene_bytes)
+        row = {"particles": base.n, "n_range": f"{base.n_min}..{base.n_max}", "arena_mb": scene_bytes / 1e6,
+               "l2_flushed": flush}
+        for key, cfg in variants.items():
+            sc_ = make_scene(apbf, cfg, rho0)
+            tot, per, _ = timed_run(apbf, torch, sc_, cfg, args.warmup, steps, flush=flush)
+            ms = d.max(tot / steps)
+            row[key] = {"ms_per_step": ms, "p99_ms": metrics.percentile(per, 99),
+                        "mean_abs_density_error": float(apbf.apbf_density_stats(sc_)[0])}
+            apbf.apbf_destroy_scene(sc_)
+        t = row["pbf_nmax"]["ms_per_step"]
+        row["improvement_dtc"] = metrics.improvement(t, row["apbf_dtc"]["ms_per_step"])
+        row["improvement_dtvs"] = metrics.improvement(t, row["apbf_dtvs"]["ms_per_step"])
+        row["paper"] = PAPER_TABLE1[name]
+        rows[name] = row
+        print(f"{name:24s} PBF{base.n_min}: {row['pbf_nmin']['ms_per_step']:.3f} ms  "
+              f"PBF{base.n_max}: {t:.3f} ms  DTC: {row['apbf_dtc']['ms_per_step']:.3f} ms "
+              f"({100 * row['improvement_dtc']:+.0f} %)  DTVS: {row['apbf_dtvs']['ms_per_step']:.3f} ms "
+              f"({100 * row['improvement_dtvs']:+.0f} %)", file=sys.stderr, flush=True)
+    line = {"metric": "Table 1 analogue: ms/step of PBF N_min, PBF N_max, APBF DTC and DTVS; "
+                      "improvement T_PBF(N_max)/T_APBF - 1", "value": None, "unit": "ms/step", "n_gpus": d.ws,
+            "steps": steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "table1_analogues", "dtvs_view": "1280x720, 60 degree vertical field of view",
+                       "tuning": "defaults (block 256, compacted levels)"},
+            "scenarios": rows}
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
 def tune_summary(res):
     return {"block": res["block"], "mask_threshold": res["mask_threshold"], "trial_ms": res["ms_per_step"],
             "candidates": len(res["trials"])}
@@ -776,6 +833,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-particles", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--table1", action="store_true",
+                    help="time the analogues of the three scenarios of the paper's Table 1 instead")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pbf", action="store_true")
@@ -795,6 +854,8 @@ def main():
     torch.cuda.set_device(d.local)
     build.build()
     apbf.lib()
+    if args.table1:
+        return run_table1(args, apbf, torch, d)
     if args.workload == "batch_256":
         return run_batch(args, apbf, torch, d)
     if args.workload == "serve":
