@@ -264,16 +264,16 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.start = (uint32_t *)P(4 * (size_t)(sc.ncell + 1));
     b.tile_sums = (uint32_t *)P(4 * tiles);
     b.tmp = (uint32_t *)P(4 * n);
-    b.recA = (float4 *)P(16 * n);
-    b.recB = (float4 *)P(16 * n);
+    b.recA = (float4 *)P(16 * (n + 1));
+    b.recB = (float4 *)P(16 * (n + 1));
     b.xs32 = (float4 *)P(16 * n);
-    b.xt = (float4 *)P(16 * n);
+    b.xt = (float4 *)P(16 * (n + 1));
     b.id_s = (uint32_t *)P(4 * n);
     b.cell_s = (uint32_t *)P(4 * n);
     b.lvl_s = (uint8_t *)P(n);
     b.nbr_cnt = (uint8_t *)P(n);
     b.prev_cnt = (uint8_t *)P(n);
-    b.nbr = (uint32_t *)P(4 * (size_t)sc.max_nbr * n);
+    b.nbr = (uint32_t *)P(4 * (size_t)list_rows(sc.max_nbr) * n);
     b.rho = (float *)P(4 * n);
     b.lodd = (float *)P(4 * n);
     b.act = (uint32_t *)P(4 * n);

@@ -15,6 +15,18 @@ namespace apbf {
 constexpr uint32_t kDefaultMaxNeighbors = 128;
 constexpr uint32_t kSlotBits = 27;  // neighbour entry: slot (27 bits) | cell offset code (5 bits)
 constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
+// Neighbour lists are padded to a multiple of kListPad entries with an entry
+// naming slot n, a record placed far outside every grid (the record arrays
+// hold n + 1 entries), so the solver reads its batches without bounds checks.
+#ifndef APBF_UNROLL
+#define APBF_UNROLL 4  // neighbour batch depth of the solver passes
+#endif
+constexpr uint32_t kListPad = APBF_UNROLL;
+constexpr uint32_t kSentinelCode = 13;  // the zero cell offset
+__host__ __device__ constexpr uint32_t list_rows(uint32_t max_nbr)
+{
+    return (max_nbr + kListPad - 1) / kListPad * kListPad;
+}
 constexpr int kBlock = 256;          // threads per block of the per-particle kernels
 constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
 constexpr int kLevelTile = 1024;     // particles per block of the active-set partition

@@ -11,7 +11,11 @@
 //   nbr               u32 neighbour entries, entry k of particle p at k*n + p
 //                     (a warp of consecutive particles reads one 128-byte line
 //                     per k); low 27 bits: sorted slot, high 5 bits: which of
-//                     the 27 neighbour cells the neighbour was found in.
+//                     the 27 neighbour cells the neighbour was found in. Each
+//                     list is padded to a multiple of the batch depth with
+//                     entries naming slot n, whose record (recA, recB and xt
+//                     hold n + 1) lies far outside the grid, so the solver
+//                     reads whole batches without bounds checks.
 //
 // Positions inside the solver are stored relative to the particle's cell
 // origin (m + c) * q, with q = h rounded to 8 significant bits so that every
@@ -87,25 +91,77 @@ __device__ __forceinline__ uint32_t lod_level(float d, float dmin, float dmax, c
     return sc.n_max - (uint32_t)b;
 }
 
-// Cell-origin difference o_i - o_j = -(offset) q for the 27 neighbour cells.
-__device__ __forceinline__ void fill_dtab(float4 *dtab, float q)
+// Cell-origin difference o_i - o_j = -(offset) q for the 27 neighbour cells,
+// by the entry's code c = (dx+1) + 3 (dy+1) + 9 (dz+1). The x and y parts
+// are one 8-byte word and z a 4-byte word: two shared loads per neighbour
+// with fewer bank conflicts than one 16-byte load of a float4 table.
+struct OffsetTab {
+    float2 xy[27];
+    float z[27];
+};
+
+__device__ __forceinline__ void fill_dtab(OffsetTab *dtab, float q)
 {
     if (threadIdx.x < 27) {
         int c = threadIdx.x;
         float ox = (float)(c % 3 - 1), oy = (float)((c / 3) % 3 - 1), oz = (float)(c / 9 - 1);
-        dtab[c] = make_float4(-ox * q, -oy * q, -oz * q, 0.0f);
+        dtab->xy[c] = make_float2(-ox * q, -oy * q);
+        dtab->z[c] = -oz * q;
     }
+}
+
+// The same offsets decoded arithmetically (the velocity pass, where this
+// measured faster than the table): cz = c / 9, cy = (c mod 9) / 3, cx = c mod 3
+// by multiply-shift (exact for c < 27), then q - q * cx and so on, exact
+// because q has 8 significant bits.
+__device__ __forceinline__ float3 cell_offset_arith(uint32_t c, float q)
+{
+    const uint32_t cz = (c * 57u) >> 9, r = c - 9u * cz, cy = (r * 11u) >> 5, cx = r - 3u * cy;
+    return make_float3(__fmaf_rn(-q, (float)cx, q), __fmaf_rn(-q, (float)cy, q), __fmaf_rn(-q, (float)cz, q));
+}
+
+// Paired FP32 arithmetic (sm_100 and later): two IEEE round-to-nearest
+// operations in one instruction, each lane's result the same bits as the
+// scalar operation's.
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0, %1}, rc;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+__device__ __forceinline__ float2 fma2_rn(float2 a, float2 b, float2 c)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
 }
 
 // Neighbour batch depth and the minimum resident blocks per SM the solver
 // kernels are compiled for (register budget); tuned on the GB300.
-#ifndef APBF_UNROLL
-#define APBF_UNROLL 4
-#endif
 #ifndef APBF_SOLVER_MIN_BLOCKS
 #define APBF_SOLVER_MIN_BLOCKS 6
 #endif
-constexpr uint32_t kNoEntry = 0xffffffffu;  // code 31: never a valid neighbour entry
 constexpr int kUnroll = APBF_UNROLL;
 
 // Visit the neighbour entries of one particle in batches of kUnroll: the
@@ -117,19 +173,19 @@ template <int UNR = kUnroll, typename F>
 __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ e_ptr, size_t stride, uint32_t nn,
                                                   const float4 *__restrict__ rec, F &&f)
 {
+    static_assert(kListPad % UNR == 0, "lists are padded to a multiple of the batch depth");
     for (uint32_t k = 0; k < nn; k += UNR) {
         uint32_t e[UNR];
         float4 r[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            e[u] = (k + u < nn) ? __ldcs(e_ptr + (size_t)(k + u) * stride) : kNoEntry;
+            e[u] = __ldcs(e_ptr + (size_t)(k + u) * stride);
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            r[u] = (e[u] != kNoEntry) ? __ldg(&rec[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            r[u] = __ldg(&rec[e[u] & kSlotMask]);
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            if (e[u] != kNoEntry)
-                f(e[u], r[u]);
+            f(e[u], r[u]);
     }
 }
 
@@ -966,6 +1022,12 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
             bins[k] = 0u;
     __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {  // the padding entries' record: beyond reach of every particle (r^2 = inf)
+        const float4 far = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+        b.recA[sc.n] = far;
+        b.recB[sc.n] = far;
+        b.xt[sc.n] = far;
+    }
     uint32_t cnt = 0;
     if (t < sc.n) {
         const uint32_t p = part ? b.act[t] : t;
@@ -988,27 +1050,39 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                                j1 = b.start[row + xr + 1];
                 const uint32_t code_row = (uint32_t)(3 * (dy + 1) + 9 * (dz + 1));
                 const bool own_row = dy == 0 && dz == 0;  // the only row that holds p itself
-                for (uint32_t j = j0; j < j1; j += kUnroll) {
-                    float4 xj[kUnroll];
-                    // past the window's end: a far point, which the predicate rejects (r2 = inf)
+                // the window in chunks of up to 32 candidates: first the predicate for each
+                // (a hit mask), then one list write per hit, so a warp's lanes share the
+                // write loop only as often as the lane with the most hits needs it
+                for (uint32_t j = j0; j < j1; j += 32) {
+                    const uint32_t je = min(j1, j + 32u);
+                    uint32_t hits = 0;
+                    for (uint32_t jj = j; jj < je; jj += kUnroll) {
+                        float4 xj[kUnroll];
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u)
-                        xj[u] = (j + u < j1) ? b.xs32[j + u] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+                        for (int u = 0; u < kUnroll; ++u)
+                            xj[u] = (jj + u < je) ? b.xs32[jj + u] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+                        uint32_t nib = 0;
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        const uint32_t q = j + u;
-                        // FP32 predicate, rounded after every operation
-                        const float dx = __fsub_rn(xi.x, xj[u].x);
-                        const float dy2 = __fsub_rn(xi.y, xj[u].y);
-                        const float dz2 = __fsub_rn(xi.z, xj[u].z);
-                        float r2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy2, dy2));
-                        r2 = __fadd_rn(r2, __fmul_rn(dz2, dz2));
-                        if (r2 < sc.h2 && !(own_row && q == p)) {
-                            const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
-                            if (cnt < sc.max_nbr)
-                                b.nbr[(size_t)cnt * n + t] = q | ((code_row + dxc) << kSlotBits);
-                            ++cnt;
+                        for (int u = 0; u < kUnroll; ++u) {
+                            const float2 dxy = sub2_rn(make_float2(xi.x, xi.y), make_float2(xj[u].x, xj[u].y));
+                            const float2 sq = mul2_rn(dxy, dxy);
+                            const float dz2 = __fsub_rn(xi.z, xj[u].z);
+                            float r2 = __fadd_rn(sq.x, sq.y);
+                            r2 = __fadd_rn(r2, __fmul_rn(dz2, dz2));
+                            if (r2 < sc.h2)
+                                nib |= 1u << u;
                         }
+                        hits |= nib << (jj - j);
+                    }
+                    if (own_row && p - j < 32u)
+                        hits &= ~(1u << (p - j));
+                    while (hits) {
+                        const uint32_t q = j + (uint32_t)(__ffs(hits) - 1);
+                        hits &= hits - 1u;
+                        const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
+                        if (cnt < sc.max_nbr)
+                            b.nbr[(size_t)cnt * n + t] = q | ((code_row + dxc) << kSlotBits);
+                        ++cnt;
                     }
                 }
             }
@@ -1018,6 +1092,9 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
             cnt = sc.max_nbr;
         }
         b.nbr_cnt[t] = (uint8_t)cnt;
+        const uint32_t sentinel = sc.n | (kSentinelCode << kSlotBits);
+        for (uint32_t k = cnt; k % kListPad; ++k)
+            b.nbr[(size_t)k * n + t] = sentinel;
         if (part && cnt)
             atomicAdd(&bins[sc.n_max - b.lvl_s[p]], cnt);
     }
@@ -1230,16 +1307,17 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
 // instantiations that inline it (dense or compacted, block size, batch
 // depth UNR): a particle's result is the same bits whichever computes it.
 template <int UNR = kUnroll>
-__device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *dtab, const float4 *__restrict__ A,
+__device__ __forceinline__ void lambda_one(const StepConst &sc, const OffsetTab *dtab, const float4 *__restrict__ A,
                                            const uint32_t *__restrict__ e_ptr, size_t n, uint32_t nn, const float4 &ai,
                                            float &lam, float &rho)
 {
-    float racc = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, s2 = 0.0f;
+    float racc = 0.0f, gz = 0.0f, s2 = 0.0f;
+    float2 gxy = make_float2(0.0f, 0.0f);
     for_each_neighbor<UNR>(e_ptr, n, nn, A, [&](uint32_t e, const float4 &aj) {
-        const float4 o = dtab[e >> kSlotBits];
-        const float dx = __fadd_rn(__fsub_rn(ai.x, aj.x), o.x);
-        const float dy = __fadd_rn(__fsub_rn(ai.y, aj.y), o.y);
-        const float dz = __fadd_rn(__fsub_rn(ai.z, aj.z), o.z);
+        const uint32_t c = e >> kSlotBits;
+        const float2 dxy = add2_rn(sub2_rn(make_float2(ai.x, ai.y), make_float2(aj.x, aj.y)), dtab->xy[c]);
+        const float dx = dxy.x, dy = dxy.y;
+        const float dz = __fadd_rn(__fsub_rn(ai.z, aj.z), dtab->z[c]);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         if (r2 < sc.h2) {
             const float u = __fsub_rn(sc.h2, r2);
@@ -1248,8 +1326,7 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *dt
                 const float ir = rsqrtf(r2);
                 const float hr = __fmaf_rn(-r2, ir, sc.h);
                 const float gw = __fmul_rn(__fmul_rn(hr, hr), ir);  // |grad W| / (45/(pi h^6)) / r
-                gx = __fmaf_rn(gw, dx, gx);
-                gy = __fmaf_rn(gw, dy, gy);
+                gxy = fma2_rn(make_float2(gw, gw), dxy, gxy);
                 gz = __fmaf_rn(gw, dz, gz);
                 s2 = __fmaf_rn(__fmul_rn(gw, gw), r2, s2);
             }
@@ -1257,7 +1334,7 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *dt
     });
     rho = __fmul_rn(sc.mass_poly6, __fadd_rn(sc.h6, racc));
     const float C = __fmaf_rn(rho, sc.inv_rho0, -1.0f);
-    const float g2 = __fadd_rn(__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))), s2);
+    const float g2 = __fadd_rn(__fmaf_rn(gz, gz, __fmaf_rn(gxy.y, gxy.y, __fmul_rn(gxy.x, gxy.x))), s2);
     const float denom = __fmaf_rn(sc.c_lam, g2, sc.eps);
     lam = __fdiv_rn(-C, denom);
 }
@@ -1279,8 +1356,9 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
     const uint32_t *__restrict__ act, const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt,
     const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr, int part)
 {
-    __shared__ float4 dtab[27];
-    fill_dtab(dtab, sc.q);
+    __shared__ OffsetTab dtab_s;
+    const OffsetTab *dtab = &dtab_s;
+    fill_dtab(&dtab_s, sc.q);
     __syncthreads();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
     const uint32_t cnt_prev = DENSE ? sc.n : lvl_count[l - 1];
@@ -1349,17 +1427,18 @@ __device__ __forceinline__ BoxK box_of(const DynParams *dyn)
 // relative to its cell origin; explicit rounding intrinsics as in lambda_one,
 // so the result does not depend on which instantiation computes it.
 template <int NPOW, bool BATCH, int UNR = kUnroll>
-__device__ __forceinline__ float3 deltap_one(const StepConst &sc, const float4 *dtab, const float4 *__restrict__ B,
+__device__ __forceinline__ float3 deltap_one(const StepConst &sc, const OffsetTab *dtab, const float4 *__restrict__ B,
                                              const uint32_t *__restrict__ e_ptr, size_t n, uint32_t nn, const float4 &bi,
                                              uint32_t p, const uint32_t *__restrict__ cell_s,
                                              const DynParams *__restrict__ dyn, const Buffers &b, const BoxK &bk)
 {
-    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+    float2 axy = make_float2(0.0f, 0.0f);
+    float az = 0.0f;
     for_each_neighbor<UNR>(e_ptr, n, nn, B, [&](uint32_t e, const float4 &bj) {
-        const float4 o = dtab[e >> kSlotBits];
-        const float dx = __fadd_rn(__fsub_rn(bi.x, bj.x), o.x);
-        const float dy = __fadd_rn(__fsub_rn(bi.y, bj.y), o.y);
-        const float dz = __fadd_rn(__fsub_rn(bi.z, bj.z), o.z);
+        const uint32_t c = e >> kSlotBits;
+        const float2 dxy = add2_rn(sub2_rn(make_float2(bi.x, bi.y), make_float2(bj.x, bj.y)), dtab->xy[c]);
+        const float dx = dxy.x, dy = dxy.y;
+        const float dz = __fadd_rn(__fsub_rn(bi.z, bj.z), dtab->z[c]);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         if (r2 < sc.h2 && r2 > 0.0f) {
             const float ir = rsqrtf(r2);
@@ -1368,14 +1447,13 @@ __device__ __forceinline__ float3 deltap_one(const StepConst &sc, const float4 *
             const float u = __fmul_rn(__fsub_rn(sc.h2, r2), sc.inv_wdq);  // W(r) / W(dq) = u^3
             const float scorr = __fmul_rn(sc.neg_k, powi<NPOW>(__fmul_rn(__fmul_rn(u, u), u), sc.scorr_n));
             const float f = __fmul_rn(__fadd_rn(__fadd_rn(bi.w, bj.w), scorr), gw);
-            ax = __fmaf_rn(f, dx, ax);
-            ay = __fmaf_rn(f, dy, ay);
+            axy = fma2_rn(make_float2(f, f), dxy, axy);
             az = __fmaf_rn(f, dz, az);
         }
     });
     // new position; contacts: obstacles, then the box, expressed relative to the cell origin
-    float px = __fmaf_rn(sc.c_dp, ax, bi.x);
-    float py = __fmaf_rn(sc.c_dp, ay, bi.y);
+    float px = __fmaf_rn(sc.c_dp, axy.x, bi.x);
+    float py = __fmaf_rn(sc.c_dp, axy.y, bi.y);
     float pz = __fmaf_rn(sc.c_dp, az, bi.z);
     if (BATCH) {
         const uint32_t s = scene_of<true>(b, p);
@@ -1408,8 +1486,9 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
     const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr,
     int part)
 {
-    __shared__ float4 dtab[27];
-    fill_dtab(dtab, sc.q);
+    __shared__ OffsetTab dtab_s;
+    const OffsetTab *dtab = &dtab_s;
+    fill_dtab(&dtab_s, sc.q);
     __syncthreads();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
     const bool masked = !DENSE && (float)cnt_l >= mask_thr * (float)sc.n;
@@ -1432,9 +1511,6 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers b, int part)
 {
-    __shared__ float4 dtab[27];
-    fill_dtab(dtab, sc.q);
-    __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // list column
     if (t >= sc.n)
         return;
@@ -1454,18 +1530,15 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
         float4 aj[kUnroll], xj[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            e[u] = (k + u < nn) ? __ldcs(e_ptr + (size_t)(k + u) * n) : kNoEntry;
+            e[u] = __ldcs(e_ptr + (size_t)(k + u) * n);
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const bool ok = e[u] != kNoEntry;
-            aj[u] = ok ? __ldg(&b.recA[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            xj[u] = ok ? __ldg(&b.xt[e[u] & kSlotMask]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            aj[u] = __ldg(&b.recA[e[u] & kSlotMask]);
+            xj[u] = __ldg(&b.xt[e[u] & kSlotMask]);
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            if (e[u] == kNoEntry)
-                continue;
-            const float4 o = dtab[e[u] >> kSlotBits];
+            const float3 o = cell_offset_arith(e[u] >> kSlotBits, sc.q);
             const float dx = (af.x - aj[u].x) + o.x;
             const float dy = (af.y - aj[u].y) + o.y;
             const float dz = (af.z - aj[u].z) + o.z;

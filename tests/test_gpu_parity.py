@@ -81,6 +81,9 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
         code = (e >> 27).astype(np.int64)
         off = np.stack([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], 1)
         assert np.array_equal(cells[got] - cells[q], off), q
+        # padding to a multiple of 4 entries: slot n (the far record), zero cell offset
+        pad = nbr[cnt[q]: min(-(-cnt[q] // 4) * 4, nbr.shape[0]), q]
+        assert np.all(pad == (n | (13 << 27))), q
     lvl = st.level_presort[st.order]
     if cfg.lod_mode in (scenes.LOD_DTC, scenes.LOD_DTVS) and p.n_max > p.n_min:
         apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
