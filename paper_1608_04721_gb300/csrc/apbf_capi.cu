@@ -1297,23 +1297,29 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
     }
     if (bytes != size || (size && !host))
         return fail(s, APBF_ERR_INVALID_ARG, "debug_read size mismatch: field needs " + std::to_string(size) + " bytes");
-    if ((field == APBF_DBG_NBR || field == APBF_DBG_NBR_COUNT) && !s->lists_by_slot && n) {
-        // stored by active-list position: report by sorted slot, as documented
-        std::vector<uint32_t> act(n);
-        APBF_CUDA(s, cudaMemcpyAsync(act.data(), b.act, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+    if ((field == APBF_DBG_NBR || field == APBF_DBG_NBR_COUNT) && n && (field == APBF_DBG_NBR || !s->lists_by_slot)) {
+        // stored in entry blocks by list column (the active-list position when
+        // the step is partitioned): report entry k of sorted slot p at k*n + p
+        std::vector<uint32_t> col(n);
+        if (s->lists_by_slot) {
+            for (size_t t = 0; t < n; ++t)
+                col[t] = (uint32_t)t;
+        } else {
+            APBF_CUDA(s, cudaMemcpyAsync(col.data(), b.act, 4 * n, cudaMemcpyDeviceToHost, s->stream));
+        }
         if (field == APBF_DBG_NBR_COUNT) {
             std::vector<uint8_t> raw(n);
             APBF_CUDA(s, cudaMemcpyAsync(raw.data(), b.nbr_cnt, n, cudaMemcpyDeviceToHost, s->stream));
             APBF_CUDA(s, cudaStreamSynchronize(s->stream));
             for (size_t t = 0; t < n; ++t)
-                ((uint8_t *)host)[act[t]] = raw[t];
+                ((uint8_t *)host)[col[t]] = raw[t];
         } else {
-            std::vector<uint32_t> raw((size_t)sc.max_nbr * n);
+            std::vector<uint32_t> raw((size_t)list_rows(sc.max_nbr) * n);
             APBF_CUDA(s, cudaMemcpyAsync(raw.data(), b.nbr, 4 * raw.size(), cudaMemcpyDeviceToHost, s->stream));
             APBF_CUDA(s, cudaStreamSynchronize(s->stream));
-            for (size_t k = 0; k < sc.max_nbr; ++k)
+            for (uint32_t k = 0; k < sc.max_nbr; ++k)
                 for (size_t t = 0; t < n; ++t)
-                    ((uint32_t *)host)[k * n + act[t]] = raw[k * n + t];
+                    ((uint32_t *)host)[k * n + col[t]] = raw[entry_index(k, t, n)];
         }
         return check_device_errors(s);
     }

@@ -15,13 +15,18 @@ namespace apbf {
 constexpr uint32_t kDefaultMaxNeighbors = 128;
 constexpr uint32_t kSlotBits = 27;  // neighbour entry: slot (27 bits) | cell offset code (5 bits)
 constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
-// Neighbour lists are padded to a multiple of kListPad entries with an entry
-// naming slot n, a record placed far outside every grid (the record arrays
-// hold n + 1 entries), so the solver reads its batches without bounds checks.
-#ifndef APBF_UNROLL
-#define APBF_UNROLL 4  // neighbour batch depth of the solver passes
-#endif
-constexpr uint32_t kListPad = APBF_UNROLL;
+// Neighbour entries are stored in blocks of kEntryBlock per particle: entry k
+// of list column t at ((k / 4) * n + t) * 4 + k % 4, so a thread reads a
+// block with one 16-byte load and a warp's block loads are contiguous. Lists
+// are padded to whole blocks with an entry naming slot n, a record placed far
+// outside every grid (the record arrays hold n + 1 entries), so the solver
+// reads whole blocks without bounds checks.
+constexpr uint32_t kEntryBlock = 4;
+constexpr uint32_t kListPad = kEntryBlock;
+__host__ __device__ inline size_t entry_index(uint32_t k, size_t t, size_t n)
+{
+    return ((size_t)(k / kEntryBlock) * n + t) * kEntryBlock + k % kEntryBlock;
+}
 constexpr uint32_t kSentinelCode = 13;  // the zero cell offset
 __host__ __device__ constexpr uint32_t list_rows(uint32_t max_nbr)
 {

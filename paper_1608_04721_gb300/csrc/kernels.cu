@@ -8,14 +8,16 @@
 //   xs32              float4 absolute predicted position (FP32), for the
 //                     neighbour predicate
 //   xt                float4 start-of-step position relative to the cell origin
-//   nbr               u32 neighbour entries, entry k of particle p at k*n + p
-//                     (a warp of consecutive particles reads one 128-byte line
-//                     per k); low 27 bits: sorted slot, high 5 bits: which of
-//                     the 27 neighbour cells the neighbour was found in. Each
-//                     list is padded to a multiple of the batch depth with
-//                     entries naming slot n, whose record (recA, recB and xt
-//                     hold n + 1) lies far outside the grid, so the solver
-//                     reads whole batches without bounds checks.
+//   nbr               u32 neighbour entries in blocks of 4 per list column:
+//                     entry k of column t at ((k/4)*n + t)*4 + k%4 (a thread
+//                     reads a block with one 16-byte load; a warp of
+//                     consecutive columns reads 512 contiguous bytes); low 27
+//                     bits: sorted slot, high 5 bits: which of the 27
+//                     neighbour cells the neighbour was found in. Each list is
+//                     padded to whole blocks with entries naming slot n, whose
+//                     record (recA, recB and xt hold n + 1) lies far outside
+//                     the grid, so the solver reads whole blocks without
+//                     bounds checks.
 //
 // Positions inside the solver are stored relative to the particle's cell
 // origin (m + c) * q, with q = h rounded to 8 significant bits so that every
@@ -162,7 +164,7 @@ __device__ __forceinline__ float2 fma2_rn(float2 a, float2 b, float2 c)
 #ifndef APBF_SOLVER_MIN_BLOCKS
 #define APBF_SOLVER_MIN_BLOCKS 6
 #endif
-constexpr int kUnroll = APBF_UNROLL;
+constexpr int kUnroll = (int)kEntryBlock;
 
 // Visit the neighbour entries of one particle in batches of kUnroll: the
 // batch's entries are loaded first, then its records, then f runs on each,
@@ -170,16 +172,15 @@ constexpr int kUnroll = APBF_UNROLL;
 // once per pass (streaming hint, they should not displace the records that
 // neighbouring threads reuse from L1).
 template <int UNR = kUnroll, typename F>
-__device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ e_ptr, size_t stride, uint32_t nn,
+__device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
                                                   const float4 *__restrict__ rec, F &&f)
 {
-    static_assert(kListPad % UNR == 0, "lists are padded to a multiple of the batch depth");
+    static_assert(UNR == (int)kEntryBlock, "one entry block per batch");
+    const uint4 *e_ptr = reinterpret_cast<const uint4 *>(nbr) + t;
     for (uint32_t k = 0; k < nn; k += UNR) {
-        uint32_t e[UNR];
+        const uint4 eb = __ldcs(e_ptr + (size_t)(k / UNR) * n);
+        const uint32_t e[UNR] = {eb.x, eb.y, eb.z, eb.w};
         float4 r[UNR];
-#pragma unroll
-        for (int u = 0; u < UNR; ++u)
-            e[u] = __ldcs(e_ptr + (size_t)(k + u) * stride);
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
             r[u] = __ldg(&rec[e[u] & kSlotMask]);
@@ -1015,12 +1016,6 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b, int part)
 {
-    __shared__ uint32_t sh[32];
-    __shared__ uint32_t bins[256];  // pairs per level bin (part only)
-    if (part)
-        for (uint32_t k = threadIdx.x; k < sc.K; k += blockDim.x)
-            bins[k] = 0u;
-    __syncthreads();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {  // the padding entries' record: beyond reach of every particle (r^2 = inf)
         const float4 far = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
@@ -1028,13 +1023,17 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
         b.recB[sc.n] = far;
         b.xt[sc.n] = far;
     }
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, bin = 0;
     if (t < sc.n) {
         const uint32_t p = part ? b.act[t] : t;
+        if (part)
+            bin = sc.n_max - b.lvl_s[p];
         const Geo g = geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p));
         const float4 xi = b.xs32[p];
         const int3 c = unpack_cell(b.cell_s[p]);
         const size_t n = sc.n;
+        uint4 *eblk = reinterpret_cast<uint4 *>(b.nbr) + t;  // entry blocks of column t, stride n
+        uint4 eb = make_uint4(0u, 0u, 0u, 0u);                // the block being filled
         // the cells x-1..x+1 of one row (y+dy, z+dz) are contiguous in sorted order
         const int xl = max(c.x - 1, 0), xr = min(c.x + 1, g.nx - 1);
         for (int dz = -1; dz <= 1; ++dz) {
@@ -1080,8 +1079,14 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                         const uint32_t q = j + (uint32_t)(__ffs(hits) - 1);
                         hits &= hits - 1u;
                         const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
-                        if (cnt < sc.max_nbr)
-                            b.nbr[(size_t)cnt * n + t] = q | ((code_row + dxc) << kSlotBits);
+                        const uint32_t e = q | ((code_row + dxc) << kSlotBits);
+                        const uint32_t s = cnt % kEntryBlock;
+                        eb.x = s == 0 ? e : eb.x;
+                        eb.y = s == 1 ? e : eb.y;
+                        eb.z = s == 2 ? e : eb.z;
+                        eb.w = s == 3 ? e : eb.w;
+                        if (s == kEntryBlock - 1 && cnt < sc.max_nbr)  // a full block: one 16-byte store
+                            eblk[(size_t)(cnt / kEntryBlock) * n] = eb;
                         ++cnt;
                     }
                 }
@@ -1092,20 +1097,29 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
             cnt = sc.max_nbr;
         }
         b.nbr_cnt[t] = (uint8_t)cnt;
-        const uint32_t sentinel = sc.n | (kSentinelCode << kSlotBits);
-        for (uint32_t k = cnt; k % kListPad; ++k)
-            b.nbr[(size_t)k * n + t] = sentinel;
-        if (part && cnt)
-            atomicAdd(&bins[sc.n_max - b.lvl_s[p]], cnt);
+        const uint32_t s = cnt % kEntryBlock;
+        if (s) {  // the last, partial block, padded
+            const uint32_t sentinel = sc.n | (kSentinelCode << kSlotBits);
+            eb.y = s <= 1 ? sentinel : eb.y;
+            eb.z = s <= 2 ? sentinel : eb.z;
+            eb.w = sentinel;
+            eblk[(size_t)(cnt / kEntryBlock) * n] = eb;
+        }
     }
-    uint32_t tot = block_sum_u32(cnt, sh);
-    if (threadIdx.x == 0 && tot)
-        atomicAdd(&b.counters[0], (unsigned long long)tot);
+    // pair counts, total and per level bin: one atomic per warp (no block
+    // barrier, so a warp retires as soon as its own lanes are done); the
+    // active list is level-major, so a warp almost always holds one level
+    const uint32_t wsum = warp_sum(cnt);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0 && wsum)
+        atomicAdd(&b.counters[0], (unsigned long long)wsum);
     if (part) {
-        __syncthreads();
-        for (uint32_t k = threadIdx.x; k < sc.K; k += blockDim.x)
-            if (bins[k])
-                atomicAdd(&b.counters[2 + k], (unsigned long long)bins[k]);
+        if (__all_sync(kFull, bin == __shfl_sync(kFull, bin, 0))) {
+            if (lane == 0 && wsum)
+                atomicAdd(&b.counters[2 + bin], (unsigned long long)wsum);
+        } else if (cnt) {
+            atomicAdd(&b.counters[2 + bin], (unsigned long long)cnt);
+        }
     }
 }
 
@@ -1308,12 +1322,13 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
 // depth UNR): a particle's result is the same bits whichever computes it.
 template <int UNR = kUnroll>
 __device__ __forceinline__ void lambda_one(const StepConst &sc, const OffsetTab *dtab, const float4 *__restrict__ A,
-                                           const uint32_t *__restrict__ e_ptr, size_t n, uint32_t nn, const float4 &ai,
+                                           const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
+                                           const float4 &ai,
                                            float &lam, float &rho)
 {
     float racc = 0.0f, gz = 0.0f, s2 = 0.0f;
     float2 gxy = make_float2(0.0f, 0.0f);
-    for_each_neighbor<UNR>(e_ptr, n, nn, A, [&](uint32_t e, const float4 &aj) {
+    for_each_neighbor<UNR>(nbr, t, n, nn, A, [&](uint32_t e, const float4 &aj) {
         const uint32_t c = e >> kSlotBits;
         const float2 dxy = add2_rn(sub2_rn(make_float2(ai.x, ai.y), make_float2(aj.x, aj.y)), dtab->xy[c]);
         const float dx = dxy.x, dy = dxy.y;
@@ -1384,7 +1399,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
             continue;
         }
         float lam, rho;
-        lambda_one(sc, dtab, A, nbr + t, n, nbr_cnt[t], ai, lam, rho);
+        lambda_one(sc, dtab, A, nbr, t, n, nbr_cnt[t], ai, lam, rho);
         B[p] = make_float4(ai.x, ai.y, ai.z, lam);
         rho_out[p] = rho;
     }
@@ -1428,13 +1443,14 @@ __device__ __forceinline__ BoxK box_of(const DynParams *dyn)
 // so the result does not depend on which instantiation computes it.
 template <int NPOW, bool BATCH, int UNR = kUnroll>
 __device__ __forceinline__ float3 deltap_one(const StepConst &sc, const OffsetTab *dtab, const float4 *__restrict__ B,
-                                             const uint32_t *__restrict__ e_ptr, size_t n, uint32_t nn, const float4 &bi,
+                                             const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
+                                             const float4 &bi,
                                              uint32_t p, const uint32_t *__restrict__ cell_s,
                                              const DynParams *__restrict__ dyn, const Buffers &b, const BoxK &bk)
 {
     float2 axy = make_float2(0.0f, 0.0f);
     float az = 0.0f;
-    for_each_neighbor<UNR>(e_ptr, n, nn, B, [&](uint32_t e, const float4 &bj) {
+    for_each_neighbor<UNR>(nbr, t, n, nn, B, [&](uint32_t e, const float4 &bj) {
         const uint32_t c = e >> kSlotBits;
         const float2 dxy = add2_rn(sub2_rn(make_float2(bi.x, bi.y), make_float2(bj.x, bj.y)), dtab->xy[c]);
         const float dx = dxy.x, dy = dxy.y;
@@ -1500,7 +1516,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
         if (masked && b.lvl_s[p] < l)
             continue;
         const float4 bi = B[p];
-        const float3 np = deltap_one<NPOW, BATCH>(sc, dtab, B, nbr + t, n, nbr_cnt[t], bi, p, cell_s, dyn, b, bk);
+        const float3 np = deltap_one<NPOW, BATCH>(sc, dtab, B, nbr, t, n, nbr_cnt[t], bi, p, cell_s, dyn, b, bk);
         const float px = np.x, py = np.y, pz = np.z;
         A[p] = make_float4(px, py, pz, bi.w);
     }
@@ -1524,13 +1540,11 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     const uint32_t nn = b.nbr_cnt[t];
     b.prev_cnt[p] = (uint8_t)nn;  // by state slot, for the next step's depth image
-    const uint32_t *e_ptr = b.nbr + t;
+    const uint4 *e_ptr = reinterpret_cast<const uint4 *>(b.nbr) + t;
     for (uint32_t k = 0; k < nn; k += kUnroll) {
-        uint32_t e[kUnroll];
+        const uint4 eb = __ldcs(e_ptr + (size_t)(k / kUnroll) * n);
+        const uint32_t e[kUnroll] = {eb.x, eb.y, eb.z, eb.w};
         float4 aj[kUnroll], xj[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            e[u] = __ldcs(e_ptr + (size_t)(k + u) * n);
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             aj[u] = __ldg(&b.recA[e[u] & kSlotMask]);
@@ -1595,7 +1609,7 @@ __global__ void __launch_bounds__(kBlock) density_kernel(StepConst sc, Buffers b
         float racc = 0.0f;
         const uint32_t nn = b.nbr_cnt[p];
         for (uint32_t k = 0; k < nn; ++k) {
-            const uint32_t j = b.nbr[(size_t)k * n + p] & kSlotMask;
+            const uint32_t j = b.nbr[entry_index(k, p, n)] & kSlotMask;
             const float4 xj = b.xs32[j];
             const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
