@@ -4,11 +4,11 @@
  * Method: Koster & Kruger, "Adaptive Position-Based Fluids: Improving
  * Performance of Fluid Simulations for Real-Time Applications", IJCGA 6(3),
  * 2016. One call of apbf_step() advances a scene by the simulation loop of
- * Fig. 7 (Sec. 5): external forces and prediction (lines 1-4), neighbour
- * discovery by a counting-sort uniform grid with particle reordering (lines
- * 5-6, Sec. 6), N_max Jacobi solver iterations of the density constraint
- * (Eq. 4-7, lines 12-23) in which particle i is active only in iterations
- * 1..N_i (Eq. 9-11), and the velocity/position update (lines 24-27). N_i is
+ * Fig. 7 (Sec. 5): external forces and prediction, neighbour discovery by a
+ * counting-sort uniform grid with particle reordering (Sec. 6), N_max Jacobi
+ * solver iterations of the density constraint (Eq. 4-7) in which particle i
+ * is active only in iterations 1..N_i (Eq. 9-11), and the velocity/position
+ * update. N_i is
  * the particle's level of detail (Eq. 8) from its distance to the camera
  * (Sec. 4.1, DTC model) or from its distance behind the visible surface of
  * the particles rendered as spheres (Sec. 4.1 and Sec. 6, DTVS model).
@@ -71,7 +71,7 @@ typedef enum apbf_status {
  *  grid_lo/hi   static uniform-grid extent (cells of size h). Every particle
  *               must lie inside it. Cells per axis: floor((hi-lo)*(1/h)) + 1
  *               (FP32), at most 2047 (x, y) and 1023 (z).
- *  box_lo/hi    collision box (contacts, Fig. 7 line 18), inside the grid extent.
+ *  box_lo/hi    collision box (contacts, the collision response of Fig. 7), inside the grid extent.
  *  h            smoothing length = neighbour radius = cell size, > 0.
  *  dt           time step, > 0.
  *  mass         particle mass (uniform), > 0; w = 1/mass (Sec. 3).
@@ -81,12 +81,12 @@ typedef enum apbf_status {
  *               tensile term s_corr = -k (W(r)/W(dq))^n added to lambda_i +
  *               lambda_j in Eq. 7; k in m^2 (lambda's unit), 0 <= dq < h, n <= 16.
  *  xsph_c       XSPH viscosity, v_i += c sum_j (m/rho0) (v_j - v_i) W_ij.
- *  gravity      external acceleration f_ext (Fig. 7 line 2).
+ *  gravity      external acceleration f_ext (the external force of Fig. 7).
  *  n_min, n_max iteration range, 1 <= n_min <= n_max <= 255 (Eq. 8: levels 1..N_l).
  *  lod_mode     APBF_LOD_FIXED, APBF_LOD_DTC or APBF_LOD_DTVS (not in batches or servers:
  *               APBF_ERR_NOT_SUPPORTED).
  *  stabil_iters, stabil_s
- *               pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11) of the set of
+ *               pre-stabilisation (Sec. 4.3, the pre-stabilisation loop of Fig. 7) of the set of
  *               Eq. 11 for l = S, i.e. the particles of level < S: before the
  *               solver, stabil_iters times (<= 64), each such particle's
  *               position at the start of the step is moved out of the
@@ -209,7 +209,7 @@ APBF_API apbf_status apbf_set_view(apbf_scene *scene, uint32_t width, uint32_t h
 /*
  * Rigid obstacles (the paper's signed-distance-field obstacles of Sec. 6, here
  * analytic solids), used from the next step on by the contact response of
- * Fig. 7 line 18 -- after every position update of the solver, a predicted
+ * The collision response of Fig. 7 -- after every position update of the solver, a predicted
  * position strictly inside an obstacle moves to the nearest point of its
  * surface (obstacles in order), then into the box -- and by the
  * pre-stabilisation above. The prediction itself is only clamped to the box.
@@ -313,12 +313,12 @@ APBF_API apbf_status apbf_density_stats_static(const float *pos, uint32_t n, flo
 #define APBF_STAGE_SCAN 2u       /* a4/a6: exclusive scan = cell start/end */
 #define APBF_STAGE_SCATTER 3u    /* a4: slot scatter */
 #define APBF_STAGE_REORDER 4u    /* a4/a5: stable rank and reorder */
-#define APBF_STAGE_NEIGHBORS 5u  /* neighbour lists (Fig. 7 line 6) */
+#define APBF_STAGE_NEIGHBORS 5u  /* neighbour lists (the neighbour search of Fig. 7) */
 #define APBF_STAGE_LEVELS 6u     /* a7: active-set partition */
 #define APBF_STAGE_LAMBDA 7u     /* a8 */
 #define APBF_STAGE_DELTAP 8u     /* a9 */
 #define APBF_STAGE_FINALIZE 9u   /* a10 */
-#define APBF_STAGE_PRESTAB 10u   /* pre-stabilisation (Fig. 7 lines 7-11), between LEVELS and LAMBDA */
+#define APBF_STAGE_PRESTAB 10u   /* pre-stabilisation (the pre-stabilisation loop of Fig. 7), between LEVELS and LAMBDA */
 #define APBF_STAGE_COUNT 11u
 
 /* Enable (1) or disable (0) per-stage CUDA-event timing of apbf_step. While

@@ -11,16 +11,16 @@
  *  - W is poly6, grad W is spiky's gradient; the tensile term is
  *    s_corr = -k (W(r)/W(dq))^n; XSPH weights neighbours by m/rho0.
  *  - Neighbour sets are found once per step on the predicted positions
- *    (Fig. 7 line 6) and kept for every iteration; pairs that separate past h
+ *    (the neighbour search of Fig. 7) and kept for every iteration; pairs that separate past h
  *    contribute nothing because both kernels vanish there.
  *  - Inactive neighbours enter Eq. 7 with their last lambda (Fig. 7 computes
  *    lambda only over P_iter while Eq. 7 sums over all neighbours).
  *  - A particle of level L takes part in iterations 1..L (Eq. 9-10).
- *  - Contacts (Fig. 7 line 18): after every position update, a predicted
+ *  - Contacts (the collision response of Fig. 7): after every position update, a predicted
  *    position strictly inside an obstacle moves to the nearest point of its
  *    surface (obstacles in order), then into the box; the prediction itself is
  *    only clamped to the box.
- *  - Pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11) of the set of Eq. 11 for
+ *  - Pre-stabilisation (Sec. 4.3, the pre-stabilisation loop of Fig. 7) of the set of Eq. 11 for
  *    l = S, i.e. the particles of level < S: stabil_iters times, the position
  *    at the start of the step is moved out of the obstacles and into the box,
  *    and the predicted position is moved by the same amount, so v = (x* - x)/dt
@@ -396,7 +396,7 @@ int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *leve
     return 0;
 }
 
-/* Fig. 7 lines 1-4: v' = v + dt g, x* = x + dt v', then x* clamped to the box. */
+/* The prediction step of Fig. 7: v' = v + dt g, x* = x + dt v', then x* clamped to the box. */
 int orc_predict(const orc_params *p, int32_t n, const float *x, const float *v, float *xpred)
 {
     if (!p || n < 0 || (n > 0 && (!x || !v || !xpred)))
@@ -866,7 +866,7 @@ static int validate(const orc_params *p, int32_t n)
     return 0;
 }
 
-/* One step of Fig. 7 (lines 1-27). */
+/* One step of Fig. 7. */
 int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, orc_record *rec)
 {
     if (validate(p, n) != 0 || (n > 0 && (!x || !v || !id)))
@@ -902,9 +902,9 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
     rc = orc_lod_levels(p, n, x, level0, range);
     if (rc)
         goto done;
-    /* Fig. 7 lines 1-4 (FP32). */
+    /* The prediction step of Fig. 7 (FP32). */
     orc_predict(p, n, x, v, xpred);
-    /* Fig. 7 lines 5-6: counting sort by cell, ties by particle id (the
+    /* The neighbour search of Fig. 7: counting sort by cell, ties by particle id (the
        counting sort is stable and is fed the particles in id order), then
        neighbour sets. */
     orc_cell_keys(p, n, xpred, keys);
@@ -989,7 +989,7 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
         xs[k] = (double)xs32[k];
         x0d[k] = (double)x0s[k];
     }
-    /* Fig. 7 lines 7-11: pre-stabilisation of the particles of level < S. */
+    /* The pre-stabilisation loop of Fig. 7: pre-stabilisation of the particles of level < S. */
     for (int32_t s = 0; s < n; ++s) {
         if (!(lvl[s] < p->stabil_s))
             continue;
@@ -1004,7 +1004,7 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
             }
         }
     }
-    /* Fig. 7 lines 12-23: N_max Jacobi iterations over the active sets P_l. */
+    /* The solver loop of Fig. 7: N_max Jacobi iterations over the active sets P_l. */
     for (int32_t l = 1; l <= p->n_max; ++l) {
         for (int32_t s = 0; s < n; ++s) {
             int active = lvl[s] >= l;
@@ -1037,7 +1037,7 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
             memcpy(rec->xs + (size_t)(l - 1) * 3 * n, xs, sizeof(double) * 3 * (size_t)n);
     }
 
-    /* Fig. 7 lines 24-27: v = (x* - x) / dt, XSPH smoothing, x = x*. */
+    /* The last step of Fig. 7: v = (x* - x) / dt, XSPH smoothing, x = x*. */
     for (int32_t s = 0; s < n; ++s)
         for (int a = 0; a < 3; ++a)
             vel[3 * s + a] = (xs[3 * s + a] - x0d[3 * s + a]) / (double)p->dt;

@@ -75,7 +75,7 @@ typedef struct orc_params {
     int32_t lambda_mode;          /* ORC_LAMBDA_* */
     int32_t lod_rounding;         /* 0: equal-width bins, 1: rounded interpolation */
     orc_view view;                /* DTVS only */
-    /* Pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11): particles of level < stabil_s
+    /* Pre-stabilisation (Sec. 4.3, the pre-stabilisation loop of Fig. 7): particles of level < stabil_s
        (the set of Eq. 11 for l = S) are moved out of the obstacles and into the box
        stabil_iters times before the solver, current and predicted positions alike. */
     int32_t stabil_iters, stabil_s;
@@ -147,7 +147,7 @@ int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *leve
    returns 1 and writes q when x is inside, 0 (q = x) otherwise. */
 int orc_obstacle_project(const orc_obstacle *o, const double x[3], double q[3]);
 
-/* Fig. 7 lines 1-4 plus the box clamp, FP32. */
+/* The prediction step of Fig. 7 plus the box clamp, FP32. */
 int orc_predict(const orc_params *p, int32_t n, const float *x, const float *v, float *xpred);
 
 /* Cell index of each position (FP32). */

@@ -36,7 +36,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float3 predict_position(float4 x, float4 v, const StepConst &sc, const DynParams *dyn)
 {
-    // Fig. 7 lines 1-4 in FP32, rounded after every operation (no FMA):
+    // The prediction step of Fig. 7 in FP32, rounded after every operation (no FMA):
     // v' = v + dt g, x* = x + dt v', then the box clamp.
     float vx = __fadd_rn(v.x, __fmul_rn(sc.dt, sc.g[0]));
     float vy = __fadd_rn(v.y, __fmul_rn(sc.dt, sc.g[1]));
@@ -1209,7 +1209,7 @@ __global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc,
 }
 
 // ------------------------------------------- contacts with obstacles
-// Fig. 7 line 18 with the obstacles of Sec. 6 (analytic solids): a position
+// The collision response of Fig. 7 with the obstacles of Sec. 6 (analytic solids): a position
 // strictly inside an obstacle moves to the nearest point of its surface.
 // Positions are relative to the particle's cell origin og; each obstacle is
 // taken relative to og as well, so the arithmetic acts at the scale of the
@@ -1291,7 +1291,7 @@ __device__ __forceinline__ void contact_obstacles(const DynParams *d, float3 og,
         project_obstacle(d->obst[k], og, px, py, pz);
 }
 
-// Fig. 7 lines 7-11 (Sec. 4.3): the particles of level < S are moved out of
+// The pre-stabilisation loop of Fig. 7 (Sec. 4.3): the particles of level < S are moved out of
 // the obstacles and into the box stabil_iters times, the start-of-step
 // position (xt) and the prediction (recA) by the same amount, so the
 // velocity (x* - x)/dt gains nothing from it.

@@ -1,5 +1,5 @@
-"""Parity of the CUDA obstacle contacts (Fig. 7 line 18, Sec. 6) and
-pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11) with the oracle, with the
+"""Parity of the CUDA obstacle contacts (the collision response of Fig. 7, Sec. 6) and
+pre-stabilisation (Sec. 4.3, the pre-stabilisation loop of Fig. 7) with the oracle, with the
 one-step tolerances of test_gpu_parity (positions 1e-5 h, velocities
 1e-5 h / dt). The obstacles overlap the initial fluid block, so contacts
 act from the first iteration and pre-stabilisation has work to do."""

@@ -1,5 +1,5 @@
-"""Pins of the oracle's obstacle contacts (Sec. 6, Fig. 7 line 18) and
-pre-stabilisation (Sec. 4.3, Fig. 7 lines 7-11), checked against geometry
+"""Pins of the oracle's obstacle contacts (Sec. 6, the collision response of Fig. 7) and
+pre-stabilisation (Sec. 4.3, the pre-stabilisation loop of Fig. 7), checked against geometry
 and closed forms computed here:
 
   orc_obstacle_project  the projection of an interior point is the nearest point of a dense
