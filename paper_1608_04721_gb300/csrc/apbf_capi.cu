@@ -266,7 +266,7 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.tmp = (uint32_t *)P(4 * n);
     b.recA = (float4 *)P(16 * (n + 1));
     b.recB = (float4 *)P(16 * (n + 1));
-    b.xs32 = (float4 *)P(16 * n);
+    b.xs32 = (float4 *)P(16 * (n + kEntryBlock));  // slack: the neighbour search reads whole batches
     b.xt = (float4 *)P(16 * (n + 1));
     b.id_s = (uint32_t *)P(4 * n);
     b.cell_s = (uint32_t *)P(4 * n);

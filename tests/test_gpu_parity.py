@@ -151,6 +151,20 @@ def test_stagewise_parity_small(name):
     check_final(cfg, scene, p, st)
 
 
+def test_list_capacity_not_a_multiple_of_four():
+    """max_neighbors set to the step's longest list (or one more), whichever is
+    not a multiple of 4: the longest lists end in a padded block inside the
+    allocation, and every stage and the step still match the oracle."""
+    cfg, kw = SMALL["apbf_5200"]()
+    scene, p, x, v = make(cfg, **kw)
+    st = oracle.step(p, x, v, record=True, rec_iters=1)
+    longest = int(np.diff(st.nbr_off).max())
+    cap = longest if longest % 4 else longest + 1
+    scene, p, x, v = make(cfg, max_neighbors=cap, **kw)
+    st = check_stages(cfg, scene, p, x, v)
+    check_final(cfg, scene, p, st)
+
+
 def test_one_step_parity_131k():
     cfg = scenes.config_dam_break_131k()
     scene, p, x, v = make(cfg)
