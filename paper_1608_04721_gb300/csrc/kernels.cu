@@ -172,15 +172,10 @@ __device__ __forceinline__ void wait_for_predecessor()
 // Neighbour batch depth and the minimum resident blocks per SM the solver
 // kernels are compiled for (register budget); tuned on the GB300.
 #ifndef APBF_SOLVER_MIN_BLOCKS
-#define APBF_SOLVER_MIN_BLOCKS 6
+#define APBF_SOLVER_MIN_BLOCKS 5
 #endif
 constexpr int kUnroll = (int)kEntryBlock;
-#ifndef APBF_PREFETCH
-#define APBF_PREFETCH 1
-#endif
-#ifndef APBF_NBRLOAD
-#define APBF_NBRLOAD 1
-#endif
+
 
 // Visit the neighbour entries of one particle in batches of kUnroll: the
 // batch's entries are loaded first, then its records, then f runs on each,
@@ -193,7 +188,6 @@ __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ n
 {
     static_assert(UNR == (int)kEntryBlock, "one entry block per batch");
     const uint4 *e_ptr = reinterpret_cast<const uint4 *>(nbr) + t;
-#if APBF_PREFETCH
     // the next block's entries are requested before this block's records, so
     // the chain of dependent loads per batch is one load deep, not two
     uint4 nxt = nn ? __ldcs(e_ptr) : make_uint4(0u, 0u, 0u, 0u);
@@ -201,10 +195,6 @@ __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ n
         const uint4 eb = nxt;
         if (k + UNR < nn)
             nxt = __ldcs(e_ptr + (size_t)(k / UNR + 1) * n);
-#else
-    for (uint32_t k = 0; k < nn; k += UNR) {
-        const uint4 eb = __ldcs(e_ptr + (size_t)(k / UNR) * n);
-#endif
         const uint32_t e[UNR] = {eb.x, eb.y, eb.z, eb.w};
         float4 r[UNR];
 #pragma unroll
@@ -1085,11 +1075,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                         float4 xj[kUnroll];
 #pragma unroll
                         for (int u = 0; u < kUnroll; ++u)
-#if APBF_NBRLOAD
                             xj[u] = b.xs32[jj + u];  // past je: the next cells (or the slack); masked below
-#else
-                            xj[u] = (jj + u < je) ? b.xs32[jj + u] : make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
-#endif
                         uint32_t nib = 0;
 #pragma unroll
                         for (int u = 0; u < kUnroll; ++u) {
@@ -1103,10 +1089,8 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                         }
                         hits |= nib << (jj - j);
                     }
-#if APBF_NBRLOAD
                     if (je - j < 32u)
                         hits &= (1u << (je - j)) - 1u;
-#endif
                     if (own_row && p - j < 32u)
                         hits &= ~(1u << (p - j));
                     while (hits) {
