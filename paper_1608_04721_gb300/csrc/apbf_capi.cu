@@ -890,6 +890,13 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     for (int a = 0; a < 3; ++a)
         s->view.up[a] = up[a];
     s->view.radius = radius;
+    {
+        const double ax = (double)tan_half_fov * width / height, ay = tan_half_fov;
+        const double g = std::atan(std::sqrt(ax * ax + ay * ay)) + 0.01;
+        // the cosine form of the cull holds while gamma + beta <= pi (beta <= pi/2)
+        s->view.cull_cos = g < 1.5 ? (float)std::cos(g) : -1.0e30f;
+        s->view.cull_sin = g < 1.5 ? (float)std::sin(g) : 0.0f;
+    }
     s->view_set = true;
     drop_graph(s);
     return APBF_OK;

@@ -123,6 +123,9 @@ struct ViewConst {
     float tan_half = 0.0f;  // tan of half the vertical field of view
     float up[3] = {0.0f, 0.0f, 1.0f};
     float radius = 0.0f;    // sphere radius of the rendered particles
+    // frustum cull: cos and sin of gamma + 0.01, gamma the angle between the
+    // view direction and an image corner's ray (cos = -1e30 turns it off)
+    float cull_cos = -1.0e30f, cull_sin = 0.0f;
     uint32_t *depth = nullptr;  // W*H float bits, row 0 at the top
     float4 *ray = nullptr;      // W*H unit pixel rays of the current camera
     // binning of the rendered spheres into kTilePx x kTilePx pixel tiles

@@ -479,8 +479,9 @@ __global__ void __launch_bounds__(kBlock) view_rays_kernel(ViewConst v, const Dy
     v.depth[p] = 0x7f7f7f7fu;
 }
 
-// Screen box of a particle's sphere: the pixels around the projections of the
-// 8 corners of its bounding cube, widened by one pixel (conservative: every
+// Screen box of a particle's sphere: the pixels around its projection (the
+// tangent-plane bounds, or near the camera plane the projections of the 8
+// corners of its bounding cube), widened by one pixel (conservative: every
 // pixel whose ray enters the sphere is inside). Returns 0 when the sphere is
 // not rendered (the eye is inside it) or lies entirely outside the image, 1
 // for a box, 2 when a corner is not in front of the camera (then the box is
@@ -502,42 +503,58 @@ __device__ __forceinline__ int splat_box(const Basis &B, const ViewConst &v, con
     o.cc = __fsub_rn(len2, r2);
     if (!(o.cc > 0.0f))
         return 0;
-    {
-        // frustum cull: every pixel ray lies within the angle gamma of f (the
-        // image corner), and a ray entering the sphere lies within its angular
-        // radius beta of rel, so a sphere whose direction is further than
-        // gamma + beta (+ 0.01 rad for rounding) from f is entered by no pixel
-        // ray. This also drops every sphere behind the camera.
-        const float len = sqrtf(len2);
-        // no ray enters the sphere closer than len - r; 4e-6 len (32 units in
-        // the last place) covers the rounding of the FP32 entry distance there
-        o.near = (len - rad) - 4.0e-6f * len;
-        const float zc = dot3_rn(o.rel0, o.rel1, o.rel2, B.f[0], B.f[1], B.f[2]);
-        const float theta = acosf(fminf(fmaxf(zc / len, -1.0f), 1.0f));
-        const float beta = asinf(fminf(rad / len, 1.0f));
-        const float gamma = atanf(sqrtf(B.ax * B.ax + B.ay * B.ay));
-        if (theta > beta + gamma + 0.01f)
-            return 0;
-    }
+    // no ray enters the sphere closer than len - r; 4e-6 len (32 units in the
+    // last place) covers the rounding of the FP32 entry distance there
+    const float len = sqrtf(len2);
+    o.near = (len - rad) - 4.0e-6f * len;
+    const float zc = dot3_rn(o.rel0, o.rel1, o.rel2, B.f[0], B.f[1], B.f[2]);
+    // frustum cull: every pixel ray lies within the angle gamma of f (the image
+    // corner), and a ray entering the sphere lies within its angular radius
+    // beta of rel, so a sphere whose direction is further than gamma' = gamma +
+    // 0.01 rad (rounding) + beta from f is entered by no pixel ray. With
+    // cos(beta) = sqrt(cc) / len and sin(beta) = r / len that is
+    // zc < sqrt(cc) cos(gamma') - r sin(gamma'). This also drops every sphere
+    // behind the camera.
+    if (zc < sqrtf(o.cc) * v.cull_cos - rad * v.cull_sin)
+        return 0;
     const int W = (int)v.W, H = (int)v.H;
     o.x0 = 0;
     o.x1 = W - 1;
     o.y0 = 0;
     o.y1 = H - 1;
     float fx_lo = 3.0e38f, fx_hi = -3.0e38f, fy_lo = 3.0e38f, fy_hi = -3.0e38f;
+    if (zc > 2.0f * rad) {
+        // the sphere's exact extent in x/z and y/z: the planes through the
+        // eye's vertical (horizontal) axis tangent to the sphere have slopes
+        // (c zc +- r sqrt(c^2 + zc^2 - r^2)) / (zc^2 - r^2), c the centre's
+        // right (up) coordinate; FP32 rounding moves them by far less than
+        // the one-pixel widening below (zc > 2r keeps zc^2 - r^2 well apart)
+        const float xc = dot3_rn(o.rel0, o.rel1, o.rel2, B.r[0], B.r[1], B.r[2]);
+        const float yc = dot3_rn(o.rel0, o.rel1, o.rel2, B.u[0], B.u[1], B.u[2]);
+        const float D = zc * zc - r2, iD = 1.0f / D;
+        const float sxq = rad * sqrtf(xc * xc + D), syq = rad * sqrtf(yc * yc + D);
+        const float hx = 0.5f * (float)W / B.ax, hy = 0.5f * (float)H / B.ay;
+        fx_lo = ((xc * zc - sxq) * iD) * hx + 0.5f * (float)W;
+        fx_hi = ((xc * zc + sxq) * iD) * hx + 0.5f * (float)W;
+        fy_lo = 0.5f * (float)H - ((yc * zc + syq) * iD) * hy;
+        fy_hi = 0.5f * (float)H - ((yc * zc - syq) * iD) * hy;
+    } else {
+        // near the camera plane: the projections of the 8 corners of the
+        // sphere's bounding cube
 #pragma unroll 1
-    for (int c = 0; c < 8; ++c) {
-        const float q0 = __fadd_rn(o.rel0, (c & 1) ? rad : -rad);
-        const float q1 = __fadd_rn(o.rel1, (c & 2) ? rad : -rad);
-        const float q2 = __fadd_rn(o.rel2, (c & 4) ? rad : -rad);
-        const float zc = dot3_rn(q0, q1, q2, B.f[0], B.f[1], B.f[2]);
-        if (!(zc > 0.0f))
-            return 2;
-        const float2 xy = image_xy(B, v, q0, q1, q2, zc);
-        fx_lo = fminf(fx_lo, xy.x);
-        fx_hi = fmaxf(fx_hi, xy.x);
-        fy_lo = fminf(fy_lo, xy.y);
-        fy_hi = fmaxf(fy_hi, xy.y);
+        for (int c = 0; c < 8; ++c) {
+            const float q0 = __fadd_rn(o.rel0, (c & 1) ? rad : -rad);
+            const float q1 = __fadd_rn(o.rel1, (c & 2) ? rad : -rad);
+            const float q2 = __fadd_rn(o.rel2, (c & 4) ? rad : -rad);
+            const float zq = dot3_rn(q0, q1, q2, B.f[0], B.f[1], B.f[2]);
+            if (!(zq > 0.0f))
+                return 2;
+            const float2 xy = image_xy(B, v, q0, q1, q2, zq);
+            fx_lo = fminf(fx_lo, xy.x);
+            fx_hi = fmaxf(fx_hi, xy.x);
+            fy_lo = fminf(fy_lo, xy.y);
+            fy_hi = fmaxf(fy_hi, xy.y);
+        }
     }
     if (fx_hi < -1.0f || fy_hi < -1.0f || fx_lo > (float)W + 1.0f || fy_lo > (float)H + 1.0f)
         return 0;
@@ -1562,8 +1579,11 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
     const uint32_t nn = b.nbr_cnt[t];
     b.prev_cnt[p] = (uint8_t)nn;  // by state slot, for the next step's depth image
     const uint4 *e_ptr = reinterpret_cast<const uint4 *>(b.nbr) + t;
+    uint4 nxt = nn ? __ldcs(e_ptr) : make_uint4(0u, 0u, 0u, 0u);  // next block requested early
     for (uint32_t k = 0; k < nn; k += kUnroll) {
-        const uint4 eb = __ldcs(e_ptr + (size_t)(k / kUnroll) * n);
+        const uint4 eb = nxt;
+        if (k + kUnroll < nn)
+            nxt = __ldcs(e_ptr + (size_t)(k / kUnroll + 1) * n);
         const uint32_t e[kUnroll] = {eb.x, eb.y, eb.z, eb.w};
         float4 aj[kUnroll], xj[kUnroll];
 #pragma unroll
