@@ -140,6 +140,7 @@ struct ViewConst {
     uint8_t *accepted = nullptr;     // n: the sphere is in the tile lists
     uint2 *box = nullptr;            // n: screen box of an accepted sphere (x0 | x1 << 16, y0 | y1 << 16)
     float *near = nullptr;           // n: lower bound of the sphere's entry distances
+    uint32_t *open_mask = nullptr;   // n: which of an accepted sphere's <= 32 box tiles it is listed in
     uint32_t *tile_max = nullptr;    // tiles: farthest depth bits of the phase-0 image
     uint32_t *big = nullptr;         // n: spheres rasterised one block each
     uint32_t *big_cnt = nullptr;

@@ -609,6 +609,7 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
     const bool member = valid && ((b.prev_cnt[i] < kFrontNeighbors) == (phase == 0));
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
     float near = 0.0f;
+    uint32_t mask = 0;  // pass 0: the open tiles of a box of at most 32 tiles
     if (pass == 1) {
         const bool mine = member && v.accepted[i];
         if (mine) {
@@ -640,6 +641,27 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
         }
         if (ntb == 0 || ntb > 32)
             return;
+        // the tiles recorded open in pass 0: all four atomics of a group are
+        // issued before the list writes that wait for them
+        uint32_t mk = v.open_mask[i];
+        while (mk) {
+            uint32_t t4[4], s4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                t4[q] = 0xffffffffu;
+                if (mk) {
+                    const int bit = __ffs(mk) - 1;
+                    mk &= mk - 1u;
+                    t4[q] = (uint32_t)(ty0 + bit / tw) * v.tiles_x + (uint32_t)(tx0 + bit % tw);
+                    s4[q] = atomicAdd(&v.tile_fill[t4[q]], 1u);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (t4[q] != 0xffffffffu)
+                    v.tile_list[v.tile_start[t4[q]] + s4[q]] = i;
+        }
+        return;
     } else {
         int kind = 0;
         uint32_t nt = 0;
@@ -659,9 +681,14 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
                 if ((uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1)) > kMaxSplatTiles) {
                     kind = 2;
                 } else {
+                    int bit = 0;
                     for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx)
-                            nt += tile_open(v, phase, (uint32_t)ty * v.tiles_x + (uint32_t)tx, near) ? 1u : 0u;
+                        for (int tx = tx0; tx <= tx1; ++tx, ++bit)
+                            if (tile_open(v, phase, (uint32_t)ty * v.tiles_x + (uint32_t)tx, near)) {
+                                ++nt;
+                                if (bit < 32)
+                                    mask |= 1u << bit;
+                            }
                     if (nt == 0)
                         kind = 0;  // hidden in every tile it covers
                 }
@@ -690,17 +717,23 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
         v.accepted[i] = 1;
         v.box[i] = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
         v.near[i] = near;
+        v.open_mask[i] = mask;
     }
+    // pass 0: count the sphere in each tile it is listed in
     const int tx0 = x0 / kTilePx, tx1 = x1 / kTilePx, ty0 = y0 / kTilePx, ty1 = y1 / kTilePx;
+    const int tw = tx1 - tx0 + 1;
+    if (tw * (ty1 - ty0 + 1) <= 32) {
+        for (uint32_t mk = mask; mk; mk &= mk - 1u) {
+            const int bit = __ffs(mk) - 1;
+            atomicAdd(&v.tile_cnt[(uint32_t)(ty0 + bit / tw) * v.tiles_x + (uint32_t)(tx0 + bit % tw)], 1u);
+        }
+        return;
+    }
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
             const uint32_t t = (uint32_t)ty * v.tiles_x + (uint32_t)tx;
-            if (!tile_open(v, phase, t, near))
-                continue;
-            if (pass == 0)
+            if (tile_open(v, phase, t, near))
                 atomicAdd(&v.tile_cnt[t], 1u);
-            else
-                v.tile_list[v.tile_start[t] + atomicAdd(&v.tile_fill[t], 1u)] = i;
         }
 }
 
@@ -796,8 +829,9 @@ __global__ void __launch_bounds__(kBlock) splat_big_kernel(StepConst sc, Buffers
 // atomic minimum (several chunks of a crowded tile may finish in any order).
 __global__ void __launch_bounds__(kTilePx *kTilePx) splat_tile_kernel(StepConst sc, Buffers b, ViewConst v)
 {
+    static_assert(kTilePx == 8, "one bit per pixel of a tile in a 64-bit mask");
     __shared__ float4 sp[kTilePx * kTilePx];
-    __shared__ uint2 sbox[kTilePx * kTilePx];
+    __shared__ unsigned long long smask[kTilePx * kTilePx];  // pixels of the tile inside each sphere's box
     const uint32_t T = v.tiles_x * v.tiles_y;
     const uint32_t nwork = v.chunk_start[T];
     const float r2 = __fmul_rn(v.radius, v.radius);
@@ -815,8 +849,9 @@ __global__ void __launch_bounds__(kTilePx *kTilePx) splat_tile_kernel(StepConst 
         const uint32_t tile = lo;
         const uint32_t beg = v.tile_start[tile] + (w - v.chunk_start[tile]) * kSplatChunk;
         const uint32_t end = min(beg + kSplatChunk, v.tile_start[tile + 1]);
-        const uint32_t px = (tile % v.tiles_x) * kTilePx + (threadIdx.x % kTilePx);
-        const uint32_t py = (tile / v.tiles_x) * kTilePx + (threadIdx.x / kTilePx);
+        const uint32_t px0 = (tile % v.tiles_x) * kTilePx, py0 = (tile / v.tiles_x) * kTilePx;
+        const uint32_t px = px0 + (threadIdx.x % kTilePx);
+        const uint32_t py = py0 + (threadIdx.x / kTilePx);
         const bool inside = px < v.W && py < v.H;
         const uint32_t p = py * v.W + px;
         const float4 ray = inside ? v.ray[p] : make_float4(0.0f, 0.0f, 1.0f, 0.0f);
@@ -827,14 +862,26 @@ __global__ void __launch_bounds__(kTilePx *kTilePx) splat_tile_kernel(StepConst 
                 const uint32_t i = v.tile_list[k];
                 const float4 x = b.state_x[i];
                 sp[threadIdx.x] = make_float4(__fsub_rn(x.x, e0), __fsub_rn(x.y, e1), __fsub_rn(x.z, e2), 0.0f);
-                sbox[threadIdx.x] = v.box[i];
+                // the box clipped to the tile as a pixel mask: bit 8 row + column
+                const uint2 bx = v.box[i];
+                const int c0 = max((int)(bx.x & 0xffffu) - (int)px0, 0), c1 = min((int)(bx.x >> 16) - (int)px0, 7);
+                const int r0 = max((int)(bx.y & 0xffffu) - (int)py0, 0), r1 = min((int)(bx.y >> 16) - (int)py0, 7);
+                unsigned long long mk = 0ull;
+                if (c0 <= c1 && r0 <= r1) {
+                    const unsigned long long row = (0xffull >> (7 - (c1 - c0))) << c0;
+                    const unsigned long long rows = (r1 == 7 ? ~0ull : ((1ull << (8 * (r1 + 1))) - 1ull)) &
+                                                    ~((1ull << (8 * r0)) - 1ull);
+                    mk = (row * 0x0101010101010101ull) & rows;
+                }
+                smask[threadIdx.x] = mk;
             }
             __syncthreads();
             const uint32_t m = min((uint32_t)(kTilePx * kTilePx), end - c);
             if (inside)
                 for (uint32_t j = 0; j < m; ++j) {
-                    const uint2 bx = sbox[j];
-                    if (px < (bx.x & 0xffffu) || px > (bx.x >> 16) || py < (bx.y & 0xffffu) || py > (bx.y >> 16))
+                    // this warp's 32 pixels (half the tile): skip the sphere together
+                    const uint32_t wm = (uint32_t)(smask[j] >> (threadIdx.x & 32u));
+                    if (wm == 0u || !((wm >> (threadIdx.x & 31u)) & 1u))
                         continue;
                     const float4 q = sp[j];
                     best = min(best, entry_bits(ray, q.x, q.y, q.z, r2));
