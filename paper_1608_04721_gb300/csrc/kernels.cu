@@ -159,11 +159,11 @@ __device__ __forceinline__ float2 fma2_rn(float2 a, float2 b, float2 c)
     return r;
 }
 
-// Programmatic dependent launch: a solver kernel is launched while its
+// Programmatic dependent launch: a kernel of the step is launched while its
 // predecessor in the stream drains and waits here, before its first global
 // memory access, until the predecessor has completed and its writes are
-// visible; the launch latency between the many short iterations overlaps
-// the predecessor's tail (measured: 4 us of a 1.84 ms step).
+// visible; the launch latency between the step's many short kernels overlaps
+// the predecessor's tail.
 __device__ __forceinline__ void wait_for_predecessor()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -358,6 +358,7 @@ __device__ __forceinline__ float3 origin_in(int3 c, const Geo &g, float q)
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers b)
 {
+    wait_for_predecessor();
     __shared__ float smin[kBlock / 32], smax[kBlock / 32];
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < sc.n;
@@ -944,6 +945,7 @@ __global__ void __launch_bounds__(kBlock) dtvs_distance_kernel(StepConst sc, Buf
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buffers b, int diag)
 {
+    wait_for_predecessor();
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = i < sc.n;
     uint32_t key = 0xffffffffu;
@@ -993,6 +995,7 @@ __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buff
 __global__ void __launch_bounds__(1024) scan_reduce_kernel(const uint32_t *__restrict__ cnt, uint32_t ncell,
                                                            uint32_t *__restrict__ tile_sums)
 {
+    wait_for_predecessor();
     __shared__ uint32_t sh[32];
     uint32_t base = blockIdx.x * kScanTile + threadIdx.x * 4;
     uint32_t s = 0;
@@ -1012,6 +1015,7 @@ __global__ void __launch_bounds__(1024) scan_apply_kernel(uint32_t *__restrict__
                                                           const uint32_t *__restrict__ tile_sums,
                                                           uint32_t *__restrict__ start, uint32_t n)
 {
+    wait_for_predecessor();
     __shared__ uint32_t sh[32];
     uint32_t pre = 0;
     for (uint32_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x)
@@ -1049,6 +1053,7 @@ __global__ void __launch_bounds__(1024) scan_apply_kernel(uint32_t *__restrict__
 
 __global__ void __launch_bounds__(kBlock) scatter_kernel(StepConst sc, Buffers b)
 {
+    wait_for_predecessor();
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < sc.n)
         b.tmp[b.start[b.key[i]] + b.slot[i]] = b.state_id[i];
@@ -1059,6 +1064,7 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(StepConst sc, Buffers b
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b, int diag)
 {
+    wait_for_predecessor();
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc.n)
         return;
@@ -1096,6 +1102,7 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b, int part)
 {
+    wait_for_predecessor();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {  // the padding entries' record: beyond reach of every particle (r^2 = inf)
         const float4 far = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
@@ -1211,6 +1218,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
 
 __global__ void __launch_bounds__(kLevelTile) level_hist_kernel(StepConst sc, Buffers b)
 {
+    wait_for_predecessor();
     extern __shared__ uint32_t sh[];  // K counts
     const uint32_t K = sc.K;
     for (uint32_t k = threadIdx.x; k < K; k += blockDim.x)
@@ -1226,6 +1234,7 @@ __global__ void __launch_bounds__(kLevelTile) level_hist_kernel(StepConst sc, Bu
 
 __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers b)
 {
+    wait_for_predecessor();
     __shared__ uint32_t sh[32];
     const uint32_t E = sc.K * sc.level_tiles;
     const uint32_t chunk = (E + blockDim.x - 1) / blockDim.x;
@@ -1257,6 +1266,7 @@ __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers 
 
 __global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc, Buffers b)
 {
+    wait_for_predecessor();
     extern __shared__ uint32_t wc[];  // 32 warps x K
     const uint32_t K = sc.K;
     for (uint32_t k = threadIdx.x; k < 32 * K; k += blockDim.x)
@@ -1808,71 +1818,16 @@ int occupancy(const void *fn, int block = kBlock)
 
 // ------------------------------------------------------------- launchers
 
-cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
-{
-    if (sc.n)
-        (sc.scenes > 1 ? lod_range_kernel<true> : lod_range_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
-{
-    if (sc.n)
-        (sc.scenes > 1 ? predict_hash_kernel<true> : predict_hash_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0,
-                                                                                   s>>>(sc, b, diag ? 1 : 0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s)
-{
-    unsigned tiles = blocks_for(sc.ncell, kScanTile);
-    scan_reduce_kernel<<<tiles, 1024, 0, s>>>(b.cnt, sc.ncell, b.tile_sums);
-    scan_apply_kernel<<<tiles, 1024, 0, s>>>(b.cnt, sc.ncell, b.tile_sums, b.start, sc.n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s)
-{
-    if (sc.n)
-        scatter_kernel<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(sc, b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
-{
-    if (sc.n)
-        (sc.scenes > 1 ? reorder_kernel<true> : reorder_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
-            sc, b, diag ? 1 : 0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, bool part)
-{
-    if (sc.n)
-        (sc.scenes > 1 ? neighbors_kernel<true> : neighbors_kernel<false>)<<<blocks_for(sc.n, kBlock), kBlock, 0, s>>>(
-            sc, b, part ? 1 : 0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
-{
-    if (!sc.n)
-        return cudaGetLastError();
-    level_hist_kernel<<<sc.level_tiles, kLevelTile, sc.K * sizeof(uint32_t), s>>>(sc, b);
-    level_scan_kernel<<<1, 1024, 0, s>>>(sc, b);
-    level_scatter_kernel<<<sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s>>>(sc, b);
-    return cudaGetLastError();
-}
-
 // Launches k with the programmatic-dependent-launch attribute (see
 // wait_for_predecessor); in a captured graph this becomes a programmatic edge.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_after(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args)
+cudaError_t launch_after_smem(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              Args... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1880,6 +1835,72 @@ cudaError_t launch_after(void (*k)(KArgs...), unsigned grid, unsigned block, cud
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch_after(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args)
+{
+    return launch_after_smem(k, grid, block, 0, s, args...);
+}
+
+cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        return launch_after(sc.scenes > 1 ? lod_range_kernel<true> : lod_range_kernel<false>, blocks_for(sc.n, kBlock),
+                            kBlock, s, sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
+{
+    if (sc.n)
+        return launch_after(sc.scenes > 1 ? predict_hash_kernel<true> : predict_hash_kernel<false>,
+                            blocks_for(sc.n, kBlock), kBlock, s, sc, b, diag ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    unsigned tiles = blocks_for(sc.ncell, kScanTile);
+    cudaError_t e = launch_after(scan_reduce_kernel, tiles, 1024, s, b.cnt, sc.ncell, b.tile_sums);
+    if (e != cudaSuccess)
+        return e;
+    return launch_after(scan_apply_kernel, tiles, 1024, s, b.cnt, sc.ncell, b.tile_sums, b.start, sc.n);
+}
+
+cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (sc.n)
+        return launch_after(scatter_kernel, blocks_for(sc.n, kBlock), kBlock, s, sc, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
+{
+    if (sc.n)
+        return launch_after(sc.scenes > 1 ? reorder_kernel<true> : reorder_kernel<false>, blocks_for(sc.n, kBlock),
+                            kBlock, s, sc, b, diag ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, bool part)
+{
+    if (sc.n)
+        return launch_after(sc.scenes > 1 ? neighbors_kernel<true> : neighbors_kernel<false>, blocks_for(sc.n, kBlock),
+                            kBlock, s, sc, b, part ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
+{
+    if (!sc.n)
+        return cudaGetLastError();
+    cudaError_t e = launch_after_smem(level_hist_kernel, sc.level_tiles, kLevelTile, sc.K * sizeof(uint32_t), s, sc, b);
+    if (e == cudaSuccess)
+        e = launch_after(level_scan_kernel, 1, 1024, s, sc, b);
+    if (e == cudaSuccess)
+        e = launch_after_smem(level_scatter_kernel, sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s, sc,
+                              b);
+    return e;
 }
 
 template <int BS>

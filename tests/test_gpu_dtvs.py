@@ -81,6 +81,10 @@ CASES = {
     # a single pixel
     "one_pixel_1000": lambda: (_dam((10, 10, 10), 1, 4), (-1.0, 0.25, 0.25), (1.0, 0.0, 0.0),
                                (1, 1, 0.4, (0, 0, 1), 0.025)),
+    # a very wide view (~172 degrees vertically): the corner angle is past the
+    # range in which the frustum cull is used, so every sphere is binned
+    "wide_view_1000": lambda: (_dam((10, 10, 10), 1, 5), (-0.06, 0.25, 0.25), (1.0, 0.1, 0.05),
+                               (96, 64, 15.0, (0, 0, 1), 0.03)),
 }
 
 
