@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -278,14 +279,24 @@ def stage_profile(apbf, scene, cfg, first_step, steps, drive_fn=None):
     return ms_tot, ln_tot, pairs, nbr_pairs, iters, s
 
 
+def kernel_source_digest() -> str:
+    """First 16 hex digits of the sha256 of kernels.cu without its comments
+    and blank lines: a change to the code invalidates a traffic capture, a
+    change to a comment does not."""
+    src = open(os.path.join(ROOT, "paper_1608_04721_gb300", "csrc", "kernels.cu"), encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def read_traffic(kernel: str, workload_name: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload_name}.txt")
     if not os.path.exists(path):
         return None
-    src = open(os.path.join(ROOT, "paper_1608_04721_gb300", "csrc", "kernels.cu"), "rb").read()
-    digest = hashlib.sha256(src).hexdigest()[:16]
+    digest = kernel_source_digest()
     for ln in open(path):
         parts = ln.split()
         if len(parts) >= 3 and parts[0] == kernel and not ln.startswith("#"):

@@ -22,9 +22,10 @@
 // Positions inside the solver are stored relative to the particle's cell
 // origin (m + c) * q, with q = h rounded to 8 significant bits so that every
 // origin and every origin difference (+-q per axis) is exact in FP32. The
-// difference of two positions is then (p_i - p_j) + dtab[code] with |p| ~ h,
-// which keeps FP32 rounding at the scale of h instead of the scale of the
-// domain (a 10 m basin has an FP32 spacing of ~1e-6 m).
+// difference of two positions is then (p_i - p_j) + (o_i - o_j), the origin
+// difference looked up by the entry's cell code, with |p| ~ h, which keeps
+// FP32 rounding at the scale of h instead of the scale of the domain (a 10 m
+// basin has an FP32 spacing of ~1e-6 m).
 #include "apbf_internal.h"
 
 namespace apbf {
