@@ -247,6 +247,14 @@ APBF_API apbf_status apbf_step(apbf_scene *scene, uint32_t nsteps);
  * of each particle's last lambda pass in the last step, 0 before the first). */
 APBF_API apbf_status apbf_read_state(apbf_scene *scene, float *pos, float *vel, uint8_t *n_iter, float *rho);
 
+/* Queue a copy of the positions (3n floats, particle-id order) to host memory
+ * without waiting: the copy runs on a stream of its own, so it overlaps the
+ * next apbf_step. pos should be pinned (page-locked) host memory; it is
+ * complete once apbf_sync returns, and must stay valid until then. A later
+ * readback waits for this copy before reusing the library's staging buffer.
+ * Device errors are reported by the next synchronising call. */
+APBF_API apbf_status apbf_read_positions_async(apbf_scene *scene, float *pos);
+
 /* Synchronise and report density-error statistics of the current positions
  * (Fig. 9): stats (host, 4 doubles) = {mean |rho/rho0-1|, max |rho/rho0-1|,
  * mean (rho/rho0-1), mean max(0, rho/rho0-1)}, with a fresh neighbour search.
@@ -256,7 +264,8 @@ APBF_API apbf_status apbf_density_stats(apbf_scene *scene, double stats[4]);
 /* Synchronise and return the counters of the last step (host struct). */
 APBF_API apbf_status apbf_get_step_info(apbf_scene *scene, apbf_step_info *info);
 
-/* Wait for the scene's queued work; returns the first error seen. */
+/* Wait for the scene's queued work, asynchronous readbacks included; returns
+ * the first error seen. */
 APBF_API apbf_status apbf_sync(apbf_scene *scene);
 
 /* Last error message of the scene (library-owned, valid until the next call

@@ -147,7 +147,7 @@ EXPORTS = [
     "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
     "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune", "apbf_server_bytes",
     "apbf_server_create", "apbf_server_submit", "apbf_server_tick", "apbf_server_query", "apbf_server_last_error",
-    "apbf_server_destroy", "apbf_set_view", "apbf_set_obstacles",
+    "apbf_server_destroy", "apbf_set_view", "apbf_set_obstacles", "apbf_read_positions_async",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -189,6 +189,7 @@ def lib():
         L.apbf_density_stats.argtypes = [V, P(C.c_double)]
         L.apbf_get_step_info.argtypes = [V, P(apbf_step_info)]
         L.apbf_sync.argtypes = [V]
+        L.apbf_read_positions_async.argtypes = [V, V]
         L.apbf_last_error.restype = C.c_char_p
         L.apbf_last_error.argtypes = [V]
         L.apbf_destroy_scene.restype = None
@@ -464,6 +465,15 @@ def apbf_read_state(scene: Scene, pos=True, vel=True, n_iter=False, rho=False):
                                None if it is None else it.ctypes.data_as(C.POINTER(C.c_uint8)), _fptr(r))
     _check(st, "apbf_read_state", scene)
     return out
+
+
+def apbf_read_positions_async(scene: Scene, pos_ptr: int):
+    """Queue a copy of the positions (n x 3 float32, particle-id order) to the
+    host memory at pos_ptr (a pinned buffer's address, e.g. a pinned torch
+    tensor's data_ptr()); it is complete after apbf_sync. The buffer must
+    stay alive until then."""
+    _check(lib().apbf_read_positions_async(scene.handle, C.c_void_p(int(pos_ptr))), "apbf_read_positions_async",
+           scene)
 
 
 def apbf_density_stats(scene: Scene) -> np.ndarray:

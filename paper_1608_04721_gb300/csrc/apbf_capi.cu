@@ -942,6 +942,8 @@ APBF_API apbf_status apbf_read_state(apbf_scene *s, float *pos, float *vel, uint
     const size_t n = s->sc.n;
     if (n == 0)
         return APBF_OK;
+    if (s->copy_pending)  // the staging buffer may still be on its way to the host
+        APBF_CUDA(s, cudaStreamWaitEvent(s->stream, s->copy_ev, 0));
     float *outs_f[3] = {pos, vel, nullptr};
     for (uint32_t what = 0; what < 2; ++what) {
         if (!outs_f[what])
@@ -958,6 +960,32 @@ APBF_API apbf_status apbf_read_state(apbf_scene *s, float *pos, float *vel, uint
         APBF_CUDA(s, cudaMemcpyAsync(rho, s->b.stage_f, 4 * n, cudaMemcpyDeviceToHost, s->stream));
     }
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_read_positions_async(apbf_scene *s, float *pos)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!pos)
+        return fail(s, APBF_ERR_INVALID_ARG, "pos is NULL");
+    const size_t n = s->sc.n;
+    if (n == 0)
+        return APBF_OK;
+    if (!s->copy_stream) {
+        APBF_CUDA(s, cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
+        APBF_CUDA(s, cudaEventCreateWithFlags(&s->unperm_ev, cudaEventDisableTiming));
+        APBF_CUDA(s, cudaEventCreateWithFlags(&s->copy_ev, cudaEventDisableTiming));
+    }
+    if (s->copy_pending)  // the previous copy still reads the staging buffer
+        APBF_CUDA(s, cudaStreamWaitEvent(s->stream, s->copy_ev, 0));
+    APBF_CUDA(s, launch_unpermute(s->sc, s->b, s->stream, 0));
+    APBF_CUDA(s, cudaEventRecord(s->unperm_ev, s->stream));
+    APBF_CUDA(s, cudaStreamWaitEvent(s->copy_stream, s->unperm_ev, 0));
+    APBF_CUDA(s, cudaMemcpyAsync(pos, s->b.stage_f, 12 * n, cudaMemcpyDeviceToHost, s->copy_stream));
+    APBF_CUDA(s, cudaEventRecord(s->copy_ev, s->copy_stream));
+    s->copy_pending = true;
     return APBF_OK;
 }
 
@@ -1044,6 +1072,10 @@ APBF_API apbf_status apbf_sync(apbf_scene *s)
     apbf_status st = enter(s);
     if (st != APBF_OK)
         return st;
+    if (s->copy_pending) {
+        APBF_CUDA(s, cudaEventSynchronize(s->copy_ev));
+        s->copy_pending = false;
+    }
     return check_device_errors(s);
 }
 
@@ -1060,6 +1092,12 @@ APBF_API void apbf_destroy_scene(apbf_scene *s)
         return;
     if (s->stream || s->arena)
         cudaStreamSynchronize(s->stream);
+    if (s->copy_stream) {
+        cudaStreamSynchronize(s->copy_stream);
+        cudaStreamDestroy(s->copy_stream);
+        cudaEventDestroy(s->unperm_ev);
+        cudaEventDestroy(s->copy_ev);
+    }
     if (s->gexec)
         cudaGraphExecDestroy(s->gexec);
     if (s->graph)

@@ -229,6 +229,11 @@ struct apbf_scene {
     std::vector<cudaEvent_t> ev_pool;
     double stage_ms[APBF_STAGE_COUNT] = {};
     uint64_t stage_launches[APBF_STAGE_COUNT] = {};
+    // asynchronous position readback: the copy runs on its own stream while
+    // the next step computes; copy_ev marks the end of the last such copy
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t unperm_ev = nullptr, copy_ev = nullptr;
+    bool copy_pending = false;
     // host pinned scratch for small readbacks
     void *pinned_small = nullptr;
 };

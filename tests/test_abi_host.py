@@ -25,7 +25,7 @@ def _declared():
 
 def test_exports_every_declared_symbol():
     names = _declared()
-    assert len(names) == 34
+    assert len(names) == 35
     out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout
     exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))

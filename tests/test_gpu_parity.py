@@ -322,6 +322,42 @@ def test_one_cell_cluster_and_box_faces():
     assert err <= 1e-5 * cfg.h, err
 
 
+def test_async_position_readback_equals_sync_readback():
+    """Positions queued to pinned host memory while the next step runs arrive
+    intact: two alternating buffers hold the same bits as a synchronous read
+    of an identical scene after the same step, and a synchronous read after
+    an asynchronous one is unaffected."""
+    import torch
+
+    cfg = scenes.config_dam_break_4k()
+    x, v = scenes.make_scene(cfg)
+    r0 = rest_density(cfg)
+    a = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    b = apbf.apbf_create_scene(apbf.desc_from_config(cfg, x, v, r0))
+    bufs = [torch.empty((cfg.n, 3), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    refs = []
+    for k in range(6):
+        apbf.apbf_step(a, 1)
+        apbf.apbf_read_positions_async(a, bufs[k % 2].data_ptr())
+        apbf.apbf_step(b, 1)
+        refs.append(apbf.apbf_read_state(b, pos=True, vel=False)["pos"])
+        if k % 2 == 1:
+            apbf.apbf_sync(a)
+            assert np.array_equal(bufs[0].numpy(), refs[k - 1]), k
+            assert np.array_equal(bufs[1].numpy(), refs[k]), k
+    apbf.apbf_step(a, 1)
+    apbf.apbf_read_positions_async(a, bufs[0].data_ptr())
+    got = apbf.apbf_read_state(a, pos=True, vel=False)["pos"]
+    apbf.apbf_step(b, 1)
+    ref = apbf.apbf_read_state(b, pos=True, vel=False)["pos"]
+    apbf.apbf_sync(a)
+    assert np.array_equal(got, ref) and np.array_equal(bufs[0].numpy(), ref)
+    with pytest.raises(apbf.ApbfError):
+        apbf.apbf_read_positions_async(a, 0)
+    apbf.apbf_destroy_scene(a)
+    apbf.apbf_destroy_scene(b)
+
+
 def test_neighbor_overflow_is_reported_and_sticky():
     cfg = scenes.config_dam_break_4k()
     rng = np.random.default_rng(4)
