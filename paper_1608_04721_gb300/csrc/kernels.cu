@@ -365,7 +365,15 @@ __global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers
     const bool valid = i < sc.n;
     const uint32_t s = valid ? scene_of<BATCH>(b, i) : 0u;
     float dmin = 3.0e38f, dmax = 0.0f;
-    if (valid) {
+    if (!BATCH) {
+        // one scene: a grid-stride loop over a capped grid, so only a few
+        // hundred blocks contend for the two atomics
+        for (uint32_t k = i; k < sc.n; k += gridDim.x * blockDim.x) {
+            const float d = camera_distance(b.state_x[k], b.dyn);
+            dmin = fminf(dmin, d);
+            dmax = fmaxf(dmax, d);
+        }
+    } else if (valid) {
         const float d = camera_distance(b.state_x[i], b.dyn + s);
         dmin = d;
         dmax = d;
@@ -1240,15 +1248,34 @@ __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers 
     const uint32_t E = sc.K * sc.level_tiles;
     const uint32_t chunk = (E + blockDim.x - 1) / blockDim.x;
     const uint32_t e0 = min(E, threadIdx.x * chunk), e1 = min(E, e0 + chunk);
+    constexpr uint32_t kHeld = 16;  // a thread's chunk is loaded once into registers when it fits
+    uint32_t held[kHeld];
     uint32_t s = 0;
-    for (uint32_t e = e0; e < e1; ++e)
-        s += b.lvl_hist[e];
+    if (chunk <= kHeld) {
+#pragma unroll
+        for (uint32_t q = 0; q < kHeld; ++q) {
+            held[q] = (e0 + q < e1) ? b.lvl_hist[e0 + q] : 0u;
+            s += held[q];
+        }
+    } else {
+        for (uint32_t e = e0; e < e1; ++e)
+            s += b.lvl_hist[e];
+    }
     uint32_t total;
     uint32_t run = block_exclusive_scan_u32(s, sh, &total);
-    for (uint32_t e = e0; e < e1; ++e) {
-        uint32_t v = b.lvl_hist[e];
-        b.lvl_off[e] = run;
-        run += v;
+    if (chunk <= kHeld) {
+#pragma unroll
+        for (uint32_t q = 0; q < kHeld; ++q)
+            if (e0 + q < e1) {
+                b.lvl_off[e0 + q] = run;
+                run += held[q];
+            }
+    } else {
+        for (uint32_t e = e0; e < e1; ++e) {
+            uint32_t v = b.lvl_hist[e];
+            b.lvl_off[e] = run;
+            run += v;
+        }
     }
     __syncthreads();
     for (uint32_t l = threadIdx.x; l <= sc.n_max + 1; l += blockDim.x) {
@@ -1846,8 +1873,9 @@ cudaError_t launch_after(void (*k)(KArgs...), unsigned grid, unsigned block, cud
 cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (sc.n)
-        return launch_after(sc.scenes > 1 ? lod_range_kernel<true> : lod_range_kernel<false>, blocks_for(sc.n, kBlock),
-                            kBlock, s, sc, b);
+        return sc.scenes > 1 ? launch_after(lod_range_kernel<true>, blocks_for(sc.n, kBlock), kBlock, s, sc, b)
+                             : launch_after(lod_range_kernel<false>, min(blocks_for(sc.n, kBlock), 512u), kBlock, s,
+                                            sc, b);
     return cudaGetLastError();
 }
 
