@@ -1310,6 +1310,8 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
     const void *src = nullptr;
     size_t size = 0;
     const float4 *cur = s->cur_buf ? b.recB : b.recA;
+    if (s->copy_pending)  // some fields are staged in the buffer an asynchronous readback may still copy
+        APBF_CUDA(s, cudaStreamWaitEvent(s->stream, s->copy_ev, 0));
     switch (field) {
     case APBF_DBG_KEYS: src = b.key; size = 4 * n; break;
     case APBF_DBG_STATE_IDS: src = b.state_id; size = 4 * n; break;
