@@ -776,20 +776,42 @@ __global__ void __launch_bounds__(1024) splat_tile_scan_kernel(ViewConst v)
     __shared__ uint32_t sh32[32];
     const uint32_t T = v.tiles_x * v.tiles_y;
     const uint32_t per = (T + blockDim.x - 1) / blockDim.x;
-    const uint32_t a = threadIdx.x * per, e = min(a + per, T);
+    const uint32_t a = min(threadIdx.x * per, T), e = min(a + per, T);
+    constexpr uint32_t kHeld = 16;  // a thread's counts are loaded once into registers when they fit
+    uint32_t held[kHeld];
     uint32_t sum = 0, chunks = 0;
-    for (uint32_t k = a; k < e; ++k) {
-        sum += v.tile_cnt[k];
-        chunks += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+    if (per <= kHeld) {
+#pragma unroll
+        for (uint32_t q = 0; q < kHeld; ++q) {
+            held[q] = (a + q < e) ? v.tile_cnt[a + q] : 0u;
+            sum += held[q];
+            chunks += (held[q] + kSplatChunk - 1) / kSplatChunk;
+        }
+    } else {
+        for (uint32_t k = a; k < e; ++k) {
+            sum += v.tile_cnt[k];
+            chunks += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+        }
     }
     uint32_t total, ctotal;
     uint32_t run = block_exclusive_scan_u32(sum, sh32, &total);
     uint32_t crun = block_exclusive_scan_u32(chunks, sh32, &ctotal);
-    for (uint32_t k = a; k < e; ++k) {
-        v.tile_start[k] = run;
-        v.chunk_start[k] = crun;
-        run += v.tile_cnt[k];
-        crun += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+    if (per <= kHeld) {
+#pragma unroll
+        for (uint32_t q = 0; q < kHeld; ++q)
+            if (a + q < e) {
+                v.tile_start[a + q] = run;
+                v.chunk_start[a + q] = crun;
+                run += held[q];
+                crun += (held[q] + kSplatChunk - 1) / kSplatChunk;
+            }
+    } else {
+        for (uint32_t k = a; k < e; ++k) {
+            v.tile_start[k] = run;
+            v.chunk_start[k] = crun;
+            run += v.tile_cnt[k];
+            crun += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+        }
     }
     if (threadIdx.x == 0) {
         v.tile_start[T] = total;
