@@ -845,10 +845,11 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     const uint32_t tx = (width + kTilePx - 1) / kTilePx, ty = (height + kTilePx - 1) / kTilePx;
     const size_t tiles = (size_t)tx * ty, n = s->sc.n;
     const size_t cap = (size_t)kSplatListPerParticle * n + 65536;
-    size_t off[15], total = 0;
-    const size_t sizes[15] = {4 * pix, 16 * pix, 4 * tiles, 4 * tiles, 4 * (tiles + 1), 4 * cap, 4 * n, 4,
-                              4 * (tiles + 1), 8, n, 8 * n, 4 * n, 4 * tiles, 4 * n};
-    for (int k = 0; k < 15; ++k) {
+    size_t off[16], total = 0;
+    const size_t sizes[16] = {4 * pix, 16 * pix, 4 * tiles, 4 * tiles, 4 * (tiles + 1), 4 * cap, 4 * n, 4,
+                              4 * (tiles + 1), 8, n, 8 * n, 4 * n, 4 * tiles, 4 * n,
+                              4 * (tiles + cap / kSplatChunk + 1)};
+    for (int k = 0; k < 16; ++k) {
         off[k] = total;
         total = align_up(total + (sizes[k] ? sizes[k] : 1));
     }
@@ -882,6 +883,7 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     s->view.near = (float *)(base + off[12]);
     s->view.tile_max = (uint32_t *)(base + off[13]);
     s->view.open_mask = (uint32_t *)(base + off[14]);
+    s->view.chunk_tile = (uint32_t *)(base + off[15]);
     s->view.list_cap = (uint32_t)cap;
     s->view.tiles_x = tx;
     s->view.tiles_y = ty;

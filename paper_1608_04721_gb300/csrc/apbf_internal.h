@@ -134,6 +134,7 @@ struct ViewConst {
     uint32_t *tile_fill = nullptr;   // fill counters of the scatter pass
     uint32_t *tile_start = nullptr;  // tiles + 1 list offsets
     uint32_t *chunk_start = nullptr; // tiles + 1 offsets of the tiles' kSplatChunk-entry work chunks
+    uint32_t *chunk_tile = nullptr;  // the tile of each work chunk (tiles + list_cap / kSplatChunk + 1)
     uint32_t *tile_list = nullptr;   // list_cap particle indices
     uint32_t list_cap = 0;
     unsigned long long *list_used = nullptr;  // entries reserved this step (64-bit: rejected reservations count too)

@@ -802,15 +802,21 @@ __global__ void __launch_bounds__(1024) splat_tile_scan_kernel(ViewConst v)
             if (a + q < e) {
                 v.tile_start[a + q] = run;
                 v.chunk_start[a + q] = crun;
+                const uint32_t nch = (held[q] + kSplatChunk - 1) / kSplatChunk;
+                for (uint32_t c = 0; c < nch; ++c)
+                    v.chunk_tile[crun + c] = a + q;
                 run += held[q];
-                crun += (held[q] + kSplatChunk - 1) / kSplatChunk;
+                crun += nch;
             }
     } else {
         for (uint32_t k = a; k < e; ++k) {
             v.tile_start[k] = run;
             v.chunk_start[k] = crun;
+            const uint32_t nch = (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+            for (uint32_t c = 0; c < nch; ++c)
+                v.chunk_tile[crun + c] = k;
             run += v.tile_cnt[k];
-            crun += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
+            crun += nch;
         }
     }
     if (threadIdx.x == 0) {
@@ -870,15 +876,7 @@ __global__ void __launch_bounds__(kTilePx *kTilePx) splat_tile_kernel(StepConst 
     const DynParams *dyn = b.dyn;
     const float e0 = dyn->eye[0], e1 = dyn->eye[1], e2 = dyn->eye[2];
     for (uint32_t w = blockIdx.x; w < nwork; w += gridDim.x) {
-        uint32_t lo = 0, hi = T;  // the tile whose chunks hold w: chunk_start[lo] <= w < chunk_start[lo + 1]
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (v.chunk_start[mid] <= w)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const uint32_t tile = lo;
+        const uint32_t tile = v.chunk_tile[w];  // chunk_start[tile] <= w < chunk_start[tile + 1]
         const uint32_t beg = v.tile_start[tile] + (w - v.chunk_start[tile]) * kSplatChunk;
         const uint32_t end = min(beg + kSplatChunk, v.tile_start[tile + 1]);
         const uint32_t px0 = (tile % v.tiles_x) * kTilePx, py0 = (tile / v.tiles_x) * kTilePx;
