@@ -8,18 +8,22 @@
  * counting-sort uniform grid with particle reordering (Sec. 6), N_max Jacobi
  * solver iterations of the density constraint (Eq. 4-7) in which particle i
  * is active only in iterations 1..N_i (Eq. 9-11), and the velocity/position
- * update. N_i is
- * the particle's level of detail (Eq. 8) from its distance to the camera
+ * update. N_i is the particle's level of detail (Eq. 8) from its distance to
+ * the camera
  * (Sec. 4.1, DTC model) or from its distance behind the visible surface of
  * the particles rendered as spheres (Sec. 4.1 and Sec. 6, DTVS model).
  *
  * Conventions for every entry point:
  *  - Returns apbf_status; nothing aborts, throws or exits.
  *  - "host" pointers are ordinary CPU memory owned by the caller and only
- *    read/written during the call. "device" pointers are CUDA global memory.
+ *    read/written during the call (except apbf_read_positions_async, which
+ *    fills its buffer after returning, by the next apbf_sync). "device"
+ *    pointers are CUDA global memory.
  *  - Calls on one scene are not thread-safe; different scenes are independent.
  *  - All GPU work of a scene is issued on the stream given at creation, in
- *    call order. apbf_step() returns before the GPU finishes; a GPU-side error
+ *    call order (apbf_read_positions_async copies on a second stream of the
+ *    library's, ordered after the step it reads and before any later reuse of
+ *    its staging buffer). apbf_step() returns before the GPU finishes; a GPU-side error
  *    (e.g. a neighbour-list overflow) is reported by the next synchronising
  *    call (apbf_read_state, apbf_density_stats, apbf_sync, apbf_debug_read)
  *    and then sticks to the scene: every later call returns it.
