@@ -9,9 +9,9 @@
  * solver iterations of the density constraint (Eq. 4-7) in which particle i
  * is active only in iterations 1..N_i (Eq. 9-11), and the velocity/position
  * update. N_i is the particle's level of detail (Eq. 8) from its distance to
- * the camera
- * (Sec. 4.1, DTC model) or from its distance behind the visible surface of
- * the particles rendered as spheres (Sec. 4.1 and Sec. 6, DTVS model).
+ * the camera (Sec. 4.1, DTC model) or from its distance behind the visible
+ * surface of the particles rendered as spheres (Sec. 4.1 and Sec. 6, DTVS
+ * model).
  *
  * Conventions for every entry point:
  *  - Returns apbf_status; nothing aborts, throws or exits.
