@@ -1474,18 +1474,21 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const OffsetTab 
         const float dx = dxy.x, dy = dxy.y;
         const float dz = __fadd_rn(__fsub_rn(ai.z, aj.z), dtab->z[c]);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (r2 < sc.h2) {
-            const float u = __fsub_rn(sc.h2, r2);
-            racc = __fmaf_rn(__fmul_rn(u, u), u, racc);
-            if (r2 > 0.0f) {
-                const float ir = rsqrtf(r2);
-                const float hr = __fmaf_rn(-r2, ir, sc.h);
-                const float gw = __fmul_rn(__fmul_rn(hr, hr), ir);  // |grad W| / (45/(pi h^6)) / r
-                gxy = fma2_rn(make_float2(gw, gw), dxy, gxy);
-                gz = __fmaf_rn(gw, dz, gz);
-                s2 = __fmaf_rn(__fmul_rn(gw, gw), r2, s2);
-            }
-        }
+        // branch-free: every pair runs the same instructions; a pair at or past
+        // h adds an exact zero (u = 0, gw = 0), and so does the gradient of a
+        // coincident pair (its rsqrt is kept finite by the 1e-30 floor, far
+        // below the square of any nonzero distance these coordinates hold), so
+        // the sums have the bits of a form that skips those pairs
+        const bool in = r2 < sc.h2;
+        const float r2c = in ? r2 : sc.h2;
+        const float u = __fsub_rn(sc.h2, r2c);
+        racc = __fmaf_rn(__fmul_rn(u, u), u, racc);
+        const float ir = rsqrtf(fmaxf(r2c, 1.0e-30f));
+        const float hr = __fmaf_rn(-r2c, ir, sc.h);
+        const float gw = (in && r2 > 0.0f) ? __fmul_rn(__fmul_rn(hr, hr), ir) : 0.0f;
+        gxy = fma2_rn(make_float2(gw, gw), dxy, gxy);
+        gz = __fmaf_rn(gw, dz, gz);
+        s2 = __fmaf_rn(__fmul_rn(gw, gw), r2c, s2);
     });
     rho = __fmul_rn(sc.mass_poly6, __fadd_rn(sc.h6, racc));
     const float C = __fmaf_rn(rho, sc.inv_rho0, -1.0f);
@@ -1597,16 +1600,17 @@ __device__ __forceinline__ float3 deltap_one(const StepConst &sc, const OffsetTa
         const float dx = dxy.x, dy = dxy.y;
         const float dz = __fadd_rn(__fsub_rn(bi.z, bj.z), dtab->z[c]);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (r2 < sc.h2 && r2 > 0.0f) {
-            const float ir = rsqrtf(r2);
-            const float hr = __fmaf_rn(-r2, ir, sc.h);
-            const float gw = __fmul_rn(__fmul_rn(hr, hr), ir);
-            const float u = __fmul_rn(__fsub_rn(sc.h2, r2), sc.inv_wdq);  // W(r) / W(dq) = u^3
-            const float scorr = __fmul_rn(sc.neg_k, powi<NPOW>(__fmul_rn(__fmul_rn(u, u), u), sc.scorr_n));
-            const float f = __fmul_rn(__fadd_rn(__fadd_rn(bi.w, bj.w), scorr), gw);
-            axy = fma2_rn(make_float2(f, f), dxy, axy);
-            az = __fmaf_rn(f, dz, az);
-        }
+        // as in lambda_one: pairs at or past h and coincident pairs add an exact zero
+        const bool in = r2 < sc.h2 && r2 > 0.0f;
+        const float r2c = in ? r2 : sc.h2;
+        const float ir = rsqrtf(r2c);
+        const float hr = __fmaf_rn(-r2c, ir, sc.h);
+        const float gw = in ? __fmul_rn(__fmul_rn(hr, hr), ir) : 0.0f;
+        const float u = __fmul_rn(__fsub_rn(sc.h2, r2c), sc.inv_wdq);  // W(r) / W(dq) = u^3
+        const float scorr = __fmul_rn(sc.neg_k, powi<NPOW>(__fmul_rn(__fmul_rn(u, u), u), sc.scorr_n));
+        const float f = __fmul_rn(__fadd_rn(__fadd_rn(bi.w, bj.w), scorr), gw);
+        axy = fma2_rn(make_float2(f, f), dxy, axy);
+        az = __fmaf_rn(f, dz, az);
     });
     // new position; contacts: obstacles, then the box, expressed relative to the cell origin
     float px = __fmaf_rn(sc.c_dp, axy.x, bi.x);
