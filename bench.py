@@ -279,6 +279,13 @@ def stage_profile(apbf, scene, cfg, first_step, steps, drive_fn=None):
     return ms_tot, ln_tot, pairs, nbr_pairs, iters, s
 
 
+# What bounds the solver passes, from the committed ncu summary (not measured
+# by this run): the roofline fraction above is against the FP32 pipes.
+LIMITER_NOTE = ("L1 throughput: ncu puts the dense solver passes at 88-91 % of the L1 peak (warp-level gathers of "
+                "neighbour records, ~20 sectors per request), DRAM at 31 %, the FMA pipe at 37-42 % "
+                "(profiles/solver_kernels_apbf_ocean_1048576.md)")
+
+
 def kernel_source_digest() -> str:
     """First 16 hex digits of the sha256 of kernels.cu without its comments
     and blank lines: a change to the code invalidates a traffic capture, a
@@ -493,6 +500,7 @@ def run_batch(args, apbf, torch, d):
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "traffic": read_traffic(f"{top}_kernel", "apbf_batch_256"),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+                "limiter": LIMITER_NOTE,
                 "flops_per_pair": FLOPS_PER_PAIR[top], "pairs_per_launch": pairs / launches,
                 "avg_launch_us": avg_launch_s * 1e6}
     per_step_iters = iters / args.profile_steps
@@ -998,6 +1006,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz",
+                "limiter": LIMITER_NOTE,
                 "flops_per_pair": FLOPS_PER_PAIR[top], "pairs_per_launch": pairs / launches,
                 "avg_launch_us": avg_launch_s * 1e6}
     particle_iters_per_step = iters / args.profile_steps
