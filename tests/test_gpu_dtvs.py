@@ -149,6 +149,22 @@ def test_dtvs_131k_one_step_parity():
     check_final(cfg, scene, p, st)
 
 
+def test_dtvs_one_step_parity_1m_bench_configuration():
+    """The benchmark's DTVS line: the 1,048,576-particle ocean scene under its
+    spline camera at 1280 x 720 with spheres of half the particle spacing:
+    depth image, distances and levels bit for bit, sampled neighbour sets, the
+    first iteration's lambda and rho for every particle, and the final state."""
+    cfg = scenes.config_ocean_1m().replace(lod_mode=scenes.LOD_DTVS)
+    eye, direction = scenes.camera_at(cfg, 0)
+    view = (1280, 720, TAN30, (0, 0, 1), 0.5 * cfg.spacing)
+    scene, p, x, v = make(cfg, tuple(float(a) for a in eye), tuple(float(a) for a in direction), view)
+    depth, dist, lv = check_lod(scene, p, x)
+    assert len(np.unique(lv)) > 3
+    rng = np.random.default_rng(5)
+    st = check_stages(cfg, scene, p, x, v, iters=False, sample=rng.choice(cfg.n, 2048, replace=False))
+    check_final(cfg, scene, p, st)
+
+
 def test_dtvs_graph_equals_eager_and_follows_camera_and_view_changes():
     cfg, eye, direction, view = CASES["oblique_5200"]()
     g, p, x, v = make(cfg, eye, direction, view)
