@@ -110,6 +110,35 @@ def test_each_scene_of_a_batch_matches_the_oracle_after_one_step():
         off += n
 
 
+def test_full_size_batch_256_sampled_scenes_match_the_oracle():
+    """The benchmark's batch (256 dam breaks of 2,048-65,536 particles, 4.8 M
+    in all, seeded as the benchmark's rank 0) stepped once as one graph: the
+    smallest, the largest and two other scenes match the oracle's step."""
+    cfgs = scenes.config_batch_256(seed=1608_04721)
+    r0 = rest_density(cfgs[0])
+    inputs = [scenes.make_scene(c) for c in cfgs]
+    batch = apbf.apbf_create_batch([apbf.desc_from_config(c, x, v, r0) for c, (x, v) in zip(cfgs, inputs)])
+    for k, c in enumerate(cfgs):
+        apbf.apbf_set_camera_at(batch, k, c.eye)
+    apbf.apbf_step(batch, 1)
+    got = apbf.apbf_read_state(batch, pos=True, vel=True, n_iter=True)
+    offs = np.concatenate([[0], np.cumsum([c.n for c in cfgs])])
+    sizes = np.array([c.n for c in cfgs])
+    picks = sorted({int(sizes.argmin()), int(sizes.argmax()), 17, 200})
+    for k in picks:
+        c = cfgs[k]
+        x, v = inputs[k]
+        p = oracle.make_params(c, rho0=r0, eye=c.eye)
+        st = oracle.step(p, x, v)
+        inv = np.argsort(st.ids)
+        a, b = offs[k], offs[k + 1]
+        assert np.abs(got["pos"][a:b] - st.x[inv]).max() <= 1e-5 * c.h, k
+        assert np.abs(got["vel"][a:b] - st.v[inv]).max() <= 1e-5 * c.h / c.dt, k
+        lv, _ = oracle.lod_levels(p, x)
+        assert np.array_equal(got["n_iter"][a:b].astype(np.int32), lv), k
+    apbf.apbf_destroy_scene(batch)
+
+
 def test_batch_graph_replay_equals_eager_and_density_aggregates():
     cfgs = _batch_configs(5, 3)
     r0 = rest_density(cfgs[0])
