@@ -82,6 +82,49 @@ def test_each_scene_matches_itself_alone_bitwise():
     apbf.apbf_server_destroy(srv)
 
 
+def test_serving_templates_match_alone_and_the_oracle():
+    """Scenes of the served workload's own templates (4,096-262,144 particles,
+    N_i 5..10, at rest, as the benchmark submits them): the smallest, the
+    largest and three others served together through a pool that forces one
+    to queue, each bit-identical to itself alone; the largest also against
+    the oracle's step."""
+    temps = scenes.config_serve_templates()
+    sizes = np.array([c.n for c in temps])
+    picks = [int(sizes.argmin()), int(sizes.argmax()), 5, 20, 40]
+    cfgs = [temps[k] for k in picks]
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    xs = [scenes.make_scene(c)[0] for c in cfgs]
+    descs = [apbf.desc_from_config(c, x, None, r0) for c, x in zip(cfgs, xs)]
+    cap = sum(c.n for c in cfgs) - min(c.n for c in cfgs[1:]) // 2
+    srv = apbf.apbf_server_create(descs[0], max_particles=cap, max_cells=16 * 10**6, max_scenes=8)
+    steps = [3, 2, 4, 3, 2]
+    t = [apbf.apbf_server_submit(srv, descs[k], cfgs[k].eye, steps[k], want_vel=True) for k in range(len(cfgs))]
+    log = []
+    for _ in range(40):
+        info = apbf.apbf_server_tick(srv)
+        log.append(info)
+        if info["resident_scenes"] == 0 and info["queued"] == 0:
+            break
+    assert any(i["queued"] > 0 for i in log), "the capacity never made a request wait"
+    for k in range(len(cfgs)):
+        pos, vel = apbf.apbf_server_result(srv, t[k])
+        ref_pos, ref_vel = _alone(descs[k], cfgs[k].eye, steps[k])
+        assert np.array_equal(pos, ref_pos) and np.array_equal(vel, ref_vel), k
+    # the largest template after its first step, against the oracle
+    big = 1
+    s1 = apbf.apbf_create_scene(descs[big])
+    apbf.apbf_set_camera(s1, cfgs[big].eye)
+    apbf.apbf_step(s1, 1)
+    got = apbf.apbf_read_state(s1, pos=True, vel=True)
+    p = oracle.make_params(cfgs[big], rho0=r0, eye=cfgs[big].eye)
+    st = oracle.step(p, xs[big], np.zeros_like(xs[big]))
+    inv = np.argsort(st.ids)
+    assert np.abs(got["pos"] - st.x[inv]).max() <= 1e-5 * cfgs[big].h
+    assert np.abs(got["vel"] - st.v[inv]).max() <= 1e-5 * cfgs[big].h / cfgs[big].dt
+    apbf.apbf_destroy_scene(s1)
+    apbf.apbf_server_destroy(srv)
+
+
 def test_one_scene_after_another_reuses_the_pool():
     cfgs = _configs(3, 5)
     r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
