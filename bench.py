@@ -286,11 +286,12 @@ LIMITER_NOTE = ("L1 throughput: ncu puts the dense solver passes at 88-91 % of t
                 "(profiles/solver_kernels_apbf_ocean_1048576.md)")
 
 
-def kernel_source_digest() -> str:
-    """First 16 hex digits of the sha256 of kernels.cu without its comments
-    and blank lines: a change to the code invalidates a traffic capture, a
-    change to a comment does not."""
-    src = open(os.path.join(ROOT, "paper_1608_04721_gb300", "csrc", "kernels.cu"), encoding="utf-8").read()
+def kernel_source_digest(src: str | None = None) -> str:
+    """First 16 hex digits of the sha256 of kernels.cu (or of the source text
+    given) without its comments and blank lines: a change to the code
+    invalidates a traffic capture, a change to a comment does not."""
+    if src is None:
+        src = open(os.path.join(ROOT, "paper_1608_04721_gb300", "csrc", "kernels.cu"), encoding="utf-8").read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
     code = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())

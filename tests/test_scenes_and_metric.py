@@ -69,3 +69,20 @@ def test_table1_improvement_definition():
                     assert math.floor(100 * imp + 0.5) == int(r[icol]), (scen, r)
                     checked += 1
     assert checked == 12
+
+
+def test_traffic_capture_digest_ignores_comments_only():
+    """bench.py keeps a committed ncu traffic figure only while the kernel code
+    is the code it was taken on: comments and blank lines do not count, a
+    change to any statement does."""
+    import bench
+
+    src = "// header\n__global__ void k(float *x)\n{\n    x[0] = 1.0f;  /* one */\n}\n"
+    base = bench.kernel_source_digest(src)
+    assert bench.kernel_source_digest(src.replace("// header", "// another header\n\n")) == base
+    assert bench.kernel_source_digest(src.replace("/* one */", "/* a longer\n comment */")) == base
+    assert bench.kernel_source_digest(src.replace("1.0f", "2.0f")) != base
+    assert bench.kernel_source_digest(src.replace("x[0]", "x[1]")) != base
+    # the committed capture matches the committed kernels
+    assert bench.read_traffic("lambda_kernel", "apbf_ocean_1048576") is not None
+    assert bench.read_traffic("deltap_kernel", "apbf_ocean_1048576") is not None
