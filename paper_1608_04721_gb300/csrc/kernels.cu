@@ -1149,7 +1149,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
         const int3 c = unpack_cell(b.cell_s[p]);
         const size_t n = sc.n;
         uint4 *eblk = reinterpret_cast<uint4 *>(b.nbr) + t;  // entry blocks of column t, stride n
-        uint4 eb = make_uint4(0u, 0u, 0u, 0u);                // the block being filled
+        uint4 eb = make_uint4(0u, 0u, 0u, 0u);                // the last four entries written
         // the cells x-1..x+1 of one row (y+dy, z+dz) are contiguous in sorted order
         const int xl = max(c.x - 1, 0), xr = min(c.x + 1, g.nx - 1);
         for (int dz = -1; dz <= 1; ++dz) {
@@ -1198,12 +1198,8 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                         hits &= hits - 1u;
                         const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
                         const uint32_t e = q | ((code_row + dxc) << kSlotBits);
-                        const uint32_t s = cnt % kEntryBlock;
-                        eb.x = s == 0 ? e : eb.x;
-                        eb.y = s == 1 ? e : eb.y;
-                        eb.z = s == 2 ? e : eb.z;
-                        eb.w = s == 3 ? e : eb.w;
-                        if (s == kEntryBlock - 1 && cnt < sc.max_nbr)  // a full block: one 16-byte store
+                        eb = make_uint4(eb.y, eb.z, eb.w, e);  // the last four entries, oldest first
+                        if (cnt % kEntryBlock == kEntryBlock - 1 && cnt < sc.max_nbr)  // a full block
                             eblk[(size_t)(cnt / kEntryBlock) * n] = eb;
                         ++cnt;
                     }
@@ -1218,10 +1214,11 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
         const uint32_t s = cnt % kEntryBlock;
         if (s) {  // the last, partial block, padded
             const uint32_t sentinel = sc.n | (kSentinelCode << kSlotBits);
-            eb.y = s <= 1 ? sentinel : eb.y;
-            eb.z = s <= 2 ? sentinel : eb.z;
-            eb.w = sentinel;
-            eblk[(size_t)(cnt / kEntryBlock) * n] = eb;
+            // its s entries are the last s of eb
+            const uint4 out = make_uint4(s == 1 ? eb.w : (s == 2 ? eb.z : eb.y),
+                                         s == 1 ? sentinel : (s == 2 ? eb.w : eb.z),
+                                         s == 3 ? eb.w : sentinel, sentinel);
+            eblk[(size_t)(cnt / kEntryBlock) * n] = out;
         }
     }
     // pair counts, total and per level bin: one atomic per warp (no block
