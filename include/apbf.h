@@ -212,8 +212,8 @@ APBF_API apbf_status apbf_set_view(apbf_scene *scene, uint32_t width, uint32_t h
 
 /*
  * Rigid obstacles (the paper's signed-distance-field obstacles of Sec. 6, here
- * analytic solids), used from the next step on by the contact response of
- * The collision response of Fig. 7 -- after every position update of the solver, a predicted
+ * analytic solids), used from the next step on by the collision response of
+ * Fig. 7 -- after every position update of the solver, a predicted
  * position strictly inside an obstacle moves to the nearest point of its
  * surface (obstacles in order), then into the box -- and by the
  * pre-stabilisation above. The prediction itself is only clamped to the box.
