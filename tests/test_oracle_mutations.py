@@ -79,6 +79,13 @@ MUTATIONS = [
     ("block contacts ignore the upper faces",
      "            if (dh < best) {", "            if (0 && dh < best) {",
      lambda: obst.test_projection_is_the_nearest_surface_point(obst.BLOCK)),
+    ("finished neighbours enter Eq. 7 with lambda = 0 instead of their last lambda",
+     "                if (p->lambda_mode == ORC_LAMBDA_ZERO)\n                    lam[s] = 0.0;",
+     "                lam[s] = 0.0;",
+     lambda: pins.test_finished_neighbour_enters_with_its_last_lambda(O.ORC_LAMBDA_STALE, "stale")),
+    ("lambda recomputed for finished particles too",
+     "if (active || p->lambda_mode == ORC_LAMBDA_RECOMPUTE) {", "if (1) {",
+     lambda: pins.test_finished_neighbour_enters_with_its_last_lambda(O.ORC_LAMBDA_STALE, "stale")),
     ("contact response left out of the solver's position update",
      "                contact_obstacles(p, xs + 3 * s);\n                clamp_box(p, xs + 3 * s);",
      "                clamp_box(p, xs + 3 * s);",

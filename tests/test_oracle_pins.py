@@ -25,7 +25,10 @@ result, or brute force. What pins each oracle function:
   orc_predict/orc_step isolated particle in free fall (closed form); clamp
                        keeps the box; APBF with every N_i = N_max is PBF;
                        nested active sets; finished particles stay fixed;
-                       interior of a jitter-free lattice unchanged
+                       interior of a jitter-free lattice unchanged; a
+                       finished neighbour enters Eq. 7 with its last lambda
+                       (two-particle closed form that also tells the zero
+                       and recompute-all options apart)
 """
 import math
 
@@ -380,3 +383,81 @@ def test_zero_gravity_lattice_interior_unchanged(rho0_lattice):
     assert np.abs(st.x_final[inner] - x0[inner]).max() < 1e-12
     assert np.abs(st.x_final[depth == 0] - x0[depth == 0]).max() > 1e-4
     assert np.abs(st.v_final[depth >= 6]).max() < 1e-9
+
+
+# ------------------------------------------- lambda of finished neighbours
+
+def _two_particle_step(p, xa: float, xb: float, lam_b_second: str):
+    """Closed form of one step of two particles on the x axis, particle a of
+    level 2 and b of level 1, written out from Eq. 4-7 for the scalar case
+    (no gravity, no velocity, box far away). Returns (x_a, x_b) after the step.
+
+    lam_b_second says which lambda of b enters a's correction in iteration 2,
+    where b is no longer active: 'stale' (b's lambda of iteration 1, the
+    reading the compensation of Sec. 4.2 / Fig. 5 needs), 'zero', or
+    'recompute' (b's lambda at the positions of iteration 2)."""
+    h = float(p.h)
+    m = float(p.mass)
+    w = 1.0 / m
+    rho0 = float(p.rho0)
+    eps = float(p.eps)
+    k = float(p.scorr_k)
+    n = int(p.scorr_n)
+    dq = float(p.scorr_dq)
+    c_poly6 = 315.0 / (64.0 * math.pi * h ** 9)
+    c_spiky = 45.0 / (math.pi * h ** 6)
+
+    def W(r):
+        return c_poly6 * (h * h - r * r) ** 3 if r < h else 0.0
+
+    def lam_of(r):
+        # rho = m (W(0) + W(r)); |grad_a C| = |grad_b C| = (m / rho0) |grad W(r)|
+        C = m * (W(0.0) + W(r)) / rho0 - 1.0
+        g = m / rho0 * c_spiky * (h - r) ** 2
+        return -C / (w * 2.0 * g * g + eps)
+
+    def dxa(r, lam_a, lam_b):
+        # Eq. 7 for a: (w m / rho0) (lam_a + lam_b + s_corr) grad W(x_a - x_b), and
+        # grad W(x_a - x_b) points from a to b (x_a < x_b) with magnitude c (h - r)^2
+        scorr = -k * (W(r) / W(dq)) ** n
+        return w * m / rho0 * (lam_a + lam_b + scorr) * c_spiky * (h - r) ** 2
+
+    r1 = xb - xa
+    lam1 = lam_of(r1)
+    d1 = dxa(r1, lam1, lam1)
+    xa, xb = xa + d1, xb - d1                 # iteration 1: both move, b opposite to a
+    r2 = xb - xa
+    lam_a2 = lam_of(r2)
+    lam_b = {"stale": lam1, "zero": 0.0, "recompute": lam_a2}[lam_b_second]
+    xa = xa + dxa(r2, lam_a2, lam_b)          # iteration 2: only a moves
+    return xa, xb
+
+
+@pytest.mark.parametrize("mode,name", [(O.ORC_LAMBDA_STALE, "stale"), (O.ORC_LAMBDA_ZERO, "zero"),
+                                       (O.ORC_LAMBDA_RECOMPUTE, "recompute")])
+def test_finished_neighbour_enters_with_its_last_lambda(mode, name):
+    """Particle b finishes after iteration 1 (level 1), a takes part in
+    iteration 2 (level 2, nearer the camera). In iteration 2 a's correction
+    uses b's lambda from iteration 1 (stale reading); the zero and
+    recompute-all options of the oracle give their own closed forms, and the
+    three differ by far more than the tolerance."""
+    xa0, xb0 = np.float32(1.0), np.float32(1.06)
+    x = np.array([[xa0, 1.0, 1.0], [xb0, 1.0, 1.0]], np.float32)
+    v = np.zeros_like(x)
+    h = np.float32(H)
+    w0 = 315.0 / (64.0 * math.pi * float(h) ** 3)          # W(0)
+    # rest density 5 % above the pair's own density: a small, well-conditioned correction
+    rho_pair = w0 * (1.0 + (1.0 - (float(xb0) - float(xa0)) ** 2 / float(h) ** 2) ** 3)
+    p = _params(rho0=1.05 * rho_pair, n_min=1, n_max=2, lod_mode=O.ORC_LOD_DTC, eye=(0.0, 1.0, 1.0),
+                lambda_mode=mode)
+    lv, _ = O.lod_levels(p, x)
+    assert list(lv) == [2, 1]
+    st = O.step(p, x, v, want_final64=True)
+    got = st.x_final[np.argsort(st.ids)]
+    expect = {nm: _two_particle_step(p, float(xa0), float(xb0), nm) for nm in ("stale", "zero", "recompute")}
+    ea, eb = expect[name]
+    assert abs(got[0, 0] - ea) < 1e-12 and abs(got[1, 0] - eb) < 1e-12, (got[:, 0], ea, eb)
+    assert np.all(got[:, 1:] == 1.0)
+    others = [expect[nm][0] for nm in expect if nm != name]
+    # the readings are told apart by far more than the 1e-5 h position tolerance
+    assert min(abs(ea - o) for o in others) > 1e-5 * H
