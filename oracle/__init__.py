@@ -133,6 +133,8 @@ def lib():
                                P(OrcRecord)]
         L.orc_density_stats.argtypes = [P(OrcParams), C.c_int32, P(C.c_float), P(C.c_double),
                                         P(C.c_double)]
+        L.orc_set_threads.argtypes = [C.c_int32]
+        L.orc_set_threads.restype = C.c_int32
         L.orc_obstacle_project.argtypes = [P(OrcObstacle), P(C.c_double), P(C.c_double)]
         L.orc_obstacle_project.restype = C.c_int
         L.orc_view_basis.argtypes = [P(OrcView), P(C.c_float), P(C.c_float), P(C.c_float)]
@@ -209,6 +211,12 @@ def make_params(cfg=None, *, rho0: float, box_lo=None, box_hi=None, eye=(0.0, 0.
         p.obstacles[k].a[:] = [float(t) for t in a]
         p.obstacles[k].b[:] = [float(t) for t in b]
     return p
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's per-particle loops (n <= 0: keep the current
+    count); returns the count in use. Results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def poly6(r2: float, h: float) -> float:

@@ -31,6 +31,25 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-particle loops (the Jacobi passes, XSPH, the density
+   diagnostic and the neighbour lists). Every particle's own arithmetic is the
+   same at any thread count, so results are bit-identical; only whole-set
+   reductions (the density statistics) and the sort stay serial. */
+int orc_set_threads(int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
 
 static const double ORC_PI = 3.14159265358979323846;
 
@@ -495,13 +514,12 @@ static int build_neighbors_sorted(const orc_params *p, const int32_t dims[3], in
         return -3;
     int32_t *idx = NULL;
     for (int pass = 0; pass < 2; ++pass) {
-        int64_t total = 0;
+        /* pass 0 counts each list into off[i + 1], pass 1 fills it from off[i] */
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; ++i) {
-            if (pass == 0)
-                off[i] = (int32_t)total;
             int32_t c[3];
             cell_coords(p, dims, inv_h, xs32 + 3 * i, c);
-            int64_t w = off[i];
+            int64_t w = pass == 0 ? 0 : off[i];
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
@@ -516,13 +534,19 @@ static int build_neighbors_sorted(const orc_params *p, const int32_t dims[3], in
                                 if (pass == 1)
                                     idx[w] = (int32_t)j;
                                 ++w;
-                                ++total;
                             }
                         }
                     }
+            if (pass == 0)
+                off[i + 1] = (int32_t)w;
         }
         if (pass == 0) {
-            off[n] = (int32_t)total;
+            int64_t total = 0;
+            off[0] = 0;
+            for (int32_t i = 0; i < n; ++i) {
+                total += off[i + 1];
+                off[i + 1] = (int32_t)total;
+            }
             idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
             if (!idx) {
                 free(off);
@@ -581,6 +605,7 @@ static int neighbors_alloc(const orc_params *p, int32_t n, const float *x, int32
     off[0] = 0;
     for (int32_t i = 0; i < n; ++i)
         off[i + 1] = off[i] + deg[i];
+#pragma omp parallel for schedule(static)
     for (int32_t s = 0; s < n; ++s) {
         int32_t i = order[s];
         int32_t w = off[i];
@@ -727,6 +752,7 @@ int orc_delta_p(const orc_params *p, int32_t n, const double *xs, const double *
 {
     if (!p || n < 0 || (n > 0 && (!xs || !lam || !nbr_off || !dp)))
         return -1;
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i)
         delta_p_one(p, xs, lam, nbr_off, nbr_idx, i, dp + 3 * i);
     return 0;
@@ -740,6 +766,7 @@ int orc_xsph(const orc_params *p, int32_t n, const double *xs, const double *v, 
     if (!p || n < 0 || (n > 0 && (!xs || !v || !nbr_off || !vout)))
         return -1;
     double c = p->xsph_c, mr = (double)p->mass / (double)p->rho0;
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double acc[3] = {0.0, 0.0, 0.0};
         for (int32_t k = nbr_off[i]; k < nbr_off[i + 1]; ++k) {
@@ -1006,6 +1033,7 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
     }
     /* The solver loop of Fig. 7: N_max Jacobi iterations over the active sets P_l. */
     for (int32_t l = 1; l <= p->n_max; ++l) {
+#pragma omp parallel for schedule(static)
         for (int32_t s = 0; s < n; ++s) {
             int active = lvl[s] >= l;
             if (active || p->lambda_mode == ORC_LAMBDA_RECOMPUTE) {
@@ -1022,9 +1050,11 @@ int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, or
         }
         if (rec && rec->lam && l <= rec->rec_iters)
             memcpy(rec->lam + (size_t)(l - 1) * n, lam, sizeof(double) * (size_t)n);
+#pragma omp parallel for schedule(static)
         for (int32_t s = 0; s < n; ++s)
             if (lvl[s] >= l)
                 delta_p_one(p, xs, lam, noff, nidx, s, dp + 3 * s);
+#pragma omp parallel for schedule(static)
         for (int32_t s = 0; s < n; ++s)
             if (lvl[s] >= l) {
                 xs[3 * s + 0] += dp[3 * s + 0];
@@ -1096,13 +1126,19 @@ int orc_density_stats(const orc_params *p, int32_t n, const float *x, double *rh
     }
     for (size_t k = 0; k < 3 * (size_t)n; ++k)
         xd[k] = (double)x[k];
+    double *rho_all = rho_out ? rho_out : (double *)malloc(sizeof(double) * (size_t)n);
+    if (!rho_all) {
+        free(xd);
+        free(off);
+        free(idx);
+        return -3;
+    }
+#pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < n; ++i)
+        orc_constraint(p, n, xd, off, idx, i, &rho_all[i], NULL, NULL, NULL);
     double s_abs = 0.0, s_max = 0.0, s_sgn = 0.0, s_pos = 0.0;
     for (int32_t i = 0; i < n; ++i) {
-        double rho;
-        orc_constraint(p, n, xd, off, idx, i, &rho, NULL, NULL, NULL);
-        if (rho_out)
-            rho_out[i] = rho;
-        double e = rho / (double)p->rho0 - 1.0;
+        double e = rho_all[i] / (double)p->rho0 - 1.0;
         s_abs += fabs(e);
         if (fabs(e) > s_max)
             s_max = fabs(e);
@@ -1113,6 +1149,8 @@ int orc_density_stats(const orc_params *p, int32_t n, const float *x, double *rh
     stats[1] = s_max;
     stats[2] = s_sgn / n;
     stats[3] = s_pos / n;
+    if (rho_all != rho_out)
+        free(rho_all);
     free(xd);
     free(off);
     free(idx);

@@ -180,6 +180,11 @@ int orc_xsph(const orc_params *p, int32_t n, const double *xs, const double *v,
    the order of the input. */
 int orc_step(const orc_params *p, int32_t n, float *x, float *v, int32_t *id, orc_record *rec);
 
+/* Threads of the per-particle loops (OpenMP; <= 0 keeps the current count).
+   Returns the count now in use (1 when built without OpenMP). Results are
+   bit-identical at any thread count. */
+int orc_set_threads(int32_t nthreads);
+
 /* Density diagnostic at the given positions (fresh neighbour search):
    stats = {mean |rho/rho0-1|, max |rho/rho0-1|, mean (rho/rho0-1), mean max(0, rho/rho0-1)}. */
 int orc_density_stats(const orc_params *p, int32_t n, const float *x, double *rho, double stats[4]);

@@ -461,3 +461,28 @@ def test_finished_neighbour_enters_with_its_last_lambda(mode, name):
     others = [expect[nm][0] for nm in expect if nm != name]
     # the readings are told apart by far more than the 1e-5 h position tolerance
     assert min(abs(ea - o) for o in others) > 1e-5 * H
+
+
+def test_thread_count_does_not_change_any_bit():
+    """The per-particle loops run on OpenMP threads; every particle's own sums
+    keep their order, so a step, the neighbour lists and the density
+    statistics are bit-identical at any thread count."""
+    cfg = S.config_dam_break_4k().replace(lattice=(14, 12, 10), lod_mode=S.LOD_DTC, n_min=2, n_max=6,
+                                          camera="fixed", eye=(-1.0, 0.3, 0.3))
+    x, v = S.make_scene(cfg)
+    p = O.make_params(cfg, rho0=O.rest_density(H, 1.0, 0.05), eye=cfg.eye)
+    before = O.set_threads(0)
+    try:
+        out = []
+        for t in (1, 4):
+            O.set_threads(t)
+            st = O.step(p, x, v, record=True, rec_iters=6, want_final64=True)
+            stats, rho = O.density_stats(p, st.x, want_rho=True)
+            out.append((st, stats, rho, O.neighbors(p, st.x)))
+        (a, sa, ra, na), (b, sb, rb, nb) = out
+        for k in ("x", "v", "ids", "lam", "rho", "xs", "x_final", "v_final", "nbr_off", "nbr_idx"):
+            assert np.array_equal(getattr(a, k), getattr(b, k), equal_nan=True), k
+        assert np.array_equal(sa, sb) and np.array_equal(ra, rb)
+        assert np.array_equal(na[0], nb[0]) and np.array_equal(na[1], nb[1])
+    finally:
+        O.set_threads(before)
