@@ -1,0 +1,79 @@
+"""Multi-step comparison of a CUDA run with the oracle by density statistics.
+
+A multi-step run is chaotic: FP32 and FP64 trajectories part within a few
+steps, so they are compared by statistics of |rho/rho0 - 1| per step (the
+average-density error Fig. 9 plots), each evaluated by the oracle's density
+diagnostic at the run's own positions:
+
+  mean   the mean |rho/rho0 - 1|; within 0.2 percentage points at every step.
+  p99    the robust maximum: the 99th percentile of |rho/rho0 - 1|, i.e. the
+         largest error once the 1 % most extreme particles are set aside. The
+         per-particle maximum itself belongs to whichever splash particle is
+         most isolated in each run (it saturates at 1 - W(0)/rho0 = 0.806) and
+         is printed, not compared.
+
+A percentile of a few thousand particles is itself noisy under chaos: two
+oracle runs whose positions differ by one unit in the last place per step
+give 99th percentiles up to 0.35 points apart at 4,096 particles after 20
+steps, and 0.02 points apart at 131,072 particles. So at small sizes the bar
+for p99 is 0.2 points plus that spread, measured beside the run by four
+oracle runs whose positions are nudged by one unit in the last place after
+every step, each with its own seed (the running maximum of their distance
+from the plain oracle); at benchmark
+sizes (strict=True) the bar is 0.2 points, for p99 and the 99.9th percentile.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_1608_04721_gb300 import apbf
+
+BAR = 0.002  # 0.2 percentage points
+ENSEMBLE = 4
+
+
+def tail_stats(p, x) -> np.ndarray:
+    """[mean, 99th percentile, 99.9th percentile, max] of |rho/rho0 - 1| at x."""
+    _, rho = oracle.density_stats(p, x, want_rho=True)
+    e = np.abs(rho / float(p.rho0) - 1.0)
+    return np.array([e.mean(), np.quantile(e, 0.99), np.quantile(e, 0.999), e.max()])
+
+
+def _nudge(x: np.ndarray, rng) -> np.ndarray:
+    y = x.copy()
+    m = rng.random(y.shape) < 0.5
+    y[m] = np.nextafter(y[m], np.float32(np.inf))
+    return y
+
+
+def compare_runs(scene, p, x, v, steps: int, *, strict: bool = False):
+    """Step the CUDA scene and the oracle `steps` times from (x, v); assert the
+    statistics above at every step. Returns (gpu, oracle) statistics per step."""
+    xo, vo, io = x, v, None
+    nudged = [] if strict else [[x, v, None, np.random.default_rng(12345 + k)] for k in range(ENSEMBLE)]
+    g_all, o_all, env = [], [], np.zeros(4)
+    for k in range(steps):
+        apbf.apbf_step(scene, 1)
+        pos = apbf.apbf_read_state(scene, pos=True, vel=False)["pos"]
+        st = oracle.step(p, xo, vo, io)
+        xo, vo, io = st.x, st.v, st.ids
+        g, o = tail_stats(p, pos), tail_stats(p, xo)
+        for q in nudged:
+            sq = oracle.step(p, q[0], q[1], q[2])
+            q[0], q[1], q[2] = _nudge(sq.x, q[3]), sq.v, sq.ids
+            env = np.maximum(env, np.abs(tail_stats(p, q[0]) - o))
+        g_all.append(g)
+        o_all.append(o)
+        print(f"step {k + 1}: mean {g[0]:.5f}/{o[0]:.5f} p99 {g[1]:.4f}/{o[1]:.4f} "
+              f"p99.9 {g[2]:.4f}/{o[2]:.4f} max {g[3]:.4f}/{o[3]:.4f} (gpu/oracle)"
+              + ("" if strict else f" chaos spread p99 {env[1]:.4f}"))
+        assert abs(g[0] - o[0]) <= BAR, f"step {k + 1}: mean |rho/rho0-1| {g[0]:.5f} vs {o[0]:.5f}"
+        assert abs(g[1] - o[1]) <= BAR + env[1], f"step {k + 1}: p99 {g[1]:.5f} vs {o[1]:.5f}"
+        if strict:
+            assert abs(g[2] - o[2]) <= BAR, f"step {k + 1}: p99.9 {g[2]:.5f} vs {o[2]:.5f}"
+    # the CUDA density diagnostic at the CUDA run's positions agrees far more tightly
+    same = oracle.density_stats(p, pos)
+    got = apbf.apbf_density_stats(scene)
+    assert np.allclose(got, same, rtol=1e-5, atol=1e-6), (got, same)
+    return np.array(g_all), np.array(o_all)

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_1608_04721_gb300 import apbf, build, scenes
+from tests.multistep import compare_runs
 from tests.test_gpu_parity import check_final, check_stages, rest_density
 
 pytestmark = pytest.mark.gpu
@@ -112,17 +113,11 @@ def test_obstacles_in_a_batch_match_each_scene_alone_bitwise():
 
 
 def test_prestabilisation_multi_step_statistics_match_oracle():
+    """12 steps with obstacles and pre-stabilisation below level 5, compared by
+    density statistics per step (tests/multistep.py)."""
     cfg = _dam(lattice=(20, 20, 13), lod_mode=scenes.LOD_DTC, n_min=2, n_max=7, stabil_s=5, stabil_iters=2)
     scene, p, x, v = make(cfg, OBST)
-    xo, vo, ids = x, v, None
-    diffs = []
-    for k in range(12):
-        apbf.apbf_step(scene, 1)
-        st = oracle.step(p, xo, vo, ids)
-        xo, vo, ids = st.x, st.v, st.ids
-        diffs.append(abs(apbf.apbf_density_stats(scene)[0] - oracle.density_stats(p, xo)[0]))
-    assert max(diffs) <= 0.002, diffs
-
+    compare_runs(scene, p, x, v, 12)
 
 def test_obstacle_arguments_are_validated():
     cfg = _dam()

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from paper_1608_04721_gb300 import apbf, build, scenes
+from tests.multistep import compare_runs
 
 pytestmark = pytest.mark.gpu
 
@@ -241,31 +242,22 @@ def test_checkpoint_resume_is_bitwise():
 
 def test_multi_step_density_statistics_match_oracle():
     """20 steps of the 4096-particle dam break (chaotic, so compared by
-    statistics): at every step the mean |rho/rho0 - 1| of the GPU run and of
-    the oracle run agree within 0.2 percentage points, hence so does its
-    maximum over time (Fig. 9's worst average-density deviation). The
-    per-particle maximum of a single step belongs to whichever splash
-    particle is most isolated in each run; it is reported, not compared."""
+    statistics, tests/multistep.py): mean |rho/rho0 - 1| within 0.2 points
+    at every step and its 99th percentile (the robust maximum) within 0.2
+    points plus the chaotic spread of the oracle itself."""
     cfg = scenes.config_dam_break_4k()
     scene, p, x, v = make(cfg)
-    xo, vo, ids = x, v, None
-    g_series, o_series = [], []
-    for k in range(cfg.steps):
-        apbf.apbf_step(scene, 1)
-        st = oracle.step(p, xo, vo, ids)
-        xo, vo, ids = st.x, st.v, st.ids
-        g_series.append(apbf.apbf_density_stats(scene))
-        o_series.append(oracle.density_stats(p, xo))
-    g, o = np.array(g_series), np.array(o_series)
-    diff = np.abs(g[:, 0] - o[:, 0])
-    print("mean |rho/rho0-1| per step: gpu", np.round(g[:, 0], 5), "oracle", np.round(o[:, 0], 5))
-    print("per-particle max at the last step: gpu %.4f oracle %.4f" % (g[-1, 1], o[-1, 1]))
-    assert diff.max() <= 0.002, diff
+    g, o = compare_runs(scene, p, x, v, cfg.steps)
     assert abs(g[:, 0].max() - o[:, 0].max()) <= 0.002
-    # the GPU diagnostic at identical positions agrees far more tightly
-    pos = apbf.apbf_read_state(scene, pos=True, vel=False)["pos"]
-    same = oracle.density_stats(p, pos)
-    assert np.allclose(g[-1], same, rtol=1e-5, atol=1e-6), (g[-1], same)
+
+
+def test_multi_step_density_statistics_131k():
+    """12 steps of the 131,072-particle APBF dam break (N_i 5..10, camera 4 m
+    outside the end wall, dt = 1/60 s) against the oracle: mean, 99th and
+    99.9th percentile of |rho/rho0 - 1| within 0.2 points at every step."""
+    cfg = scenes.config_dam_break_131k()
+    scene, p, x, v = make(cfg)
+    compare_runs(scene, p, x, v, 12, strict=True)
 
 
 def test_empty_scene():
