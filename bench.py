@@ -41,8 +41,27 @@ UNIT = "ms/step"
 FP32_LANES_PER_SM = 128
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# algorithmic FP32 operations per in-range neighbour pair (sqrt and divide count 1)
-FLOPS_PER_PAIR = {"lambda": 25, "deltap": 28, "finalize": 26}
+# algorithmic FP32 operations per in-range neighbour pair, the hot-path scope's
+# figures: lambda ~30 (difference, r^2, poly6, spiky, the gradient and |grad|^2
+# sums), delta-p ~35 plus one sqrt (spiky, poly6 for s_corr, its 4th power, the
+# scaled vector sum); XSPH counted as in the kernel table (difference, r^2, W,
+# neighbour velocity, difference x W, sum)
+FLOPS_PER_PAIR = {"lambda": 30, "deltap": 36, "finalize": 26}
+# algorithmic bytes per unit of the HBM-bound stages (each distinct array
+# element read or written once per launch): unit "particle" or "cell"
+STAGE_BYTES = {
+    "lod_range": (16, "particle", "x read"),
+    "predict": (41, "particle", "x, v read (32 B); key, slot, level written (9 B)"),
+    "scan": (12, "cell", "counts read, starts written, counts zeroed"),
+    "scatter": (16, "particle", "key, slot read; start gathered; id written"),
+    "reorder": (102, "particle", "45 B read (x, v, id, level, key, slot), 57 B written (records, x*, ids, levels, cells)"),
+    "levels": (9, "particle", "level read twice, active index written"),
+    "finalize": (76, "particle", "records, start positions read; x, v, id written (own particle; "
+                                 "neighbour records via cache)"),
+}
+# per-step device state of one scene, for the L2 decision (neighbour lists at
+# 128 entries dominate): an estimate shared by both arms of the benchmark
+STATE_BYTES_PER_PARTICLE = 660
 STAGE_NAMES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
                "finalize", "prestab"]
 
@@ -200,10 +219,26 @@ L2_BYTES = 129 * 2 ** 20
 _flush_buf = None
 
 
-def needs_flush(apbf, scene_bytes: int) -> bool:
-    """A scene whose arena is below 4x the L2 could be served from L2 across
-    steps; such scenes are timed step by step with an L2 flush in between."""
-    return scene_bytes < 4 * L2_BYTES
+def needs_flush(n_particles: int) -> bool:
+    """A scene whose per-step state is below 4x the L2 could be served from L2
+    across steps; such scenes are timed step by step with an L2 flush in between."""
+    return n_particles * STATE_BYTES_PER_PARTICLE < 4 * L2_BYTES
+
+
+def l2_note(n_particles: int) -> str:
+    if needs_flush(n_particles):
+        return ("flushed between timed steps (4x L2 written outside the timed intervals): per-step state "
+                f"~{n_particles * STATE_BYTES_PER_PARTICLE / 1e6:.0f} MB")
+    return (f"no flush: per-step state ~{n_particles * STATE_BYTES_PER_PARTICLE / 1e6:.0f} MB, over 4x the "
+            "129 MB L2")
+
+
+def workload_config(cfg, pbf_n: int, ws: int) -> dict:
+    """The `config` of the JSON line, identical for the CUDA arm and the
+    reference (oracle) arm of the same workload."""
+    return {"workload": cfg.name, "particles": cfg.n, "n_range": f"{cfg.n_min}..{cfg.n_max}",
+            "lod": "distance to camera, automatic range", "pbf_n": pbf_n,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "l2": l2_note(cfg.n)}
 
 
 def flush_l2(torch):
@@ -286,6 +321,31 @@ LIMITER_NOTE = ("L1 throughput: ncu puts the dense solver passes at 88-91 % of t
                 "(profiles/solver_kernels_apbf_ocean_1048576.md)")
 
 
+def hbm_peak():
+    """(GB/s, source) from the measured peaks file, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy kernel)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no measured peak found)"
+
+
+def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int) -> dict:
+    """Achieved HBM fraction of each HBM-bound stage: its algorithmic bytes per
+    step (STAGE_BYTES x particles or cells) over its CUDA-event time per step."""
+    peak, src = hbm_peak()
+    out = {"peak_gbs": peak, "peak_source": src, "stages": {}}
+    for name, (bpu, unit, what) in STAGE_BYTES.items():
+        t = stage_ms.get(name, 0.0)
+        if t <= 0.0:
+            continue
+        units = n_particles if unit == "particle" else n_cells
+        gbs = bpu * units / (t * 1e-3) / 1e9
+        out["stages"][name] = {"bytes_per_" + unit: bpu, "units": units, "us_per_step": t * 1e3,
+                               "achieved_gbs": gbs, "frac": gbs / peak, "bytes": what}
+    return out
+
+
 def kernel_source_digest(src: str | None = None) -> str:
     """First 16 hex digits of the sha256 of kernels.cu (or of the source text
     given) without its comments and blank lines: a change to the code
@@ -314,85 +374,41 @@ def read_traffic(kernel: str, workload_name: str):
     return None
 
 
-def cpu_baseline(cfg, n_full, budget_s=20.0):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload: the bottom z-layers of the same block (same basin, camera,
-    wall, LOD range), one step, time scaled by particles to the full scene."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_step_ms(oracle, cfg, rho0, step: int, threads: int, x=None, v=None, ids=None):
+    """One oracle step of the whole workload at the given thread count; the
+    camera and wall of the given step. Returns (ms, threads used, state)."""
+    used = oracle.set_threads(threads)
+    if x is None:
+        x, v = scenes.make_scene(cfg)
+    eye, _ = scenes.camera_at(cfg, step)
+    lo, hi = scenes.box_at(cfg, step)
+    p = oracle.make_params(cfg, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi)
+    t0 = time.perf_counter()
+    st = oracle.step(p, x, v, ids)
+    return (time.perf_counter() - t0) * 1e3, used, (st.x, st.v, st.ids)
+
+
+def cpu_baseline(cfg):
+    """The oracle as it stands on the host cores: one step of the whole
+    workload (every particle, no extrapolation) on all cores, and one on a
+    single thread."""
     import oracle
 
     rho0 = float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
-    nx, ny, nz = cfg.lattice
-    layers = max(1, nz // 4)
-    sub = cfg.replace(lattice=(nx, ny, layers))
-    x, v = scenes.make_scene(sub)
-    eye, _ = scenes.camera_at(cfg, 0)
-    lo, hi = scenes.box_at(cfg, 0)
-    p = oracle.make_params(sub, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi)
-    t0 = time.perf_counter()
-    oracle.step(p, x, v)
-    dt = time.perf_counter() - t0
-    scale = n_full / sub.n
-    return {"value": dt * 1e3 * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle step of {sub.n} of the {n_full} particles (bottom {layers} of {nz} lattice "
-                      f"layers, same basin, camera, wall and N_i range), time x {scale:g}",
-            "sample_seconds": dt}
-
-
-# Table 1 of the paper: frame time improvement T_PBF(N_max)/T_APBF - 1 on the GTX 680 / HD7850,
-# per scenario, for the DTC and DTVS models (the paper's GPUs and scenes, not these analogues).
-PAPER_TABLE1 = {
-    "dam_break_216k": {"pbf_n": (3, 6), "dtc": (0.63, 0.53), "dtvs": (0.70, 0.59)},
-    "double_dam_break_673k": {"pbf_n": (5, 10), "dtc": (0.70, 0.64), "dtvs": (0.77, 0.69)},
-    "multi_dam_break_225k": {"pbf_n": (4, 8), "dtc": (0.42, 0.40), "dtvs": (0.59, 0.46)},
-}
-
-
-def run_table1(args, apbf, torch, d):
-    """Analogues of the three scenarios of Table 1, each as PBF with N_min and
-    with N_max iterations, APBF with the DTC model and with the DTVS model
-    (its depth image rendered here, 1280x720), on identical inputs and
-    drivers; improvement = T_PBF(N_max) / T_APBF - 1 as in Table 1."""
-    steps = min(args.steps, 300)
-    rows = {}
-    for name in PAPER_TABLE1:
-        base = scenes.CONFIGS[name]()
-        rho0 = float(np.float32(apbf.apbf_rest_density(base.h, base.mass, base.spacing)))
-        variants = {
-            "pbf_nmin": base.replace(lod_mode=scenes.LOD_FIXED, n_min=base.n_min, n_max=base.n_min, stabil_s=1),
-            "pbf_nmax": base.replace(lod_mode=scenes.LOD_FIXED, n_min=base.n_max),
-            "apbf_dtc": base,
-            "apbf_dtvs": base.replace(lod_mode=scenes.LOD_DTVS),
-        }
-        scene_bytes = apbf.apbf_scene_bytes(apbf.desc_from_config(base, *scenes.make_scene(base), rho0))
-        flush = needs_flush(apbf, scene_bytes)
-        row = {"particles": base.n, "n_range": f"{base.n_min}..{base.n_max}", "arena_mb": scene_bytes / 1e6,
-               "l2_flushed": flush}
-        for key, cfg in variants.items():
-            sc_ = make_scene(apbf, cfg, rho0)
-            tot, per, _ = timed_run(apbf, torch, sc_, cfg, args.warmup, steps, flush=flush)
-            ms = d.max(tot / steps)
-            row[key] = {"ms_per_step": ms, "p99_ms": metrics.percentile(per, 99),
-                        "mean_abs_density_error": float(apbf.apbf_density_stats(sc_)[0])}
-            apbf.apbf_destroy_scene(sc_)
-        t = row["pbf_nmax"]["ms_per_step"]
-        row["improvement_dtc"] = metrics.improvement(t, row["apbf_dtc"]["ms_per_step"])
-        row["improvement_dtvs"] = metrics.improvement(t, row["apbf_dtvs"]["ms_per_step"])
-        row["paper"] = PAPER_TABLE1[name]
-        rows[name] = row
-        print(f"{name:24s} PBF{base.n_min}: {row['pbf_nmin']['ms_per_step']:.3f} ms  "
-              f"PBF{base.n_max}: {t:.3f} ms  DTC: {row['apbf_dtc']['ms_per_step']:.3f} ms "
-              f"({100 * row['improvement_dtc']:+.0f} %)  DTVS: {row['apbf_dtvs']['ms_per_step']:.3f} ms "
-              f"({100 * row['improvement_dtvs']:+.0f} %)", file=sys.stderr, flush=True)
-    line = {"metric": "Table 1 analogue: ms/step of PBF N_min, PBF N_max, APBF DTC and DTVS; "
-                      "improvement T_PBF(N_max)/T_APBF - 1", "value": None, "unit": "ms/step", "n_gpus": d.ws,
-            "steps": steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "table1_analogues", "dtvs_view": "1280x720, 60 degree vertical field of view",
-                       "tuning": "defaults (block 256, compacted levels)"},
-            "scenarios": rows}
-    if d.rank == 0:
-        print(json.dumps(line), flush=True)
-    d.close()
-    return 0
+    ms_all, used, _ = oracle_step_ms(oracle, cfg, rho0, 0, host_cores())
+    ms_one, _, _ = oracle_step_ms(oracle, cfg, rho0, 0, 1)
+    oracle.set_threads(host_cores())
+    return {"value": ms_all, "unit": UNIT, "cores": used, "kind": "oracle", "nproc": host_cores(),
+            "sample": f"one oracle step of the whole workload ({cfg.n} particles, first step's camera and wall), "
+                      f"OpenMP over particles on {used} threads",
+            "single_thread": {"value": ms_one, "unit": UNIT, "cores": 1}}
 
 
 def tune_summary(res):
@@ -717,44 +733,44 @@ def run_reference(args):
     if args.workload == "serve":
         return run_reference_serve(args, ws)
     cfg = workload(args.workload, "apbf")
+    pbf_cfg = workload(args.workload, "pbf")
     import oracle
 
     rho0 = float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
-    nx, ny, nz = cfg.lattice
-    # calibrate on one layer, then size the sample so W + K steps take ~budget
-    budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "150"))
-    cal = cfg.replace(lattice=(nx, ny, 1))
-    xc, vc = scenes.make_scene(cal)
-    eye, _ = scenes.camera_at(cfg, 0)
-    lo, hi = scenes.box_at(cfg, 0)
-    t0 = time.perf_counter()
-    oracle.step(oracle.make_params(cal, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi), xc, vc)
-    per_layer = max(time.perf_counter() - t0, 1e-4)
-    layers = int(max(1, min(nz, budget / max(1, args.steps + args.warmup) / per_layer)))
-    sub = cfg.replace(lattice=(nx, ny, layers))
-    x, v = scenes.make_scene(sub)
-    ids = np.arange(sub.n, dtype=np.int32)
+    budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "240"))
+    cores = host_cores()
+    # calibrate with one full step; the timed steps continue the trajectory from its state
+    ms0, used, state = oracle_step_ms(oracle, cfg, rho0, 0, cores)
+    full = (args.steps + args.warmup) * ms0 * 1e-3 <= budget
+    sub, scale = cfg, 1.0
+    if not full:
+        # W + K whole steps would not fit the budget: the bottom lattice layers of the same scene
+        nx, ny, nz = cfg.lattice
+        layers = int(max(1, min(nz, nz * budget / ((args.steps + args.warmup) * ms0 * 1e-3))))
+        sub = cfg.replace(lattice=(nx, ny, layers))
+        scale = cfg.n / sub.n
+        state = (None, None, None)
+    x, v, ids = state
     times = []
     for s in range(args.warmup + args.steps):
-        eye, _ = scenes.camera_at(cfg, s)
-        lo, hi = scenes.box_at(cfg, s)
-        p = oracle.make_params(sub, rho0=rho0, eye=eye, box_lo=lo, box_hi=hi)
-        t0 = time.perf_counter()
-        st = oracle.step(p, x, v, ids)
-        dt = time.perf_counter() - t0
-        x, v, ids = st.x, st.v, st.ids
+        ms, _, (x, v, ids) = oracle_step_ms(oracle, sub, rho0, s + (1 if full else 0), cores, x, v, ids)
         if s >= args.warmup:
-            times.append(dt * 1e3 * cfg.n / sub.n)
+            times.append(ms * scale)
     value = float(np.mean(times))
-    sample = (f"each step: one oracle step of {sub.n} of the {cfg.n} particles (bottom {layers} of {nz} lattice "
-              f"layers, same basin, camera, wall and N_i range), time x {cfg.n / sub.n:g}")
+    if full:
+        sample = (f"each step: one oracle step of the whole workload ({cfg.n} particles, the trajectory's camera "
+                  f"and wall), OpenMP over particles on {used} threads")
+    else:
+        sample = (f"each step: one oracle step of {sub.n} of the {cfg.n} particles (bottom {sub.lattice[2]} of "
+                  f"{cfg.lattice[2]} lattice layers, same basin, camera, wall and N_i range) on {used} threads, "
+                  f"time x {scale:g}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "particles": cfg.n, "n_range": f"{cfg.n_min}..{cfg.n_max}",
-                       "lod": "distance to camera"},
+            "config": workload_config(cfg, pbf_cfg.n_max, ws),
             "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "nproc": cores,
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -863,8 +879,6 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-particles", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--table1", action="store_true",
-                    help="time the analogues of the three scenarios of the paper's Table 1 instead")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pbf", action="store_true")
@@ -884,8 +898,6 @@ def main():
     torch.cuda.set_device(d.local)
     build.build()
     apbf.lib()
-    if args.table1:
-        return run_table1(args, apbf, torch, d)
     if args.workload == "batch_256":
         return run_batch(args, apbf, torch, d)
     if args.workload == "serve":
@@ -895,8 +907,7 @@ def main():
     rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))
 
     dtvs_cfg = workload(args.workload, "dtvs")
-    scene_bytes = apbf.apbf_scene_bytes(apbf.desc_from_config(cfg, *scenes.make_scene(cfg), rho0))
-    flush = needs_flush(apbf, scene_bytes)
+    flush = needs_flush(cfg.n)
     scene = make_scene(apbf, cfg, rho0)
     pbf = None if args.no_pbf else make_scene(apbf, pbf_cfg, rho0)
     dtvs = None if args.no_dtvs else make_scene(apbf, dtvs_cfg, rho0)
@@ -1011,19 +1022,16 @@ def main():
                 "flops_per_pair": FLOPS_PER_PAIR[top], "pairs_per_launch": pairs / launches,
                 "avg_launch_us": avg_launch_s * 1e6}
     particle_iters_per_step = iters / args.profile_steps
+    dims = apbf.apbf_debug_dims(scene)[0]
+    stage_hbm = stage_roofline(stage_ms, cfg.n, int(dims[0]) * int(dims[1]) * int(dims[2]))
     value = ms_step
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": cfg.name, "particles": cfg.n, "n_range": f"{cfg.n_min}..{cfg.n_max}",
-                   "lod": "distance to camera, automatic range", "pbf_n": pbf_cfg.n_max,
-                   "parallelism": f"replicas x{d.ws}" if d.ws > 1 else "single GPU",
-                   "l2": (f"flushed between timed steps (4x L2 written outside the timed intervals): scene arena "
-                          f"{scene_bytes / 1e6:.0f} MB" if flush else
-                          f"no flush: scene arena {scene_bytes / 1e6:.0f} MB, over 4x the 129 MB L2"),
-                   "launch": "captured CUDA graph per step",
-                   "tuning": tuning or "defaults (block 256, compacted levels)"},
+        "config": workload_config(cfg, pbf_cfg.n_max, d.ws),
+        "launch": "captured CUDA graph per step",
+        "tuning": tuning or "defaults (block 256, compacted levels)",
         "p50_ms": metrics.percentile(per, 50), "p99_ms": metrics.percentile(per, 99),
         "particle_iterations_per_step": particle_iters_per_step,
         "particle_iterations_per_s": d.sum(particle_iters_per_step / (ms_step * 1e-3)),
@@ -1037,6 +1045,7 @@ def main():
                              if pbf_line and dtvs_line else None),
         "roofline": roofline,
         "stage_ms_per_step": stage_ms,
+        "stage_roofline": stage_hbm,
         "e2e": e2e,
         "gpu_launches": kernels_per_step(cfg) * args.steps,
         "clocks": clock_info,
@@ -1045,7 +1054,7 @@ def main():
         line["density"]["pbf_nmax"] = pbf_line["density"]
         line["density"]["mean_abs_diff_points"] = 100 * abs(apbf_density[0] - pbf_line["density"][0])
     if d.rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, cfg.n)
+        line["cpu_baseline"] = cpu_baseline(cfg)
     apbf.apbf_destroy_scene(scene)
     if pbf is not None:
         apbf.apbf_destroy_scene(pbf)

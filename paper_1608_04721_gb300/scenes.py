@@ -5,11 +5,10 @@ parameters, and per-step scene drivers (camera path, moving wall). It holds
 none of the solver's arithmetic (no kernels, no densities, no constraints), so
 both the CUDA path and the CPU oracle can take their inputs from it.
 
-The paper publishes no scene geometry (Sec. 7 names a dam break of 216k
-particles, a double dam break of 673k and a multi dam break of 225k, and gives
-only particle counts and iteration ranges, Table 1). The scenes below are
-synthetic stand-ins of the same kind and size class: dam-break blocks on a
-lattice of spacing h/2 with uniform jitter, in an axis-aligned box.
+The paper publishes no scene geometry (Sec. 7 gives only particle counts and
+iteration ranges, Table 1). The scenes below are synthetic stand-ins of the
+same kind and size class: dam-break blocks on a lattice of spacing h/2 with
+uniform jitter, in an axis-aligned box.
 
 Random numbers come from a counter-based generator: draw k of stream s is
 ``splitmix64(seed + (k + 1) * GOLDEN + s * STREAM)`` where splitmix64 is the
@@ -134,29 +133,6 @@ def config_ocean_1m(lod_mode: int = LOD_DTC, n_min: int = 3, n_max: int = 15) ->
                        camera="spline", wall="oscillate_xlo")
 
 
-def config_dam_break_216k(lod_mode: int = LOD_DTC, n_min: int = 3, n_max: int = 6) -> SceneConfig:
-    """Analogue of the paper's dam break (Sec. 7.1): one 60x60x60 block
-    (216,000 particles, 3 m cube) in the corner of a 6.4x3.2x3.2 m box, camera
-    4 m outside the x = 0 end wall, N_i in 3..6, time step 0.0016 s."""
-    return SceneConfig(name="apbf_dam_break_216000", lattice=(60, 60, 60), spacing=0.05,
-                       block_lo=(0.0, 0.0, 0.0), box_lo=(0.0, 0.0, 0.0), box_hi=(6.4, 3.2, 3.2),
-                       n_min=n_min, n_max=n_max, lod_mode=lod_mode, steps=300, dt=0.0016,
-                       camera="fixed", eye=(-4.0, 1.6, 1.6), target=(3.2, 1.6, 1.0))
-
-
-def config_double_dam_break_673k(lod_mode: int = LOD_DTC, n_min: int = 5, n_max: int = 10) -> SceneConfig:
-    """Analogue of the paper's double dam break (Sec. 7.2): two 58x58x100
-    columns (672,800 particles) of an inviscid fluid (no XSPH) at the two ends
-    of a 12.8x3.2x6.4 m box, collapsing into each other; camera beside the box
-    looking at its middle, N_i in 5..10, time step 0.0016 s."""
-    w = 58 * 0.05
-    return SceneConfig(name="apbf_double_dam_break_672800", lattice=(58, 58, 100), spacing=0.05,
-                       block_lo=(0.0, 0.0, 0.0), blocks=((0.0, 0.0, 0.0), (12.8 - w, 0.0, 0.0)),
-                       box_lo=(0.0, 0.0, 0.0), box_hi=(12.8, 3.2, 6.4), xsph_c=0.0,
-                       n_min=n_min, n_max=n_max, lod_mode=lod_mode, steps=300, dt=0.0016,
-                       camera="fixed", eye=(6.4, -6.0, 4.0), target=(6.4, 1.6, 1.5))
-
-
 def config_multi_dam_break_225k(lod_mode: int = LOD_DTC, n_min: int = 4, n_max: int = 8) -> SceneConfig:
     """Analogue of the paper's multi dam break (Sec. 7.3): four blocks of
     38x38x39 particles (225,264 in all) in the corners of a 6.4x6.4x3.2 m box
@@ -230,8 +206,6 @@ CONFIGS = {
     "dam_break_131k": config_dam_break_131k,
     "ocean_1m": config_ocean_1m,
     "multi_dam_break_225k": config_multi_dam_break_225k,
-    "dam_break_216k": config_dam_break_216k,
-    "double_dam_break_673k": config_double_dam_break_673k,
 }
 
 

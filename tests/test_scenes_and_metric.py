@@ -83,6 +83,45 @@ def test_traffic_capture_digest_ignores_comments_only():
     assert bench.kernel_source_digest(src.replace("/* one */", "/* a longer\n comment */")) == base
     assert bench.kernel_source_digest(src.replace("1.0f", "2.0f")) != base
     assert bench.kernel_source_digest(src.replace("x[0]", "x[1]")) != base
-    # the committed capture matches the committed kernels
-    assert bench.read_traffic("lambda_kernel", "apbf_ocean_1048576") is not None
-    assert bench.read_traffic("deltap_kernel", "apbf_ocean_1048576") is not None
+
+
+
+def test_traffic_from_a_stale_or_missing_capture_is_null(tmp_path, monkeypatch):
+    """A traffic figure counts only for the kernel source it was captured on:
+    a capture of other code, or none at all, reads as traffic null."""
+    import bench
+
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_1608_04721_gb300" / "csrc").mkdir(parents=True)
+    (tmp_path / "paper_1608_04721_gb300" / "csrc" / "kernels.cu").write_text("__global__ void k() {}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.read_traffic("lambda_kernel", "w") is None
+    digest = bench.kernel_source_digest()
+    (tmp_path / "profiles" / "traffic_w.txt").write_text(
+        f"# header\nlambda_kernel dram_bytes_per_launch=123 source={digest}\n"
+        "deltap_kernel dram_bytes_per_launch=456 source=0000000000000000\n")
+    assert bench.read_traffic("lambda_kernel", "w") == 123.0
+    assert bench.read_traffic("deltap_kernel", "w") is None
+
+
+def test_reference_arm_runs_the_whole_workload_with_the_same_config():
+    """bench.py --impl reference times the oracle on every particle of the
+    workload (no extrapolation when W + K steps fit its budget) and reports
+    the CUDA arm's config dict."""
+    import json
+    import subprocess
+    import sys
+
+    import bench
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "dam_break_4k",
+                          "--steps", "2", "--warmup", "3"], cwd=root, capture_output=True, text=True, timeout=600,
+                         check=True)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    cfg = bench.workload("dam_break_4k", "apbf")
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["config"] == bench.workload_config(cfg, bench.workload("dam_break_4k", "pbf").n_max, 1)
+    assert "whole workload" in line["cpu_baseline"]["sample"] and "x " not in line["cpu_baseline"]["sample"]
+    assert line["cpu_baseline"]["cores"] >= 1 and line["value"] > 0
+    assert line["e2e"]["value"] == line["value"]
