@@ -239,12 +239,21 @@ apbf_status fail(apbf_status st, const std::string &m)
 
 // The device address of the static scratch array on the current device,
 // looked up once per device (the host-side symbol is not a device address).
-apbf_status scratch_for_current_device(uint32_t **out)
+// The stream must belong to that device: its kernels would otherwise run on
+// the stream's device against an address taken on another.
+apbf_status scratch_for_current_device(cudaStream_t stream, uint32_t **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return fail(APBF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    int sdev = -1;
+    e = cudaStreamGetDevice(stream, &sdev);
+    if (e != cudaSuccess)
+        return fail(APBF_ERR_INVALID_ARG, std::string("cuda_stream: ") + cudaGetErrorString(e));
+    if (sdev != dev)
+        return fail(APBF_ERR_INVALID_ARG, "cuda_stream belongs to device " + std::to_string(sdev) +
+                                              ", not to the current device " + std::to_string(dev));
     if (dev < 0 || dev >= 64)
         return fail(APBF_ERR_NOT_SUPPORTED, "device ordinal above 63");
     std::lock_guard<std::mutex> lock(g_setup_mu);
@@ -277,6 +286,8 @@ extern "C" APBF_API apbf_status apbf_density_stats_static(const float *pos, uint
     P.n = n;
     P.inv_h = 1.0f / h;
     P.h2 = h * h;
+    if (!std::isfinite(P.inv_h) || !(P.h2 > 0.0f))
+        return fail(APBF_ERR_INVALID_ARG, "h is too small: 1/h or h*h is not a positive finite float");
     uint64_t ncell = 1;
     int dims[3];
     for (int a = 0; a < 3; ++a) {
@@ -285,7 +296,7 @@ extern "C" APBF_API apbf_status apbf_density_stats_static(const float *pos, uint
         volatile float ext = grid_hi[a] - grid_lo[a];
         volatile float t = ext * P.inv_h;
         const double fl = std::floor((double)t);
-        if (fl >= (double)kMaxCells)
+        if (!(fl >= 0.0 && fl < (double)kMaxCells))
             return fail(APBF_ERR_INVALID_ARG, "grid exceeds the static scratch maximum of " +
                                                   std::to_string(kMaxCells) + " cells");
         dims[a] = (int)fl + 1;
@@ -305,11 +316,11 @@ extern "C" APBF_API apbf_status apbf_density_stats_static(const float *pos, uint
     P.h6 = (float)(h2 * h2 * h2);
     P.rho0 = (double)rho0;
 
+    cudaStream_t s = (cudaStream_t)cuda_stream;
     uint32_t *sw = nullptr;
-    apbf_status st = scratch_for_current_device(&sw);
+    apbf_status st = scratch_for_current_device(s, &sw);
     if (st != APBF_OK)
         return st;
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     // the cell counts are the only scratch that must start at zero
     cudaError_t e = cudaMemsetAsync(sw + kCount, 0, 4 * (size_t)P.ncell, s);
     const unsigned nb = (n + kSB - 1) / kSB;
