@@ -83,6 +83,8 @@ def workload(name: str, lod: str):
         raise SystemExit(f"unknown workload {name}")
     if lod == "pbf":
         cfg = cfg.replace(lod_mode=scenes.LOD_FIXED, n_min=cfg.n_max)
+    elif lod == "pbf_nmin":
+        cfg = cfg.replace(lod_mode=scenes.LOD_FIXED, n_max=cfg.n_min, stabil_s=1)
     elif lod == "dtvs":
         cfg = cfg.replace(lod_mode=scenes.LOD_DTVS)
     return cfg
@@ -411,6 +413,20 @@ def cpu_baseline(cfg):
             "single_thread": {"value": ms_one, "unit": UNIT, "cores": 1}}
 
 
+def partition_scenes(sizes, ws: int):
+    """Particle-balanced split of independent scenes over ws ranks: largest
+    first, each to the rank with the fewest particles so far (ties to the
+    lower rank). Returns each rank's scene indices, ascending. No scene is
+    split and no data crosses ranks."""
+    load = [0] * ws
+    parts = [[] for _ in range(ws)]
+    for k in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(ws), key=lambda r: (load[r], r))
+        parts[r].append(k)
+        load[r] += sizes[k]
+    return [sorted(p) for p in parts]
+
+
 def tune_summary(res):
     return {"block": res["block"], "mask_threshold": res["mask_threshold"], "trial_ms": res["ms_per_step"],
             "candidates": len(res["trials"])}
@@ -421,9 +437,11 @@ def run_batch(args, apbf, torch, d):
     log-uniform in 2048..65536 particles, N_i in 4..8 by camera distance)
     stepped as one batch, one launch per stage over all scenes, against the
     same scenes stepped one at a time (one scene, one graph, per call).
-    Each rank steps its own batch (seeded by rank): weak scaling, no
-    collective on the data path."""
-    cfgs = scenes.config_batch_256(seed=1608_04721 + 7 * d.rank)
+    Under N ranks the 256 scenes are split by partition_scenes (whole scenes,
+    particle-balanced): strong scaling, no collective on the data path."""
+    all_cfgs = scenes.config_batch_256()
+    mine = partition_scenes([c.n for c in all_cfgs], d.ws)[d.rank]
+    cfgs = [all_cfgs[k] for k in mine]
     c0 = cfgs[0]
     rho0 = float(np.float32(apbf.apbf_rest_density(c0.h, c0.mass, c0.spacing)))
     descs = []
@@ -431,6 +449,7 @@ def run_batch(args, apbf, torch, d):
         x, v = scenes.make_scene(c)
         descs.append(apbf.desc_from_config(c, x, v, rho0))
     n_total = sum(c.n for c in cfgs)
+    n_job = int(d.sum(n_total))
     batch = apbf.apbf_create_batch(descs)
     for k, c in enumerate(cfgs):
         apbf.apbf_set_camera_at(batch, k, c.eye)
@@ -524,11 +543,13 @@ def run_batch(args, apbf, torch, d):
     line = {
         "metric": "batched APBF ms/step for 256 independent scenes vs one at a time", "value": ms_step,
         "unit": UNIT, "n_gpus": d.ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "apbf_batch_256", "scenes": len(cfgs), "particles": n_total,
+        "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "apbf_batch_256", "scenes": len(all_cfgs), "particles": n_job,
+                   "scenes_on_rank0": len(cfgs), "particles_on_rank0": n_total,
                    "particles_per_scene": f"log-uniform {min(c.n for c in cfgs)}..{max(c.n for c in cfgs)}",
                    "n_range": f"{c0.n_min}..{c0.n_max}", "lod": "distance to camera, automatic range per scene",
-                   "parallelism": f"one batch per rank x{d.ws}" if d.ws > 1 else "single GPU",
+                   "parallelism": (f"scenes split over {d.ws} ranks, particle-balanced" if d.ws > 1
+                                   else "single GPU"),
                    "l2": "no flush: each step touches > 1 GB (> 129 MB L2)",
                    "launch": "one captured CUDA graph per batch step", "tuning": tuning},
         "p50_ms": metrics.percentile(per, 50), "p99_ms": metrics.percentile(per, 99),
@@ -556,45 +577,38 @@ def run_batch(args, apbf, torch, d):
 SERVE_METRIC = "served APBF particle-steps/s, Poisson arrivals, budget-sized pool; queueing and latency"
 
 
-def run_serve(args, apbf, torch, d):
-    """Served scenes: Poisson arrivals (200/s) of dam breaks with 4096..262144
-    particles for 30..300 steps each (N_i in 5..10), admitted in arrival order
-    into one pool sized from an HBM budget, every resident scene stepped once
-    per tick. Runs for the arrival window on the wall clock; reports
-    throughput, queueing and latency. Each rank serves its own arrivals."""
-    temps = scenes.config_serve_templates()
-    arrivals = scenes.serve_arrivals(seconds=args.serve_seconds, templates=len(temps), seed=1608_04721 + 11 * d.rank)
-    c0 = temps[0]
-    rho0 = float(np.float32(apbf.apbf_rest_density(c0.h, c0.mass, c0.spacing)))
-    # the templates start at rest: no velocity arrays, so queued requests hold positions only
-    descs = [apbf.desc_from_config(c, scenes.make_scene(c)[0], None, rho0) for c in temps]
-    budget = int(args.serve_budget_gb * 1e9)
-    pool_bytes, cap_n, cap_c = apbf.apbf_server_bytes(descs[0], max_particles=args.serve_max_particles,
-                                                      budget_bytes=budget)
-    srv = apbf.apbf_server_create(descs[0], max_particles=args.serve_max_particles, budget_bytes=budget)
-    # warm-up: a few ticks of a few scenes (graph capture, first launches), then drain
-    for k in range(args.warmup):
+def _pct(v, q):
+    return metrics.percentile(v, q) if v else None
+
+
+def serve_pooled(apbf, torch, temps, descs, arrivals, seconds, budget, max_particles, target_ms, warmup):
+    """The serving loop on the wall clock for `seconds`: arrivals submitted as
+    their time comes, one tick (one batched step of every resident scene) after
+    another. Returns the run's statistics."""
+    srv = apbf.apbf_server_create(descs[0], max_particles=max_particles, budget_bytes=budget,
+                                  target_step_ms=target_ms)
+    pool_bytes, cap_n, cap_c = apbf.apbf_server_bytes(descs[0], max_particles=max_particles, budget_bytes=budget,
+                                                      target_step_ms=target_ms)
+    for k in range(warmup):  # graph capture, first launches; then drain
         apbf.apbf_server_submit(srv, descs[k % len(descs)], temps[k % len(temps)].eye, 3, want_pos=False)
     while True:
         info = apbf.apbf_server_tick(srv)
         if info["resident_scenes"] == 0 and info["queued"] == 0:
             break
+    iters0 = info["total_particle_iterations"]
     torch.cuda.synchronize()
-    d.barrier()
-    clocks = ClockSampler(torch.cuda.current_device())
     tick_start, infos, reqs = [], [], []
     ai = 0
     t0 = time.perf_counter()
     first_tick = None
-    h2d = d2h = 0
     idle = True
     while True:
         now = time.perf_counter() - t0
-        if now >= args.serve_seconds:
+        if now >= seconds:
             break
         if idle and (ai >= len(arrivals) or arrivals[ai][0] > now):
             # nothing resident or queued: wait for the next arrival instead of ticking empty
-            time.sleep(min(args.serve_seconds, arrivals[ai][0] if ai < len(arrivals) else args.serve_seconds) - now)
+            time.sleep(min(seconds, arrivals[ai][0] if ai < len(arrivals) else seconds) - now)
             continue
         while ai < len(arrivals) and arrivals[ai][0] <= now:
             ta, k, steps = arrivals[ai]
@@ -609,60 +623,154 @@ def run_serve(args, apbf, torch, d):
         idle = info["resident_scenes"] == 0 and info["queued"] == 0
     torch.cuda.synchronize()
     elapsed = time.perf_counter() - t0
-    d.barrier()
-    clock_info = clocks.stop()
+    # one more tick collects the last step's device time and the iteration count; what it
+    # admits or retires happened after the window and is not counted
+    last = apbf.apbf_server_tick(srv)
+    n_ticks = len(tick_start)
     stepped = [i["resident_particles"] for i in infos if i["resident_scenes"] > 0]
+    step_ms = [infos[k + 1]["prev_step_ms"] for k in range(len(infos) - 1) if infos[k]["resident_scenes"] > 0]
+    if infos and infos[-1]["resident_scenes"] > 0:
+        step_ms.append(last["prev_step_ms"])
     timeline = []
-    for sec in range(int(math.ceil(args.serve_seconds))):
+    for sec in range(int(math.ceil(seconds))):
         ks = [k for k, t in enumerate(tick_start) if sec <= t < sec + 1]
         if ks:
             timeline.append([sec, len(ks), int(sum(infos[k]["resident_particles"] for k in ks)),
                              int(max(infos[k]["resident_particles"] for k in ks)),
                              int(max(infos[k]["resident_scenes"] for k in ks)), int(infos[ks[-1]]["queued"])])
-    step_ms = [infos[k + 1]["prev_step_ms"] for k in range(len(infos) - 1) if infos[k]["resident_scenes"] > 0]
-    particle_steps = float(sum(stepped))
-    waits, lat, done, adm = [], [], 0, 0
+    waits, lat, done, adm, h2d, d2h = [], [], 0, 0, 0, 0
     for tk, ta, k, steps in reqs:
         q = apbf.apbf_server_query(srv, tk)
-        if q["state"] in (apbf.APBF_REQ_RESIDENT, apbf.APBF_REQ_DONE):
+        if q["state"] in (apbf.APBF_REQ_RESIDENT, apbf.APBF_REQ_DONE) and q["admit_tick"] - first_tick < n_ticks:
             adm += 1
             waits.append(tick_start[q["admit_tick"] - first_tick] - ta)
             h2d += 24 * temps[k].n
-        if q["state"] == apbf.APBF_REQ_DONE:
+        if q["state"] == apbf.APBF_REQ_DONE and q["done_tick"] - first_tick < n_ticks:
             done += 1
             lat.append(tick_start[q["done_tick"] - first_tick] - ta)
             d2h += 12 * temps[k].n
             srv._outputs.pop(tk, None)
-    offered = sum(temps[k].n * steps for _, k, steps in arrivals) / args.serve_seconds
-    value = d.sum(particle_steps / elapsed)
+    iters = last["total_particle_iterations"] - iters0
+    apbf.apbf_server_destroy(srv)
     ticks = len(stepped)
+    return {"elapsed_s": elapsed, "particle_steps": float(sum(stepped)), "particle_iterations": float(iters),
+            "particle_steps_per_s": sum(stepped) / elapsed, "particle_iterations_per_s": iters / elapsed,
+            "ticks": ticks, "step_ms_p50": _pct(step_ms, 50), "step_ms_p99": _pct(step_ms, 99),
+            "step_ms_max": max(step_ms) if step_ms else None,
+            "pool_gb": pool_bytes / 1e9, "capacity_particles": cap_n, "capacity_cells": cap_c,
+            "target_step_ms": target_ms or None,
+            "resident_particles_mean": float(np.mean(stepped)) if stepped else 0.0,
+            "resident_particles_max": int(max(stepped)) if stepped else 0,
+            "resident_scenes_max": int(max(i["resident_scenes"] for i in infos)) if infos else 0,
+            "particle_limit_last": infos[-1]["particle_limit"] if infos else None,
+            "requests": {"submitted": len(reqs), "admitted": adm, "completed": done,
+                         "queued_at_end": infos[-1]["queued"] if infos else 0,
+                         "queue_wait_s_p50": _pct(waits, 50), "queue_wait_s_p99": _pct(waits, 99),
+                         "latency_s_p50": _pct(lat, 50), "latency_s_p99": _pct(lat, 99)},
+            "timeline": {"fields": ["second", "ticks", "particle_steps", "resident_particles_max",
+                                    "resident_scenes_max", "queued_at_end"], "rows": timeline},
+            "h2d_bytes": h2d, "d2h_bytes": d2h}
+
+
+def serve_one_at_a_time(apbf, torch, temps, descs, arrivals, seconds):
+    """The same arrivals served first in, first out, one scene at a time: each
+    request gets its own scene (created on the device, stepped alone through
+    its captured graph, read back, destroyed) before the next one starts."""
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    ai, queue = 0, []
+    steps_done, iters, step_ms, waits, lat, done = 0, 0, [], [], [], 0
+    while True:
+        now = time.perf_counter() - t0
+        if now >= seconds:
+            break
+        while ai < len(arrivals) and arrivals[ai][0] <= now:
+            queue.append(arrivals[ai])
+            ai += 1
+        if not queue:
+            time.sleep(min(seconds, arrivals[ai][0] if ai < len(arrivals) else seconds) - now)
+            continue
+        ta, k, steps = queue.pop(0)
+        waits.append(now - ta)
+        s = apbf.apbf_create_scene(descs[k])
+        apbf.apbf_set_camera(s, temps[k].eye)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        ran = 0
+        for j in range(steps):
+            apbf.apbf_step(s, 1)
+            evs[j + 1].record(stream)
+            ran += 1
+            if j % 16 == 15 and time.perf_counter() - t0 >= seconds:
+                break
+        out = apbf.apbf_read_state(s, pos=True, vel=False)
+        torch.cuda.synchronize()
+        step_ms += [evs[j].elapsed_time(evs[j + 1]) for j in range(ran)]
+        iters += apbf.apbf_get_step_info(s)["total_particle_iterations"]
+        apbf.apbf_destroy_scene(s)
+        steps_done += ran * temps[k].n
+        if ran == steps:
+            done += 1
+            lat.append(time.perf_counter() - t0 - ta)
+        del out
+    elapsed = time.perf_counter() - t0
+    return {"elapsed_s": elapsed, "particle_steps": float(steps_done), "particle_iterations": float(iters),
+            "particle_steps_per_s": steps_done / elapsed, "particle_iterations_per_s": iters / elapsed,
+            "step_ms_p50": _pct(step_ms, 50), "step_ms_p99": _pct(step_ms, 99),
+            "requests": {"submitted": ai, "completed": done, "queued_at_end": len(queue),
+                         "queue_wait_s_p50": _pct(waits, 50), "queue_wait_s_p99": _pct(waits, 99),
+                         "latency_s_p50": _pct(lat, 50), "latency_s_p99": _pct(lat, 99)}}
+
+
+def run_serve(args, apbf, torch, d):
+    """Served scenes: Poisson arrivals (200/s) of dam breaks with 4096..262144
+    particles for 30..300 steps each (N_i in 5..10), admitted in arrival order
+    into one pool sized from an HBM budget, every resident scene stepped once
+    per tick, for the arrival window on the wall clock. The same trace runs
+    three ways: the pool admitting while it has room, the pool admitting under
+    a step-latency target, and first in, first out one scene at a time. Each
+    rank serves its own arrivals."""
+    temps = scenes.config_serve_templates()
+    arrivals = scenes.serve_arrivals(seconds=args.serve_seconds, templates=len(temps), seed=1608_04721 + 11 * d.rank)
+    c0 = temps[0]
+    rho0 = float(np.float32(apbf.apbf_rest_density(c0.h, c0.mass, c0.spacing)))
+    # the templates start at rest: no velocity arrays, so queued requests hold positions only
+    descs = [apbf.desc_from_config(c, scenes.make_scene(c)[0], None, rho0) for c in temps]
+    budget = int(args.serve_budget_gb * 1e9)
+    d.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    pooled = serve_pooled(apbf, torch, temps, descs, arrivals, args.serve_seconds, budget, args.serve_max_particles,
+                          0.0, args.warmup)
+    targeted = None
+    if args.serve_target_ms > 0:
+        targeted = serve_pooled(apbf, torch, temps, descs, arrivals, args.serve_seconds, budget,
+                                args.serve_max_particles, args.serve_target_ms, args.warmup)
+    fifo = None if args.no_fifo else serve_one_at_a_time(apbf, torch, temps, descs, arrivals, args.serve_seconds)
+    d.barrier()
+    clock_info = clocks.stop()
+    offered = sum(temps[k].n * steps for _, k, steps in arrivals) / args.serve_seconds
+    value = d.sum(pooled["particle_steps_per_s"])
+    ticks = pooled["ticks"]
     line = {
         "metric": SERVE_METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": d.ws,
-        "steps": ticks, "warmup": args.warmup, "ms_per_step": metrics.percentile(step_ms, 50) if step_ms else None,
+        "steps": ticks, "warmup": args.warmup, "ms_per_step": pooled["step_ms_p50"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "apbf_serve", "arrivals_per_s": 200.0, "seconds": args.serve_seconds,
                    "particles_per_scene": "log-uniform 4096..262144 (64 seeded templates)",
                    "steps_per_scene": "uniform 30..300", "n_range": f"{c0.n_min}..{c0.n_max}",
-                   "budget_gb": args.serve_budget_gb, "pool_gb": pool_bytes / 1e9,
-                   "capacity_particles": cap_n, "capacity_cells": cap_c,
+                   "budget_gb": args.serve_budget_gb, "pool_gb": pooled["pool_gb"],
+                   "capacity_particles": pooled["capacity_particles"], "capacity_cells": pooled["capacity_cells"],
                    "admission": "FIFO while particles, cells and scenes fit the pool",
                    "l2": "no flush: resident state far above 129 MB", "launch": "one captured graph per membership"},
         "offered_particle_steps_per_s": offered,
-        "timeline": {"fields": ["second", "ticks", "particle_steps", "resident_particles_max", "resident_scenes_max",
-                                "queued_at_end"], "rows": timeline},
-        "ticks": ticks, "step_ms_p50": metrics.percentile(step_ms, 50) if step_ms else None,
-        "step_ms_p99": metrics.percentile(step_ms, 99) if step_ms else None,
-        "resident_particles_mean": float(np.mean(stepped)) if stepped else 0.0,
-        "resident_particles_max": int(max(stepped)) if stepped else 0,
-        "resident_scenes_max": int(max(i["resident_scenes"] for i in infos)) if infos else 0,
-        "requests": {"submitted": len(reqs), "admitted": adm, "completed": done,
-                     "queued_at_end": infos[-1]["queued"] if infos else 0,
-                     "queue_wait_s_p50": metrics.percentile(waits, 50) if waits else None,
-                     "queue_wait_s_p99": metrics.percentile(waits, 99) if waits else None,
-                     "latency_s_p50": metrics.percentile(lat, 50) if lat else None,
-                     "latency_s_p99": metrics.percentile(lat, 99) if lat else None},
-        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d / max(1, ticks),
-                "d2h_bytes_per_step": d2h / max(1, ticks),
+        "particle_iterations_per_s": d.sum(pooled["particle_iterations_per_s"]),
+        "step_ms_p50": pooled["step_ms_p50"], "step_ms_p99": pooled["step_ms_p99"],
+        "pooled": pooled, "latency_target": targeted, "one_at_a_time": fifo,
+        "pooled_vs_one_at_a_time": ({"particle_steps": pooled["particle_steps_per_s"] / fifo["particle_steps_per_s"],
+                                     "particle_iterations": pooled["particle_iterations_per_s"]
+                                     / fifo["particle_iterations_per_s"]} if fifo else None),
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": pooled["h2d_bytes"] / max(1, ticks),
+                "d2h_bytes_per_step": pooled["d2h_bytes"] / max(1, ticks),
                 "what": "wall clock of the serving loop: host submit, admission uploads, ticks, result readback"},
         "roofline": None,
         "gpu_launches": ticks * kernels_per_step(c0),
@@ -670,7 +778,6 @@ def run_serve(args, apbf, torch, d):
     }
     if d.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = serve_cpu_baseline(temps, rho0)
-    apbf.apbf_server_destroy(srv)
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.close()
@@ -678,10 +785,12 @@ def run_serve(args, apbf, torch, d):
 
 
 def serve_cpu_baseline(temps, rho0, budget_s=20.0):
-    """The oracle, single-threaded: particle-steps/s over one step of each of
-    the smallest serving templates until the budget is spent."""
+    """The oracle on the host cores (OpenMP over particles): particle-steps/s
+    over one step of each of the smallest serving templates until the budget
+    is spent."""
     import oracle
 
+    cores = oracle.set_threads(host_cores())
     t_used, n_used, done = 0.0, 0, 0
     for c in sorted(temps, key=lambda c: c.n):
         x, v = scenes.make_scene(c)
@@ -693,16 +802,18 @@ def serve_cpu_baseline(temps, rho0, budget_s=20.0):
         done += 1
         if t_used > budget_s:
             break
-    return {"value": n_used / t_used, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+    return {"value": n_used / t_used, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"one oracle step of each of the {done} smallest of {len(temps)} serving templates "
                       f"({n_used} particles)", "sample_seconds": t_used}
 
 
 def batch_cpu_baseline(cfgs, rho0, budget_s=20.0):
-    """The oracle, single-threaded, stepping the batch's scenes in order until
-    the budget is spent; the per-particle time scaled to the whole batch."""
+    """The oracle on the host cores (OpenMP over particles), stepping the
+    batch's scenes in order until the budget is spent; the per-particle time
+    scaled to the whole batch."""
     import oracle
 
+    cores = oracle.set_threads(host_cores())
     t_used, n_used, done = 0.0, 0, 0
     for c in sorted(cfgs, key=lambda c: c.n):
         x, v = scenes.make_scene(c)
@@ -716,9 +827,58 @@ def batch_cpu_baseline(cfgs, rho0, budget_s=20.0):
             break
     n_total = sum(c.n for c in cfgs)
     scale = n_total / n_used
-    return {"value": t_used * 1e3 * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": t_used * 1e3 * scale, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one oracle step of the {done} smallest of the {len(cfgs)} scenes ({n_used} of {n_total} "
                       f"particles), time x {scale:.3g}", "sample_seconds": t_used}
+
+
+def run_lod_analysis(args, apbf, torch, d):
+    """Where the adaptive models put the iterations: the workload stepped as
+    APBF with the distance-to-camera model (DTC), APBF with the
+    distance-to-the-visible-surface model (DTVS) and PBF with N_max, side by
+    side on identical inputs and drivers; every `--analysis-every` steps,
+    each run's particles per level N_i (from |P_l|), its mean N_i, its density
+    error, and for DTVS the share of particles outside the view (they take
+    N_min)."""
+    cfg = workload(args.workload, "apbf")
+    rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))
+    runs = {"dtc": cfg, "dtvs": workload(args.workload, "dtvs"), "pbf_nmax": workload(args.workload, "pbf")}
+    sc = {k: make_scene(apbf, c, rho0) for k, c in runs.items()}
+    series = {k: [] for k in runs}
+    for step in range(args.steps):
+        for k, c in runs.items():
+            drive(apbf, sc[k], c, step)
+            apbf.apbf_step(sc[k], 1)
+        if (step + 1) % args.analysis_every and step + 1 != args.steps:
+            continue
+        for k, c in runs.items():
+            info = apbf.apbf_get_step_info(sc[k])
+            ac = info["active_count"].astype(np.int64)
+            per_level = {int(lv): int(ac[lv] - ac[lv + 1]) for lv in range(c.n_min, c.n_max + 1)
+                         if ac[lv] - ac[lv + 1] > 0}
+            row = {"step": step + 1, "mean_level": info["particle_iterations"] / c.n, "per_level": per_level,
+                   "density": [float(v) for v in apbf.apbf_density_stats(sc[k])]}
+            if k == "dtvs":
+                dist = apbf.apbf_debug_read(sc[k], apbf.APBF_DBG_LOD_DISTANCE)
+                row["outside_view"] = float(np.mean(dist < 0.0))
+                row["visible"] = float(np.mean(dist == 0.0))
+                row["d_range"] = [float(v) for v in info["d_range"]]
+            series[k].append(row)
+        print(f"step {step + 1}: " + "  ".join(f"{k} mean N {series[k][-1]['mean_level']:.2f} "
+                                               f"|rho/rho0-1| {100 * series[k][-1]['density'][0]:.3f} %"
+                                               for k in runs), file=sys.stderr, flush=True)
+    line = {"metric": "LOD analysis: particles per level, mean N_i and density error of DTC, DTVS and PBF N_max",
+            "value": None, "unit": None, "n_gpus": d.ws, "steps": args.steps, "warmup": 0, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(cfg, runs["pbf_nmax"].n_max, d.ws),
+            "dtvs_view": {"width": DTVS_VIEW[0], "height": DTVS_VIEW[1], "fov_y_deg": 60.0,
+                          "radius": 0.5 * cfg.spacing},
+            "series": series}
+    for k in sc:
+        apbf.apbf_destroy_scene(sc[k])
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
 
 
 def run_reference(args):
@@ -785,6 +945,7 @@ def run_reference_serve(args, ws):
     temps = sorted(scenes.config_serve_templates(), key=lambda c: c.n)
     c0 = temps[0]
     rho0 = float(np.float32(oracle.rest_density(c0.h, c0.mass, c0.spacing)))
+    cores = oracle.set_threads(host_cores())
     budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "150")) / max(1, args.steps + args.warmup)
     states, t_cal = [], 0.0
     for c in temps:
@@ -811,7 +972,7 @@ def run_reference_serve(args, ws):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "apbf_serve", "n_range": f"{c0.n_min}..{c0.n_max}"},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -827,6 +988,7 @@ def run_reference_batch(args, ws):
     cfgs = sorted(scenes.config_batch_256(), key=lambda c: c.n)
     c0 = cfgs[0]
     rho0 = float(np.float32(oracle.rest_density(c0.h, c0.mass, c0.spacing)))
+    cores = oracle.set_threads(host_cores())
     budget = float(os.environ.get("APBF_REFERENCE_BUDGET_S", "150")) / max(1, args.steps + args.warmup)
     states = []
     t_cal = 0.0
@@ -860,7 +1022,7 @@ def run_reference_batch(args, ws):
             "config": {"workload": "apbf_batch_256", "scenes": len(cfgs), "particles": n_total,
                        "n_range": f"{c0.n_min}..{c0.n_max}", "lod": "distance to camera"},
             "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -878,6 +1040,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-particles", type=int, default=0)
+    ap.add_argument("--serve-target-ms", type=float, default=33.3,
+                    help="step-latency target of the second pooled run (0: skip that run)")
+    ap.add_argument("--no-fifo", action="store_true", help="skip the one-scene-at-a-time serving arm")
+    ap.add_argument("--lod-analysis", action="store_true",
+                    help="record particles per level and density of DTC, DTVS and PBF N_max instead of timing")
+    ap.add_argument("--analysis-every", type=int, default=50)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -902,6 +1070,8 @@ def main():
         return run_batch(args, apbf, torch, d)
     if args.workload == "serve":
         return run_serve(args, apbf, torch, d)
+    if args.lod_analysis:
+        return run_lod_analysis(args, apbf, torch, d)
     cfg = workload(args.workload, "apbf")
     pbf_cfg = workload(args.workload, "pbf")
     rho0 = float(np.float32(apbf.apbf_rest_density(cfg.h, cfg.mass, cfg.spacing)))
@@ -910,6 +1080,8 @@ def main():
     flush = needs_flush(cfg.n)
     scene = make_scene(apbf, cfg, rho0)
     pbf = None if args.no_pbf else make_scene(apbf, pbf_cfg, rho0)
+    pbf_lo_cfg = workload(args.workload, "pbf_nmin")
+    pbf_lo = None if args.no_pbf else make_scene(apbf, pbf_lo_cfg, rho0)
     dtvs = None if args.no_dtvs else make_scene(apbf, dtvs_cfg, rho0)
     tuning = {}
     if not args.no_autotune:
@@ -919,6 +1091,8 @@ def main():
         if pbf is not None:
             drive(apbf, pbf, pbf_cfg, 0)
             tuning["pbf_nmax"] = tune_summary(apbf.apbf_autotune(pbf, 4))
+            drive(apbf, pbf_lo, pbf_lo_cfg, 0)
+            tuning["pbf_nmin"] = tune_summary(apbf.apbf_autotune(pbf_lo, 4))
         if dtvs is not None:
             drive(apbf, dtvs, dtvs_cfg, 0)
             tuning["apbf_dtvs"] = tune_summary(apbf.apbf_autotune(dtvs, 4))
@@ -933,6 +1107,15 @@ def main():
     d.barrier()
     ms_step = d.max(tot / args.steps)
     apbf_density = apbf.apbf_density_stats(scene)
+    # ---- PBF(N_min) on identical inputs and drivers: the other end of the adaptive range
+    pbf_lo_line = None
+    if pbf_lo is not None:
+        d.barrier()
+        ltot, lper, _ = timed_run(apbf, torch, pbf_lo, pbf_lo_cfg, args.warmup, args.steps, flush=flush)
+        d.barrier()
+        pbf_lo_line = {"ms_per_step": d.max(ltot / args.steps), "p50_ms": metrics.percentile(lper, 50),
+                       "p99_ms": metrics.percentile(lper, 99), "n": pbf_lo_cfg.n_max,
+                       "density": [float(v) for v in apbf.apbf_density_stats(pbf_lo)]}
     # ---- PBF(N_max) on identical inputs and drivers
     pbf_line = None
     if pbf is not None:
@@ -1039,6 +1222,7 @@ def main():
         "density": {"apbf": [float(v) for v in apbf_density],
                     "fields": ["mean|rho/rho0-1|", "max|rho/rho0-1|", "mean(rho/rho0-1)", "mean max(0,rho/rho0-1)"]},
         "pbf_nmax": pbf_line,
+        "pbf_nmin": pbf_lo_line,
         "improvement": metrics.improvement(pbf_line["ms_per_step"], ms_step) if pbf_line else None,
         "apbf_dtvs": dtvs_line,
         "improvement_dtvs": (metrics.improvement(pbf_line["ms_per_step"], dtvs_line["ms_per_step"])
@@ -1052,12 +1236,14 @@ def main():
     }
     if pbf_line:
         line["density"]["pbf_nmax"] = pbf_line["density"]
+        line["density"]["pbf_nmin"] = pbf_lo_line["density"]
         line["density"]["mean_abs_diff_points"] = 100 * abs(apbf_density[0] - pbf_line["density"][0])
     if d.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     apbf.apbf_destroy_scene(scene)
     if pbf is not None:
         apbf.apbf_destroy_scene(pbf)
+        apbf.apbf_destroy_scene(pbf_lo)
     if dtvs is not None:
         apbf.apbf_destroy_scene(dtvs)
     if d.rank == 0:

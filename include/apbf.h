@@ -127,6 +127,10 @@ typedef struct apbf_step_info {
     uint64_t lambda_pairs;          /* pairs visited by all lambda passes: sum_l sum_{i in P_l} |nbrs i| */
     uint32_t active_count[256];     /* |P_l| for l = 0..255 (l > n_max: 0) */
     float d_range[2];               /* distance range used by the LOD (0, 0 when fixed) */
+    uint64_t total_particle_iterations; /* sum of particle_iterations over every apbf_step since the scene
+                                           was created (kept on the device: reading it once at the end
+                                           measures sum_i N_i over a run without a sync per step;
+                                           apbf_autotune's trial steps do not count) */
 } apbf_step_info;
 
 /* Human-readable name of a status code (static string). */
@@ -304,12 +308,17 @@ APBF_API void apbf_destroy_scene(apbf_scene *scene);
  *  stats      device, 4 doubles: {mean |rho/rho0-1|, max |rho/rho0-1|,
  *             mean (rho/rho0-1), mean max(0, rho/rho0-1)}, written
  *             asynchronously on cuda_stream (NULL = the legacy default stream).
+ *  cuda_stream must belong to the current device (else APBF_ERR_INVALID_ARG).
  * Larger n or grids return APBF_ERR_INVALID_ARG with a message in
  * apbf_last_error(NULL). The call makes no cudaMalloc, cudaFree or other
  * allocating call: all scratch (about 3.9 MB) is one static device array that
  * every GPU loading this library keeps until the process exits. The first call
- * on each device looks up that array's device address; make that first call
- * before capturing any stream. All calls share the one array and it keeps the
+ * on each device does the set-up: it looks up that array's device address and,
+ * since CUDA loads a library's kernels lazily by default, that first lookup and
+ * launch load the module, which reserves the array on the device then (an
+ * implicit allocation that may synchronise). Make that first call once at
+ * initialisation, outside any frame loop and before capturing any stream;
+ * later calls allocate nothing. All calls share the one array and it keeps the
  * previous call's contents (the call clears what must start at zero), so calls
  * that overlap on the GPU -- on different streams, or from several host
  * threads -- race and must be serialised by the caller.
@@ -397,6 +406,12 @@ typedef struct apbf_server_desc {
     uint32_t max_cells;             /* resident grid-cell capacity (< 2^31); 0 = 4 x max_particles */
     uint32_t max_scenes;            /* resident scenes (<= 65535); 0 = 4096 */
     size_t budget_bytes;            /* device bytes the pool may use; 0 = no limit (max_particles required) */
+    double target_step_ms;          /* step-latency target of admission; 0 = off (admit while the pool has
+                                       room). When > 0, a queued request is admitted only while the resident
+                                       particles times the measured cost per particle-step stay below 0.9 x
+                                       this target (a request is always admitted into an empty pool). The
+                                       cost is a running average of the device time per particle of the
+                                       ticks that stepped at least 262144 particles, 2 ns before the first. */
 } apbf_server_desc;
 
 typedef struct apbf_request {
@@ -416,8 +431,11 @@ typedef struct apbf_tick_info {
     uint32_t admitted;              /* requests admitted by this tick */
     uint32_t completed;             /* requests retired (results written) by this tick */
     uint32_t queued;                /* requests still waiting */
-    uint32_t pad;
+    uint32_t failed;                /* requests retired as failed by this tick (see apbf_request_info.status) */
     double prev_step_ms;            /* device time of the previous tick's step (0 if it stepped nothing) */
+    uint64_t total_particle_iterations; /* sum_i N_i over every step the pool completed so far */
+    uint32_t particle_limit;        /* resident particles admission allows now (capacity, or the latency target's) */
+    uint32_t pad;
 } apbf_tick_info;
 
 #define APBF_REQ_QUEUED 0u
@@ -430,6 +448,10 @@ typedef struct apbf_request_info {
     uint32_t steps_done;
     uint32_t n, steps;
     uint64_t submit_tick, admit_tick, done_tick; /* tick counter at submit, admission, retirement */
+    apbf_status status;             /* APBF_REQ_FAILED: why; APBF_ERR_NEIGHBOR_OVERFLOW when one of its
+                                       particles had more neighbours than max_neighbors (only that request
+                                       fails: the other resident scenes' lists are their own) */
+    uint32_t pad;
 } apbf_request_info;
 
 /* Pool bytes and resolved capacities of a description (host-only, no GPU);
@@ -447,9 +469,13 @@ APBF_API apbf_status apbf_server_create(const apbf_server_desc *desc, void *cuda
 APBF_API apbf_status apbf_server_submit(apbf_server *server, const apbf_request *req, uint64_t *ticket);
 
 /* One tick: wait for the previous tick's step, retire the scenes it finished
- * (results to their buffers), close the pool's gaps, admit queued requests,
- * and enqueue one step of every resident scene (returns before it finishes).
- * info (host, may be NULL) receives the tick's counts. */
+ * (results to their buffers) and the scenes whose particles overflowed their
+ * neighbour lists in it (APBF_REQ_FAILED, no results; the other scenes go on
+ * unaffected), close the pool's gaps, admit queued requests in arrival order
+ * (while the pool has room and, with target_step_ms, while the step stays
+ * within the latency target), and enqueue one step of every resident scene
+ * (returns before it finishes). info (host, may be NULL) receives the tick's
+ * counts. */
 APBF_API apbf_status apbf_server_tick(apbf_server *server, apbf_tick_info *info);
 
 /* State of a request (host output). */

@@ -72,6 +72,7 @@ class apbf_step_info(C.Structure):
         ("lambda_pairs", C.c_uint64),
         ("active_count", C.c_uint32 * 256),
         ("d_range", C.c_float * 2),
+        ("total_particle_iterations", C.c_uint64),
     ]
 
 
@@ -98,6 +99,7 @@ class apbf_server_desc(C.Structure):
         ("max_cells", C.c_uint32),
         ("max_scenes", C.c_uint32),
         ("budget_bytes", C.c_size_t),
+        ("target_step_ms", C.c_double),
     ]
 
 
@@ -121,8 +123,11 @@ class apbf_tick_info(C.Structure):
         ("admitted", C.c_uint32),
         ("completed", C.c_uint32),
         ("queued", C.c_uint32),
-        ("pad", C.c_uint32),
+        ("failed", C.c_uint32),
         ("prev_step_ms", C.c_double),
+        ("total_particle_iterations", C.c_uint64),
+        ("particle_limit", C.c_uint32),
+        ("pad", C.c_uint32),
     ]
 
 
@@ -135,6 +140,8 @@ class apbf_request_info(C.Structure):
         ("submit_tick", C.c_uint64),
         ("admit_tick", C.c_uint64),
         ("done_tick", C.c_uint64),
+        ("status", C.c_int32),
+        ("pad", C.c_uint32),
     ]
 
 
@@ -488,7 +495,8 @@ def apbf_get_step_info(scene: Scene) -> dict:
     _check(lib().apbf_get_step_info(scene.handle, C.byref(info)), "apbf_get_step_info", scene)
     return dict(particle_iterations=int(info.particle_iterations), neighbor_pairs=int(info.neighbor_pairs),
                 lambda_pairs=int(info.lambda_pairs), active_count=np.array(info.active_count[:], np.int64),
-                d_range=np.array(info.d_range[:], np.float32))
+                d_range=np.array(info.d_range[:], np.float32),
+                total_particle_iterations=int(info.total_particle_iterations))
 
 
 def apbf_sync(scene: Scene):
@@ -614,26 +622,28 @@ def _server_check(st: int, where: str, server=None):
         raise ApbfError(st, where, lib().apbf_server_last_error(h).decode())
 
 
-def _server_desc(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0):
+def _server_desc(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0, target_step_ms=0.0):
     phys = physics[0] if isinstance(physics, tuple) else physics
     d = apbf_server_desc()
     d.physics = C.pointer(phys)
     d.max_particles, d.max_cells, d.max_scenes, d.budget_bytes = max_particles, max_cells, max_scenes, budget_bytes
+    d.target_step_ms = float(target_step_ms)
     return d, phys
 
 
-def apbf_server_bytes(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0):
+def apbf_server_bytes(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0, target_step_ms=0.0):
     """(pool bytes, particle capacity, cell capacity) of a server description."""
-    d, _ = _server_desc(physics, max_particles, max_cells, max_scenes, budget_bytes)
+    d, _ = _server_desc(physics, max_particles, max_cells, max_scenes, budget_bytes, target_step_ms)
     nb, npart, ncell = C.c_size_t(), C.c_uint32(), C.c_uint32()
     _server_check(lib().apbf_server_bytes(C.byref(d), C.byref(nb), C.byref(npart), C.byref(ncell)),
                   "apbf_server_bytes")
     return nb.value, npart.value, ncell.value
 
 
-def apbf_server_create(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0, stream=None) -> Server:
-    d, phys = _server_desc(physics, max_particles, max_cells, max_scenes, budget_bytes)
-    _, npart, ncell = apbf_server_bytes(physics, max_particles, max_cells, max_scenes, budget_bytes)
+def apbf_server_create(physics, max_particles=0, max_cells=0, max_scenes=0, budget_bytes=0, stream=None,
+                       target_step_ms=0.0) -> Server:
+    d, phys = _server_desc(physics, max_particles, max_cells, max_scenes, budget_bytes, target_step_ms)
+    _, npart, ncell = apbf_server_bytes(physics, max_particles, max_cells, max_scenes, budget_bytes, target_step_ms)
     stream_ptr, _, _, _ = _stream_and_arena(lambda: 0, stream, None)
     h = C.c_void_p()
     _server_check(lib().apbf_server_create(C.byref(d), C.c_void_p(stream_ptr), C.byref(h)), "apbf_server_create")
@@ -676,7 +686,7 @@ def apbf_server_tick(server: Server) -> dict:
 def apbf_server_query(server: Server, ticket: int) -> dict:
     info = apbf_request_info()
     _server_check(lib().apbf_server_query(server.handle, ticket, C.byref(info)), "apbf_server_query", server)
-    return {f: getattr(info, f) for f, _ in apbf_request_info._fields_}
+    return {f: getattr(info, f) for f, _ in apbf_request_info._fields_ if f != "pad"}
 
 
 def apbf_server_result(server: Server, ticket: int):

@@ -17,7 +17,6 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr size_t kAlign = 256;
-constexpr uint32_t kCounterSlots = 2 + 256 + 2;  // pairs, lambda pairs, per-bin pairs, diagnostic scratch
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -283,6 +282,7 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.counters = (unsigned long long *)P(8 * kCounterSlots);
     b.drange = (uint32_t *)P(8 * (size_t)sc.scenes);
     b.err = (uint32_t *)P(4);
+    b.err_scene = (uint32_t *)P(4 * (size_t)sc.scenes);
     b.dyn = (DynParams *)P(sizeof(DynParams) * (size_t)sc.scenes);
     b.geo = (const SceneGeom *)P(sizeof(SceneGeom) * (size_t)sc.scenes);
     b.sid = (const uint16_t *)P(2 * n);
@@ -1002,7 +1002,7 @@ APBF_API apbf_status apbf_density_stats(apbf_scene *s, double stats[4])
     if (s->sc.n == 0)
         return check_device_errors(s);
     Buffers bb = s->b;
-    bb.counters = s->b.counters + (kCounterSlots - 2);  // keep the step's counters
+    bb.counters = s->b.counters + kDiagCounterSlot;  // keep the step's counters
     cudaStream_t q = s->stream;
     int nb = 0;
     APBF_CUDA(s, launch_predict_hash(s->sc, bb, q, true));
@@ -1043,6 +1043,7 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     APBF_CUDA(s, cudaMemcpy(&dr[1], s->b.drange + sc.scenes, 4, cudaMemcpyDeviceToHost));
     const bool partitioned = sc.lod_mode != APBF_LOD_FIXED && sc.K > 1;
     info->neighbor_pairs = c[0];
+    info->total_particle_iterations = c[kIterTotalSlot];
     for (uint32_t l = 0; l < 256; ++l) {
         uint32_t a = 0;
         if (l <= sc.n_max)
@@ -1224,6 +1225,9 @@ APBF_API apbf_status apbf_autotune(apbf_scene *s, uint32_t trial_steps, apbf_tun
         return st;
     if ((st = copy_state(s, true)) != APBF_OK)
         return st;
+    // the trial steps do not count in the running total of particle-iterations
+    APBF_CUDA(s, cudaMemcpyAsync(s->b.counters + kIterSaveSlot, s->b.counters + kIterTotalSlot, 8,
+                                 cudaMemcpyDeviceToDevice, s->stream));
     cudaEvent_t e0 = get_event(s), e1 = get_event(s);
     const bool timing = s->timing;
     s->timing = false;
@@ -1266,6 +1270,8 @@ APBF_API apbf_status apbf_autotune(apbf_scene *s, uint32_t trial_steps, apbf_tun
     out->tried = k;
     if ((st = copy_state(s, false)) != APBF_OK)
         return st;
+    APBF_CUDA(s, cudaMemcpyAsync(s->b.counters + kIterTotalSlot, s->b.counters + kIterSaveSlot, 8,
+                                 cudaMemcpyDeviceToDevice, s->stream));
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));
     s->tune = best_t;
     drop_graph(s);

@@ -45,6 +45,16 @@ constexpr uint8_t kFrontNeighbors = 28;    // phase-0 spheres: fewer neighbours 
 // Device error word bits.
 constexpr uint32_t kErrNeighborOverflow = 1u;
 
+// Slots of the 64-bit counters: [0] neighbour pairs of the step, [2 + bin]
+// pairs per level bin (reset each step), two slots of scratch for the density
+// diagnostic, and the running total of particle-iterations (sum_l |P_l|, Eq.
+// 10) over every completed step, which nothing resets (the autotuner keeps a
+// copy in the slot after it while its trial steps run).
+constexpr uint32_t kDiagCounterSlot = 2 + 256;
+constexpr uint32_t kIterTotalSlot = kDiagCounterSlot + 2;
+constexpr uint32_t kIterSaveSlot = kIterTotalSlot + 1;
+constexpr uint32_t kCounterSlots = kIterSaveSlot + 1;
+
 // Step constants, fixed for a scene's lifetime (passed by value as kernel
 // arguments and therefore baked into the captured step graph).
 struct StepConst {
@@ -163,11 +173,12 @@ struct Buffers {
     float *rho;
     float *lodd;                   // DTVS distance behind the visible surface, state order (-1: outside the view)
     uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
-    unsigned long long *counters;  // [0] pairs, [1] lambda pairs
+    unsigned long long *counters;  // kCounterSlots: see kDiagCounterSlot, kIterTotalSlot
     uint32_t *drange;              // float bits of d_min (scenes entries), then d_max (scenes entries)
     const SceneGeom *geo;          // per scene
     const uint16_t *sid;           // scene of each particle slot (constant)
-    uint32_t *err;
+    uint32_t *err;                 // device error word (kErr* bits) of the step
+    uint32_t *err_scene;           // the same bits per scene (a batch fails only the scenes that set them)
     DynParams *dyn;                // per scene
     float4 *snap_x, *snap_v;       // state snapshot for the autotuner
     uint32_t *snap_id;

@@ -1208,6 +1208,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
         }
         if (cnt > sc.max_nbr) {
             atomicOr(b.err, kErrNeighborOverflow);
+            atomicOr(&b.err_scene[scene_of<BATCH>(b, p)], kErrNeighborOverflow);
             cnt = sc.max_nbr;
         }
         b.nbr_cnt[t] = (uint8_t)cnt;
@@ -1672,6 +1673,15 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
 {
     wait_for_predecessor();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;  // list column
+    if (t == 0) {  // running total of particle-iterations: sum over l >= 1 of |P_l| (Eq. 10)
+        unsigned long long it = (unsigned long long)sc.n * sc.n_max;
+        if (part) {
+            it = 0;
+            for (uint32_t l = 1; l <= sc.n_max; ++l)
+                it += b.lvl_count[l];
+        }
+        b.counters[kIterTotalSlot] += it;
+    }
     if (t >= sc.n)
         return;
     const uint32_t p = part ? b.act[t] : t;

@@ -35,6 +35,7 @@ struct Request {
     float *pos_out = nullptr, *vel_out = nullptr;
     std::vector<Obstacle> obst;  // the scene's obstacles
     uint32_t state = APBF_REQ_QUEUED;
+    apbf_status status = APBF_OK;  // why a failed request failed
     uint64_t submit_tick = 0, admit_tick = 0, done_tick = 0;
     uint32_t p0 = 0, cell_base = 0;  // place in the pool while resident
 };
@@ -154,6 +155,8 @@ std::string resolve(const apbf_server_desc *d, StepConst &phys, StepConst &cap, 
     };
     if (d->max_cells >= (1u << 31))
         return "max_cells must be below 2^31";
+    if (!std::isfinite(d->target_step_ms) || d->target_step_ms < 0.0)
+        return "target_step_ms must be finite and >= 0";
     uint32_t n = d->max_particles;
     if (n == 0) {
         if (d->budget_bytes == 0)
@@ -197,6 +200,13 @@ struct apbf_server {
     MoveSeg *d_seg = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool in_flight = false;
+    // host pinned: the step's error word, the per-scene error words, the running particle-iterations
+    uint32_t *h_err = nullptr;
+    unsigned long long *h_iters = nullptr;
+    unsigned long long total_iters = 0;
+    // admission by step-latency target: measured device ms per particle-step (running average)
+    double target_ms = 0.0, cost_ms = 2.0e-6;
+    uint32_t n_stepped = 0;
     apbf_status sticky = APBF_OK;
     std::string msg;
 };
@@ -227,6 +237,7 @@ apbf_status pool_fail(apbf_server *sv, apbf_status st)
 {
     for (Request *r : sv->resident) {
         r->state = APBF_REQ_FAILED;
+        r->status = st;
         r->done_tick = sv->tick;
     }
     return sfail(sv, st, std::string("pool: ") + apbf_last_error(sv->pool));
@@ -325,16 +336,48 @@ apbf_status tick_impl(apbf_server *sv, apbf_tick_info *info)
         SV_CUDA(sv, cudaEventElapsedTime(&ms, sv->ev0, sv->ev1));
         info->prev_step_ms = ms;
         sv->in_flight = false;
+        if (sv->n_stepped >= 262144u) {
+            const double c = (double)ms / sv->n_stepped;
+            sv->cost_ms = 0.7 * sv->cost_ms + 0.3 * c;
+        }
+        // a neighbour overflow fails only the scenes that had it: their words are
+        // read, those requests retire as failed, and the words are cleared, so the
+        // pool itself goes on (any other device error still fails the pool)
+        const uint32_t count = (uint32_t)sv->resident.size();
+        SV_CUDA(sv, cudaMemcpyAsync(sv->h_err, s->b.err, 4, cudaMemcpyDeviceToHost, s->stream));
+        SV_CUDA(sv, cudaMemcpyAsync(sv->h_err + 1, s->b.err_scene, 4 * (size_t)count, cudaMemcpyDeviceToHost,
+                                    s->stream));
+        SV_CUDA(sv, cudaMemcpyAsync(sv->h_iters, s->b.counters + kIterTotalSlot, 8, cudaMemcpyDeviceToHost,
+                                    s->stream));
+        SV_CUDA(sv, cudaStreamSynchronize(s->stream));
+        sv->total_iters = *sv->h_iters;
+        if (sv->h_err[0] == kErrNeighborOverflow) {
+            for (uint32_t k = 0; k < count; ++k)
+                if (sv->h_err[1 + k] & kErrNeighborOverflow) {
+                    Request *r = sv->resident[k];
+                    r->state = APBF_REQ_FAILED;
+                    r->status = APBF_ERR_NEIGHBOR_OVERFLOW;
+                    r->done_tick = sv->tick;
+                }
+            SV_CUDA(sv, cudaMemsetAsync(s->b.err, 0, 4, s->stream));
+            SV_CUDA(sv, cudaMemsetAsync(s->b.err_scene, 0, 4 * (size_t)count, s->stream));
+        }
         apbf_status st = apbf_sync(s);
         if (st != APBF_OK)
             return pool_fail(sv, st);
     }
+    info->total_particle_iterations = sv->total_iters;
     // 2. retire finished scenes
     std::vector<Request *> fin, kept;
-    for (Request *r : sv->resident)
-        (r->done >= r->steps ? fin : kept).push_back(r);
+    uint32_t failed = 0;
+    for (Request *r : sv->resident) {
+        if (r->state == APBF_REQ_FAILED)
+            ++failed;
+        else
+            (r->done >= r->steps ? fin : kept).push_back(r);
+    }
     bool changed = false;
-    if (!fin.empty()) {
+    if (!fin.empty() || failed) {
         apbf_status st = read_back(sv, fin);
         if (st != APBF_OK)
             return st;
@@ -343,6 +386,7 @@ apbf_status tick_impl(apbf_server *sv, apbf_tick_info *info)
             r->done_tick = sv->tick;
         }
         info->completed = (uint32_t)fin.size();
+        info->failed = failed;
         // 3. close the gaps: survivors keep their order and move down
         std::vector<MoveSeg> seg;
         uint32_t p = 0, c = 0;
@@ -374,11 +418,19 @@ apbf_status tick_impl(apbf_server *sv, apbf_tick_info *info)
     // 4. admit from the queue in arrival order while the pool has room
     const uint32_t first_new = (uint32_t)sv->resident.size();
     const uint32_t n_before = sv->n_res;
+    uint32_t limit = sv->cap.n;
+    if (sv->target_ms > 0.0) {
+        const double l = 0.9 * sv->target_ms / sv->cost_ms;
+        limit = l < (double)sv->cap.n ? (uint32_t)l : sv->cap.n;
+    }
+    info->particle_limit = limit;
     while (!sv->queue.empty()) {
         Request *r = sv->queue.front();
         if ((uint64_t)sv->n_res + r->desc.n > sv->cap.n || (uint64_t)sv->c_res + r->geo.ncell > sv->cap.ncell ||
             sv->resident.size() + 1 > sv->cap.scenes)
             break;
+        if (!sv->resident.empty() && (uint64_t)sv->n_res + r->desc.n > limit)
+            break;  // the step would exceed the latency target: wait (arrival order is kept)
         sv->queue.pop_front();
         r->p0 = sv->n_res;
         r->cell_base = sv->c_res;
@@ -425,6 +477,7 @@ apbf_status tick_impl(apbf_server *sv, apbf_tick_info *info)
     info->queued = (uint32_t)sv->queue.size();
     if (!sv->resident.empty()) {
         SV_CUDA(sv, cudaEventRecord(sv->ev0, s->stream));
+        sv->n_stepped = sv->n_res;
         apbf_status st = apbf_step(s, 1);
         if (st != APBF_OK)
             return pool_fail(sv, st);
@@ -472,6 +525,7 @@ APBF_API apbf_status apbf_server_create(const apbf_server_desc *desc, void *cuda
     if (!sv)
         return sfail(nullptr, APBF_ERR_OUT_OF_MEMORY, "host allocation failed");
     sv->cap = cap;
+    sv->target_ms = desc->target_step_ms;
     sv->physics = *desc->physics;
     sv->physics.pos = nullptr;
     sv->physics.vel = nullptr;
@@ -481,6 +535,8 @@ APBF_API apbf_status apbf_server_create(const apbf_server_desc *desc, void *cuda
     cudaError_t e;
     if ((e = cudaMalloc(&sv->d_seg, sizeof(MoveSeg) * cap.scenes)) != cudaSuccess ||
         (e = cudaEventCreate(&sv->ev0)) != cudaSuccess || (e = cudaEventCreate(&sv->ev1)) != cudaSuccess ||
+        (e = cudaMallocHost(&sv->h_err, 4 * (size_t)(cap.scenes + 1))) != cudaSuccess ||
+        (e = cudaMallocHost(&sv->h_iters, 8)) != cudaSuccess ||
         (e = cudaStreamSynchronize(sv->pool->stream)) != cudaSuccess) {
         cudaGetLastError();
         apbf_server_destroy(sv.release());
@@ -591,6 +647,8 @@ APBF_API apbf_status apbf_server_query(apbf_server *sv, uint64_t ticket, apbf_re
     info->submit_tick = r.submit_tick;
     info->admit_tick = r.admit_tick;
     info->done_tick = r.done_tick;
+    info->status = r.status;
+    info->pad = 0;
     return APBF_OK;
 }
 
@@ -611,6 +669,10 @@ APBF_API void apbf_server_destroy(apbf_server *sv)
         cudaEventDestroy(sv->ev0);
     if (sv->ev1)
         cudaEventDestroy(sv->ev1);
+    if (sv->h_err)
+        cudaFreeHost(sv->h_err);
+    if (sv->h_iters)
+        cudaFreeHost(sv->h_iters);
     delete sv;
 }
 

@@ -156,3 +156,32 @@ def test_server_bytes_rejects_bad_physics():
     with pytest.raises(apbf.ApbfError) as e:
         apbf.apbf_server_bytes(_desc(h=0.0), max_particles=1000)
     assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct of include/apbf.h, compiled by the host C compiler, has the
+    size and field offsets of its ctypes mirror in the binding."""
+    import ctypes
+    import subprocess
+
+    structs = [apbf.apbf_scene_desc, apbf.apbf_step_info, apbf.apbf_obstacle, apbf.apbf_tune_result,
+               apbf.apbf_server_desc, apbf.apbf_request, apbf.apbf_tick_info, apbf.apbf_request_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "apbf.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                    check=True).stdout.splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)

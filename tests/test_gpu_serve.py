@@ -204,3 +204,118 @@ def test_served_scenes_with_obstacles_and_prestabilisation_match_alone():
     with pytest.raises(apbf.ApbfError):
         apbf.apbf_server_submit(srv, descs[0], cfgs[0].eye, 2, obstacles=[(9, (0, 0, 0), (1, 1, 1))])
     apbf.apbf_server_destroy(srv)
+
+
+def _run_server(srv, descs, eyes, steps, arrive, crowded=()):
+    """Tick until every request has left; returns (tickets, tick infos)."""
+    tickets, log, tick = {}, [], 0
+    while True:
+        for k in range(len(descs)):
+            if arrive[k] == tick:
+                tickets[k] = apbf.apbf_server_submit(srv, descs[k], eyes[k], steps[k], want_pos=True, want_vel=True)
+        info = apbf.apbf_server_tick(srv)
+        log.append(info)
+        tick += 1
+        if len(tickets) == len(descs) and info["resident_scenes"] == 0 and info["queued"] == 0:
+            return tickets, log
+        assert tick < 400
+
+
+def _alone_total_iterations(desc, eye, steps):
+    s = apbf.apbf_create_scene(desc)
+    apbf.apbf_set_camera(s, eye)
+    apbf.apbf_step(s, steps)
+    t = apbf.apbf_get_step_info(s)["total_particle_iterations"]
+    apbf.apbf_destroy_scene(s)
+    return t
+
+
+def test_neighbour_overflow_fails_only_its_request():
+    """A request whose 300 particles sit in a 2 cm cube (299 neighbours each,
+    over the list capacity) fails with APBF_ERR_NEIGHBOR_OVERFLOW at its first
+    step; the scenes sharing the pool with it finish bit-identical to
+    themselves alone, and the server keeps serving."""
+    cfgs = _configs(4, 77)
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    descs = [apbf.desc_from_config(c, *scenes.make_scene(c), r0) for c in cfgs]
+    c = cfgs[1]
+    rng = np.random.default_rng(5)
+    lo = np.asarray(c.box_lo, np.float64) + 0.3
+    xc = (lo + 0.02 * rng.random((300, 3))).astype(np.float32)
+    bad = apbf.desc_from_config(c, xc, None, r0)
+    descs.insert(2, bad)
+    eyes = [cc.eye for cc in cfgs]
+    eyes.insert(2, c.eye)
+    steps = [5, 6, 4, 7, 3]
+    arrive = [0, 0, 1, 1, 2]
+    srv = apbf.apbf_server_create(descs[0], max_particles=60000, max_cells=4 * 10**6, max_scenes=8)
+    tickets, log = _run_server(srv, descs, eyes, steps, arrive)
+    assert sum(i["failed"] for i in log) == 1
+    q = apbf.apbf_server_query(srv, tickets[2])
+    assert q["state"] == apbf.APBF_REQ_FAILED and q["status"] == apbf.APBF_ERR_NEIGHBOR_OVERFLOW
+    assert q["done_tick"] == q["admit_tick"] + 1
+    for k in (0, 1, 3, 4):
+        q = apbf.apbf_server_query(srv, tickets[k])
+        assert q["state"] == apbf.APBF_REQ_DONE and q["status"] == apbf.APBF_OK, k
+        pos, vel = apbf.apbf_server_result(srv, tickets[k])
+        ref_pos, ref_vel = _alone(descs[k], eyes[k], steps[k])
+        assert np.array_equal(pos, ref_pos) and np.array_equal(vel, ref_vel), k
+    # still serving after the failure
+    t = apbf.apbf_server_submit(srv, descs[0], eyes[0], 2)
+    for _ in range(4):
+        apbf.apbf_server_tick(srv)
+    assert apbf.apbf_server_query(srv, t)["state"] == apbf.APBF_REQ_DONE
+    apbf.apbf_server_destroy(srv)
+
+
+def test_latency_target_limits_residency_and_keeps_results():
+    """With a step-latency target far below any step, admission keeps one
+    scene resident at a time (a request is always admitted into an empty
+    pool); the results are still each scene's own, and the pool's running
+    total of particle-iterations is exactly the sum of the scenes' totals
+    alone."""
+    cfgs = _configs(5, 91)
+    r0 = float(np.float32(oracle.rest_density(cfgs[0].h, cfgs[0].mass, cfgs[0].spacing)))
+    descs = [apbf.desc_from_config(c, *scenes.make_scene(c), r0) for c in cfgs]
+    eyes = [c.eye for c in cfgs]
+    steps = [4, 3, 5, 2, 3]
+    arrive = [0, 0, 0, 1, 1]
+    srv = apbf.apbf_server_create(descs[0], max_particles=60000, max_cells=4 * 10**6, max_scenes=8,
+                                  target_step_ms=1e-6)
+    tickets, log = _run_server(srv, descs, eyes, steps, arrive)
+    assert max(i["resident_scenes"] for i in log) == 1
+    assert all(i["particle_limit"] < 60000 for i in log)
+    for k in range(len(cfgs)):
+        pos, vel = apbf.apbf_server_result(srv, tickets[k])
+        ref_pos, ref_vel = _alone(descs[k], eyes[k], steps[k])
+        assert np.array_equal(pos, ref_pos) and np.array_equal(vel, ref_vel), k
+    total = sum(_alone_total_iterations(descs[k], eyes[k], steps[k]) for k in range(len(cfgs)))
+    assert log[-1]["total_particle_iterations"] == total
+    apbf.apbf_server_destroy(srv)
+    # without a target the same arrivals share the pool
+    srv = apbf.apbf_server_create(descs[0], max_particles=60000, max_cells=4 * 10**6, max_scenes=8)
+    tickets, log = _run_server(srv, descs, eyes, steps, arrive)
+    assert max(i["resident_scenes"] for i in log) >= 3
+    assert log[-1]["total_particle_iterations"] == total
+    apbf.apbf_server_destroy(srv)
+
+
+def test_running_particle_iterations_equal_the_per_step_counts():
+    """apbf_step_info.total_particle_iterations is the sum of every step's
+    particle_iterations (sum_l |P_l|, Eq. 10); the autotuner's trial steps do
+    not count."""
+    c = _configs(1, 5)[0]
+    r0 = float(np.float32(oracle.rest_density(c.h, c.mass, c.spacing)))
+    s = apbf.apbf_create_scene(apbf.desc_from_config(c, *scenes.make_scene(c), r0))
+    apbf.apbf_set_camera(s, c.eye)
+    total = 0
+    for k in range(6):
+        apbf.apbf_step(s, 1)
+        info = apbf.apbf_get_step_info(s)
+        total += info["particle_iterations"]
+        assert info["total_particle_iterations"] == total
+        if k == 2:
+            apbf.apbf_autotune(s, 2)
+            assert apbf.apbf_get_step_info(s)["total_particle_iterations"] == total
+    assert total > c.n * c.n_min
+    apbf.apbf_destroy_scene(s)
