@@ -28,7 +28,12 @@
  *    call (apbf_read_state, apbf_density_stats, apbf_sync, apbf_debug_read)
  *    and then sticks to the scene: every later call returns it.
  *  - Positions and velocities are FP32, 3 values per particle (x, y, z),
- *    in particle-id order (the order of apbf_scene_desc.pos).
+ *    in particle-id order (the order of apbf_scene_desc.pos). Inside a step
+ *    the solver holds positions in fixed point: integers of u = 2^e metres
+ *    relative to the grid origin, u the smallest power of two with 2^22 u >= h
+ *    (so u <= h / 2^21) unless the grid spans 8e8 units or more on an axis
+ *    (about 190 h), when u doubles until it does not. The neighbour search,
+ *    the cell hash and the LOD use the FP32 positions themselves.
  */
 #ifndef APBF_H
 #define APBF_H
@@ -165,7 +170,9 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *desc, void *cuda_s
  * A scene inside a batch evolves bit-identically to the same scene created
  * alone. Every scene's description must agree with scene 0 in everything but
  * n, pos, vel, grid_lo/hi and box_lo/hi (APBF_ERR_INVALID_ARG otherwise);
- * count <= 65535 and the total particle count < 2^27.
+ * count <= 65535 and the total particle count < 2^27. A batch shares one
+ * fixed-point unit: a scene whose grid needs a coarser unit than its h gives
+ * (one spanning 8e8 units on an axis) steps alone (APBF_ERR_NOT_SUPPORTED).
  *  descs  host, count descriptions (copied, as for apbf_create_scene).
  * On a batch, apbf_set_camera / apbf_set_box set every scene (the _at forms
  * set one); apbf_read_state returns all particles, scene after scene, each
@@ -465,7 +472,9 @@ APBF_API apbf_status apbf_server_bytes(const apbf_server_desc *desc, size_t *byt
 APBF_API apbf_status apbf_server_create(const apbf_server_desc *desc, void *cuda_stream, apbf_server **out);
 
 /* Queue a request (validated and copied; APBF_ERR_INVALID_ARG if it could never
- * fit the pool alone). ticket (host) receives its id. Does not touch the GPU. */
+ * fit the pool alone; APBF_ERR_NOT_SUPPORTED if its grid needs a coarser
+ * fixed-point unit than the pool's, as for batches). ticket (host) receives
+ * its id. Does not touch the GPU. */
 APBF_API apbf_status apbf_server_submit(apbf_server *server, const apbf_request *req, uint64_t *ticket);
 
 /* One tick: wait for the previous tick's step, retire the scenes it finished

@@ -49,6 +49,13 @@ bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1])
 }  // namespace
 
 namespace apbf {
+int fx_exponent_for_h(float h)
+{
+    int e2;
+    const double f = std::frexp((double)h, &e2);  // h = f 2^e2, f in [0.5, 1)
+    return (f == 0.5 ? e2 - 1 : e2) - 22;          // ceil(log2 h) - 22
+}
+
 // Derived constants of a description; returns an error message or "".
 std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
 {
@@ -118,16 +125,20 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.inv_dt = (float)(1.0 / (double)d->dt);
     for (int a = 0; a < 3; ++a)
         sc.g[a] = d->gravity[a];
-    // local-origin lattice spacing: h rounded to 8 significant bits
-    int e2;
-    double f = std::frexp((double)d->h, &e2);
-    sc.q = (float)std::ldexp(std::nearbyint(f * 256.0), e2 - 8);
-    for (int a = 0; a < 3; ++a) {
-        double m = std::nearbyint((double)d->grid_lo[a] / (double)sc.q);
-        if (std::fabs(m) + dims[a] + 2 > 32767.0)
-            return "grid origin too far from 0 relative to h";
-        sc.m[a] = (int32_t)m;
+    // fixed-point unit: the smallest power of two u with 2^22 u >= h whose grid
+    // spans fewer than kFxSpan units (a longer grid takes a coarser unit)
+    sc.fx_e = fx_exponent_for_h(d->h);
+    for (;;) {
+        double span = 0.0;
+        for (int a = 0; a < 3; ++a)
+            span = std::max(span, std::ldexp((double)d->grid_hi[a] - (double)d->grid_lo[a], -sc.fx_e) + 2.0);
+        if (span < kFxSpan)
+            break;
+        ++sc.fx_e;
     }
+    sc.fx_u = (float)std::ldexp(1.0, sc.fx_e);
+    sc.fx_inv_u = (float)std::ldexp(1.0, -sc.fx_e);
+    sc.fx_off = (float)std::ldexp(-1.5, 23 + sc.fx_e);
     const double PI = 3.14159265358979323846;
     const double h = d->h, m = d->mass, rho0 = d->rho0, w = 1.0 / m;
     const double poly6 = 315.0 / (64.0 * PI * std::pow(h, 9));
@@ -139,6 +150,8 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.c_lam = (float)(w * (m * spiky / rho0) * (m * spiky / rho0));
     sc.eps = d->eps;
     sc.c_dp = (float)(-(w * m / rho0) * spiky);
+    sc.c_dpu = (float)std::ldexp((double)sc.c_dp, -sc.fx_e);
+    sc.v_scale = (float)((double)sc.fx_u / (double)d->dt);
     const double dq = d->scorr_dq;
     sc.inv_wdq = (float)(1.0 / (h2 - dq * dq));
     sc.neg_k = -d->scorr_k;
@@ -201,11 +214,16 @@ std::string derive_batch(const apbf_scene_desc *descs, uint32_t count, StepConst
             if (!same_physics(descs[0], descs[k]))
                 return "scene " + std::to_string(k) + " differs from scene 0 in a physics parameter";
         }
-        SceneGeom &g = geo[k];
-        for (int ax = 0; ax < 3; ++ax) {
-            g.glo[ax] = sk.glo[ax];
-            g.m[ax] = sk.m[ax];
+        if (count > 1 && sk.fx_e != fx_exponent_for_h(descs[k].h)) {
+            // a batch shares one fixed-point unit, the one a scene of that h takes alone
+            st = APBF_ERR_NOT_SUPPORTED;
+            return "scene " + std::to_string(k) + ": its grid spans 8e8 or more fixed-point units of 2^" +
+                   std::to_string(fx_exponent_for_h(descs[k].h)) + " m on an axis; such scenes step alone, "
+                   "not in a batch";
         }
+        SceneGeom &g = geo[k];
+        for (int ax = 0; ax < 3; ++ax)
+            g.glo[ax] = sk.glo[ax];
         g.nx = sk.nx;
         g.ny = sk.ny;
         g.nz = sk.nz;

@@ -42,6 +42,14 @@ constexpr uint32_t kSplatChunk = 1024;     // list entries per work chunk of the
 constexpr uint32_t kSplatListPerParticle = 16;  // tile-list capacity: 16 entries per particle + 65536
 constexpr uint8_t kFrontNeighbors = 28;    // phase-0 spheres: fewer neighbours than this in the last step
 
+// Fixed-point solver positions: every scene's positions, in units of
+// StepConst::fx_u relative to its grid origin, must span fewer than kFxSpan
+// units, so that the difference of any two of them, biased by kFxMagic, is the
+// bit pattern of a finite float (see kernels.cu).
+constexpr double kFxSpan = 8.0e8;
+constexpr int32_t kFxMagic = 0x4B400000;  // bit pattern of 1.5 * 2^23
+constexpr int32_t kFxFar = -(1 << 30);    // the padding record: at least 3h from every particle
+
 // Device error word bits.
 constexpr uint32_t kErrNeighborOverflow = 1u;
 
@@ -67,10 +75,11 @@ struct StepConst {
     float h2;           // fl(h*h): the FP32 neighbour predicate bound
     float dt, inv_dt;
     float g[3];
-    // local-origin lattice: origin of cell c on axis a is (float)(m[a] + c) * q,
-    // exact for |m + c| < 2^16 because q has at most 8 significant bits.
-    float q;
-    int32_t m[3];
+    // Solver positions in fixed point (see kernels.cu): integers of the unit
+    // fx_u = 2^fx_e metres, relative to the scene's grid origin; 2^22 fx_u >= h.
+    float fx_u, fx_inv_u;
+    float fx_off;       // -1.5 * 2^23 * fx_u: with the bias kFxMagic, one FMA turns a difference into metres
+    int32_t fx_e;
     // solver coefficients (FP32 from FP64 host values)
     float mass_poly6;   // m * 315 / (64 pi h^9)
     float h6;           // (h^2)^3: self term of the density sum
@@ -78,6 +87,8 @@ struct StepConst {
     float c_lam;        // w (m * 45/(pi h^6) / rho0)^2
     float eps;
     float c_dp;         // -(w m / rho0) * 45/(pi h^6)
+    float c_dpu;        // c_dp / fx_u: the correction in fixed-point units
+    float v_scale;      // fx_u / dt: velocity of a displacement of one unit
     float inv_wdq;      // 1 / (h^2 - dq^2)
     float neg_k;        // -k
     uint32_t scorr_n;
@@ -98,9 +109,7 @@ struct SceneGeom {
     float glo[3];
     int32_t nx, ny, nz;
     uint32_t cell_base;
-    int32_t m[3];  // local-origin lattice offsets (see StepConst::q)
     uint32_t p0, n;
-    uint32_t pad;
 };
 
 // Per-step values that callers change between steps (device copy read by kernels,
@@ -282,6 +291,9 @@ int iteration_grid(int sms);
 
 // Host helpers shared by the scene / batch entry points and the server (apbf_capi.cu).
 std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st);
+// Exponent e of the fixed-point unit 2^e of a scene with this h whose grid is
+// short enough: the smallest e with 2^(e + 22) >= h.
+int fx_exponent_for_h(float h);
 bool same_physics(const apbf_scene_desc &a, const apbf_scene_desc &d);
 size_t carve(const StepConst &sc, char *base, Buffers &b);
 apbf_status alloc_scene(const StepConst &cap, uint32_t flags, void *cuda_stream, void *device_arena,

@@ -3,11 +3,11 @@
 //
 // Data layout (structure of arrays, sorted by cell after the reorder):
 //   state_x, state_v  float4 per particle (w unused), the state between steps
-//   recA / recB       float4 per particle: position relative to the particle's
-//                     cell origin (xyz) and lambda (w); the two Jacobi buffers
+//   recA / recB       16 bytes per particle: position in fixed point (xyz, see
+//                     below) and lambda (w, FP32); the two Jacobi buffers
 //   xs32              float4 absolute predicted position (FP32), for the
 //                     neighbour predicate
-//   xt                float4 start-of-step position relative to the cell origin
+//   xt                16 bytes: start-of-step position in fixed point
 //   nbr               u32 neighbour entries in blocks of 4 per list column:
 //                     entry k of column t at ((k/4)*n + t)*4 + k%4 (a thread
 //                     reads a block with one 16-byte load; a warp of
@@ -19,13 +19,16 @@
 //                     the grid, so the solver reads whole blocks without
 //                     bounds checks.
 //
-// Positions inside the solver are stored relative to the particle's cell
-// origin (m + c) * q, with q = h rounded to 8 significant bits so that every
-// origin and every origin difference (+-q per axis) is exact in FP32. The
-// difference of two positions is then (p_i - p_j) + (o_i - o_j), the origin
-// difference looked up by the entry's cell code, with |p| ~ h, which keeps
-// FP32 rounding at the scale of h instead of the scale of the domain (a 10 m
-// basin has an FP32 spacing of ~1e-6 m).
+// Positions inside the solver are 32-bit integers: units of u = 2^e metres
+// (2^22 u >= h > 2^21 u, so u <= h / 2^21, 3e-8 m at h = 0.1) relative to the
+// scene's grid origin. The difference of two positions is then exact, one
+// integer subtraction, at any distance from the origin (a 10 m basin has an
+// FP32 spacing of ~1e-6 m). With the bias M = 1.5 * 2^23 added, a difference
+// d with |d| < 2^22 is the bit pattern of the float M + d exactly, so one FMA
+// (bits as float) * u - M * u gives d * u in metres with no rounding. A larger
+// |d| gives a value of magnitude >= 2^22 u >= h, which the kernels treat as
+// out of range, as it is; as long as a scene spans fewer than 8e8 units, no
+// difference reaches a bit pattern of an infinity or a NaN.
 #include "apbf_internal.h"
 
 namespace apbf {
@@ -65,10 +68,6 @@ __device__ __forceinline__ int3 unpack_cell(uint32_t v)
     return make_int3((int)(v & 2047u), (int)((v >> 11) & 2047u), (int)(v >> 22));
 }
 
-__device__ __forceinline__ float3 cell_origin(int3 c, const StepConst &sc)
-{
-    return make_float3((float)(sc.m[0] + c.x) * sc.q, (float)(sc.m[1] + c.y) * sc.q, (float)(sc.m[2] + c.z) * sc.q);
-}
 
 __device__ __forceinline__ float camera_distance(float4 x, const DynParams *dyn)
 {
@@ -94,34 +93,33 @@ __device__ __forceinline__ uint32_t lod_level(float d, float dmin, float dmax, c
     return sc.n_max - (uint32_t)b;
 }
 
-// Cell-origin difference o_i - o_j = -(offset) q for the 27 neighbour cells,
-// by the entry's code c = (dx+1) + 3 (dy+1) + 9 (dz+1). The x and y parts
-// are one 8-byte word and z a 4-byte word: two shared loads per neighbour
-// with fewer bank conflicts than one 16-byte load of a float4 table.
-struct OffsetTab {
-    float2 xy[27];
-    float z[27];
-};
-
-__device__ __forceinline__ void fill_dtab(OffsetTab *dtab, float q)
+// Fixed-point solver positions (see the top of this file).
+__device__ __forceinline__ long long fx_anchor(float glo, float inv_u)
 {
-    if (threadIdx.x < 27) {
-        int c = threadIdx.x;
-        float ox = (float)(c % 3 - 1), oy = (float)((c / 3) % 3 - 1), oz = (float)(c / 9 - 1);
-        dtab->xy[c] = make_float2(-ox * q, -oy * q);
-        dtab->z[c] = -oz * q;
-    }
+    return __float2ll_rd(__fmul_rn(glo, inv_u));  // the grid origin in units, rounded down
 }
 
-// The same offsets decoded arithmetically (the velocity pass, where this
-// measured faster than the table): cz = c / 9, cy = (c mod 9) / 3, cx = c mod 3
-// by multiply-shift (exact for c < 27), then q - q * cx and so on, exact
-// because q has 8 significant bits.
-__device__ __forceinline__ float3 cell_offset_arith(uint32_t c, float q)
+// A position in units relative to the anchor: x * 2^-e is exact in FP32, so
+// the only rounding is the conversion to the nearest integer.
+__device__ __forceinline__ int32_t fx_of(float x, long long anchor, float inv_u)
 {
-    const uint32_t cz = (c * 57u) >> 9, r = c - 9u * cz, cy = (r * 11u) >> 5, cx = r - 3u * cy;
-    return make_float3(__fmaf_rn(-q, (float)cx, q), __fmaf_rn(-q, (float)cy, q), __fmaf_rn(-q, (float)cz, q));
+    return (int32_t)(__float2ll_rn(__fmul_rn(x, inv_u)) - anchor);
 }
+
+// The FP32 absolute position nearest to a fixed-point one (one rounding).
+__device__ __forceinline__ float fx_abs(int32_t a, long long anchor, float u)
+{
+    return __fmul_rn(__ll2float_rn((long long)a + anchor), u);
+}
+
+__device__ __forceinline__ int32_t fx_bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ float fx_word(int32_t v) { return __int_as_float(v); }
+
+// A particle's biased position: (M + x_i / u) mod 2^32, M = kFxMagic.
+__device__ __forceinline__ uint32_t fx_biased(float v) { return __float_as_uint(v) + (uint32_t)kFxMagic; }
+
+// The float with the bit pattern (M + (x_i - x_j) / u) mod 2^32 (wrapping, unsigned).
+__device__ __forceinline__ float fx_diff_word(uint32_t mi, float vj) { return __uint_as_float(mi - __float_as_uint(vj)); }
 
 // Paired FP32 arithmetic (sm_100 and later): two IEEE round-to-nearest
 // operations in one instruction, each lane's result the same bits as the
@@ -131,14 +129,6 @@ __device__ __forceinline__ float2 sub2_rn(float2 a, float2 b)
     float2 r;
     asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
         "sub.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0, %1}, rc;\n\t}"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return r;
-}
-__device__ __forceinline__ float2 add2_rn(float2 a, float2 b)
-{
-    float2 r;
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "add.rn.f32x2 rc, ra, rb;\n\tmov.b64 {%0, %1}, rc;\n\t}"
         : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return r;
 }
@@ -298,7 +288,6 @@ struct Geo {
     float glo[3];
     int nx, ny, nz;
     uint32_t cell_base;
-    int m[3];
 };
 
 template <bool BATCH>
@@ -320,9 +309,6 @@ __device__ __forceinline__ Geo geo_of(const StepConst &sc, const Buffers &b, uin
         g.ny = __ldg(&t->ny);
         g.nz = __ldg(&t->nz);
         g.cell_base = __ldg(&t->cell_base);
-        g.m[0] = __ldg(&t->m[0]);
-        g.m[1] = __ldg(&t->m[1]);
-        g.m[2] = __ldg(&t->m[2]);
     } else {
         g.glo[0] = sc.glo[0];
         g.glo[1] = sc.glo[1];
@@ -331,9 +317,6 @@ __device__ __forceinline__ Geo geo_of(const StepConst &sc, const Buffers &b, uin
         g.ny = sc.ny;
         g.nz = sc.nz;
         g.cell_base = 0u;
-        g.m[0] = sc.m[0];
-        g.m[1] = sc.m[1];
-        g.m[2] = sc.m[2];
     }
     return g;
 }
@@ -349,9 +332,17 @@ __device__ __forceinline__ uint32_t key_in(int3 c, const Geo &g)
     return g.cell_base + ((uint32_t)c.z * (uint32_t)g.ny + (uint32_t)c.y) * (uint32_t)g.nx + (uint32_t)c.x;
 }
 
-__device__ __forceinline__ float3 origin_in(int3 c, const Geo &g, float q)
+// The scene's fixed-point anchors (its grid origin in units).
+struct Anchor {
+    long long a[3];
+};
+
+__device__ __forceinline__ Anchor anchor_of(const Geo &g, const StepConst &sc)
 {
-    return make_float3((float)(g.m[0] + c.x) * q, (float)(g.m[1] + c.y) * q, (float)(g.m[2] + c.z) * q);
+    Anchor A;
+    for (int k = 0; k < 3; ++k)
+        A.a[k] = fx_anchor(g.glo[k], sc.fx_inv_u);
+    return A;
 }
 
 // ------------------------------------------------------------- a1: range
@@ -1114,9 +1105,12 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
     b.xs32[p] = make_float4(xp.x, xp.y, xp.z, 0.0f);
     b.cell_s[p] = pack_cell(c);
     if (!diag) {
-        float3 o = origin_in(c, g, sc.q);
-        b.recA[p] = make_float4(__fsub_rn(xp.x, o.x), __fsub_rn(xp.y, o.y), __fsub_rn(xp.z, o.z), 0.0f);
-        b.xt[p] = make_float4(__fsub_rn(x.x, o.x), __fsub_rn(x.y, o.y), __fsub_rn(x.z, o.z), 0.0f);
+        const Anchor A = anchor_of(g, sc);
+        const float iu = sc.fx_inv_u;
+        b.recA[p] = make_float4(fx_word(fx_of(xp.x, A.a[0], iu)), fx_word(fx_of(xp.y, A.a[1], iu)),
+                                fx_word(fx_of(xp.z, A.a[2], iu)), 0.0f);
+        b.xt[p] = make_float4(fx_word(fx_of(x.x, A.a[0], iu)), fx_word(fx_of(x.y, A.a[1], iu)),
+                              fx_word(fx_of(x.z, A.a[2], iu)), 0.0f);
         b.id_s[p] = id;
         b.lvl_s[p] = b.lvl[i];
     }
@@ -1133,8 +1127,8 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
 {
     wait_for_predecessor();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) {  // the padding entries' record: beyond reach of every particle (r^2 = inf)
-        const float4 far = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.0f);
+    if (t == 0) {  // the padding entries' record: at least 3h from every particle on every axis
+        const float4 far = make_float4(fx_word(kFxFar), fx_word(kFxFar), fx_word(kFxFar), 0.0f);
         b.recA[sc.n] = far;
         b.recB[sc.n] = far;
         b.xt[sc.n] = far;
@@ -1419,6 +1413,49 @@ __device__ __forceinline__ void contact_obstacles(const DynParams *d, float3 og,
         project_obstacle(d->obst[k], og, px, py, pz);
 }
 
+// The box in fixed point: the first and last unit inside [box_lo, box_hi].
+struct BoxFx {
+    int32_t lo[3], hi[3];
+};
+
+__device__ __forceinline__ BoxFx box_fx(const DynParams *d, const Anchor &A, float inv_u)
+{
+    BoxFx k;
+    for (int a = 0; a < 3; ++a) {
+        k.lo[a] = (int32_t)(__float2ll_ru(__fmul_rn(d->box_lo[a], inv_u)) - A.a[a]);
+        k.hi[a] = (int32_t)(__float2ll_rd(__fmul_rn(d->box_hi[a], inv_u)) - A.a[a]);
+    }
+    return k;
+}
+
+// Contacts of a fixed-point position (the collision response of Fig. 7):
+// the obstacles in order, then the box. The obstacles act in FP32 relative to
+// og, the FP32 position nearest the particle's own: og is a whole number of
+// units, so the particle's offset from it and the move back are exact, and the
+// arithmetic is at the scale of the obstacle, not of the domain.
+__device__ __forceinline__ void obstacles_fx(const DynParams *d, const Anchor &A, const StepConst &sc,
+                                             int32_t (&a)[3])
+{
+    {
+        long long ogu[3];
+        float og[3], p[3];
+        for (int k = 0; k < 3; ++k) {
+            og[k] = fx_abs(a[k], A.a[k], sc.fx_u);
+            ogu[k] = __float2ll_rn(__fmul_rn(og[k], sc.fx_inv_u));
+            p[k] = __fmul_rn(__ll2float_rn((long long)a[k] + A.a[k] - ogu[k]), sc.fx_u);
+        }
+        contact_obstacles(d, make_float3(og[0], og[1], og[2]), p[0], p[1], p[2]);
+        for (int k = 0; k < 3; ++k)
+            a[k] = (int32_t)(ogu[k] - A.a[k] + __float2ll_rn(__fmul_rn(p[k], sc.fx_inv_u)));
+    }
+}
+
+__device__ __forceinline__ void clamp_fx(const BoxFx &bx, int32_t (&a)[3])
+{
+    for (int k = 0; k < 3; ++k)
+        a[k] = min(max(a[k], bx.lo[k]), bx.hi[k]);
+}
+
 // The pre-stabilisation loop of Fig. 7 (Sec. 4.3): the particles of level < S are moved out of
 // the obstacles and into the box stabil_iters times, the start-of-step
 // position (xt) and the prediction (recA) by the same amount, so the
@@ -1432,23 +1469,23 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
     const uint32_t s = scene_of<BATCH>(b, p);
     const Geo g = geo_of<BATCH>(sc, b, s);
     const DynParams *d = b.dyn + s;
-    const float3 og = origin_in(unpack_cell(b.cell_s[p]), g, sc.q);
-    float4 x0 = b.xt[p], xs = b.recA[p];
+    const Anchor A = anchor_of(g, sc);
+    const BoxFx bx = box_fx(d, A, sc.fx_inv_u);
+    const float4 x0f = b.xt[p], xsf = b.recA[p];
+    int32_t x0[3] = {fx_bits(x0f.x), fx_bits(x0f.y), fx_bits(x0f.z)};
+    int32_t xs[3] = {fx_bits(xsf.x), fx_bits(xsf.y), fx_bits(xsf.z)};
     for (uint32_t it = 0; it < sc.stabil_iters; ++it) {
-        float qx = x0.x, qy = x0.y, qz = x0.z;
-        contact_obstacles(d, og, qx, qy, qz);
-        qx = fminf(fmaxf(qx, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
-        qy = fminf(fmaxf(qy, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
-        qz = fminf(fmaxf(qz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
-        xs.x += qx - x0.x;
-        xs.y += qy - x0.y;
-        xs.z += qz - x0.z;
-        x0.x = qx;
-        x0.y = qy;
-        x0.z = qz;
+        int32_t q[3] = {x0[0], x0[1], x0[2]};
+        if (d->n_obst)
+            obstacles_fx(d, A, sc, q);
+        clamp_fx(bx, q);
+        for (int k = 0; k < 3; ++k) {
+            xs[k] += q[k] - x0[k];
+            x0[k] = q[k];
+        }
     }
-    b.xt[p] = x0;
-    b.recA[p] = xs;
+    b.xt[p] = make_float4(fx_word(x0[0]), fx_word(x0[1]), fx_word(x0[2]), x0f.w);
+    b.recA[p] = make_float4(fx_word(xs[0]), fx_word(xs[1]), fx_word(xs[2]), xsf.w);
 }
 
 // ---------------------------------------------------------- a8: lambda pass
@@ -1459,18 +1496,21 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
 // instantiations that inline it (dense or compacted, block size, batch
 // depth UNR): a particle's result is the same bits whichever computes it.
 template <int UNR = kUnroll>
-__device__ __forceinline__ void lambda_one(const StepConst &sc, const OffsetTab *dtab, const float4 *__restrict__ A,
+__device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__restrict__ A,
                                            const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
                                            const float4 &ai,
                                            float &lam, float &rho)
 {
     float racc = 0.0f, gz = 0.0f, s2 = 0.0f;
     float2 gxy = make_float2(0.0f, 0.0f);
+    // the particle's fixed-point position plus the bias: one subtraction per axis
+    // gives the bit pattern of M + (x_i - x_j) / u (see the top of this file)
+    const uint32_t mx = fx_biased(ai.x), my = fx_biased(ai.y), mz = fx_biased(ai.z);
+    const float2 u2 = make_float2(sc.fx_u, sc.fx_u), off2 = make_float2(sc.fx_off, sc.fx_off);
     for_each_neighbor<UNR>(nbr, t, n, nn, A, [&](uint32_t e, const float4 &aj) {
-        const uint32_t c = e >> kSlotBits;
-        const float2 dxy = add2_rn(sub2_rn(make_float2(ai.x, ai.y), make_float2(aj.x, aj.y)), dtab->xy[c]);
+        const float2 dxy = fma2_rn(make_float2(fx_diff_word(mx, aj.x), fx_diff_word(my, aj.y)), u2, off2);
         const float dx = dxy.x, dy = dxy.y;
-        const float dz = __fadd_rn(__fsub_rn(ai.z, aj.z), dtab->z[c]);
+        const float dz = __fmaf_rn(fx_diff_word(mz, aj.z), sc.fx_u, sc.fx_off);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         // branch-free: every pair runs the same instructions; a pair at or past
         // h adds an exact zero (u = 0, gw = 0), and so does the gradient of a
@@ -1512,10 +1552,6 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
     const uint32_t *__restrict__ act, const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt,
     const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr, int part)
 {
-    __shared__ OffsetTab dtab_s;
-    const OffsetTab *dtab = &dtab_s;
-    fill_dtab(&dtab_s, sc.q);
-    __syncthreads();
     wait_for_predecessor();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
     const uint32_t cnt_prev = DENSE ? sc.n : lvl_count[l - 1];
@@ -1541,7 +1577,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
             continue;
         }
         float lam, rho;
-        lambda_one(sc, dtab, A, nbr, t, n, nbr_cnt[t], ai, lam, rho);
+        lambda_one(sc, A, nbr, t, n, nbr_cnt[t], ai, lam, rho);
         B[p] = make_float4(ai.x, ai.y, ai.z, lam);
         rho_out[p] = rho;
     }
@@ -1563,40 +1599,46 @@ __device__ __forceinline__ float powi(float x, uint32_t n)
     return r;
 }
 
-// The scene's box and obstacle count read once per kernel (single scene).
-struct BoxK {
-    float lo[3], hi[3];
-    uint32_t n_obst;
+// The single scene's fixed-point box, read once per kernel (the anchors are
+// recomputed where obstacles need them, so they hold no registers in the loop).
+struct SceneK {
+    BoxFx bx;
+    bool obstacles;
 };
 
-__device__ __forceinline__ BoxK box_of(const DynParams *dyn)
+__device__ __forceinline__ Anchor scene_anchor(const StepConst &sc)
 {
-    BoxK k;
-    for (int a = 0; a < 3; ++a) {
-        k.lo[a] = dyn->box_lo[a];
-        k.hi[a] = dyn->box_hi[a];
-    }
-    k.n_obst = dyn->n_obst;
+    Anchor A;
+    for (int a = 0; a < 3; ++a)
+        A.a[a] = fx_anchor(sc.glo[a], sc.fx_inv_u);
+    return A;
+}
+
+__device__ __forceinline__ SceneK scene_k(const StepConst &sc, const DynParams *dyn)
+{
+    SceneK k;
+    k.bx = box_fx(dyn, scene_anchor(sc), sc.fx_inv_u);
+    k.obstacles = dyn->n_obst != 0;
     return k;
 }
 
-// Eq. 7 for one particle and the contacts after it: the new position
-// relative to its cell origin; explicit rounding intrinsics as in lambda_one,
-// so the result does not depend on which instantiation computes it.
+// Eq. 7 for one particle and the contacts after it: the new fixed-point
+// position; explicit rounding intrinsics as in lambda_one, so the result does
+// not depend on which instantiation computes it.
 template <int NPOW, bool BATCH, int UNR = kUnroll>
-__device__ __forceinline__ float3 deltap_one(const StepConst &sc, const OffsetTab *dtab, const float4 *__restrict__ B,
-                                             const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
-                                             const float4 &bi,
-                                             uint32_t p, const uint32_t *__restrict__ cell_s,
-                                             const DynParams *__restrict__ dyn, const Buffers &b, const BoxK &bk)
+__device__ __forceinline__ int3 deltap_one(const StepConst &sc, const float4 *__restrict__ B,
+                                           const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
+                                           const float4 &bi, uint32_t p, const DynParams *__restrict__ dyn,
+                                           const Buffers &b, const SceneK &sk)
 {
     float2 axy = make_float2(0.0f, 0.0f);
     float az = 0.0f;
+    const uint32_t mx = fx_biased(bi.x), my = fx_biased(bi.y), mz = fx_biased(bi.z);
+    const float2 u2 = make_float2(sc.fx_u, sc.fx_u), off2 = make_float2(sc.fx_off, sc.fx_off);
     for_each_neighbor<UNR>(nbr, t, n, nn, B, [&](uint32_t e, const float4 &bj) {
-        const uint32_t c = e >> kSlotBits;
-        const float2 dxy = add2_rn(sub2_rn(make_float2(bi.x, bi.y), make_float2(bj.x, bj.y)), dtab->xy[c]);
+        const float2 dxy = fma2_rn(make_float2(fx_diff_word(mx, bj.x), fx_diff_word(my, bj.y)), u2, off2);
         const float dx = dxy.x, dy = dxy.y;
-        const float dz = __fadd_rn(__fsub_rn(bi.z, bj.z), dtab->z[c]);
+        const float dz = __fmaf_rn(fx_diff_word(mz, bj.z), sc.fx_u, sc.fx_off);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         // as in lambda_one: pairs at or past h and coincident pairs add an exact zero
         const bool in = r2 < sc.h2 && r2 > 0.0f;
@@ -1610,28 +1652,29 @@ __device__ __forceinline__ float3 deltap_one(const StepConst &sc, const OffsetTa
         axy = fma2_rn(make_float2(f, f), dxy, axy);
         az = __fmaf_rn(f, dz, az);
     });
-    // new position; contacts: obstacles, then the box, expressed relative to the cell origin
-    float px = __fmaf_rn(sc.c_dp, axy.x, bi.x);
-    float py = __fmaf_rn(sc.c_dp, axy.y, bi.y);
-    float pz = __fmaf_rn(sc.c_dp, az, bi.z);
+    // new position in units; contacts: obstacles, then the box
+    int32_t a[3] = {fx_bits(bi.x) + __float2int_rn(__fmul_rn(sc.c_dpu, axy.x)),
+                    fx_bits(bi.y) + __float2int_rn(__fmul_rn(sc.c_dpu, axy.y)),
+                    fx_bits(bi.z) + __float2int_rn(__fmul_rn(sc.c_dpu, az))};
     if (BATCH) {
+        // per scene, each bound computed where it is used (fewer live registers)
         const uint32_t s = scene_of<true>(b, p);
-        const Geo g = geo_of<true>(sc, b, s);
         const DynParams *d = dyn + s;
-        const float3 og = origin_in(unpack_cell(cell_s[p]), g, sc.q);
-        contact_obstacles(d, og, px, py, pz);
-        px = fminf(fmaxf(px, d->box_lo[0] - og.x), d->box_hi[0] - og.x);
-        py = fminf(fmaxf(py, d->box_lo[1] - og.y), d->box_hi[1] - og.y);
-        pz = fminf(fmaxf(pz, d->box_lo[2] - og.z), d->box_hi[2] - og.z);
+        const SceneGeom *t = b.geo + s;
+        if (d->n_obst)
+            obstacles_fx(d, anchor_of(geo_of<true>(sc, b, s), sc), sc, a);
+        for (int k = 0; k < 3; ++k) {
+            const long long ak = fx_anchor(__ldg(&t->glo[k]), sc.fx_inv_u);
+            const int32_t lo = (int32_t)(__float2ll_ru(__fmul_rn(d->box_lo[k], sc.fx_inv_u)) - ak);
+            const int32_t hi = (int32_t)(__float2ll_rd(__fmul_rn(d->box_hi[k], sc.fx_inv_u)) - ak);
+            a[k] = min(max(a[k], lo), hi);
+        }
     } else {
-        const float3 og = cell_origin(unpack_cell(cell_s[p]), sc);
-        if (bk.n_obst)
-            contact_obstacles(dyn, og, px, py, pz);
-        px = fminf(fmaxf(px, bk.lo[0] - og.x), bk.hi[0] - og.x);
-        py = fminf(fmaxf(py, bk.lo[1] - og.y), bk.hi[1] - og.y);
-        pz = fminf(fmaxf(pz, bk.lo[2] - og.z), bk.hi[2] - og.z);
+        if (sk.obstacles)
+            obstacles_fx(dyn, scene_anchor(sc), sc, a);
+        clamp_fx(sk.bx, a);
     }
-    return make_float3(px, py, pz);
+    return make_int3(a[0], a[1], a[2]);
 }
 
 
@@ -1645,24 +1688,19 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_
     const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr,
     int part)
 {
-    __shared__ OffsetTab dtab_s;
-    const OffsetTab *dtab = &dtab_s;
-    fill_dtab(&dtab_s, sc.q);
-    __syncthreads();
     wait_for_predecessor();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
     const bool masked = !DENSE && (float)cnt_l >= mask_thr * (float)sc.n;
     const uint32_t work = masked ? sc.n : cnt_l;
     const size_t n = sc.n;
-    const BoxK bk = box_of(dyn);
+    const SceneK sk = scene_k(sc, dyn);
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
         const uint32_t p = part ? act[t] : t;  // t: list column (active-list position with a partition)
         if (masked && b.lvl_s[p] < l)
             continue;
         const float4 bi = B[p];
-        const float3 np = deltap_one<NPOW, BATCH>(sc, dtab, B, nbr, t, n, nbr_cnt[t], bi, p, cell_s, dyn, b, bk);
-        const float px = np.x, py = np.y, pz = np.z;
-        A[p] = make_float4(px, py, pz, bi.w);
+        const int3 np = deltap_one<NPOW, BATCH>(sc, B, nbr, t, n, nbr_cnt[t], bi, p, dyn, b, sk);
+        A[p] = make_float4(fx_word(np.x), fx_word(np.y), fx_word(np.z), bi.w);
     }
 }
 
@@ -1688,10 +1726,12 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
     const size_t n = sc.n;
     const float4 af = b.recA[p];
     const float4 x0 = b.xt[p];
-    const float vx = (af.x - x0.x) * sc.inv_dt;
-    const float vy = (af.y - x0.y) * sc.inv_dt;
-    const float vz = (af.z - x0.z) * sc.inv_dt;
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    // displacement over the step in units (exact), v = displacement * u / dt
+    const int32_t dix = fx_bits(af.x) - fx_bits(x0.x), diy = fx_bits(af.y) - fx_bits(x0.y),
+                  diz = fx_bits(af.z) - fx_bits(x0.z);
+    const float vx = (float)dix * sc.v_scale, vy = (float)diy * sc.v_scale, vz = (float)diz * sc.v_scale;
+    const uint32_t mx = fx_biased(af.x), my = fx_biased(af.y), mz = fx_biased(af.z);
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // sum of (v_j - v_i) W, velocities in units per step
     const uint32_t nn = b.nbr_cnt[t];
     b.prev_cnt[p] = (uint8_t)nn;  // by state slot, for the next step's depth image
     const uint4 *e_ptr = reinterpret_cast<const uint4 *>(b.nbr) + t;
@@ -1709,28 +1749,29 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const float3 o = cell_offset_arith(e[u] >> kSlotBits, sc.q);
-            const float dx = (af.x - aj[u].x) + o.x;
-            const float dy = (af.y - aj[u].y) + o.y;
-            const float dz = (af.z - aj[u].z) + o.z;
+            const float dx = fmaf(fx_diff_word(mx, aj[u].x), sc.fx_u, sc.fx_off);
+            const float dy = fmaf(fx_diff_word(my, aj[u].y), sc.fx_u, sc.fx_off);
+            const float dz = fmaf(fx_diff_word(mz, aj[u].z), sc.fx_u, sc.fx_off);
             const float r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < sc.h2) {
                 const float w = sc.h2 - r2;
                 const float W = w * w * w;
-                sx += ((aj[u].x - xj[u].x) * sc.inv_dt - vx) * W;
-                sy += ((aj[u].y - xj[u].y) * sc.inv_dt - vy) * W;
-                sz += ((aj[u].z - xj[u].z) * sc.inv_dt - vz) * W;
+                // (v_j - v_i) in units per step: the difference of the two displacements, exact
+                sx += (float)(fx_bits(aj[u].x) - fx_bits(xj[u].x) - dix) * W;
+                sy += (float)(fx_bits(aj[u].y) - fx_bits(xj[u].y) - diy) * W;
+                sz += (float)(fx_bits(aj[u].z) - fx_bits(xj[u].z) - diz) * W;
             }
         }
     }
     const uint32_t s = scene_of<BATCH>(b, p);
-    const float3 og = origin_in(unpack_cell(b.cell_s[p]), geo_of<BATCH>(sc, b, s), sc.q);
+    const Anchor A = anchor_of(geo_of<BATCH>(sc, b, s), sc);
     const DynParams *dyn = b.dyn + s;
-    float px = fminf(fmaxf(og.x + af.x, dyn->box_lo[0]), dyn->box_hi[0]);
-    float py = fminf(fmaxf(og.y + af.y, dyn->box_lo[1]), dyn->box_hi[1]);
-    float pz = fminf(fmaxf(og.z + af.z, dyn->box_lo[2]), dyn->box_hi[2]);
+    float px = fminf(fmaxf(fx_abs(fx_bits(af.x), A.a[0], sc.fx_u), dyn->box_lo[0]), dyn->box_hi[0]);
+    float py = fminf(fmaxf(fx_abs(fx_bits(af.y), A.a[1], sc.fx_u), dyn->box_lo[1]), dyn->box_hi[1]);
+    float pz = fminf(fmaxf(fx_abs(fx_bits(af.z), A.a[2], sc.fx_u), dyn->box_lo[2]), dyn->box_hi[2]);
+    const float cv = sc.c_xsph * sc.v_scale;
     b.state_x[p] = make_float4(px, py, pz, 0.0f);
-    b.state_v[p] = make_float4(vx + sc.c_xsph * sx, vy + sc.c_xsph * sy, vz + sc.c_xsph * sz, 0.0f);
+    b.state_v[p] = make_float4(vx + cv * sx, vy + cv * sy, vz + cv * sz, 0.0f);
     b.state_id[p] = b.id_s[p];
 }
 
@@ -1838,8 +1879,9 @@ __global__ void __launch_bounds__(kBlock) debug_xstar_kernel(StepConst sc, Buffe
     if (p >= sc.n)
         return;
     const float4 r = rec[p];
-    const float3 og = origin_in(unpack_cell(b.cell_s[p]), geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p)), sc.q);
-    b.dbg4[p] = make_float4(og.x + r.x, og.y + r.y, og.z + r.z, 0.0f);
+    const Anchor A = anchor_of(geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p)), sc);
+    b.dbg4[p] = make_float4(fx_abs(fx_bits(r.x), A.a[0], sc.fx_u), fx_abs(fx_bits(r.y), A.a[1], sc.fx_u),
+                            fx_abs(fx_bits(r.z), A.a[2], sc.fx_u), 0.0f);
 }
 
 __global__ void __launch_bounds__(kBlock) debug_lambda_kernel(StepConst sc, Buffers b, const float4 *__restrict__ rec)

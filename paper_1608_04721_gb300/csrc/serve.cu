@@ -279,7 +279,6 @@ apbf_status relayout(apbf_server *sv)
         SceneGeom &g = s->geo[k];
         for (int a = 0; a < 3; ++a) {
             g.glo[a] = r->geo.glo[a];
-            g.m[a] = r->geo.m[a];
             s->grid_hi3[3 * k + a] = r->desc.grid_hi[a];
             s->dyn[k].box_lo[a] = r->desc.box_lo[a];
             s->dyn[k].box_hi[a] = r->desc.box_hi[a];
@@ -304,10 +303,8 @@ apbf_status relayout(apbf_server *sv)
     sc.level_tiles = (sc.n + kLevelTile - 1) / kLevelTile;
     if (count == 1) {  // the single-scene kernels read the grid from the step constants
         const StepConst &g = sv->resident[0]->geo;
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3; ++a)
             sc.glo[a] = g.glo[a];
-            sc.m[a] = g.m[a];
-        }
         sc.nx = g.nx;
         sc.ny = g.ny;
         sc.nz = g.nz;
@@ -571,6 +568,9 @@ APBF_API apbf_status apbf_server_submit(apbf_server *sv, const apbf_request *req
         return sfail(sv, st, m);
     if (d->n > sv->cap.n || r->geo.ncell > sv->cap.ncell)
         return sfail(sv, APBF_ERR_INVALID_ARG, "the scene alone exceeds the server's particle or cell capacity");
+    if (r->geo.fx_e != fx_exponent_for_h(d->h))
+        return sfail(sv, APBF_ERR_NOT_SUPPORTED, "the scene's grid spans 8e8 or more fixed-point units on an axis; "
+                                                 "such scenes step alone, not in a pool");
     const size_t n3 = 3 * (size_t)d->n;
     for (size_t i = 0; i < n3; ++i)
         if (!std::isfinite(d->pos[i]) || (d->vel && !std::isfinite(d->vel[i])))

@@ -185,3 +185,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)
+
+
+def test_a_long_grid_steps_alone_but_not_in_a_batch():
+    """A grid spanning 8e8 or more fixed-point units on an axis (here 30 m at
+    h = 0.1, 1.0e9 units of 2^-25 m) takes a coarser unit when the scene is
+    alone; a batch shares the unit its h gives, so such a scene is refused
+    there (host-only sizing calls, no GPU)."""
+    cfg = scenes.config_dam_break_4k().replace(lattice=(4, 4, 4))
+    x, v = scenes.make_scene(cfg)
+    a = apbf.desc_from_config(cfg, x, v, 8078.2)
+    long_cfg = cfg.replace(box_hi=(30.0, 1.6, 1.6))
+    b = apbf.desc_from_config(long_cfg, x, v, 8078.2)
+    assert apbf.apbf_scene_bytes(b) > 0
+    assert apbf.apbf_batch_bytes([b]) > 0          # a batch of one is the scene alone
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_batch_bytes([a, b])
+    assert e.value.status == apbf.APBF_ERR_NOT_SUPPORTED and "scene 1" in apbf.apbf_last_error()
+    # 23.8 m (7.99e8 units) still shares the unit
+    ok = apbf.desc_from_config(cfg.replace(box_hi=(23.8, 1.6, 1.6)), x, v, 8078.2)
+    assert apbf.apbf_batch_bytes([a, ok]) > 0

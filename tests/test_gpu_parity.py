@@ -141,6 +141,13 @@ SMALL = {
     "apbf_33": lambda: (scenes.config_dam_break_4k().replace(lattice=(11, 3, 1), lod_mode=scenes.LOD_DTC,
                                                              n_min=1, n_max=3, camera="fixed", eye=(2.0, 0.1, 0.1)),
                         {}),
+    # a 30 m grid spans 1.0e9 units of 2^-25 m, so the solver takes the coarser unit 2^-24 m; the
+    # block sits 25 m from the grid origin and near x = 0, where FP32 positions resolve 1e-5 h
+    # (at 20 m the FP32 spacing alone is 1.9e-6 m)
+    "apbf_long_grid_4096": lambda: (
+        scenes.config_dam_break_4k().replace(box_lo=(-25.0, 0.0, 0.0), box_hi=(5.0, 1.6, 1.6),
+                                             block_lo=(0.0, 0.0, 0.0), lod_mode=scenes.LOD_DTC, n_min=2,
+                                             n_max=5, camera="fixed", eye=(-1.0, 0.8, 0.8)), {}),
 }
 
 
