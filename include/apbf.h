@@ -59,7 +59,8 @@ typedef enum apbf_status {
     APBF_ERR_TIMEOUT = 4,           /* a bounded device-side wait gave up */
     APBF_ERR_BAD_STATE = 5,         /* call not valid in the scene's current state */
     APBF_ERR_NEIGHBOR_OVERFLOW = 6, /* a particle had more neighbours than max_neighbors */
-    APBF_ERR_NOT_SUPPORTED = 7      /* option outside what this build implements */
+    APBF_ERR_NOT_SUPPORTED = 7,     /* option outside what this build implements */
+    APBF_ERR_CHECK_FAILED = 8       /* an invariant check of the debug build failed (message: which, where) */
 } apbf_status;
 
 /* Level-of-detail models (Sec. 4.1). */
@@ -530,6 +531,25 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *scene, uint32_t field, void *ho
 /* Sizes of the scene's grid: dims (3 ints), ncell, max_neighbors (host outputs). */
 APBF_API apbf_status apbf_debug_dims(apbf_scene *scene, int32_t dims[3], uint32_t *ncell,
                                      uint32_t *max_neighbors);
+
+/*
+ * Debug build (libapbf_debug.so, compiled with APBF_DEBUG_CHECKS=1; the
+ * paper has no counterpart): every step also checks, on the device, that each
+ * cell key lies in its grid, that the cell counts add up to the particle count,
+ * that each particle's sorted slot lies in its cell's range, that |P_l| <= n and
+ * |P_l| <= |P_(l-1)|, and that every neighbour entry names a particle (or the
+ * padding record). A failure keeps the guarded access inside its array, and
+ * the next synchronising call returns APBF_ERR_CHECK_FAILED (sticky) naming the
+ * first failed check and its index. The release build has none of these.
+ */
+/* 1 in the debug build, 0 in the release build. */
+APBF_API int apbf_debug_checks_enabled(void);
+
+/* Debug build only (APBF_ERR_NOT_SUPPORTED otherwise): with what = 1, every
+ * later step's neighbour search writes one entry that names the record past the
+ * padding one (still inside the scene's memory), which the checks must catch;
+ * what = 0 stops it. A test of the checks themselves. */
+APBF_API apbf_status apbf_debug_plant(apbf_scene *scene, uint32_t what);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,11 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libapbf.so")
+# APBF_LIBRARY=debug selects the build with device-side invariant checks
+# (libapbf_debug.so); any other value is taken as a path to the library.
+_CHOICE = os.environ.get("APBF_LIBRARY", "")
+LIB_PATH = (os.path.join(_HERE, "libapbf_debug.so") if _CHOICE == "debug"
+            else _CHOICE or os.path.join(_HERE, "libapbf.so"))
 
 # status codes
 APBF_OK = 0
@@ -25,6 +29,7 @@ APBF_ERR_TIMEOUT = 4
 APBF_ERR_BAD_STATE = 5
 APBF_ERR_NEIGHBOR_OVERFLOW = 6
 APBF_ERR_NOT_SUPPORTED = 7
+APBF_ERR_CHECK_FAILED = 8
 
 APBF_LOD_FIXED = 0
 APBF_LOD_DTC = 1
@@ -155,6 +160,7 @@ EXPORTS = [
     "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune", "apbf_server_bytes",
     "apbf_server_create", "apbf_server_submit", "apbf_server_tick", "apbf_server_query", "apbf_server_last_error",
     "apbf_server_destroy", "apbf_set_view", "apbf_set_obstacles", "apbf_read_positions_async",
+    "apbf_debug_checks_enabled", "apbf_debug_plant",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
 APBF_STATIC_MAX_CELLS = 262144
@@ -206,6 +212,9 @@ def lib():
         L.apbf_debug_step_to.argtypes = [V, C.c_uint32, C.c_uint32]
         L.apbf_debug_read.argtypes = [V, C.c_uint32, V, C.c_size_t]
         L.apbf_debug_dims.argtypes = [V, P(C.c_int32), P(C.c_uint32), P(C.c_uint32)]
+        L.apbf_debug_checks_enabled.restype = C.c_int
+        L.apbf_debug_checks_enabled.argtypes = []
+        L.apbf_debug_plant.argtypes = [V, C.c_uint32]
         L.apbf_batch_bytes.argtypes = [P(apbf_scene_desc), C.c_uint32, P(C.c_size_t)]
         L.apbf_create_batch.argtypes = [P(apbf_scene_desc), C.c_uint32, V, V, C.c_size_t, P(V)]
         L.apbf_set_camera_at.argtypes = [V, C.c_uint32, P(C.c_float), P(C.c_float), C.c_float, C.c_float]
@@ -527,6 +536,14 @@ def apbf_timing_report(scene: Scene):
 
 def apbf_debug_step_to(scene: Scene, stage: int, iteration: int = 0):
     _check(lib().apbf_debug_step_to(scene.handle, stage, iteration), "apbf_debug_step_to", scene)
+
+
+def apbf_debug_checks_enabled() -> bool:
+    return bool(lib().apbf_debug_checks_enabled())
+
+
+def apbf_debug_plant(scene: Scene, what: int):
+    _check(lib().apbf_debug_plant(scene.handle, what), "apbf_debug_plant", scene)
 
 
 def apbf_debug_dims(scene: Scene):

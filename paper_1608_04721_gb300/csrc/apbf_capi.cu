@@ -24,7 +24,8 @@ apbf_status fail(apbf_scene *s, apbf_status st, const std::string &m)
 {
     if (s) {
         s->msg = m;
-        if (st == APBF_ERR_CUDA || st == APBF_ERR_NEIGHBOR_OVERFLOW || st == APBF_ERR_TIMEOUT)
+        if (st == APBF_ERR_CUDA || st == APBF_ERR_NEIGHBOR_OVERFLOW || st == APBF_ERR_TIMEOUT ||
+            st == APBF_ERR_CHECK_FAILED)
             s->sticky = st;
     } else {
         g_create_error = m;
@@ -301,6 +302,7 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.drange = (uint32_t *)P(8 * (size_t)sc.scenes);
     b.err = (uint32_t *)P(4);
     b.err_scene = (uint32_t *)P(4 * (size_t)sc.scenes);
+    b.dbg = (uint32_t *)P(16);
     b.dyn = (DynParams *)P(sizeof(DynParams) * (size_t)sc.scenes);
     b.geo = (const SceneGeom *)P(sizeof(SceneGeom) * (size_t)sc.scenes);
     b.sid = (const uint16_t *)P(2 * n);
@@ -462,6 +464,16 @@ apbf_status check_device_errors(apbf_scene *s)
     uint32_t *h = (uint32_t *)s->pinned_small;
     APBF_CUDA(s, cudaMemcpyAsync(h, s->b.err, 4, cudaMemcpyDeviceToHost, s->stream));
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (*h & kErrDebugCheck) {
+        static const char *what[] = {"?", "cell key outside the grid", "cell counts do not add up to n",
+                                     "sorted slot outside its cell's range", "active count above n or not nested",
+                                     "neighbour entry beyond the padding record"};
+        uint32_t dbg[2] = {0, 0};
+        APBF_CUDA(s, cudaMemcpy(dbg, s->b.dbg, 8, cudaMemcpyDeviceToHost));
+        return fail(s, APBF_ERR_CHECK_FAILED, std::string("debug check ") + std::to_string(dbg[0]) + " (" +
+                                                  what[dbg[0] < 6 ? dbg[0] : 0] + ") failed at index " +
+                                                  std::to_string(dbg[1]));
+    }
     if (*h & kErrNeighborOverflow)
         return fail(s, APBF_ERR_NEIGHBOR_OVERFLOW,
                     "a particle had more neighbours than max_neighbors (" + std::to_string(s->sc.max_nbr) + ")");
@@ -518,6 +530,7 @@ APBF_API const char *apbf_status_string(apbf_status st)
     case APBF_ERR_BAD_STATE: return "bad state";
     case APBF_ERR_NEIGHBOR_OVERFLOW: return "neighbour list overflow";
     case APBF_ERR_NOT_SUPPORTED: return "not supported";
+    case APBF_ERR_CHECK_FAILED: return "debug check failed";
     }
     return "unknown status";
 }
@@ -1401,6 +1414,22 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
         APBF_CUDA(s, cudaMemcpyAsync(host, src, size, cudaMemcpyDeviceToHost, s->stream));
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));
     return check_device_errors(s);
+}
+
+APBF_API int apbf_debug_checks_enabled(void) { return APBF_DEBUG_CHECKS ? 1 : 0; }
+
+APBF_API apbf_status apbf_debug_plant(apbf_scene *s, uint32_t what)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (!APBF_DEBUG_CHECKS)
+        return fail(s, APBF_ERR_NOT_SUPPORTED, "apbf_debug_plant needs the debug build (libapbf_debug.so)");
+    if (what > 1)
+        return fail(s, APBF_ERR_INVALID_ARG, "what must be 0 or 1");
+    APBF_CUDA(s, cudaMemcpyAsync(s->b.dbg + 2, &what, 4, cudaMemcpyHostToDevice, s->stream));
+    APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    return APBF_OK;
 }
 
 APBF_API apbf_status apbf_debug_dims(apbf_scene *s, int32_t dims[3], uint32_t *ncell, uint32_t *max_neighbors)

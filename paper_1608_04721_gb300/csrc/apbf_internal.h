@@ -52,6 +52,21 @@ constexpr int32_t kFxFar = -(1 << 30);    // the padding record: at least 3h fro
 
 // Device error word bits.
 constexpr uint32_t kErrNeighborOverflow = 1u;
+constexpr uint32_t kErrDebugCheck = 2u;  // a debug-build invariant check failed (see APBF_DEBUG_CHECKS)
+
+// Debug-build invariant checks (compiled in with -DAPBF_DEBUG_CHECKS=1; the
+// release library has none). A failed check sets kErrDebugCheck, records the
+// first failure's code and index in Buffers::dbg (dbg[0], dbg[1]) and keeps
+// the access it guards inside its array. dbg[2] != 0 asks the neighbour
+// search to plant one out-of-range entry (a test of the checks themselves).
+#ifndef APBF_DEBUG_CHECKS
+#define APBF_DEBUG_CHECKS 0
+#endif
+constexpr uint32_t kCheckCellKey = 1u;      // a cell key outside the scene's grid
+constexpr uint32_t kCheckScanTotal = 2u;    // the cell counts do not add up to the particle count
+constexpr uint32_t kCheckSortedSlot = 3u;   // a particle's sorted slot outside its cell's range
+constexpr uint32_t kCheckActiveCount = 4u;  // |P_l| above n or above |P_(l-1)|
+constexpr uint32_t kCheckNeighbor = 5u;     // a neighbour entry naming a slot beyond the padding record
 
 // Slots of the 64-bit counters: [0] neighbour pairs of the step, [2 + bin]
 // pairs per level bin (reset each step), two slots of scratch for the density
@@ -188,6 +203,7 @@ struct Buffers {
     const uint16_t *sid;           // scene of each particle slot (constant)
     uint32_t *err;                 // device error word (kErr* bits) of the step
     uint32_t *err_scene;           // the same bits per scene (a batch fails only the scenes that set them)
+    uint32_t *dbg;                 // debug-build checks: first failure's code and index, plant request
     DynParams *dyn;                // per scene
     float4 *snap_x, *snap_v;       // state snapshot for the autotuner
     uint32_t *snap_id;

@@ -150,6 +150,24 @@ __device__ __forceinline__ float2 fma2_rn(float2 a, float2 b, float2 c)
     return r;
 }
 
+// Debug-build invariant check (see APBF_DEBUG_CHECKS): true when ok; a failure
+// is recorded (the first one's code and index) and the caller keeps its access
+// in range. In the release build it is the constant true.
+__device__ __forceinline__ bool check_ok(bool ok, uint32_t code, uint32_t index, uint32_t *err, uint32_t *dbg)
+{
+#if APBF_DEBUG_CHECKS
+    if (!ok) {
+        atomicOr(err, kErrDebugCheck);
+        if (atomicCAS(&dbg[0], 0u, code) == 0u)
+            dbg[1] = index;
+    }
+    return ok;
+#else
+    (void)code, (void)index, (void)err, (void)dbg;
+    return true;
+#endif
+}
+
 // Programmatic dependent launch: a kernel of the step is launched while its
 // predecessor in the stream drains and waits here, before its first global
 // memory access, until the predecessor has completed and its writes are
@@ -162,8 +180,11 @@ __device__ __forceinline__ void wait_for_predecessor()
 
 // Neighbour batch depth and the minimum resident blocks per SM the solver
 // kernels are compiled for (register budget); tuned on the GB300.
-#ifndef APBF_SOLVER_MIN_BLOCKS
-#define APBF_SOLVER_MIN_BLOCKS 5
+#ifndef APBF_LAMBDA_MIN_BLOCKS
+#define APBF_LAMBDA_MIN_BLOCKS 5
+#endif
+#ifndef APBF_DELTAP_MIN_BLOCKS
+#define APBF_DELTAP_MIN_BLOCKS 5
 #endif
 constexpr int kUnroll = (int)kEntryBlock;
 
@@ -173,9 +194,14 @@ constexpr int kUnroll = (int)kEntryBlock;
 // so a thread has kUnroll independent gathers in flight. Entries are read
 // once per pass (streaming hint, they should not displace the records that
 // neighbouring threads reuse from L1).
+// Where the debug-build checks record a failure (unused in the release build).
+struct Chk {
+    uint32_t *err, *dbg;
+};
+
 template <int UNR = kUnroll, typename F>
 __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
-                                                  const float4 *__restrict__ rec, F &&f)
+                                                  const float4 *__restrict__ rec, Chk chk, F &&f)
 {
     static_assert(UNR == (int)kEntryBlock, "one entry block per batch");
     const uint4 *e_ptr = reinterpret_cast<const uint4 *>(nbr) + t;
@@ -186,7 +212,13 @@ __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ n
         const uint4 eb = nxt;
         if (k + UNR < nn)
             nxt = __ldcs(e_ptr + (size_t)(k / UNR + 1) * n);
-        const uint32_t e[UNR] = {eb.x, eb.y, eb.z, eb.w};
+        uint32_t e[UNR] = {eb.x, eb.y, eb.z, eb.w};
+#if APBF_DEBUG_CHECKS
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (!check_ok((e[u] & kSlotMask) <= n, kCheckNeighbor, (uint32_t)t, chk.err, chk.dbg))
+                e[u] = (uint32_t)n | (e[u] & ~kSlotMask);
+#endif
         float4 r[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
@@ -358,8 +390,23 @@ __global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers
     float dmin = 3.0e38f, dmax = 0.0f;
     if (!BATCH) {
         // one scene: a grid-stride loop over a capped grid, so only a few
-        // hundred blocks contend for the two atomics
-        for (uint32_t k = i; k < sc.n; k += gridDim.x * blockDim.x) {
+        // hundred blocks contend for the two atomics; four independent loads
+        // in flight per thread
+        const uint32_t stride = gridDim.x * blockDim.x;
+        uint32_t k = i;
+        for (; k + 3 * stride < sc.n; k += 4 * stride) {
+            float4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                x[u] = b.state_x[k + u * stride];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float d = camera_distance(x[u], b.dyn);
+                dmin = fminf(dmin, d);
+                dmax = fmaxf(dmax, d);
+            }
+        }
+        for (; k < sc.n; k += stride) {
             const float d = camera_distance(b.state_x[k], b.dyn);
             dmin = fminf(dmin, d);
             dmax = fmaxf(dmax, d);
@@ -996,6 +1043,8 @@ __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buff
             p = predict_position(x, b.state_v[i], sc, dyn);
         }
         key = key_in(cell_in(p, g, sc.inv_h), g);
+        if (!check_ok(key < sc.ncell, kCheckCellKey, i, b.err, b.dbg))
+            key = sc.ncell - 1;
         b.key[i] = key;
     }
     // warp-aggregated histogram: one atomic per distinct cell in the warp
@@ -1033,7 +1082,7 @@ __global__ void __launch_bounds__(1024) scan_reduce_kernel(const uint32_t *__res
 
 __global__ void __launch_bounds__(1024) scan_apply_kernel(uint32_t *__restrict__ cnt, uint32_t ncell,
                                                           const uint32_t *__restrict__ tile_sums,
-                                                          uint32_t *__restrict__ start, uint32_t n)
+                                                          uint32_t *__restrict__ start, uint32_t n, Chk chk)
 {
     wait_for_predecessor();
     __shared__ uint32_t sh[32];
@@ -1065,6 +1114,8 @@ __global__ void __launch_bounds__(1024) scan_apply_kernel(uint32_t *__restrict__
             start[base + k] = run;
         run += v[k];
     }
+    if (ncell && base <= ncell - 1 && ncell - 1 < base + 4)  // the last cell: every particle counted
+        check_ok(run == n, kCheckScanTotal, run, chk.err, chk.dbg);
     if (blockIdx.x == 0 && threadIdx.x == 0)
         start[ncell] = n;
 }
@@ -1097,6 +1148,8 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
     for (uint32_t j = s0; j < s1; ++j)
         r += (b.tmp[j] < id) ? 1u : 0u;
     uint32_t p = s0 + r;
+    if (!check_ok(s1 <= sc.n && p < s1, kCheckSortedSlot, i, b.err, b.dbg))
+        return;
     const uint32_t s = scene_of<BATCH>(b, i);
     const Geo g = geo_of<BATCH>(sc, b, s);
     float4 x = b.state_x[i];
@@ -1191,7 +1244,13 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                         const uint32_t q = j + (uint32_t)(__ffs(hits) - 1);
                         hits &= hits - 1u;
                         const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
-                        const uint32_t e = q | ((code_row + dxc) << kSlotBits);
+                        uint32_t qe = q;
+#if APBF_DEBUG_CHECKS
+                        check_ok(q < sc.n, kCheckNeighbor, t, b.err, b.dbg);
+                        if (t == 0 && cnt == 0 && b.dbg[2] != 0u)
+                            qe = sc.n + 1u;  // planted: the record past the padding one (inside the arena)
+#endif
+                        const uint32_t e = qe | ((code_row + dxc) << kSlotBits);
                         eb = make_uint4(eb.y, eb.z, eb.w, e);  // the last four entries, oldest first
                         if (cnt % kEntryBlock == kEntryBlock - 1 && cnt < sc.max_nbr)  // a full block
                             eblk[(size_t)(cnt / kEntryBlock) * n] = eb;
@@ -1300,6 +1359,8 @@ __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers 
             uint32_t bin_end = sc.n_max - l + 1;  // bins 0..n_max-l hold levels >= l
             c = (bin_end >= sc.K) ? sc.n : b.lvl_off[(size_t)bin_end * sc.level_tiles];
         }
+        if (!check_ok(c <= sc.n, kCheckActiveCount, l, b.err, b.dbg))
+            c = sc.n;
         b.lvl_count[l] = c;
     }
 }
@@ -1498,7 +1559,7 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
 template <int UNR = kUnroll>
 __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__restrict__ A,
                                            const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
-                                           const float4 &ai,
+                                           const float4 &ai, Chk chk,
                                            float &lam, float &rho)
 {
     float racc = 0.0f, gz = 0.0f, s2 = 0.0f;
@@ -1507,23 +1568,24 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__
     // gives the bit pattern of M + (x_i - x_j) / u (see the top of this file)
     const uint32_t mx = fx_biased(ai.x), my = fx_biased(ai.y), mz = fx_biased(ai.z);
     const float2 u2 = make_float2(sc.fx_u, sc.fx_u), off2 = make_float2(sc.fx_off, sc.fx_off);
-    for_each_neighbor<UNR>(nbr, t, n, nn, A, [&](uint32_t e, const float4 &aj) {
+    for_each_neighbor<UNR>(nbr, t, n, nn, A, chk, [&](uint32_t e, const float4 &aj) {
         const float2 dxy = fma2_rn(make_float2(fx_diff_word(mx, aj.x), fx_diff_word(my, aj.y)), u2, off2);
         const float dx = dxy.x, dy = dxy.y;
         const float dz = __fmaf_rn(fx_diff_word(mz, aj.z), sc.fx_u, sc.fx_off);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
         // branch-free: every pair runs the same instructions; a pair at or past
-        // h adds an exact zero (u = 0, gw = 0), and so does the gradient of a
-        // coincident pair (its rsqrt is kept finite by the 1e-30 floor, far
-        // below the square of any nonzero distance these coordinates hold), so
+        // h adds an exact zero (u = 0, gw = 0), and the gradient terms of a
+        // coincident pair are exact zeros too (its rsqrt is kept finite by the
+        // 1e-30 floor, far below u^2, the smallest nonzero squared distance of
+        // the fixed-point positions, and its pair vector is exactly zero), so
         // the sums have the bits of a form that skips those pairs
         const bool in = r2 < sc.h2;
-        const float r2c = in ? r2 : sc.h2;
+        const float r2c = fminf(r2, sc.h2);
         const float u = __fsub_rn(sc.h2, r2c);
         racc = __fmaf_rn(__fmul_rn(u, u), u, racc);
         const float ir = rsqrtf(fmaxf(r2c, 1.0e-30f));
         const float hr = __fmaf_rn(-r2c, ir, sc.h);
-        const float gw = (in && r2 > 0.0f) ? __fmul_rn(__fmul_rn(hr, hr), ir) : 0.0f;
+        const float gw = in ? __fmul_rn(__fmul_rn(hr, hr), ir) : 0.0f;
         gxy = fma2_rn(make_float2(gw, gw), dxy, gxy);
         gz = __fmaf_rn(gw, dz, gz);
         s2 = __fmaf_rn(__fmul_rn(gw, gw), r2c, s2);
@@ -1547,10 +1609,11 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__
 // when |P_l| >= mask_thr * n; the threshold is tuned per scene. Both modes do
 // identical arithmetic per particle, so the choice never changes a result.
 template <bool DENSE, int BS>
-__global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_kernel(
+__global__ void __launch_bounds__(BS, APBF_LAMBDA_MIN_BLOCKS * 256 / BS) lambda_kernel(
     StepConst sc, const float4 *__restrict__ A, float4 *__restrict__ B, float *__restrict__ rho_out,
     const uint32_t *__restrict__ act, const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt,
-    const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr, int part)
+    const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr, int part,
+    Chk chk)
 {
     wait_for_predecessor();
     const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
@@ -1577,7 +1640,7 @@ __global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) lambda_
             continue;
         }
         float lam, rho;
-        lambda_one(sc, A, nbr, t, n, nbr_cnt[t], ai, lam, rho);
+        lambda_one(sc, A, nbr, t, n, nbr_cnt[t], ai, chk, lam, rho);
         B[p] = make_float4(ai.x, ai.y, ai.z, lam);
         rho_out[p] = rho;
     }
@@ -1635,20 +1698,21 @@ __device__ __forceinline__ int3 deltap_one(const StepConst &sc, const float4 *__
     float az = 0.0f;
     const uint32_t mx = fx_biased(bi.x), my = fx_biased(bi.y), mz = fx_biased(bi.z);
     const float2 u2 = make_float2(sc.fx_u, sc.fx_u), off2 = make_float2(sc.fx_off, sc.fx_off);
-    for_each_neighbor<UNR>(nbr, t, n, nn, B, [&](uint32_t e, const float4 &bj) {
+    for_each_neighbor<UNR>(nbr, t, n, nn, B, Chk{b.err, b.dbg}, [&](uint32_t e, const float4 &bj) {
         const float2 dxy = fma2_rn(make_float2(fx_diff_word(mx, bj.x), fx_diff_word(my, bj.y)), u2, off2);
         const float dx = dxy.x, dy = dxy.y;
         const float dz = __fmaf_rn(fx_diff_word(mz, bj.z), sc.fx_u, sc.fx_off);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        // as in lambda_one: pairs at or past h and coincident pairs add an exact zero
-        const bool in = r2 < sc.h2 && r2 > 0.0f;
-        const float r2c = in ? r2 : sc.h2;
+        // as in lambda_one: pairs at or past h and coincident pairs add an exact zero (the
+        // tensile term is folded into lambda_i + lambda_j with one FMA)
+        const bool in = r2 < sc.h2;
+        const float r2c = fminf(fmaxf(r2, 1.0e-30f), sc.h2);
         const float ir = rsqrtf(r2c);
         const float hr = __fmaf_rn(-r2c, ir, sc.h);
         const float gw = in ? __fmul_rn(__fmul_rn(hr, hr), ir) : 0.0f;
         const float u = __fmul_rn(__fsub_rn(sc.h2, r2c), sc.inv_wdq);  // W(r) / W(dq) = u^3
-        const float scorr = __fmul_rn(sc.neg_k, powi<NPOW>(__fmul_rn(__fmul_rn(u, u), u), sc.scorr_n));
-        const float f = __fmul_rn(__fadd_rn(__fadd_rn(bi.w, bj.w), scorr), gw);
+        const float f = __fmul_rn(__fmaf_rn(sc.neg_k, powi<NPOW>(__fmul_rn(__fmul_rn(u, u), u), sc.scorr_n),
+                                            __fadd_rn(bi.w, bj.w)), gw);
         axy = fma2_rn(make_float2(f, f), dxy, axy);
         az = __fmaf_rn(f, dz, az);
     });
@@ -1682,7 +1746,7 @@ __device__ __forceinline__ int3 deltap_one(const StepConst &sc, const float4 *__
 // contact, Jacobi update written to A.
 
 template <bool DENSE, int NPOW, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS, APBF_SOLVER_MIN_BLOCKS * 256 / BS) deltap_kernel(
+__global__ void __launch_bounds__(BS, APBF_DELTAP_MIN_BLOCKS * 256 / BS) deltap_kernel(
     StepConst sc, const float4 *__restrict__ B, float4 *__restrict__ A, const uint32_t *__restrict__ act,
     const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt, const uint32_t *__restrict__ cell_s,
     const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr,
@@ -1740,7 +1804,13 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
         const uint4 eb = nxt;
         if (k + kUnroll < nn)
             nxt = __ldcs(e_ptr + (size_t)(k / kUnroll + 1) * n);
-        const uint32_t e[kUnroll] = {eb.x, eb.y, eb.z, eb.w};
+        uint32_t e[kUnroll] = {eb.x, eb.y, eb.z, eb.w};
+#if APBF_DEBUG_CHECKS
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (!check_ok((e[u] & kSlotMask) <= n, kCheckNeighbor, t, b.err, b.dbg))
+                e[u] = (uint32_t)n | (e[u] & ~kSlotMask);
+#endif
         float4 aj[kUnroll], xj[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
@@ -1807,7 +1877,9 @@ __global__ void __launch_bounds__(kBlock) density_kernel(StepConst sc, Buffers b
         float racc = 0.0f;
         const uint32_t nn = b.nbr_cnt[p];
         for (uint32_t k = 0; k < nn; ++k) {
-            const uint32_t j = b.nbr[entry_index(k, p, n)] & kSlotMask;
+            uint32_t j = b.nbr[entry_index(k, p, n)] & kSlotMask;
+            if (!check_ok(j < sc.n, kCheckNeighbor, p, b.err, b.dbg))
+                j = p;
             const float4 xj = b.xs32[j];
             const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
@@ -1966,7 +2038,8 @@ cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s)
     cudaError_t e = launch_after(scan_reduce_kernel, tiles, 1024, s, b.cnt, sc.ncell, b.tile_sums);
     if (e != cudaSuccess)
         return e;
-    return launch_after(scan_apply_kernel, tiles, 1024, s, b.cnt, sc.ncell, b.tile_sums, b.start, sc.n);
+    return launch_after(scan_apply_kernel, tiles, 1024, s, b.cnt, sc.ncell, b.tile_sums, b.start, sc.n,
+                        Chk{b.err, b.dbg});
 }
 
 cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s)
@@ -2012,7 +2085,7 @@ cudaError_t launch_lambda_bs(const StepConst &sc, const Buffers &b, cudaStream_t
     const int part = partitioned(sc) ? 1 : 0;
     auto k = dense ? lambda_kernel<true, BS> : lambda_kernel<false, BS>;
     return launch_after(k, sms * occupancy((const void *)k, BS), BS, s, sc, b.recA, b.recB, b.rho, b.act, b.nbr,
-                        b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr, part);
+                        b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr, part, Chk{b.err, b.dbg});
 }
 
 cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,

@@ -25,12 +25,13 @@ def _declared():
 
 def test_exports_every_declared_symbol():
     names = _declared()
-    assert len(names) == 35
-    out = subprocess.run(["nm", "-D", "--defined-only", apbf.LIB_PATH], capture_output=True, text=True,
-                         check=True).stdout
-    exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
-    assert set(names) <= exported
-    assert exported <= set(names), "library exports symbols the header does not declare"
+    assert len(names) == 37
+    for path in (apbf.LIB_PATH, build.LIB_DEBUG):   # the release and the debug-check library
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                             check=True).stdout
+        exported = set(re.findall(r"\bT\s+(apbf_\w+)", out))
+        assert set(names) <= exported, path
+        assert exported <= set(names), f"{path} exports symbols the header does not declare"
     assert sorted(apbf.EXPORTS) == names
     L = apbf.lib()
     for nm in names:
