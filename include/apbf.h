@@ -75,7 +75,7 @@ typedef enum apbf_status {
  * Scene description. Units are SI (m, s, kg). Values are FP32 as the
  * solver uses them.
  *
- *  n            particles, 0 <= n < 2^27.
+ *  n            particles, 0 <= n < 2^31 - 1.
  *  pos, vel     host, 3n floats each in particle-id order; vel may be NULL (zero).
  *               Copied at creation; the caller keeps ownership.
  *  grid_lo/hi   static uniform-grid extent (cells of size h). Every particle
@@ -171,7 +171,7 @@ APBF_API apbf_status apbf_create_scene(const apbf_scene_desc *desc, void *cuda_s
  * A scene inside a batch evolves bit-identically to the same scene created
  * alone. Every scene's description must agree with scene 0 in everything but
  * n, pos, vel, grid_lo/hi and box_lo/hi (APBF_ERR_INVALID_ARG otherwise);
- * count <= 65535 and the total particle count < 2^27. A batch shares one
+ * count <= 65535 and the total particle count < 2^31 - 1. A batch shares one
  * fixed-point unit: a scene whose grid needs a coarser unit than its h gives
  * (one spanning 8e8 units on an axis) steps alone (APBF_ERR_NOT_SUPPORTED).
  *  descs  host, count descriptions (copied, as for apbf_create_scene).
@@ -410,7 +410,7 @@ typedef struct apbf_server_desc {
     const apbf_scene_desc *physics; /* host: h, dt, mass, rho0, eps, s_corr, XSPH, gravity, n_min/n_max,
                                        lod_mode, max_neighbors, flags shared by every request (its n, pos,
                                        vel, grid and box are ignored) */
-    uint32_t max_particles;         /* resident particle capacity (< 2^27); 0 = the most that budget_bytes holds */
+    uint32_t max_particles;         /* resident particle capacity (< 2^31 - 1); 0 = the most that budget_bytes holds */
     uint32_t max_cells;             /* resident grid-cell capacity (< 2^31); 0 = 4 x max_particles */
     uint32_t max_scenes;            /* resident scenes (<= 65535); 0 = 4096 */
     size_t budget_bytes;            /* device bytes the pool may use; 0 = no limit (max_particles required) */
@@ -512,8 +512,8 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint3
 #define APBF_DBG_XPRED 5u         /* float4[n] predicted positions (FP32), sorted */
 #define APBF_DBG_LEVEL 6u         /* u8[n]   N_i, sorted */
 #define APBF_DBG_NBR_COUNT 7u     /* u8[n]   neighbour count, sorted */
-#define APBF_DBG_NBR 8u           /* u32[max_neighbors*n]: entry k of particle p at k*n+p,
-                                     low 27 bits = sorted slot, high 5 bits = cell offset code */
+#define APBF_DBG_NBR 8u           /* u32[max_neighbors*n]: entry k of particle p at k*n+p, the
+                                     neighbour's sorted slot; n pads a list to a multiple of 4 */
 #define APBF_DBG_ACTIVE 9u        /* u32[n]  sorted slots, active-set order (P_l = prefix) */
 #define APBF_DBG_LEVEL_COUNT 10u  /* u32[n_max+2] |P_l|, l = 0..n_max+1 */
 #define APBF_DBG_LAMBDA 11u       /* float[n] lambda after the stage, sorted */

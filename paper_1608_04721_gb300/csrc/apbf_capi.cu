@@ -63,8 +63,8 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     st = APBF_ERR_INVALID_ARG;
     if (!d)
         return "desc is NULL";
-    if (d->n >= (1u << kSlotBits))
-        return "n must be below 2^27";
+    if (d->n >= kMaxParticles)
+        return "n must be below 2^31 - 1";
     if (d->n > 0 && !d->pos)
         return "pos is NULL";
     if (!(d->h > 0.0f) || !std::isfinite(d->h))
@@ -234,8 +234,8 @@ std::string derive_batch(const apbf_scene_desc *descs, uint32_t count, StepConst
         n_total += sk.n;
         c_total += sk.ncell;
     }
-    if (n_total >= (1ull << kSlotBits))
-        return "the batch holds 2^27 particles or more";
+    if (n_total >= kMaxParticles)
+        return "the batch holds 2^31 - 1 particles or more";
     if (c_total >= (1ull << 31))
         return "the batch's grids hold too many cells";
     sc.n = (uint32_t)n_total;

@@ -13,8 +13,9 @@
 namespace apbf {
 
 constexpr uint32_t kDefaultMaxNeighbors = 128;
-constexpr uint32_t kSlotBits = 27;  // neighbour entry: slot (27 bits) | cell offset code (5 bits)
-constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
+// Particles of a scene, batch or pool: below 2^31, so that a neighbour entry (a
+// plain 32-bit sorted slot) can also name the padding record n.
+constexpr uint32_t kMaxParticles = 0x7fffffffu;
 // Neighbour entries are stored in blocks of kEntryBlock per particle: entry k
 // of list column t at ((k / 4) * n + t) * 4 + k % 4, so a thread reads a
 // block with one 16-byte load and a warp's block loads are contiguous. Lists
@@ -27,7 +28,6 @@ __host__ __device__ inline size_t entry_index(uint32_t k, size_t t, size_t n)
 {
     return ((size_t)(k / kEntryBlock) * n + t) * kEntryBlock + k % kEntryBlock;
 }
-constexpr uint32_t kSentinelCode = 13;  // the zero cell offset
 __host__ __device__ constexpr uint32_t list_rows(uint32_t max_nbr)
 {
     return (max_nbr + kListPad - 1) / kListPad * kListPad;

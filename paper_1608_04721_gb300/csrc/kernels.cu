@@ -11,12 +11,11 @@
 //   nbr               u32 neighbour entries in blocks of 4 per list column:
 //                     entry k of column t at ((k/4)*n + t)*4 + k%4 (a thread
 //                     reads a block with one 16-byte load; a warp of
-//                     consecutive columns reads 512 contiguous bytes); low 27
-//                     bits: sorted slot, high 5 bits: which of the 27
-//                     neighbour cells the neighbour was found in. Each list is
-//                     padded to whole blocks with entries naming slot n, whose
-//                     record (recA, recB and xt hold n + 1) lies far outside
-//                     the grid, so the solver reads whole blocks without
+//                     consecutive columns reads 512 contiguous bytes), each
+//                     the neighbour's sorted slot. Each list is padded to
+//                     whole blocks with entries naming slot n, whose record
+//                     (recA, recB and xt hold n + 1) lies far from every
+//                     particle, so the solver reads whole blocks without
 //                     bounds checks.
 //
 // Positions inside the solver are 32-bit integers: units of u = 2^e metres
@@ -216,13 +215,13 @@ __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ n
 #if APBF_DEBUG_CHECKS
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            if (!check_ok((e[u] & kSlotMask) <= n, kCheckNeighbor, (uint32_t)t, chk.err, chk.dbg))
-                e[u] = (uint32_t)n | (e[u] & ~kSlotMask);
+            if (!check_ok(e[u] <= n, kCheckNeighbor, (uint32_t)t, chk.err, chk.dbg))
+                e[u] = (uint32_t)n;
 #endif
         float4 r[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            r[u] = __ldg(&rec[e[u] & kSlotMask]);
+            r[u] = __ldg(&rec[e[u]]);
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
             f(e[u], r[u]);
@@ -1208,9 +1207,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                 if (cy < 0 || cy >= g.ny)
                     continue;
                 const uint32_t row = g.cell_base + ((uint32_t)cz * (uint32_t)g.ny + (uint32_t)cy) * (uint32_t)g.nx;
-                const uint32_t j0 = b.start[row + xl], jm = b.start[row + c.x], jp = b.start[row + c.x + 1],
-                               j1 = b.start[row + xr + 1];
-                const uint32_t code_row = (uint32_t)(3 * (dy + 1) + 9 * (dz + 1));
+                const uint32_t j0 = b.start[row + xl], j1 = b.start[row + xr + 1];
                 const bool own_row = dy == 0 && dz == 0;  // the only row that holds p itself
                 // the window in chunks of up to 32 candidates: first the predicate for each
                 // (a hit mask), then one list write per hit, so a warp's lanes share the
@@ -1243,14 +1240,13 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
                     while (hits) {
                         const uint32_t q = j + (uint32_t)(__ffs(hits) - 1);
                         hits &= hits - 1u;
-                        const uint32_t dxc = (q < jm) ? 0u : ((q < jp) ? 1u : 2u);
                         uint32_t qe = q;
 #if APBF_DEBUG_CHECKS
                         check_ok(q < sc.n, kCheckNeighbor, t, b.err, b.dbg);
                         if (t == 0 && cnt == 0 && b.dbg[2] != 0u)
                             qe = sc.n + 1u;  // planted: the record past the padding one (inside the arena)
 #endif
-                        const uint32_t e = qe | ((code_row + dxc) << kSlotBits);
+                        const uint32_t e = qe;
                         eb = make_uint4(eb.y, eb.z, eb.w, e);  // the last four entries, oldest first
                         if (cnt % kEntryBlock == kEntryBlock - 1 && cnt < sc.max_nbr)  // a full block
                             eblk[(size_t)(cnt / kEntryBlock) * n] = eb;
@@ -1267,7 +1263,7 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
         b.nbr_cnt[t] = (uint8_t)cnt;
         const uint32_t s = cnt % kEntryBlock;
         if (s) {  // the last, partial block, padded
-            const uint32_t sentinel = sc.n | (kSentinelCode << kSlotBits);
+            const uint32_t sentinel = sc.n;
             // its s entries are the last s of eb
             const uint4 out = make_uint4(s == 1 ? eb.w : (s == 2 ? eb.z : eb.y),
                                          s == 1 ? sentinel : (s == 2 ? eb.w : eb.z),
@@ -1808,14 +1804,14 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
 #if APBF_DEBUG_CHECKS
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            if (!check_ok((e[u] & kSlotMask) <= n, kCheckNeighbor, t, b.err, b.dbg))
-                e[u] = (uint32_t)n | (e[u] & ~kSlotMask);
+            if (!check_ok(e[u] <= n, kCheckNeighbor, t, b.err, b.dbg))
+                e[u] = (uint32_t)n;
 #endif
         float4 aj[kUnroll], xj[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            aj[u] = __ldg(&b.recA[e[u] & kSlotMask]);
-            xj[u] = __ldg(&b.xt[e[u] & kSlotMask]);
+            aj[u] = __ldg(&b.recA[e[u]]);
+            xj[u] = __ldg(&b.xt[e[u]]);
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
@@ -1877,7 +1873,7 @@ __global__ void __launch_bounds__(kBlock) density_kernel(StepConst sc, Buffers b
         float racc = 0.0f;
         const uint32_t nn = b.nbr_cnt[p];
         for (uint32_t k = 0; k < nn; ++k) {
-            uint32_t j = b.nbr[entry_index(k, p, n)] & kSlotMask;
+            uint32_t j = b.nbr[entry_index(k, p, n)];
             if (!check_ok(j < sc.n, kCheckNeighbor, p, b.err, b.dbg))
                 j = p;
             const float4 xj = b.xs32[j];

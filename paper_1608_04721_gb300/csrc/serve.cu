@@ -23,7 +23,7 @@ using namespace apbf;
 
 namespace {
 
-constexpr uint32_t kMaxSlots = (1u << kSlotBits) - 1u;
+constexpr uint32_t kMaxSlots = kMaxParticles - 1u;
 
 struct Request {
     uint64_t ticket = 0;
@@ -146,7 +146,7 @@ std::string resolve(const apbf_server_desc *d, StepConst &phys, StepConst &cap, 
     if (scenes > 65535u)
         return "max_scenes must be <= 65535";
     if (d->max_particles > kMaxSlots)
-        return "max_particles must be below 2^27";
+        return "max_particles must be below 2^31 - 1";
     auto cells_for = [&](uint32_t n) -> uint32_t {
         if (d->max_cells)
             return d->max_cells;

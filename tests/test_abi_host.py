@@ -131,8 +131,9 @@ def test_server_capacity_from_budget():
     assert b_small <= 1 << 30 and n_small > 0 and c_small == 4 * n_small
     over, _, _ = apbf.apbf_server_bytes(phys, max_particles=n_small + 1)
     assert over > 1 << 30
-    # 150 GB holds more than the 27-bit slot space: the capacity stops at 2^27 - 1
-    assert n_big == (1 << 27) - 1 and b_big <= 150 * 10**9
+    # the whole 150 GB budget is usable (about 200 M particles): one more particle no longer fits
+    assert n_big > 150 * 10**6 and b_big <= 150 * 10**9 and b_big > 149 * 10**9
+    assert apbf.apbf_server_bytes(phys, max_particles=n_big + 1)[0] > 150 * 10**9
     # explicit capacities; bytes grow with each of them
     b1, n1, c1 = apbf.apbf_server_bytes(phys, max_particles=100000, max_cells=50000, max_scenes=16)
     assert (n1, c1) == (100000, 50000)
@@ -143,7 +144,7 @@ def test_server_capacity_from_budget():
 @pytest.mark.parametrize("kw,status", [
     (dict(), apbf.APBF_ERR_INVALID_ARG),                                   # neither capacity nor budget
     (dict(budget_bytes=1000), apbf.APBF_ERR_OUT_OF_MEMORY),                # not even one particle
-    (dict(max_particles=1 << 27), apbf.APBF_ERR_INVALID_ARG),              # beyond the slot space
+    (dict(max_particles=(1 << 31) - 1), apbf.APBF_ERR_INVALID_ARG),        # beyond the slot space
     (dict(max_particles=1000, max_scenes=70000), apbf.APBF_ERR_INVALID_ARG),
     (dict(max_particles=10**7, budget_bytes=10**6), apbf.APBF_ERR_OUT_OF_MEMORY),
 ])

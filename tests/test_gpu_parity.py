@@ -18,7 +18,6 @@ from tests.multistep import compare_runs
 
 pytestmark = pytest.mark.gpu
 
-SLOT = (1 << 27) - 1
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -76,15 +75,13 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
     rows = range(n) if sample is None else sample
     for q in rows:
         e = nbr[: cnt[q], q]
-        got = e & SLOT
+        got = e.astype(np.int64)
         ref = st.nbr_idx[st.nbr_off[q]:st.nbr_off[q + 1]]
         assert np.array_equal(np.sort(got), np.sort(ref)), q
-        code = (e >> 27).astype(np.int64)
-        off = np.stack([code % 3 - 1, (code // 3) % 3 - 1, code // 9 - 1], 1)
-        assert np.array_equal(cells[got] - cells[q], off), q
-        # padding to a multiple of 4 entries: slot n (the far record), zero cell offset
+        assert np.all(np.abs(cells[got] - cells[q]) <= 1), q   # one of the 27 cells around q's
+        # padding to a multiple of 4 entries: slot n (the far record)
         pad = nbr[cnt[q]: min(-(-cnt[q] // 4) * 4, nbr.shape[0]), q]
-        assert np.all(pad == (n | (13 << 27))), q
+        assert np.all(pad == n), q
     lvl = st.level_presort[st.order]
     if cfg.lod_mode in (scenes.LOD_DTC, scenes.LOD_DTVS) and p.n_max > p.n_min:
         apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
