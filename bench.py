@@ -318,8 +318,9 @@ def stage_profile(apbf, scene, cfg, first_step, steps, drive_fn=None):
 
 # What bounds the solver passes, from the committed ncu summary (not measured
 # by this run): the roofline fraction above is against the FP32 pipes.
-LIMITER_NOTE = ("L1 throughput: ncu puts the dense solver passes at 88-91 % of the L1 peak (warp-level gathers of "
-                "neighbour records, ~20 sectors per request), DRAM at 31 %, the FMA pipe at 37-42 % "
+LIMITER_NOTE = ("L1 throughput: ncu puts the dense solver passes at 90 % (lambda) and 83 % (delta-p) of the L1 "
+                "peak (warp-level gathers of 16-byte neighbour records, 19.5 sectors per request), DRAM at "
+                "36-38 %, issue at 61-67 %, the FMA pipe at 42-46 % "
                 "(profiles/solver_kernels_apbf_ocean_1048576.md)")
 
 
