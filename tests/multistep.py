@@ -50,11 +50,16 @@ def _nudge(x: np.ndarray, rng, h: float) -> np.ndarray:
 
 def compare_runs(scene, p, x, v, steps: int, *, strict: bool = False):
     """Step the CUDA scene and the oracle `steps` times from (x, v); assert the
-    statistics above at every step. Returns (gpu, oracle) statistics per step."""
+    statistics above at every step. `p` is the oracle's parameters, or, for a
+    scene whose camera or walls move, a function of the step index that sets
+    the CUDA scene's camera and box for that step and returns the oracle's
+    parameters with the same ones. Returns (gpu, oracle) statistics per step."""
     xo, vo, io = x, v, None
     nudged = [] if strict else [[x, v, None, np.random.default_rng(12345 + k)] for k in range(ENSEMBLE)]
     g_all, o_all, env = [], [], np.zeros(4)
+    params = p if callable(p) else (lambda k: p)
     for k in range(steps):
+        p = params(k)
         apbf.apbf_step(scene, 1)
         pos = apbf.apbf_read_state(scene, pos=True, vel=False)["pos"]
         st = oracle.step(p, xo, vo, io)

@@ -181,13 +181,31 @@ def test_one_step_parity_131k():
 def test_one_step_parity_1m_bench_configuration():
     """The benchmark's workload (1,048,576 particles, N_i in 3..15, moving
     wall and spline camera) in the launch configuration the benchmark times
-    (captured graph): all integer stages, sampled neighbour sets, lambda and
-    rho of the first iteration for every particle, and the final state."""
+    (captured graph): all integer stages, sampled neighbour sets, and for
+    every particle lambda and rho of each of the 15 iterations and x* after
+    each, then the final state."""
     cfg = scenes.config_ocean_1m()
     scene, p, x, v = make(cfg, step=0)
     rng = np.random.default_rng(1)
-    st = check_stages(cfg, scene, p, x, v, iters=False, sample=rng.choice(cfg.n, 2048, replace=False))
+    st = check_stages(cfg, scene, p, x, v, iters=True, sample=rng.choice(cfg.n, 2048, replace=False))
     check_final(cfg, scene, p, st)
+
+
+def test_multi_step_density_statistics_1m_bench_configuration():
+    """Five steps of the benchmark's 1,048,576-particle ocean (moving wall,
+    spline camera, N_i in 3..15) against the oracle: mean, 99th and 99.9th
+    percentile of |rho/rho0 - 1| within 0.2 points at every step."""
+    cfg = scenes.config_ocean_1m()
+    scene, p0, x, v = make(cfg, step=0)
+
+    def params(k):
+        eye, d = scenes.camera_at(cfg, k)
+        lo, hi = scenes.box_at(cfg, k)
+        apbf.apbf_set_camera(scene, eye, d)
+        apbf.apbf_set_box(scene, lo, hi)
+        return oracle.make_params(cfg, rho0=rest_density(cfg), eye=eye, box_lo=lo, box_hi=hi)
+
+    compare_runs(scene, params, x, v, 5, strict=True)
 
 
 def test_apbf_with_every_level_at_nmax_is_bitwise_pbf():
