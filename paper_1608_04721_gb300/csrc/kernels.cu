@@ -1604,6 +1604,11 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__
 // (threads over all particles, inactive ones skip). The kernel picks masked
 // when |P_l| >= mask_thr * n; the threshold is tuned per scene. Both modes do
 // identical arithmetic per particle, so the choice never changes a result.
+// In the compacted mode the copies of the particles that finished in
+// iteration l-1 (list positions |P_l| .. |P_{l-1}|-1) run as a loop of their
+// own, so the loop over P_l is the dense kernel's loop with another bound
+// (one loop over P_{l-1} with a branch per particle took 8-10 us more per
+// launch on the 1M-particle ocean).
 template <bool DENSE, int BS>
 __global__ void __launch_bounds__(BS, APBF_LAMBDA_MIN_BLOCKS * 256 / BS) lambda_kernel(
     StepConst sc, const float4 *__restrict__ A, float4 *__restrict__ B, float *__restrict__ rho_out,
@@ -1612,34 +1617,47 @@ __global__ void __launch_bounds__(BS, APBF_LAMBDA_MIN_BLOCKS * 256 / BS) lambda_
     Chk chk)
 {
     wait_for_predecessor();
-    const uint32_t cnt_l = DENSE ? sc.n : lvl_count[l];
-    const uint32_t cnt_prev = DENSE ? sc.n : lvl_count[l - 1];
-    const bool masked = !DENSE && (float)cnt_l >= mask_thr * (float)sc.n;
-    const uint32_t work = masked ? sc.n : cnt_prev;
     const size_t n = sc.n;
-    // grid-stride: at any moment the whole grid works on one compact window of
-    // the (cell-sorted) work list, which keeps the gathers' working set in L2
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < work; t += gridDim.x * blockDim.x) {
-        const uint32_t p = part ? act[t] : t;  // t: list column (active-list position with a partition)
-        bool finished_last = false;  // finished in iteration l-1: keep position and lambda in B
-        if (masked) {
-            const uint32_t lv = lvl_s[p];
-            if (lv + 1 < l)
-                continue;
-            finished_last = lv < l;
-        } else if (!DENSE) {
-            finished_last = t >= cnt_l;
-        }
+    const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    // a particle of P_l: rho and lambda (Eq. 4-6) from A, written to B with its position
+    auto solve = [&](uint32_t t, uint32_t p) {
         const float4 ai = A[p];
-        if (finished_last) {
-            B[p] = make_float4(ai.x, ai.y, ai.z, B[p].w);
-            continue;
-        }
         float lam, rho;
         lambda_one(sc, A, nbr, t, n, nbr_cnt[t], ai, chk, lam, rho);
         B[p] = make_float4(ai.x, ai.y, ai.z, lam);
         rho_out[p] = rho;
+    };
+    // a particle that finished in iteration l-1: its final position into B, its lambda kept there
+    auto keep = [&](uint32_t p) {
+        const float4 ai = A[p];
+        B[p] = make_float4(ai.x, ai.y, ai.z, B[p].w);
+    };
+    // grid-stride: at any moment the whole grid works on one compact window of
+    // the (cell-sorted) work list, which keeps the gathers' working set in L2;
+    // t is the list column (the active-list position with a partition)
+    if (DENSE) {
+        for (uint32_t t = t0; t < sc.n; t += stride)
+            solve(t, part ? act[t] : t);
+        return;
     }
+    const uint32_t cnt_l = lvl_count[l], cnt_prev = lvl_count[l - 1];
+    if ((float)cnt_l >= mask_thr * (float)sc.n) {
+        for (uint32_t t = t0; t < sc.n; t += stride) {
+            const uint32_t p = part ? act[t] : t;
+            const uint32_t lv = lvl_s[p];
+            if (lv + 1 < l)
+                continue;
+            if (lv < l)
+                keep(p);
+            else
+                solve(t, p);
+        }
+        return;
+    }
+    for (uint32_t t = cnt_l + t0; t < cnt_prev; t += stride)
+        keep(part ? act[t] : t);
+    for (uint32_t t = t0; t < cnt_l; t += stride)
+        solve(t, part ? act[t] : t);
 }
 
 // ------------------------------------------- a9: position correction pass
