@@ -185,6 +185,10 @@ __device__ __forceinline__ void wait_for_predecessor()
 #ifndef APBF_DELTAP_MIN_BLOCKS
 #define APBF_DELTAP_MIN_BLOCKS 5
 #endif
+// resident blocks per SM of the deep-batch solver kernels (more registers per thread)
+#ifndef APBF_DEEP_MIN_BLOCKS
+#define APBF_DEEP_MIN_BLOCKS 3
+#endif
 constexpr int kUnroll = (int)kEntryBlock;
 
 
@@ -198,12 +202,44 @@ struct Chk {
     uint32_t *err, *dbg;
 };
 
-template <int UNR = kUnroll, typename F>
+// DEEP: two entry blocks per batch (2 * kUnroll gathers in flight), for passes
+// over so few particles that a thread's chain of dependent loads, not the
+// gather throughput, sets the time. A batch's second block past the list is
+// all padding (slot n, the far record), whose pairs add exact zeros, so f sees
+// the same pairs in the same order and every sum keeps its bits.
+template <int UNR = kUnroll, bool DEEP = false, typename F>
 __device__ __forceinline__ void for_each_neighbor(const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
                                                   const float4 *__restrict__ rec, Chk chk, F &&f)
 {
     static_assert(UNR == (int)kEntryBlock, "one entry block per batch");
     const uint4 *e_ptr = reinterpret_cast<const uint4 *>(nbr) + t;
+    if (DEEP) {
+        const uint32_t sn = (uint32_t)n;
+        const uint4 pad = make_uint4(sn, sn, sn, sn);
+        uint4 na = nn ? __ldcs(e_ptr) : pad;
+        uint4 nb = nn > (uint32_t)UNR ? __ldcs(e_ptr + n) : pad;
+        for (uint32_t k = 0; k < nn; k += 2 * UNR) {
+            const uint4 ea = na, eb = nb;
+            if (k + 2 * UNR < nn)
+                na = __ldcs(e_ptr + (size_t)(k / UNR + 2) * n);
+            nb = k + 3 * UNR < nn ? __ldcs(e_ptr + (size_t)(k / UNR + 3) * n) : pad;
+            uint32_t e[2 * UNR] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
+#if APBF_DEBUG_CHECKS
+#pragma unroll
+            for (int u = 0; u < 2 * UNR; ++u)
+                if (!check_ok(e[u] <= n, kCheckNeighbor, (uint32_t)t, chk.err, chk.dbg))
+                    e[u] = (uint32_t)n;
+#endif
+            float4 r[2 * UNR];
+#pragma unroll
+            for (int u = 0; u < 2 * UNR; ++u)
+                r[u] = __ldg(&rec[e[u]]);
+#pragma unroll
+            for (int u = 0; u < 2 * UNR; ++u)
+                f(e[u], r[u]);
+        }
+        return;
+    }
     // the next block's entries are requested before this block's records, so
     // the chain of dependent loads per batch is one load deep, not two
     uint4 nxt = nn ? __ldcs(e_ptr) : make_uint4(0u, 0u, 0u, 0u);
@@ -1552,7 +1588,7 @@ __global__ void __launch_bounds__(kBlock) prestab_kernel(StepConst sc, Buffers b
 // choice of where to fuse multiply-adds cannot differ between the kernel
 // instantiations that inline it (dense or compacted, block size, batch
 // depth UNR): a particle's result is the same bits whichever computes it.
-template <int UNR = kUnroll>
+template <int UNR = kUnroll, bool DEEP = false>
 __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__restrict__ A,
                                            const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
                                            const float4 &ai, Chk chk,
@@ -1564,7 +1600,7 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__
     // gives the bit pattern of M + (x_i - x_j) / u (see the top of this file)
     const uint32_t mx = fx_biased(ai.x), my = fx_biased(ai.y), mz = fx_biased(ai.z);
     const float2 u2 = make_float2(sc.fx_u, sc.fx_u), off2 = make_float2(sc.fx_off, sc.fx_off);
-    for_each_neighbor<UNR>(nbr, t, n, nn, A, chk, [&](uint32_t e, const float4 &aj) {
+    for_each_neighbor<UNR, DEEP>(nbr, t, n, nn, A, chk, [&](uint32_t e, const float4 &aj) {
         const float2 dxy = fma2_rn(make_float2(fx_diff_word(mx, aj.x), fx_diff_word(my, aj.y)), u2, off2);
         const float dx = dxy.x, dy = dxy.y;
         const float dz = __fmaf_rn(fx_diff_word(mz, aj.z), sc.fx_u, sc.fx_off);
@@ -1609,8 +1645,8 @@ __device__ __forceinline__ void lambda_one(const StepConst &sc, const float4 *__
 // own, so the loop over P_l is the dense kernel's loop with another bound
 // (one loop over P_{l-1} with a branch per particle took 8-10 us more per
 // launch on the 1M-particle ocean).
-template <bool DENSE, int BS>
-__global__ void __launch_bounds__(BS, APBF_LAMBDA_MIN_BLOCKS * 256 / BS) lambda_kernel(
+template <bool DENSE, bool DEEP, int BS>
+__global__ void __launch_bounds__(BS, (DEEP ? APBF_DEEP_MIN_BLOCKS : APBF_LAMBDA_MIN_BLOCKS) * 256 / BS) lambda_kernel(
     StepConst sc, const float4 *__restrict__ A, float4 *__restrict__ B, float *__restrict__ rho_out,
     const uint32_t *__restrict__ act, const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt,
     const uint8_t *__restrict__ lvl_s, const uint32_t *__restrict__ lvl_count, uint32_t l, float mask_thr, int part,
@@ -1623,7 +1659,7 @@ __global__ void __launch_bounds__(BS, APBF_LAMBDA_MIN_BLOCKS * 256 / BS) lambda_
     auto solve = [&](uint32_t t, uint32_t p) {
         const float4 ai = A[p];
         float lam, rho;
-        lambda_one(sc, A, nbr, t, n, nbr_cnt[t], ai, chk, lam, rho);
+        lambda_one<kUnroll, DEEP>(sc, A, nbr, t, n, nbr_cnt[t], ai, chk, lam, rho);
         B[p] = make_float4(ai.x, ai.y, ai.z, lam);
         rho_out[p] = rho;
     };
@@ -1702,7 +1738,7 @@ __device__ __forceinline__ SceneK scene_k(const StepConst &sc, const DynParams *
 // Eq. 7 for one particle and the contacts after it: the new fixed-point
 // position; explicit rounding intrinsics as in lambda_one, so the result does
 // not depend on which instantiation computes it.
-template <int NPOW, bool BATCH, int UNR = kUnroll>
+template <int NPOW, bool BATCH, bool DEEP = false, int UNR = kUnroll>
 __device__ __forceinline__ int3 deltap_one(const StepConst &sc, const float4 *__restrict__ B,
                                            const uint32_t *__restrict__ nbr, size_t t, size_t n, uint32_t nn,
                                            const float4 &bi, uint32_t p, const DynParams *__restrict__ dyn,
@@ -1712,7 +1748,7 @@ __device__ __forceinline__ int3 deltap_one(const StepConst &sc, const float4 *__
     float az = 0.0f;
     const uint32_t mx = fx_biased(bi.x), my = fx_biased(bi.y), mz = fx_biased(bi.z);
     const float2 u2 = make_float2(sc.fx_u, sc.fx_u), off2 = make_float2(sc.fx_off, sc.fx_off);
-    for_each_neighbor<UNR>(nbr, t, n, nn, B, Chk{b.err, b.dbg}, [&](uint32_t e, const float4 &bj) {
+    for_each_neighbor<UNR, DEEP>(nbr, t, n, nn, B, Chk{b.err, b.dbg}, [&](uint32_t e, const float4 &bj) {
         const float2 dxy = fma2_rn(make_float2(fx_diff_word(mx, bj.x), fx_diff_word(my, bj.y)), u2, off2);
         const float dx = dxy.x, dy = dxy.y;
         const float dz = __fmaf_rn(fx_diff_word(mz, bj.z), sc.fx_u, sc.fx_off);
@@ -1759,8 +1795,8 @@ __device__ __forceinline__ int3 deltap_one(const StepConst &sc, const float4 *__
 // Iteration l, threads over P_l: Eq. 7 with the tensile term from B, box
 // contact, Jacobi update written to A.
 
-template <bool DENSE, int NPOW, bool BATCH, int BS>
-__global__ void __launch_bounds__(BS, APBF_DELTAP_MIN_BLOCKS * 256 / BS) deltap_kernel(
+template <bool DENSE, bool DEEP, int NPOW, bool BATCH, int BS>
+__global__ void __launch_bounds__(BS, (DEEP ? APBF_DEEP_MIN_BLOCKS : APBF_DELTAP_MIN_BLOCKS) * 256 / BS) deltap_kernel(
     StepConst sc, const float4 *__restrict__ B, float4 *__restrict__ A, const uint32_t *__restrict__ act,
     const uint32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_cnt, const uint32_t *__restrict__ cell_s,
     const uint32_t *__restrict__ lvl_count, const DynParams *__restrict__ dyn, Buffers b, uint32_t l, float mask_thr,
@@ -1777,7 +1813,7 @@ __global__ void __launch_bounds__(BS, APBF_DELTAP_MIN_BLOCKS * 256 / BS) deltap_
         if (masked && b.lvl_s[p] < l)
             continue;
         const float4 bi = B[p];
-        const int3 np = deltap_one<NPOW, BATCH>(sc, B, nbr, t, n, nbr_cnt[t], bi, p, dyn, b, sk);
+        const int3 np = deltap_one<NPOW, BATCH, DEEP>(sc, B, nbr, t, n, nbr_cnt[t], bi, p, dyn, b, sk);
         A[p] = make_float4(fx_word(np.x), fx_word(np.y), fx_word(np.z), bi.w);
     }
 }
@@ -2092,12 +2128,25 @@ cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
     return e;
 }
 
+// The deep-batch solver kernels run every pass of a scene (or batch) with no more
+// particles than the regular kernel holds resident threads: there each thread has
+// one particle, and its chain of dependent loads, not the gather throughput, sets
+// the pass's time (131k-particle dam break 0.294 -> 0.282 ms/step; at 225k
+// particles, 1.16 per resident thread, the deep kernels lost 1.3 %). Both
+// variants give the same bits.
+bool deep_pass(const StepConst &sc, const void *regular, int block, int sms)
+{
+    return (size_t)sc.n <= (size_t)sms * (size_t)occupancy(regular, block) * (size_t)block;
+}
+
 template <int BS>
 cudaError_t launch_lambda_bs(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, bool dense, int sms,
                              float thr)
 {
     const int part = partitioned(sc) ? 1 : 0;
-    auto k = dense ? lambda_kernel<true, BS> : lambda_kernel<false, BS>;
+    const bool deep = deep_pass(sc, (const void *)lambda_kernel<true, false, BS>, BS, sms);
+    auto k = dense ? (deep ? lambda_kernel<true, true, BS> : lambda_kernel<true, false, BS>)
+                   : (deep ? lambda_kernel<false, true, BS> : lambda_kernel<false, false, BS>);
     return launch_after(k, sms * occupancy((const void *)k, BS), BS, s, sc, b.recA, b.recB, b.rho, b.act, b.nbr,
                         b.nbr_cnt, b.lvl_s, b.lvl_count, l, thr, part, Chk{b.err, b.dbg});
 }
@@ -2114,8 +2163,13 @@ cudaError_t launch_lambda(const StepConst &sc, const Buffers &b, cudaStream_t s,
 template <bool DENSE, int NPOW, bool BATCH, int BS>
 cudaError_t launch_deltap_t(const StepConst &sc, const Buffers &b, cudaStream_t s, uint32_t l, int sms, float thr)
 {
-    const int grid = sms * occupancy((const void *)deltap_kernel<DENSE, NPOW, BATCH, BS>, BS);
-    return launch_after(deltap_kernel<DENSE, NPOW, BATCH, BS>, grid, BS, s, sc, b.recB, b.recA, b.act, b.nbr,
+    if (deep_pass(sc, (const void *)deltap_kernel<true, false, NPOW, BATCH, BS>, BS, sms)) {
+        const int grid = sms * occupancy((const void *)deltap_kernel<DENSE, true, NPOW, BATCH, BS>, BS);
+        return launch_after(deltap_kernel<DENSE, true, NPOW, BATCH, BS>, grid, BS, s, sc, b.recB, b.recA, b.act,
+                            b.nbr, b.nbr_cnt, b.cell_s, b.lvl_count, b.dyn, b, l, thr, partitioned(sc) ? 1 : 0);
+    }
+    const int grid = sms * occupancy((const void *)deltap_kernel<DENSE, false, NPOW, BATCH, BS>, BS);
+    return launch_after(deltap_kernel<DENSE, false, NPOW, BATCH, BS>, grid, BS, s, sc, b.recB, b.recA, b.act, b.nbr,
                         b.nbr_cnt, b.cell_s, b.lvl_count, b.dyn, b, l, thr, partitioned(sc) ? 1 : 0);
 }
 

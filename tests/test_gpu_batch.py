@@ -82,6 +82,41 @@ def test_scenes_in_a_batch_match_the_same_scenes_alone_bitwise():
     assert info["particle_iterations"] == sum(apbf.apbf_get_step_info(a)["particle_iterations"] for a in alone)
 
 
+
+def test_deep_and_regular_solver_kernels_agree_bitwise():
+    """A scene with fewer particles than the solver kernels hold resident
+    threads is stepped by their deep-batch variants (two entry blocks of
+    gathers in flight per thread); a batch of ~400k particles by the regular
+    ones. The variants visit the same pairs in the same order, so each scene
+    in the batch keeps the bits it has alone."""
+    cfgs = scenes.config_batch_256(count=48, seed=5, n_lo=6000, n_hi=12000)
+    assert sum(c.n for c in cfgs) > 2 * 152 * 5 * 256 and max(c.n for c in cfgs) < 152 * 3 * 256
+    r0 = rest_density(cfgs[0])
+    descs = []
+    for c in cfgs:
+        x, v = scenes.make_scene(c)
+        descs.append(apbf.desc_from_config(c, x, v, r0))
+    batch = apbf.apbf_create_batch(descs)
+    alone = [apbf.apbf_create_scene(d) for d in descs]
+    for step in range(3):
+        for k, c in enumerate(cfgs):
+            _drive(batch, k, c, step, index=k)
+            _drive(alone[k], k, c, step)
+        apbf.apbf_step(batch, 1)
+        for a in alone:
+            apbf.apbf_step(a, 1)
+    got = apbf.apbf_read_state(batch, pos=True, vel=True, rho=True)
+    off = 0
+    for k, a in enumerate(alone):
+        ref = apbf.apbf_read_state(a, pos=True, vel=True, rho=True)
+        n = cfgs[k].n
+        for f in ref:
+            assert np.array_equal(got[f][off:off + n], ref[f]), (k, f)
+        off += n
+        apbf.apbf_destroy_scene(a)
+    apbf.apbf_destroy_scene(batch)
+
+
 def test_each_scene_of_a_batch_matches_the_oracle_after_one_step():
     cfgs = _batch_configs(4, 23)
     r0 = rest_density(cfgs[0])
