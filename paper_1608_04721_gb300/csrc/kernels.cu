@@ -1204,7 +1204,7 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
     }
 }
 
-// ----------------------------------------------- neighbour lists (l. 5-6)
+// ------------------------------------- neighbour lists (Fig. 7, neighbour search)
 
 // With a level partition (part), thread t takes the particle at position t
 // of the active list and writes its list into column t (entry k at k*n + t):
