@@ -345,6 +345,28 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_
     return warp_prefix + inc - v;
 }
 
+// Inclusive scan of one u32 per lane across a warp.
+__device__ __forceinline__ uint32_t warp_inclusive_scan_u32(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o)
+            v += y;
+    }
+    return v;
+}
+
+// Single-block scans of E values: warp w of the block owns the contiguous
+// segment [w * seg, (w + 1) * seg) (seg a multiple of 32) and walks it in rows
+// of 32, so every load and store of a row is one coalesced access.
+__device__ __forceinline__ uint32_t warp_segment(uint32_t E)
+{
+    const uint32_t nw = blockDim.x >> 5;
+    return (E + 32u * nw - 1u) / (32u * nw) * 32u;
+}
+
 // ------------------------------------------------- per-scene geometry
 // A batch concatenates independent scenes; a particle slot's scene is
 // constant (cell keys are scene-major, so every order the step uses keeps
@@ -843,54 +865,41 @@ __global__ void __launch_bounds__(kBlock) splat_tile_max_kernel(ViewConst v)
 }
 
 // Exclusive scans of the tile counts into tile_start and of the tiles'
-// kSplatChunk-entry work chunks into chunk_start (tiles + 1 entries each), one block.
+// kSplatChunk-entry work chunks into chunk_start (tiles + 1 entries each), one
+// block, each warp over a contiguous segment of tiles in coalesced rows.
 __global__ void __launch_bounds__(1024) splat_tile_scan_kernel(ViewConst v)
 {
     __shared__ uint32_t sh32[32];
     const uint32_t T = v.tiles_x * v.tiles_y;
-    const uint32_t per = (T + blockDim.x - 1) / blockDim.x;
-    const uint32_t a = min(threadIdx.x * per, T), e = min(a + per, T);
-    constexpr uint32_t kHeld = 16;  // a thread's counts are loaded once into registers when they fit
-    uint32_t held[kHeld];
+    const uint32_t seg = warp_segment(T), lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t s0 = min(T, w * seg), s1 = min(T, s0 + seg);
     uint32_t sum = 0, chunks = 0;
-    if (per <= kHeld) {
-#pragma unroll
-        for (uint32_t q = 0; q < kHeld; ++q) {
-            held[q] = (a + q < e) ? v.tile_cnt[a + q] : 0u;
-            sum += held[q];
-            chunks += (held[q] + kSplatChunk - 1) / kSplatChunk;
-        }
-    } else {
-        for (uint32_t k = a; k < e; ++k) {
-            sum += v.tile_cnt[k];
-            chunks += (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
-        }
+    for (uint32_t k = s0 + lane; k < s1; k += 32u) {
+        const uint32_t c = v.tile_cnt[k];
+        sum += c;
+        chunks += (c + kSplatChunk - 1) / kSplatChunk;
     }
+    sum = warp_sum(sum);
+    chunks = warp_sum(chunks);
     uint32_t total, ctotal;
-    uint32_t run = block_exclusive_scan_u32(sum, sh32, &total);
-    uint32_t crun = block_exclusive_scan_u32(chunks, sh32, &ctotal);
-    if (per <= kHeld) {
-#pragma unroll
-        for (uint32_t q = 0; q < kHeld; ++q)
-            if (a + q < e) {
-                v.tile_start[a + q] = run;
-                v.chunk_start[a + q] = crun;
-                const uint32_t nch = (held[q] + kSplatChunk - 1) / kSplatChunk;
-                for (uint32_t c = 0; c < nch; ++c)
-                    v.chunk_tile[crun + c] = a + q;
-                run += held[q];
-                crun += nch;
-            }
-    } else {
-        for (uint32_t k = a; k < e; ++k) {
-            v.tile_start[k] = run;
-            v.chunk_start[k] = crun;
-            const uint32_t nch = (v.tile_cnt[k] + kSplatChunk - 1) / kSplatChunk;
-            for (uint32_t c = 0; c < nch; ++c)
-                v.chunk_tile[crun + c] = k;
-            run += v.tile_cnt[k];
-            crun += nch;
+    uint32_t run = block_exclusive_scan_u32(lane == 0 ? sum : 0u, sh32, &total);
+    uint32_t crun = block_exclusive_scan_u32(lane == 0 ? chunks : 0u, sh32, &ctotal);
+    run = __shfl_sync(kFull, run, 0);
+    crun = __shfl_sync(kFull, crun, 0);
+    for (uint32_t r = s0; r < s1; r += 32u) {
+        const uint32_t k = r + lane;
+        const uint32_t c = k < s1 ? v.tile_cnt[k] : 0u;
+        const uint32_t nch = (c + kSplatChunk - 1) / kSplatChunk;
+        const uint32_t inc = warp_inclusive_scan_u32(c), cinc = warp_inclusive_scan_u32(nch);
+        if (k < s1) {
+            const uint32_t cs = crun + cinc - nch;
+            v.tile_start[k] = run + inc - c;
+            v.chunk_start[k] = cs;
+            for (uint32_t q = 0; q < nch; ++q)
+                v.chunk_tile[cs + q] = k;
         }
+        run += __shfl_sync(kFull, inc, 31);
+        crun += __shfl_sync(kFull, cinc, 31);
     }
     if (threadIdx.x == 0) {
         v.tile_start[T] = total;
@@ -1349,36 +1358,24 @@ __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers 
     wait_for_predecessor();
     __shared__ uint32_t sh[32];
     const uint32_t E = sc.K * sc.level_tiles;
-    const uint32_t chunk = (E + blockDim.x - 1) / blockDim.x;
-    const uint32_t e0 = min(E, threadIdx.x * chunk), e1 = min(E, e0 + chunk);
-    constexpr uint32_t kHeld = 16;  // a thread's chunk is loaded once into registers when it fits
-    uint32_t held[kHeld];
-    uint32_t s = 0;
-    if (chunk <= kHeld) {
-#pragma unroll
-        for (uint32_t q = 0; q < kHeld; ++q) {
-            held[q] = (e0 + q < e1) ? b.lvl_hist[e0 + q] : 0u;
-            s += held[q];
-        }
-    } else {
-        for (uint32_t e = e0; e < e1; ++e)
-            s += b.lvl_hist[e];
-    }
+    const uint32_t seg = warp_segment(E), lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t s0 = min(E, w * seg), s1 = min(E, s0 + seg);
+    // the warp's segment total, then the block's exclusive scan of the totals
+    uint32_t part = 0;
+    for (uint32_t i = s0 + lane; i < s1; i += 32u)
+        part += b.lvl_hist[i];
+    part = warp_sum(part);
     uint32_t total;
-    uint32_t run = block_exclusive_scan_u32(s, sh, &total);
-    if (chunk <= kHeld) {
-#pragma unroll
-        for (uint32_t q = 0; q < kHeld; ++q)
-            if (e0 + q < e1) {
-                b.lvl_off[e0 + q] = run;
-                run += held[q];
-            }
-    } else {
-        for (uint32_t e = e0; e < e1; ++e) {
-            uint32_t v = b.lvl_hist[e];
-            b.lvl_off[e] = run;
-            run += v;
-        }
+    uint32_t carry = block_exclusive_scan_u32(lane == 0 ? part : 0u, sh, &total);
+    carry = __shfl_sync(kFull, carry, 0);
+    // row by row: the exclusive offset of each entry
+    for (uint32_t r = s0; r < s1; r += 32u) {
+        const uint32_t i = r + lane;
+        const uint32_t v = i < s1 ? b.lvl_hist[i] : 0u;
+        const uint32_t inc = warp_inclusive_scan_u32(v);
+        if (i < s1)
+            b.lvl_off[i] = carry + inc - v;
+        carry += __shfl_sync(kFull, inc, 31);
     }
     __syncthreads();
     for (uint32_t l = threadIdx.x; l <= sc.n_max + 1; l += blockDim.x) {
