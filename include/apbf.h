@@ -316,7 +316,9 @@ APBF_API void apbf_destroy_scene(apbf_scene *scene);
  *  stats      device, 4 doubles: {mean |rho/rho0-1|, max |rho/rho0-1|,
  *             mean (rho/rho0-1), mean max(0, rho/rho0-1)}, written
  *             asynchronously on cuda_stream (NULL = the legacy default stream).
- *  cuda_stream must belong to the current device (else APBF_ERR_INVALID_ARG).
+ *  cuda_stream must belong to the current device (else APBF_ERR_INVALID_ARG;
+ *             not checked while the stream is being captured into a CUDA graph,
+ *             where the query would end the capture).
  * Larger n or grids return APBF_ERR_INVALID_ARG with a message in
  * apbf_last_error(NULL). The call makes no cudaMalloc, cudaFree or other
  * allocating call: all scratch (about 3.9 MB) is one static device array that
@@ -325,8 +327,9 @@ APBF_API void apbf_destroy_scene(apbf_scene *scene);
  * since CUDA loads a library's kernels lazily by default, that first lookup and
  * launch load the module, which reserves the array on the device then (an
  * implicit allocation that may synchronise). Make that first call once at
- * initialisation, outside any frame loop and before capturing any stream;
- * later calls allocate nothing. All calls share the one array and it keeps the
+ * initialisation, outside any frame loop and before capturing any stream (a
+ * first call on a capturing stream returns APBF_ERR_BAD_STATE); later calls
+ * allocate nothing and may be captured into a CUDA graph. All calls share the one array and it keeps the
  * previous call's contents (the call clears what must start at zero), so calls
  * that overlap on the GPU -- on different streams, or from several host
  * threads -- race and must be serialised by the caller.

@@ -240,23 +240,35 @@ apbf_status fail(apbf_status st, const std::string &m)
 // The device address of the static scratch array on the current device,
 // looked up once per device (the host-side symbol is not a device address).
 // The stream must belong to that device: its kernels would otherwise run on
-// the stream's device against an address taken on another.
+// the stream's device against an address taken on another. A stream that is
+// being captured into a graph cannot be asked for its device (the query would
+// end the capture), so there the check is skipped, and the first call on the
+// device (the lookup, which loads the module) is refused instead of breaking
+// the capture.
 apbf_status scratch_for_current_device(cudaStream_t stream, uint32_t **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return fail(APBF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    int sdev = -1;
-    e = cudaStreamGetDevice(stream, &sdev);
-    if (e != cudaSuccess)
-        return fail(APBF_ERR_INVALID_ARG, std::string("cuda_stream: ") + cudaGetErrorString(e));
-    if (sdev != dev)
-        return fail(APBF_ERR_INVALID_ARG, "cuda_stream belongs to device " + std::to_string(sdev) +
-                                              ", not to the current device " + std::to_string(dev));
     if (dev < 0 || dev >= 64)
         return fail(APBF_ERR_NOT_SUPPORTED, "device ordinal above 63");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess)
+        return fail(APBF_ERR_INVALID_ARG, std::string("cuda_stream: ") + cudaGetErrorString(e));
+    if (cap == cudaStreamCaptureStatusNone) {
+        int sdev = -1;
+        e = cudaStreamGetDevice(stream, &sdev);
+        if (e != cudaSuccess)
+            return fail(APBF_ERR_INVALID_ARG, std::string("cuda_stream: ") + cudaGetErrorString(e));
+        if (sdev != dev)
+            return fail(APBF_ERR_INVALID_ARG, "cuda_stream belongs to device " + std::to_string(sdev) +
+                                                  ", not to the current device " + std::to_string(dev));
+    }
     std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!g_scratch_ptr[dev] && cap != cudaStreamCaptureStatusNone)
+        return fail(APBF_ERR_BAD_STATE, "the first call on a device loads the module: make it outside stream capture");
     if (!g_scratch_ptr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_density_scratch);

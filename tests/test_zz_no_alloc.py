@@ -73,6 +73,38 @@ def test_static_density_stats_at_the_maximum_sizes():
     _run_twice(cfg, lo, hi, (2, 2))
 
 
+
+def test_a_warm_call_captures_into_a_cuda_graph():
+    """After the first call (which loads the module and its static array), a
+    call only enqueues stream work: it captures into a CUDA graph in global
+    capture mode, where an allocation or a synchronising call would end the
+    capture with an error, and each replay of the graph gives the oracle's
+    statistics."""
+    import torch
+
+    cfg = scenes.config_dam_break_4k()
+    x, _ = scenes.make_scene(cfg)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    rho0 = float(np.float32(oracle.rest_density(cfg.h, cfg.mass, cfg.spacing)))
+    p = oracle.make_params(cfg, rho0=rho0, grid_lo=cfg.box_lo, grid_hi=cfg.box_hi)
+    orc = oracle.density_stats(p, x)
+    pos_dev = torch.from_numpy(x).cuda().contiguous()
+    stats_dev = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    args = (pos_dev, cfg.n, cfg.h, cfg.mass, rho0, cfg.box_lo, cfg.box_hi, stats_dev)
+    apbf.apbf_density_stats_static(*args)  # the first call: module load
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        apbf.apbf_density_stats_static(*args)
+    for _ in range(2):
+        stats_dev.fill_(-1.0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        got = stats_dev.cpu().numpy()
+        assert np.allclose(got, orc, rtol=RTOL, atol=ATOL), (got, orc)
+
+
 def test_sizes_beyond_the_static_maximum_are_rejected():
     import torch
 
