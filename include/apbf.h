@@ -59,7 +59,7 @@ typedef enum apbf_status {
     APBF_ERR_TIMEOUT = 4,           /* a bounded device-side wait gave up */
     APBF_ERR_BAD_STATE = 5,         /* call not valid in the scene's current state */
     APBF_ERR_NEIGHBOR_OVERFLOW = 6, /* a particle had more neighbours than max_neighbors */
-    APBF_ERR_NOT_SUPPORTED = 7,     /* option outside what this build implements */
+    APBF_ERR_NOT_SUPPORTED = 7,     /* option outside what the library implements */
     APBF_ERR_CHECK_FAILED = 8       /* an invariant check of the debug build failed (message: which, where) */
 } apbf_status;
 
