@@ -183,6 +183,14 @@ struct ViewConst {
     size_t alloc_bytes = 0;
 };
 
+// A texture object over a record array (raw 32-bit words): record e is
+// texel e + off (the texture starts at the array's address rounded down to the
+// device's texture alignment). t = 0: the array has no texture object.
+struct RecTex {
+    cudaTextureObject_t t = 0;
+    uint32_t off = 0;
+};
+
 struct Buffers {
     float4 *state_x, *state_v;
     uint32_t *state_id;
@@ -194,6 +202,7 @@ struct Buffers {
     uint8_t *lvl_s, *nbr_cnt;     // nbr_cnt and nbr: by list column (see partitioned())
     uint32_t *nbr;
     uint8_t *prev_cnt;            // neighbour count of each state slot in the last step
+    RecTex texXt;                 // texture object over xt (the velocity pass), t = 0: none
     float *rho;
     float *lodd;                   // DTVS distance behind the visible surface, state order (-1: outside the view)
     uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;

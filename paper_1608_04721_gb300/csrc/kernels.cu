@@ -192,6 +192,15 @@ __device__ __forceinline__ void wait_for_predecessor()
 constexpr int kUnroll = (int)kEntryBlock;
 
 
+// Record e of an array through the texture path (see RecTex): the velocity
+// pass gathers two records per pair and takes one of them this way, so the two
+// gathers are served by the L1's load/store and texture paths side by side.
+__device__ __forceinline__ float4 tex_rec(const RecTex &tex, uint32_t e)
+{
+    const uint4 q = tex1Dfetch<uint4>(tex.t, (int)(e + tex.off));
+    return make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w));
+}
+
 // Visit the neighbour entries of one particle in batches of kUnroll: the
 // batch's entries are loaded first, then its records, then f runs on each,
 // so a thread has kUnroll independent gathers in flight. Entries are read
@@ -1862,7 +1871,7 @@ __global__ void __launch_bounds__(kBlock) finalize_kernel(StepConst sc, Buffers 
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             aj[u] = __ldg(&b.recA[e[u]]);
-            xj[u] = __ldg(&b.xt[e[u]]);
+            xj[u] = b.texXt.t ? tex_rec(b.texXt, e[u]) : __ldg(&b.xt[e[u]]);
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
