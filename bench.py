@@ -50,12 +50,12 @@ FLOPS_PER_PAIR = {"lambda": 30, "deltap": 36, "finalize": 26}
 # algorithmic bytes per unit of the HBM-bound stages (each distinct array
 # element read or written once per launch): unit "particle" or "cell"
 STAGE_BYTES = {
-    "lod_range": (16, "particle", "x read"),
-    "predict": (41, "particle", "x, v read (32 B); key, slot, level written (9 B)"),
+    "predict": (40, "particle", "x, v read (32 B); key, slot written (8 B); the camera-distance range reduced on chip"),
     "scan": (12, "cell", "counts read, starts written, counts zeroed"),
     "scatter": (16, "particle", "key, slot read; start gathered; id written"),
-    "reorder": (102, "particle", "45 B read (x, v, id, level, key, slot), 57 B written (records, x*, ids, levels, cells)"),
-    "levels": (9, "particle", "level read twice, active index written"),
+    "reorder": (102, "particle", "44 B read (x, v, id, key, start); 58 B written (records, x*, ids, cells, "
+                                 "levels in both orders)"),
+    "levels": (5, "particle", "level read, active index written (per-tile counts from the reorder pass)"),
     "finalize": (76, "particle", "records, start positions read; x, v, id written (own particle; "
                                  "neighbour records via cache)"),
 }
@@ -189,12 +189,12 @@ class ClockSampler:
 
 
 def kernels_per_step(cfg) -> int:
-    dtc = cfg.lod_mode == scenes.LOD_DTC
-    k = 1 + 2 + 1 + 1 + 1 + 1  # predict, scan (2), scatter, reorder, neighbors, finalize
-    if dtc:
-        k += 1  # camera-distance range
-        if cfg.n_max > cfg.n_min:
-            k += 3  # level histogram, scan, scatter
+    """Kernel launches of one step of a distance-to-camera (or fixed-level) scene."""
+    k = 1 + 2 + 1 + 1 + 1 + 1  # predict (with the distance range), scan (2), scatter, reorder, neighbors, finalize
+    if cfg.lod_mode != scenes.LOD_FIXED and cfg.n_max > cfg.n_min:
+        k += 2  # level scan, level scatter (the per-tile level counts come from the reorder pass)
+    if getattr(cfg, "stabil_s", 0) > 1 and getattr(cfg, "stabil_iters", 0) > 0:
+        k += 1  # pre-stabilisation
     return k + 2 * cfg.n_max
 
 

@@ -341,11 +341,12 @@ APBF_API apbf_status apbf_density_stats_static(const float *pos, uint32_t n, flo
 /* ---------------------------------------------------------------- timing */
 
 /* Stage identifiers (timing and debug). */
-#define APBF_STAGE_LOD_RANGE 0u  /* a1: camera-distance min/max */
-#define APBF_STAGE_PREDICT 1u    /* a1-a4: level, prediction, cell hash, histogram */
+#define APBF_STAGE_LOD_RANGE 0u  /* a1: DTVS depth image, distances and their range (empty for the
+                                    other LOD models) */
+#define APBF_STAGE_PREDICT 1u    /* a1-a4: camera-distance range, prediction, cell hash, histogram */
 #define APBF_STAGE_SCAN 2u       /* a4/a6: exclusive scan = cell start/end */
 #define APBF_STAGE_SCATTER 3u    /* a4: slot scatter */
-#define APBF_STAGE_REORDER 4u    /* a4/a5: stable rank and reorder */
+#define APBF_STAGE_REORDER 4u    /* a1, a4/a5: level, stable rank and reorder */
 #define APBF_STAGE_NEIGHBORS 5u  /* neighbour lists (the neighbour search of Fig. 7) */
 #define APBF_STAGE_LEVELS 6u     /* a7: active-set partition */
 #define APBF_STAGE_LAMBDA 7u     /* a8 */
@@ -509,7 +510,7 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint3
 
 #define APBF_DBG_KEYS 0u          /* u32[n]  cell key, pre-sort (state) order */
 #define APBF_DBG_STATE_IDS 1u     /* u32[n]  particle ids in state order */
-#define APBF_DBG_LEVEL_PRESORT 2u /* u8[n]   N_i, pre-sort order */
+#define APBF_DBG_LEVEL_PRESORT 2u /* u8[n]   N_i, pre-sort order (from APBF_STAGE_REORDER on) */
 #define APBF_DBG_SORTED_IDS 3u    /* u32[n]  particle ids in sorted order */
 #define APBF_DBG_CELL_START 4u    /* u32[ncell+1] */
 #define APBF_DBG_XPRED 5u         /* float4[n] predicted positions (FP32), sorted */

@@ -329,11 +329,13 @@ size_t carve(const StepConst &sc, char *base, Buffers &b)
     b.rho = (float *)P(4 * n);
     b.lodd = (float *)P(4 * n);
     b.act = (uint32_t *)P(4 * n);
-    b.lvl_hist = (uint32_t *)P(4 * lvl_e);
     b.lvl_off = (uint32_t *)P(4 * lvl_e);
     b.lvl_count = (uint32_t *)P(4 * 258);
-    b.counters = (unsigned long long *)P(8 * kCounterSlots);
+    // zeroed together at the start of every step (step_zero_bytes): the level
+    // counts per tile, the distance range and the step's pair counters
+    b.lvl_hist = (uint32_t *)P(4 * lvl_e);
     b.drange = (uint32_t *)P(8 * (size_t)sc.scenes);
+    b.counters = (unsigned long long *)P(8 * kCounterSlots);
     b.err = (uint32_t *)P(4);
     b.err_scene = (uint32_t *)P(4 * (size_t)sc.scenes);
     b.dbg = (uint32_t *)P(16);
@@ -392,28 +394,17 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
 {
     const StepConst &sc = s->sc;
     const Buffers &b = s->b;
-    const bool dtc = sc.lod_mode == APBF_LOD_DTC;
     const bool dtvs = sc.lod_mode == APBF_LOD_DTVS;
     cudaError_t e;
     if (dtvs && (!s->view_set || !s->view.depth || !s->view.ray))
         return fail(s, APBF_ERR_BAD_STATE, "a DTVS scene needs apbf_set_view before it steps");
+    // one fill resets the level counts per tile, the distance range and the pair counters
+    if ((e = cudaMemsetAsync(b.lvl_hist, 0, step_zero_bytes(b), st)) != cudaSuccess)
+        return cuda_fail(s, e, "step counters");
     if (dtvs) {  // depth image, distances behind the visible surface and their range
-        e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
-            cudaMemsetAsync(b.drange, 0x7f, 4, st);
-            cudaMemsetAsync(b.drange + 1, 0, 4, st);
-            return launch_dtvs(sc, b, s->view, s->sms, st);
-        });
+        e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] { return launch_dtvs(sc, b, s->view, s->sms, st); });
         if (e != cudaSuccess)
             return cuda_fail(s, e, "dtvs");
-    }
-    if (dtc) {  // always captured; unused when the camera gives a distance range
-        e = timed(s, st, APBF_STAGE_LOD_RANGE, [&] {
-            cudaMemsetAsync(b.drange, 0x7f, 4 * (size_t)sc.scenes, st);  // 0x7f7f7f7f = 3.4e38f
-            cudaMemsetAsync(b.drange + sc.scenes, 0, 4 * (size_t)sc.scenes, st);
-            return launch_lod_range(sc, b, st);
-        });
-        if (e != cudaSuccess)
-            return cuda_fail(s, e, "lod_range");
     }
     if (stop_stage == APBF_STAGE_LOD_RANGE)
         return APBF_OK;
@@ -442,10 +433,7 @@ apbf_status enqueue_step(apbf_scene *s, cudaStream_t st, uint32_t stop_stage, ui
     }
     if (stop_stage == APBF_STAGE_LEVELS)
         return APBF_OK;
-    e = timed(s, st, APBF_STAGE_NEIGHBORS, [&] {
-        cudaMemsetAsync(b.counters, 0, 8 * (2 + 256), st);
-        return launch_neighbors(sc, b, st, part);
-    });
+    e = timed(s, st, APBF_STAGE_NEIGHBORS, [&] { return launch_neighbors(sc, b, st, part); });
     s->lists_by_slot = !part;
     if (e != cudaSuccess)
         return cuda_fail(s, e, "neighbors");
@@ -1103,7 +1091,7 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
         return APBF_OK;
     std::vector<unsigned long long> c(kCounterSlots);
     std::vector<uint32_t> lc(258);
-    float dr[2];
+    uint32_t dr[2];
     APBF_CUDA(s, cudaMemcpy(c.data(), s->b.counters, 8 * kCounterSlots, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(lc.data(), s->b.lvl_count, 4 * 258, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(&dr[0], s->b.drange, 4, cudaMemcpyDeviceToHost));
@@ -1127,8 +1115,9 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     }
     if (sc.lod_mode != APBF_LOD_FIXED) {
         if (s->dyn[0].auto_range) {
-            info->d_range[0] = dr[0];
-            info->d_range[1] = dr[1];
+            uint32_t lo = ~dr[0];  // the minimum is kept as the complement of its bit pattern
+            std::memcpy(&info->d_range[0], &lo, 4);
+            std::memcpy(&info->d_range[1], &dr[1], 4);
         } else {
             info->d_range[0] = s->dyn[0].d_near;
             info->d_range[1] = s->dyn[0].d_far;
@@ -1451,6 +1440,9 @@ APBF_API apbf_status apbf_debug_read(apbf_scene *s, uint32_t field, void *host, 
     if (size)
         APBF_CUDA(s, cudaMemcpyAsync(host, src, size, cudaMemcpyDeviceToHost, s->stream));
     APBF_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (field == APBF_DBG_DRANGE)  // the minima are kept as the complements of their bit patterns
+        for (uint32_t k = 0; k < sc.scenes; ++k)
+            ((uint32_t *)host)[k] = ~((uint32_t *)host)[k];
     return check_device_errors(s);
 }
 

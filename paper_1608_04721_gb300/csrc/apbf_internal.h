@@ -34,6 +34,10 @@ __host__ __device__ constexpr uint32_t list_rows(uint32_t max_nbr)
 }
 constexpr int kBlock = 256;          // threads per block of the per-particle kernels
 constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 threads x 4)
+#ifndef APBF_PREDICT_BLOCKS
+#define APBF_PREDICT_BLOCKS 1024
+#endif
+constexpr unsigned kPredictBlocks = APBF_PREDICT_BLOCKS;  // grid cap of a single scene's predict pass (its range atomics)
 constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
 constexpr int kTilePx = 8;           // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
 constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles take the big-sphere path
@@ -207,7 +211,7 @@ struct Buffers {
     float *lodd;                   // DTVS distance behind the visible surface, state order (-1: outside the view)
     uint32_t *act, *lvl_hist, *lvl_off, *lvl_count;
     unsigned long long *counters;  // kCounterSlots: see kDiagCounterSlot, kIterTotalSlot
-    uint32_t *drange;              // float bits of d_min (scenes entries), then d_max (scenes entries)
+    uint32_t *drange;              // ~(float bits) of d_min (scenes entries), then float bits of d_max
     const SceneGeom *geo;          // per scene
     const uint16_t *sid;           // scene of each particle slot (constant)
     uint32_t *err;                 // device error word (kErr* bits) of the step
@@ -291,9 +295,14 @@ namespace apbf {
 // active-list position (column t holds the particle act[t]), otherwise by
 // sorted slot.
 inline bool partitioned(const StepConst &sc) { return sc.lod_mode != APBF_LOD_FIXED && sc.K > 1; }
+// Bytes of the region zeroed at the start of every step: the level counts per
+// tile, the distance range and the step's counters (carved in this order).
+inline size_t step_zero_bytes(const Buffers &b)
+{
+    return (size_t)((const char *)(b.counters + kDiagCounterSlot) - (const char *)b.lvl_hist);
+}
 
 // Kernel launchers (kernels.cu). Each returns cudaGetLastError().
-cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag);
 cudaError_t launch_scan(const StepConst &sc, const Buffers &b, cudaStream_t s);
 cudaError_t launch_scatter(const StepConst &sc, const Buffers &b, cudaStream_t s);

@@ -444,48 +444,30 @@ __device__ __forceinline__ Anchor anchor_of(const Geo &g, const StepConst &sc)
 }
 
 // ------------------------------------------------------------- a1: range
+// The camera-distance range of a step, a pair of words per scene that the
+// step's zero fill resets: the minimum as the complement of its bit pattern,
+// the maximum as its bit pattern (distances are >= 0, so their patterns order
+// like the values, and a zero word stands for "no distance yet" in both).
 
-template <bool BATCH>
-__global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers b)
+__device__ __forceinline__ float range_min(const uint32_t *drange, uint32_t s) { return __uint_as_float(~drange[s]); }
+__device__ __forceinline__ float range_max(const uint32_t *drange, uint32_t scenes, uint32_t s)
 {
-    wait_for_predecessor();
+    return __uint_as_float(drange[scenes + s]);
+}
+
+// Merges each valid thread's distances into its scene's range: one atomic pair
+// per block when the block lies in one scene (every block of a single scene).
+template <bool BATCH>
+__device__ __forceinline__ void range_merge(const StepConst &sc, const Buffers &b, bool valid, uint32_t s, float dmin,
+                                            float dmax)
+{
     __shared__ float smin[kBlock / 32], smax[kBlock / 32];
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < sc.n;
-    const uint32_t s = valid ? scene_of<BATCH>(b, i) : 0u;
-    float dmin = 3.0e38f, dmax = 0.0f;
-    if (!BATCH) {
-        // one scene: a grid-stride loop over a capped grid, so only a few
-        // hundred blocks contend for the two atomics; four independent loads
-        // in flight per thread
-        const uint32_t stride = gridDim.x * blockDim.x;
-        uint32_t k = i;
-        for (; k + 3 * stride < sc.n; k += 4 * stride) {
-            float4 x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                x[u] = b.state_x[k + u * stride];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float d = camera_distance(x[u], b.dyn);
-                dmin = fminf(dmin, d);
-                dmax = fmaxf(dmax, d);
-            }
-        }
-        for (; k < sc.n; k += stride) {
-            const float d = camera_distance(b.state_x[k], b.dyn);
-            dmin = fminf(dmin, d);
-            dmax = fmaxf(dmax, d);
-        }
-    } else if (valid) {
-        const float d = camera_distance(b.state_x[i], b.dyn + s);
-        dmin = d;
-        dmax = d;
+    if (!valid) {
+        dmin = 3.0e38f;
+        dmax = 0.0f;
     }
-    // distances are >= 0, so their bit patterns order like the values
-    const uint32_t s_first = scene_of<BATCH>(b, blockIdx.x * blockDim.x);
+    const uint32_t s_first = scene_of<BATCH>(b, min(blockIdx.x * blockDim.x, sc.n - 1));
     if (__syncthreads_and(!valid || s == s_first)) {
-        // the whole block lies in one scene: one atomic pair per block
         dmin = warp_minf(dmin);
         dmax = warp_maxf(dmax);
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -497,13 +479,13 @@ __global__ void __launch_bounds__(kBlock) lod_range_kernel(StepConst sc, Buffers
         if (w == 0) {
             dmin = warp_minf(lane < kBlock / 32 ? smin[lane] : 3.0e38f);
             dmax = warp_maxf(lane < kBlock / 32 ? smax[lane] : 0.0f);
-            if (lane == 0) {
-                atomicMin(&b.drange[s_first], __float_as_uint(dmin));
+            if (lane == 0 && dmin <= dmax) {
+                atomicMax(&b.drange[s_first], ~__float_as_uint(dmin));
                 atomicMax(&b.drange[sc.scenes + s_first], __float_as_uint(dmax));
             }
         }
     } else if (valid) {
-        atomicMin(&b.drange[s], __float_as_uint(dmin));
+        atomicMax(&b.drange[s], ~__float_as_uint(dmin));
         atomicMax(&b.drange[sc.scenes + s], __float_as_uint(dmax));
     }
 }
@@ -1054,62 +1036,67 @@ __global__ void __launch_bounds__(kBlock) dtvs_distance_kernel(StepConst sc, Buf
         dmin = warp_minf(lane < kBlock / 32 ? smin[lane] : 3.0e38f);
         dmax = warp_maxf(lane < kBlock / 32 ? smax[lane] : 0.0f);
         if (lane == 0 && dmin <= dmax) {
-            atomicMin(&b.drange[0], __float_as_uint(dmin));
+            atomicMax(&b.drange[0], ~__float_as_uint(dmin));
             atomicMax(&b.drange[1], __float_as_uint(dmax));
         }
     }
 }
 
-// ------------------------------------- a1-a4: level, predict, hash, count
+// ------------------------------------- a1-a4: range, predict, hash, count
+// The prediction and cell hash of every particle, the cell histogram, and
+// (distance-to-camera LOD) the camera-distance range of the positions at the
+// start of the step; the levels follow from the range in the reorder pass.
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) predict_hash_kernel(StepConst sc, Buffers b, int diag)
 {
     wait_for_predecessor();
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = i < sc.n;
-    uint32_t key = 0xffffffffu;
-    if (valid) {
-        const uint32_t s = scene_of<BATCH>(b, i);
-        const Geo g = geo_of<BATCH>(sc, b, s);
-        const DynParams *dyn = b.dyn + s;
-        float4 x = b.state_x[i];
-        float3 p;
-        if (diag) {
-            p = make_float3(x.x, x.y, x.z);
-        } else {
-            uint32_t lv = sc.n_max;
-            if (sc.lod_mode != APBF_LOD_FIXED) {
-                float dmin = dyn->d_near, dmax = dyn->d_far;
-                if (dyn->auto_range) {
-                    dmin = __uint_as_float(b.drange[s]);
-                    dmax = __uint_as_float(b.drange[sc.scenes + s]);
+    const bool range = !diag && sc.lod_mode == APBF_LOD_DTC;
+    float dmin = 3.0e38f, dmax = 0.0f;  // this thread's distances (a single scene loops over several)
+    bool any = false;
+    uint32_t s = 0;
+    // block-uniform loop: a batch's grid covers every particle once (one
+    // scene per thread); a single scene's grid is capped, which keeps the
+    // range's atomics few
+    for (uint32_t base = blockIdx.x * blockDim.x; base < sc.n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < sc.n;
+        uint32_t key = 0xffffffffu;
+        if (valid) {
+            s = scene_of<BATCH>(b, i);
+            const Geo g = geo_of<BATCH>(sc, b, s);
+            const DynParams *dyn = b.dyn + s;
+            float4 x = b.state_x[i];
+            float3 p;
+            if (diag) {
+                p = make_float3(x.x, x.y, x.z);
+            } else {
+                if (range) {
+                    const float d = camera_distance(x, dyn);
+                    dmin = fminf(dmin, d);
+                    dmax = fmaxf(dmax, d);
+                    any = true;
                 }
-                if (sc.lod_mode == APBF_LOD_DTC) {
-                    lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
-                } else {  // DTVS: outside the view -> n_min
-                    const float d = b.lodd[i];
-                    lv = d < 0.0f ? sc.n_min : lod_level(d, dmin, dmax, sc);
-                }
+                p = predict_position(x, b.state_v[i], sc, dyn);
             }
-            b.lvl[i] = (uint8_t)lv;
-            p = predict_position(x, b.state_v[i], sc, dyn);
+            key = key_in(cell_in(p, g, sc.inv_h), g);
+            if (!check_ok(key < sc.ncell, kCheckCellKey, i, b.err, b.dbg))
+                key = sc.ncell - 1;
+            b.key[i] = key;
         }
-        key = key_in(cell_in(p, g, sc.inv_h), g);
-        if (!check_ok(key < sc.ncell, kCheckCellKey, i, b.err, b.dbg))
-            key = sc.ncell - 1;
-        b.key[i] = key;
+        // warp-aggregated histogram: one atomic per distinct cell in the warp
+        unsigned peers = __match_any_sync(kFull, key);
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(peers) - 1;
+        uint32_t slot0 = 0;
+        if (valid && lane == leader)
+            slot0 = atomicAdd(&b.cnt[key], (uint32_t)__popc(peers));
+        slot0 = __shfl_sync(peers, slot0, leader);
+        if (valid)
+            b.slot[i] = slot0 + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
-    // warp-aggregated histogram: one atomic per distinct cell in the warp
-    unsigned peers = __match_any_sync(kFull, key);
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader)
-        base = atomicAdd(&b.cnt[key], (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    if (valid)
-        b.slot[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    if (range)  // uniform over the grid
+        range_merge<BATCH>(sc, b, any, s, dmin, dmax);
 }
 
 // ------------------------------------------------ a4/a6: scan = cell start
@@ -1183,42 +1170,70 @@ __global__ void __launch_bounds__(kBlock) scatter_kernel(StepConst sc, Buffers b
         b.tmp[b.start[b.key[i]] + b.slot[i]] = b.state_id[i];
 }
 
-// ------------------------------------------ a4/a5: stable rank + reorder
+// ------------------------------------------ a1, a4/a5: level, stable rank + reorder
+// Each particle's level (Sec. 4.1, Eq. 8) from the range the predict pass
+// reduced (or the camera's range), its sorted slot, and its records in sorted
+// order. With an active-set partition the pass also counts the particles of
+// each level in each tile of kLevelTile sorted slots (one atomic per distinct
+// (level, tile) in a warp; the counts start at zero with the step).
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b, int diag)
 {
     wait_for_predecessor();
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc.n)
-        return;
-    uint32_t k = b.key[i];
-    uint32_t s0 = b.start[k], s1 = b.start[k + 1];
-    // order within a cell by particle id: rank = number of this cell's
-    // particles with a smaller id (the slots hold ids in atomic arrival order)
-    const uint32_t id = b.state_id[i];
-    uint32_t r = 0;
-    for (uint32_t j = s0; j < s1; ++j)
-        r += (b.tmp[j] < id) ? 1u : 0u;
-    uint32_t p = s0 + r;
-    if (!check_ok(s1 <= sc.n && p < s1, kCheckSortedSlot, i, b.err, b.dbg))
-        return;
-    const uint32_t s = scene_of<BATCH>(b, i);
-    const Geo g = geo_of<BATCH>(sc, b, s);
-    float4 x = b.state_x[i];
-    float3 xp = diag ? make_float3(x.x, x.y, x.z) : predict_position(x, b.state_v[i], sc, b.dyn + s);
-    int3 c = cell_in(xp, g, sc.inv_h);
-    b.xs32[p] = make_float4(xp.x, xp.y, xp.z, 0.0f);
-    b.cell_s[p] = pack_cell(c);
-    if (!diag) {
-        const Anchor A = anchor_of(g, sc);
-        const float iu = sc.fx_inv_u;
-        b.recA[p] = make_float4(fx_word(fx_of(xp.x, A.a[0], iu)), fx_word(fx_of(xp.y, A.a[1], iu)),
-                                fx_word(fx_of(xp.z, A.a[2], iu)), 0.0f);
-        b.xt[p] = make_float4(fx_word(fx_of(x.x, A.a[0], iu)), fx_word(fx_of(x.y, A.a[1], iu)),
-                              fx_word(fx_of(x.z, A.a[2], iu)), 0.0f);
-        b.id_s[p] = id;
-        b.lvl_s[p] = b.lvl[i];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t hist_key = 0xffffffffu;  // bin * level_tiles + tile, or none
+    if (i < sc.n) {
+        const uint32_t k = b.key[i];
+        const uint32_t s0 = b.start[k], s1 = b.start[k + 1];
+        // order within a cell by particle id: rank = number of this cell's
+        // particles with a smaller id (the slots hold ids in atomic arrival order)
+        const uint32_t id = b.state_id[i];
+        uint32_t r = 0;
+        for (uint32_t j = s0; j < s1; ++j)
+            r += (b.tmp[j] < id) ? 1u : 0u;
+        const uint32_t p = s0 + r;
+        if (check_ok(s1 <= sc.n && p < s1, kCheckSortedSlot, i, b.err, b.dbg)) {
+            const uint32_t s = scene_of<BATCH>(b, i);
+            const Geo g = geo_of<BATCH>(sc, b, s);
+            const DynParams *dyn = b.dyn + s;
+            float4 x = b.state_x[i];
+            float3 xp = diag ? make_float3(x.x, x.y, x.z) : predict_position(x, b.state_v[i], sc, dyn);
+            int3 c = cell_in(xp, g, sc.inv_h);
+            b.xs32[p] = make_float4(xp.x, xp.y, xp.z, 0.0f);
+            b.cell_s[p] = pack_cell(c);
+            if (!diag) {
+                const Anchor A = anchor_of(g, sc);
+                const float iu = sc.fx_inv_u;
+                b.recA[p] = make_float4(fx_word(fx_of(xp.x, A.a[0], iu)), fx_word(fx_of(xp.y, A.a[1], iu)),
+                                        fx_word(fx_of(xp.z, A.a[2], iu)), 0.0f);
+                b.xt[p] = make_float4(fx_word(fx_of(x.x, A.a[0], iu)), fx_word(fx_of(x.y, A.a[1], iu)),
+                                      fx_word(fx_of(x.z, A.a[2], iu)), 0.0f);
+                b.id_s[p] = id;
+                uint32_t lv = sc.n_max;
+                if (sc.lod_mode != APBF_LOD_FIXED) {
+                    float dmin = dyn->d_near, dmax = dyn->d_far;
+                    if (dyn->auto_range) {
+                        dmin = range_min(b.drange, s);
+                        dmax = range_max(b.drange, sc.scenes, s);
+                    }
+                    if (sc.lod_mode == APBF_LOD_DTC) {
+                        lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
+                    } else {  // DTVS: outside the view -> n_min
+                        const float d = b.lodd[i];
+                        lv = d < 0.0f ? sc.n_min : lod_level(d, dmin, dmax, sc);
+                    }
+                }
+                b.lvl[i] = (uint8_t)lv;
+                b.lvl_s[p] = (uint8_t)lv;
+                hist_key = (sc.n_max - lv) * sc.level_tiles + p / kLevelTile;
+            }
+        }
+    }
+    if (!diag && sc.lod_mode != APBF_LOD_FIXED && sc.K > 1) {  // the partition's counts (uniform over the grid)
+        const unsigned peers = __match_any_sync(kFull, hist_key);
+        if (hist_key != 0xffffffffu && (threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1))
+            atomicAdd(&b.lvl_hist[hist_key], (uint32_t)__popc(peers));
     }
 }
 
@@ -1346,60 +1361,48 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
 // Particles are partitioned by level, highest first, stable in sorted-slot
 // order within a level. P_l is then the prefix of act of length |P_l|.
 
-__global__ void __launch_bounds__(kLevelTile) level_hist_kernel(StepConst sc, Buffers b)
-{
-    wait_for_predecessor();
-    extern __shared__ uint32_t sh[];  // K counts
-    const uint32_t K = sc.K;
-    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x)
-        sh[k] = 0u;
-    __syncthreads();
-    uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
-    if (p < sc.n)
-        atomicAdd(&sh[sc.n_max - b.lvl_s[p]], 1u);
-    __syncthreads();
-    for (uint32_t k = threadIdx.x; k < K; k += blockDim.x)
-        b.lvl_hist[(size_t)k * sc.level_tiles + blockIdx.x] = sh[k];
-}
-
+// The counts per (level bin, tile) come from the reorder pass. Block k of
+// this kernel turns bin k's row into exclusive offsets: the particles of the
+// bins before it (higher levels) plus those of bin k in the tiles before
+// each tile; the offset past the row is |P_l| for l = n_max - k.
 __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers b)
 {
     wait_for_predecessor();
     __shared__ uint32_t sh[32];
-    const uint32_t E = sc.K * sc.level_tiles;
-    const uint32_t seg = warp_segment(E), lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-    const uint32_t s0 = min(E, w * seg), s1 = min(E, s0 + seg);
-    // the warp's segment total, then the block's exclusive scan of the totals
-    uint32_t part = 0;
-    for (uint32_t i = s0 + lane; i < s1; i += 32u)
-        part += b.lvl_hist[i];
-    part = warp_sum(part);
-    uint32_t total;
-    uint32_t carry = block_exclusive_scan_u32(lane == 0 ? part : 0u, sh, &total);
-    carry = __shfl_sync(kFull, carry, 0);
-    // row by row: the exclusive offset of each entry
-    for (uint32_t r = s0; r < s1; r += 32u) {
-        const uint32_t i = r + lane;
-        const uint32_t v = i < s1 ? b.lvl_hist[i] : 0u;
-        const uint32_t inc = warp_inclusive_scan_u32(v);
-        if (i < s1)
-            b.lvl_off[i] = carry + inc - v;
-        carry += __shfl_sync(kFull, inc, 31);
-    }
-    __syncthreads();
-    for (uint32_t l = threadIdx.x; l <= sc.n_max + 1; l += blockDim.x) {
-        uint32_t c;
-        if (l > sc.n_max)
-            c = 0;
-        else if (l <= sc.n_min)
-            c = sc.n;
-        else {
-            uint32_t bin_end = sc.n_max - l + 1;  // bins 0..n_max-l hold levels >= l
-            c = (bin_end >= sc.K) ? sc.n : b.lvl_off[(size_t)bin_end * sc.level_tiles];
+    const uint32_t T = sc.level_tiles, k = blockIdx.x;
+    uint32_t before = 0;
+    for (size_t i = threadIdx.x; i < (size_t)k * T; i += blockDim.x)
+        before += b.lvl_hist[i];
+    uint32_t carry = block_sum_u32(before, sh);
+    const uint32_t *row = b.lvl_hist + (size_t)k * T;
+    uint32_t *orow = b.lvl_off + (size_t)k * T;
+    for (uint32_t c0 = 0; c0 < T; c0 += 4u * blockDim.x) {
+        const uint32_t base = c0 + 4u * threadIdx.x;
+        uint32_t v[4];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+            v[q] = base + q < T ? row[base + q] : 0u;
+        uint32_t total;
+        uint32_t run = carry + block_exclusive_scan_u32(v[0] + v[1] + v[2] + v[3], sh, &total);
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+            if (base + q < T)
+                orow[base + q] = run;
+            run += v[q];
         }
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t l = sc.n_max - k;  // levels >= l: bins 0..k
+        uint32_t c = l <= sc.n_min ? sc.n : carry;
         if (!check_ok(c <= sc.n, kCheckActiveCount, l, b.err, b.dbg))
             c = sc.n;
         b.lvl_count[l] = c;
+        if (k == 0) {
+            b.lvl_count[sc.n_max + 1] = 0;
+            for (uint32_t m = 0; m < sc.n_min; ++m)
+                b.lvl_count[m] = sc.n;
+        }
     }
 }
 
@@ -2071,20 +2074,13 @@ cudaError_t launch_after(void (*k)(KArgs...), unsigned grid, unsigned block, cud
     return launch_after_smem(k, grid, block, 0, s, args...);
 }
 
-cudaError_t launch_lod_range(const StepConst &sc, const Buffers &b, cudaStream_t s)
-{
-    if (sc.n)
-        return sc.scenes > 1 ? launch_after(lod_range_kernel<true>, blocks_for(sc.n, kBlock), kBlock, s, sc, b)
-                             : launch_after(lod_range_kernel<false>, min(blocks_for(sc.n, kBlock), 512u), kBlock, s,
-                                            sc, b);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_predict_hash(const StepConst &sc, const Buffers &b, cudaStream_t s, bool diag)
 {
     if (sc.n)
-        return launch_after(sc.scenes > 1 ? predict_hash_kernel<true> : predict_hash_kernel<false>,
-                            blocks_for(sc.n, kBlock), kBlock, s, sc, b, diag ? 1 : 0);
+        return sc.scenes > 1
+                   ? launch_after(predict_hash_kernel<true>, blocks_for(sc.n, kBlock), kBlock, s, sc, b, diag ? 1 : 0)
+                   : launch_after(predict_hash_kernel<false>, min(blocks_for(sc.n, kBlock), kPredictBlocks), kBlock, s,
+                                  sc, b, diag ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -2125,9 +2121,7 @@ cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (!sc.n)
         return cudaGetLastError();
-    cudaError_t e = launch_after_smem(level_hist_kernel, sc.level_tiles, kLevelTile, sc.K * sizeof(uint32_t), s, sc, b);
-    if (e == cudaSuccess)
-        e = launch_after(level_scan_kernel, 1, 1024, s, sc, b);
+    cudaError_t e = launch_after(level_scan_kernel, sc.K, 1024, s, sc, b);
     if (e == cudaSuccess)
         e = launch_after_smem(level_scatter_kernel, sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s, sc,
                               b);

@@ -45,7 +45,7 @@ def make(cfg, eye, direction, view, *, d_near=0.0, d_far=0.0, flags=0, step=0):
 
 def check_lod(scene, p, x):
     """Depth image, distances and levels of the first step, bit for bit."""
-    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_PREDICT)
+    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_REORDER)
     depth_ref = oracle.depth_image(p, x)
     depth = apbf.apbf_debug_read(scene, apbf.APBF_DBG_DEPTH)
     assert np.array_equal(depth.view(np.uint32), depth_ref.view(np.uint32))
@@ -111,7 +111,7 @@ def test_dtvs_two_phase_render_after_steps_is_bitwise():
     st = apbf.apbf_read_state(scene, pos=True, vel=True)
     cnt = apbf.apbf_debug_read(scene, apbf.APBF_DBG_NBR_COUNT)
     assert np.any(cnt < 28) and np.any(cnt >= 28)          # both phases have spheres
-    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_PREDICT)
+    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_REORDER)
     ids = apbf.apbf_debug_read(scene, apbf.APBF_DBG_STATE_IDS).astype(np.int64)
     xs = st["pos"][ids]                                     # positions in the scene's state order
     depth_ref = oracle.depth_image(p, xs)

@@ -59,10 +59,10 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
     # a1-a3: levels and keys, pre-sort (= id) order
     apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_PREDICT)
     assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_KEYS), st.keys)
+    # a4-a6 and the neighbour lists; the levels come from the reorder pass
+    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_NEIGHBORS)
     assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_PRESORT).astype(np.int32),
                           st.level_presort)
-    # a4-a6 and the neighbour lists
-    apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_NEIGHBORS)
     assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_SORTED_IDS).astype(np.int32), st.order)
     assert np.array_equal(apbf.apbf_debug_read(scene, apbf.APBF_DBG_CELL_START), st.cell_start)
     xpred = apbf.apbf_debug_read(scene, apbf.APBF_DBG_XPRED)[:, :3]
