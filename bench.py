@@ -62,7 +62,7 @@ STAGE_BYTES = {
 # per-step device state of one scene, for the L2 decision (neighbour lists at
 # 128 entries dominate): an estimate shared by both arms of the benchmark
 STATE_BYTES_PER_PARTICLE = 660
-STAGE_NAMES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
+STAGE_NAMES = ["depth_image", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
                "finalize", "prestab"]
 
 
@@ -333,9 +333,31 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s (no measured peak found)"
 
 
-def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int) -> dict:
+def copy_us(torch, nbytes: int, reps: int = 50) -> float:
+    """CUDA-event time (us) of one device-to-device copy that moves nbytes in
+    total (nbytes / 2 read, nbytes / 2 written), averaged over reps back-to-back
+    copies: what a kernel of that size costs at best, launch included."""
+    half = max(16, (nbytes // 2 + 15) // 16 * 16)
+    src = torch.empty(half, dtype=torch.uint8, device="cuda")
+    dst = torch.empty_like(src)
+    for _ in range(3):
+        dst.copy_(src)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        dst.copy_(src)
+    z.record()
+    torch.cuda.synchronize()
+    return 1e3 * a.elapsed_time(z) / reps
+
+
+def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int, torch=None) -> dict:
     """Achieved HBM fraction of each HBM-bound stage: its algorithmic bytes per
-    step (STAGE_BYTES x particles or cells) over its CUDA-event time per step."""
+    step (STAGE_BYTES x particles or cells) over its CUDA-event time per step.
+    With torch, each stage also gets the time of a device copy moving the same
+    bytes (copy_us) and its own time's fraction of that (frac_of_copy): stages
+    of a few MB are bound by a launch's ramp and tail, which the copy pays too."""
     peak, src = hbm_peak()
     out = {"peak_gbs": peak, "peak_source": src, "stages": {}}
     for name, (bpu, unit, what) in STAGE_BYTES.items():
@@ -346,6 +368,9 @@ def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int) -> dict:
         gbs = bpu * units / (t * 1e-3) / 1e9
         out["stages"][name] = {"bytes_per_" + unit: bpu, "units": units, "us_per_step": t * 1e3,
                                "achieved_gbs": gbs, "frac": gbs / peak, "bytes": what}
+        if torch is not None:
+            c = copy_us(torch, bpu * units)
+            out["stages"][name].update({"copy_us": c, "frac_of_copy": c / (t * 1e3)})
     return out
 
 
@@ -1207,7 +1232,7 @@ def main():
                 "avg_launch_us": avg_launch_s * 1e6}
     particle_iters_per_step = iters / args.profile_steps
     dims = apbf.apbf_debug_dims(scene)[0]
-    stage_hbm = stage_roofline(stage_ms, cfg.n, int(dims[0]) * int(dims[1]) * int(dims[2]))
+    stage_hbm = stage_roofline(stage_ms, cfg.n, int(dims[0]) * int(dims[1]) * int(dims[2]), torch)
     value = ms_step
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.ws, "steps": args.steps,

@@ -36,7 +36,7 @@ APBF_LOD_DTC = 1
 APBF_LOD_DTVS = 2
 APBF_FLAG_NO_GRAPH = 1
 
-STAGES = ["lod_range", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
+STAGES = ["depth_image", "predict", "scan", "scatter", "reorder", "neighbors", "levels", "lambda", "deltap",
           "finalize"]
 (APBF_STAGE_LOD_RANGE, APBF_STAGE_PREDICT, APBF_STAGE_SCAN, APBF_STAGE_SCATTER, APBF_STAGE_REORDER,
  APBF_STAGE_NEIGHBORS, APBF_STAGE_LEVELS, APBF_STAGE_LAMBDA, APBF_STAGE_DELTAP, APBF_STAGE_FINALIZE) = range(10)
