@@ -347,8 +347,10 @@ APBF_API apbf_status apbf_density_stats_static(const float *pos, uint32_t n, flo
 #define APBF_STAGE_SCAN 2u       /* a4/a6: exclusive scan = cell start/end */
 #define APBF_STAGE_SCATTER 3u    /* a4: slot scatter */
 #define APBF_STAGE_REORDER 4u    /* a1, a4/a5: level, stable rank and reorder */
-#define APBF_STAGE_NEIGHBORS 5u  /* neighbour lists (the neighbour search of Fig. 7) */
-#define APBF_STAGE_LEVELS 6u     /* a7: active-set partition */
+#define APBF_STAGE_NEIGHBORS 5u  /* neighbour lists (the neighbour search of Fig. 7); with levels, it
+                                    also places each particle in the active list (a7) */
+#define APBF_STAGE_LEVELS 6u     /* a7: active-set sizes and offsets per level and tile (runs before
+                                    the neighbour search) */
 #define APBF_STAGE_LAMBDA 7u     /* a8 */
 #define APBF_STAGE_DELTAP 8u     /* a9 */
 #define APBF_STAGE_FINALIZE 9u   /* a10 */
@@ -518,7 +520,8 @@ APBF_API apbf_status apbf_debug_step_to(apbf_scene *scene, uint32_t stage, uint3
 #define APBF_DBG_NBR_COUNT 7u     /* u8[n]   neighbour count, sorted */
 #define APBF_DBG_NBR 8u           /* u32[max_neighbors*n]: entry k of particle p at k*n+p, the
                                      neighbour's sorted slot; n pads a list to a multiple of 4 */
-#define APBF_DBG_ACTIVE 9u        /* u32[n]  sorted slots, active-set order (P_l = prefix) */
+#define APBF_DBG_ACTIVE 9u        /* u32[n]  sorted slots, active-set order (P_l = prefix; from
+                                     APBF_STAGE_NEIGHBORS on) */
 #define APBF_DBG_LEVEL_COUNT 10u  /* u32[n_max+2] |P_l|, l = 0..n_max+1 */
 #define APBF_DBG_LAMBDA 11u       /* float[n] lambda after the stage, sorted */
 #define APBF_DBG_RHO 12u          /* float[n] density of the last lambda pass, sorted */

@@ -1097,7 +1097,7 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
     APBF_CUDA(s, cudaMemcpy(&dr[0], s->b.drange, 4, cudaMemcpyDeviceToHost));
     APBF_CUDA(s, cudaMemcpy(&dr[1], s->b.drange + sc.scenes, 4, cudaMemcpyDeviceToHost));
     const bool partitioned = sc.lod_mode != APBF_LOD_FIXED && sc.K > 1;
-    info->neighbor_pairs = c[0];
+    info->neighbor_pairs = c[0];  // without a partition; with one, the sum of the bins below
     info->total_particle_iterations = c[kIterTotalSlot];
     for (uint32_t l = 0; l < 256; ++l) {
         uint32_t a = 0;
@@ -1108,8 +1108,10 @@ APBF_API apbf_status apbf_get_step_info(apbf_scene *s, apbf_step_info *info)
             info->particle_iterations += a;
     }
     if (partitioned) {
-        for (uint32_t bin = 0; bin < sc.K; ++bin)
+        for (uint32_t bin = 0; bin < sc.K; ++bin) {
+            info->neighbor_pairs += c[2 + bin];
             info->lambda_pairs += c[2 + bin] * (unsigned long long)(sc.n_max - bin);
+        }
     } else {
         info->lambda_pairs = c[0] * (unsigned long long)sc.n_max;
     }

@@ -38,7 +38,7 @@ constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 t
 #define APBF_PREDICT_BLOCKS 1024
 #endif
 constexpr unsigned kPredictBlocks = APBF_PREDICT_BLOCKS;  // grid cap of a single scene's predict pass (its range atomics)
-constexpr int kLevelTile = 1024;     // particles per block of the active-set partition
+constexpr int kLevelTile = kBlock;   // sorted slots per tile of the active-set partition (a block of the neighbour search)
 constexpr int kTilePx = 8;           // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
 constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles take the big-sphere path
 constexpr int kBigBlockPx = 64;            // image blocks of the big-sphere path
@@ -72,8 +72,8 @@ constexpr uint32_t kCheckSortedSlot = 3u;   // a particle's sorted slot outside 
 constexpr uint32_t kCheckActiveCount = 4u;  // |P_l| above n or above |P_(l-1)|
 constexpr uint32_t kCheckNeighbor = 5u;     // a neighbour entry naming a slot beyond the padding record
 
-// Slots of the 64-bit counters: [0] neighbour pairs of the step, [2 + bin]
-// pairs per level bin (reset each step), two slots of scratch for the density
+// Slots of the 64-bit counters: [0] neighbour pairs of the step without a
+// level partition, [2 + bin] pairs per level bin with one (reset each step), two slots of scratch for the density
 // diagnostic, and the running total of particle-iterations (sum_l |P_l|, Eq.
 // 10) over every completed step, which nothing resets (the autotuner keeps a
 // copy in the slot after it while its trial steps run).

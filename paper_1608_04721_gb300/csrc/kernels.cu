@@ -790,20 +790,33 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
                 }
             }
         }
-        // one reservation per warp: the lanes' tile counts, prefix-summed
+        // one reservation per block: the lanes' tile counts, prefix-summed in
+        // each warp, the warps' sums in shared memory (one atomic per warp on
+        // the single counter queued up behind each other: 32k per pass)
+        __shared__ uint32_t sh_w[kBlock / 32];
+        __shared__ unsigned long long sh_base;
         uint32_t incl = nt;
-        const int lane = threadIdx.x & 31;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= o)
                 incl += y;
         }
-        const uint32_t wsum = __shfl_sync(kFull, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 31 && wsum)
-            base = atomicAdd(v.list_used, (unsigned long long)wsum);
-        base = __shfl_sync(kFull, base, 31);
+        if (lane == 31)
+            sh_w[w] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int k = 0; k < kBlock / 32; ++k) {
+                const uint32_t c = sh_w[k];
+                sh_w[k] = tot;
+                tot += c;
+            }
+            sh_base = tot ? atomicAdd(v.list_used, (unsigned long long)tot) : 0ull;
+        }
+        __syncthreads();
+        const unsigned long long base = sh_base + sh_w[w];
         if (!member || kind == 0)
             return;
         if (kind == 2 || base + incl > (unsigned long long)v.list_cap) {
@@ -1239,26 +1252,56 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
 
 // ------------------------------------- neighbour lists (Fig. 7, neighbour search)
 
-// With a level partition (part), thread t takes the particle at position t
-// of the active list and writes its list into column t (entry k at k*n + t):
-// every iteration then reads a contiguous prefix of columns. Without one,
-// column = sorted slot. The entries name neighbours by sorted slot either way.
+// Thread p takes the particle in sorted slot p. With a level partition
+// (part), the block is one tile of kLevelTile slots and first places its
+// particles in the active list (see level_scan_kernel): particle p goes to
+// position t = its bin's offset for the tile + the particles of its bin in
+// the tile before it, act[t] = p, and its list is written into column t
+// (entry k at k*n + t), so every iteration reads a contiguous prefix of
+// columns. Without a partition, column = sorted slot. The entries name
+// neighbours by sorted slot either way.
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers b, int part)
 {
+    static_assert(kLevelTile == kBlock, "a block of the neighbour search is one tile of the level partition");
     wait_for_predecessor();
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) {  // the padding entries' record: at least 3h from every particle on every axis
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {  // the padding entries' record: at least 3h from every particle on every axis
         const float4 far = make_float4(fx_word(kFxFar), fx_word(kFxFar), fx_word(kFxFar), 0.0f);
         b.recA[sc.n] = far;
         b.recB[sc.n] = far;
         b.xt[sc.n] = far;
     }
-    uint32_t cnt = 0, bin = 0;
-    if (t < sc.n) {
-        const uint32_t p = part ? b.act[t] : t;
-        if (part)
-            bin = sc.n_max - b.lvl_s[p];
+    uint32_t cnt = 0, bin = 0, t = p;
+    if (part) {  // uniform over the grid
+        // the stable partition by level: each warp's count per bin, then the
+        // particle's rank among its bin in the tile
+        extern __shared__ uint32_t wc[];  // (kBlock / 32) warps x K bins
+        const uint32_t K = sc.K;
+        for (uint32_t k = threadIdx.x; k < (kBlock / 32) * K; k += blockDim.x)
+            wc[k] = 0u;
+        __syncthreads();
+        const bool valid = p < sc.n;
+        bin = valid ? sc.n_max - b.lvl_s[p] : 0xffffffffu;
+        if (valid && !check_ok(bin < K, kCheckActiveCount, p, b.err, b.dbg))
+            bin = K - 1;
+        const unsigned peers = __match_any_sync(kFull, bin);
+        const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1))
+            wc[w * K + bin] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            t = b.lvl_off[(size_t)bin * sc.level_tiles + blockIdx.x] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            for (uint32_t v = 0; v < w; ++v)
+                t += wc[v * K + bin];
+            if (!check_ok(t < sc.n, kCheckActiveCount, p, b.err, b.dbg))
+                t = p;
+            b.act[t] = p;
+        } else {
+            bin = 0;
+        }
+    }
+    if (p < sc.n) {
         const Geo g = geo_of<BATCH>(sc, b, scene_of<BATCH>(b, p));
         const float4 xi = b.xs32[p];
         const int3 c = unpack_cell(b.cell_s[p]);
@@ -1340,20 +1383,20 @@ __global__ void __launch_bounds__(kBlock) neighbors_kernel(StepConst sc, Buffers
             eblk[(size_t)(cnt / kEntryBlock) * n] = out;
         }
     }
-    // pair counts, total and per level bin: one atomic per warp (no block
-    // barrier, so a warp retires as soon as its own lanes are done); the
-    // active list is level-major, so a warp almost always holds one level
-    const uint32_t wsum = warp_sum(cnt);
+    // pair counts: per level bin with a partition (their sum is the total),
+    // else the total; one atomic per warp and per distinct bin in it (the
+    // counters are few addresses, so atomics from every lane of the warps
+    // that straddle a level boundary would queue up behind each other)
     const uint32_t lane = threadIdx.x & 31u;
-    if (lane == 0 && wsum)
-        atomicAdd(&b.counters[0], (unsigned long long)wsum);
     if (part) {
-        if (__all_sync(kFull, bin == __shfl_sync(kFull, bin, 0))) {
-            if (lane == 0 && wsum)
-                atomicAdd(&b.counters[2 + bin], (unsigned long long)wsum);
-        } else if (cnt) {
-            atomicAdd(&b.counters[2 + bin], (unsigned long long)cnt);
-        }
+        const unsigned grp = __match_any_sync(kFull, bin);
+        const uint32_t gsum = __reduce_add_sync(grp, cnt);
+        if (lane == (uint32_t)(__ffs(grp) - 1) && gsum)
+            atomicAdd(&b.counters[2 + bin], (unsigned long long)gsum);
+    } else {
+        const uint32_t wsum = warp_sum(cnt);
+        if (lane == 0 && wsum)
+            atomicAdd(&b.counters[0], (unsigned long long)wsum);
     }
 }
 
@@ -1403,32 +1446,6 @@ __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers 
             for (uint32_t m = 0; m < sc.n_min; ++m)
                 b.lvl_count[m] = sc.n;
         }
-    }
-}
-
-__global__ void __launch_bounds__(kLevelTile) level_scatter_kernel(StepConst sc, Buffers b)
-{
-    wait_for_predecessor();
-    extern __shared__ uint32_t wc[];  // 32 warps x K
-    const uint32_t K = sc.K;
-    for (uint32_t k = threadIdx.x; k < 32 * K; k += blockDim.x)
-        wc[k] = 0u;
-    __syncthreads();
-    uint32_t p = blockIdx.x * kLevelTile + threadIdx.x;
-    bool valid = p < sc.n;
-    uint32_t bin = valid ? (sc.n_max - b.lvl_s[p]) : 0xffffffffu;
-    unsigned peers = __match_any_sync(kFull, bin);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int leader = __ffs(peers) - 1;
-    uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    if (valid && lane == leader)
-        wc[w * K + bin] = (uint32_t)__popc(peers);
-    __syncthreads();
-    if (valid) {
-        uint32_t pos = b.lvl_off[(size_t)bin * sc.level_tiles + blockIdx.x] + rank;
-        for (int v = 0; v < w; ++v)
-            pos += wc[v * K + bin];
-        b.act[pos] = p;
     }
 }
 
@@ -2115,8 +2132,9 @@ cudaError_t launch_reorder(const StepConst &sc, const Buffers &b, cudaStream_t s
 cudaError_t launch_neighbors(const StepConst &sc, const Buffers &b, cudaStream_t s, bool part)
 {
     if (sc.n)
-        return launch_after(sc.scenes > 1 ? neighbors_kernel<true> : neighbors_kernel<false>, blocks_for(sc.n, kBlock),
-                            kBlock, s, sc, b, part ? 1 : 0);
+        return launch_after_smem(sc.scenes > 1 ? neighbors_kernel<true> : neighbors_kernel<false>,
+                                 blocks_for(sc.n, kBlock), kBlock, part ? (kBlock / 32) * sc.K * sizeof(uint32_t) : 0,
+                                 s, sc, b, part ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -2124,11 +2142,7 @@ cudaError_t launch_levels(const StepConst &sc, const Buffers &b, cudaStream_t s)
 {
     if (!sc.n)
         return cudaGetLastError();
-    cudaError_t e = launch_after(level_scan_kernel, sc.K, 1024, s, sc, b);
-    if (e == cudaSuccess)
-        e = launch_after_smem(level_scatter_kernel, sc.level_tiles, kLevelTile, 32 * sc.K * sizeof(uint32_t), s, sc,
-                              b);
-    return e;
+    return launch_after(level_scan_kernel, sc.K, 1024, s, sc, b);
 }
 
 // The deep-batch solver kernels run every pass of a scene (or batch) with no more

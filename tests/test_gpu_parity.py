@@ -87,6 +87,8 @@ def check_stages(cfg, scene, p, x, v, *, iters=True, sample=None):
         apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_LEVELS)
         lc = apbf.apbf_debug_read(scene, apbf.APBF_DBG_LEVEL_COUNT).astype(np.int64)
         assert np.array_equal(lc, st.active_count)
+        # the neighbour search places each particle in the active list
+        apbf.apbf_debug_step_to(scene, apbf.APBF_STAGE_NEIGHBORS)
         act = apbf.apbf_debug_read(scene, apbf.APBF_DBG_ACTIVE).astype(np.int64)
         assert np.array_equal(act, np.lexsort((np.arange(n), -lvl)))
     # a8-a9 per iteration
