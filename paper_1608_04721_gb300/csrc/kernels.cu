@@ -484,9 +484,16 @@ __device__ __forceinline__ void range_merge(const StepConst &sc, const Buffers &
                 atomicMax(&b.drange[sc.scenes + s_first], __float_as_uint(dmax));
             }
         }
-    } else if (valid) {
-        atomicMax(&b.drange[s], ~__float_as_uint(dmin));
-        atomicMax(&b.drange[sc.scenes + s], __float_as_uint(dmax));
+    } else {
+        // a block over two or more scenes: one atomic pair per warp and scene
+        // (distances are >= 0, so their order is that of their bit patterns)
+        const unsigned grp = __match_any_sync(kFull, valid ? s : 0xffffffffu);
+        const uint32_t lo = __reduce_max_sync(grp, ~__float_as_uint(dmin));
+        const uint32_t hi = __reduce_max_sync(grp, __float_as_uint(dmax));
+        if (valid && (threadIdx.x & 31u) == (uint32_t)(__ffs(grp) - 1)) {
+            atomicMax(&b.drange[s], lo);
+            atomicMax(&b.drange[sc.scenes + s], hi);
+        }
     }
 }
 
