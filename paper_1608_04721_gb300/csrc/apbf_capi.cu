@@ -163,7 +163,7 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.K = sc.n_max - sc.n_min + 1;
     sc.lod_mode = d->lod_mode;
     sc.max_nbr = d->max_neighbors ? d->max_neighbors : kDefaultMaxNeighbors;
-    sc.level_tiles = (d->n + kLevelTile - 1) / kLevelTile;
+    sc.level_tiles = level_tile_count(d->n);
     sc.rho0 = d->rho0;
     sc.stabil_s = d->stabil_s;
     sc.stabil_iters = d->stabil_iters;
@@ -241,7 +241,7 @@ std::string derive_batch(const apbf_scene_desc *descs, uint32_t count, StepConst
     sc.n = (uint32_t)n_total;
     sc.ncell = (uint32_t)c_total;
     sc.scenes = count;
-    sc.level_tiles = (sc.n + kLevelTile - 1) / kLevelTile;
+    sc.level_tiles = level_tile_count(sc.n);
     st = APBF_OK;
     return "";
 }

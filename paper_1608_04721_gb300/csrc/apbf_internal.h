@@ -39,6 +39,11 @@ constexpr int kScanTile = 4096;      // cells per block of the grid scan (1024 t
 #endif
 constexpr unsigned kPredictBlocks = APBF_PREDICT_BLOCKS;  // grid cap of a single scene's predict pass (its range atomics)
 constexpr int kLevelTile = kBlock;   // sorted slots per tile of the active-set partition (a block of the neighbour search)
+
+// Tiles of the active-set partition for n particles, rounded up to a multiple
+// of 4 (the level scan reads the per-tile counts four at a time; the extra
+// tiles hold no particle and count zero).
+inline uint32_t level_tile_count(uint64_t n) { return (uint32_t)(((n + kLevelTile - 1) / kLevelTile + 3) / 4 * 4); }
 constexpr int kTilePx = 8;           // DTVS depth tiles: kTilePx x kTilePx pixels, one block each
 constexpr uint32_t kMaxSplatTiles = 4096;  // spheres covering more tiles take the big-sphere path
 constexpr int kBigBlockPx = 64;            // image blocks of the big-sphere path

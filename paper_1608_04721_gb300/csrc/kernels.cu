@@ -700,6 +700,10 @@ __device__ __forceinline__ uint32_t entry_bits(float4 ray, float rel0, float rel
 // their bit patterns, so the depth is a minimum over unsigned integers: it
 // depends neither on list order nor on which spheres took which path, and a
 // sphere that can lower no pixel may be left out.
+// A phase-1 sphere's box as stored in phase 0 when it has none: culled, or
+// crossing the camera plane (no real box reaches these codes: x1 < 16384).
+constexpr uint32_t kBoxNone = 0xffffffffu, kBoxBig = 0xfffffffeu;
+
 __device__ __forceinline__ bool tile_open(const ViewConst &v, int phase, uint32_t t, float near)
 {
     return phase == 0 || near < __uint_as_float(v.tile_max[t]);
@@ -770,7 +774,10 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
         uint32_t nt = 0;
         if (valid)
             v.accepted[i] = 0;
-        if (member) {
+        if (phase == 0 && valid) {
+            // every sphere's screen box (it does not depend on the phase): the
+            // spheres of phase 1 store theirs here, on lanes that would idle
+            // while the few phase-0 spheres are boxed
             const Basis B = view_basis(v, b.dyn);
             SplatBox o;
             kind = splat_box(B, v, b.dyn, b.state_x[i], o);
@@ -780,6 +787,25 @@ __global__ void __launch_bounds__(kBlock) splat_bin_kernel(StepConst sc, Buffers
                 y0 = o.y0;
                 y1 = o.y1;
                 near = o.near;
+            }
+            if (!member) {
+                v.box[i] = kind == 1 ? make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16))
+                                     : make_uint2(kind == 0 ? kBoxNone : kBoxBig, 0u);
+                v.near[i] = near;
+            }
+        } else if (member) {  // phase 1: the box stored in phase 0
+            const uint2 bx = v.box[i];
+            kind = bx.x == kBoxNone ? 0 : (bx.x == kBoxBig ? 2 : 1);
+            if (kind == 1) {
+                x0 = (int)(bx.x & 0xffffu);
+                x1 = (int)(bx.x >> 16);
+                y0 = (int)(bx.y & 0xffffu);
+                y1 = (int)(bx.y >> 16);
+                near = v.near[i];
+            }
+        }
+        if (member) {
+            if (kind == 1) {
                 const int tx0 = x0 / kTilePx, tx1 = x1 / kTilePx, ty0 = y0 / kTilePx, ty1 = y1 / kTilePx;
                 if ((uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1)) > kMaxSplatTiles) {
                     kind = 2;
@@ -1419,27 +1445,25 @@ __global__ void __launch_bounds__(1024) level_scan_kernel(StepConst sc, Buffers 
 {
     wait_for_predecessor();
     __shared__ uint32_t sh[32];
+    // T is a multiple of 4 (level_tile_count), so every row starts on a
+    // 16-byte boundary and is read and written four tiles at a time
     const uint32_t T = sc.level_tiles, k = blockIdx.x;
+    const uint4 *hist4 = reinterpret_cast<const uint4 *>(b.lvl_hist);
     uint32_t before = 0;
-    for (size_t i = threadIdx.x; i < (size_t)k * T; i += blockDim.x)
-        before += b.lvl_hist[i];
+    for (size_t i = threadIdx.x; i < (size_t)k * (T / 4); i += blockDim.x) {
+        const uint4 q = hist4[i];
+        before += q.x + q.y + q.z + q.w;
+    }
     uint32_t carry = block_sum_u32(before, sh);
-    const uint32_t *row = b.lvl_hist + (size_t)k * T;
-    uint32_t *orow = b.lvl_off + (size_t)k * T;
-    for (uint32_t c0 = 0; c0 < T; c0 += 4u * blockDim.x) {
-        const uint32_t base = c0 + 4u * threadIdx.x;
-        uint32_t v[4];
-#pragma unroll
-        for (uint32_t q = 0; q < 4; ++q)
-            v[q] = base + q < T ? row[base + q] : 0u;
+    const uint4 *row4 = hist4 + (size_t)k * (T / 4);
+    uint4 *orow4 = reinterpret_cast<uint4 *>(b.lvl_off) + (size_t)k * (T / 4);
+    for (uint32_t c0 = 0; c0 < T / 4; c0 += blockDim.x) {
+        const uint32_t c = c0 + threadIdx.x;
+        const uint4 v = c < T / 4 ? row4[c] : make_uint4(0u, 0u, 0u, 0u);
         uint32_t total;
-        uint32_t run = carry + block_exclusive_scan_u32(v[0] + v[1] + v[2] + v[3], sh, &total);
-#pragma unroll
-        for (uint32_t q = 0; q < 4; ++q) {
-            if (base + q < T)
-                orow[base + q] = run;
-            run += v[q];
-        }
+        const uint32_t run = carry + block_exclusive_scan_u32(v.x + v.y + v.z + v.w, sh, &total);
+        if (c < T / 4)
+            orow4[c] = make_uint4(run, run + v.x, run + v.x + v.y, run + v.x + v.y + v.z);
         carry += total;
     }
     if (threadIdx.x == 0) {

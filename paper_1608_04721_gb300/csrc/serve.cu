@@ -108,7 +108,7 @@ StepConst capacity(const StepConst &phys, uint32_t n, uint32_t cells, uint32_t s
     c.n = n;
     c.ncell = cells;
     c.scenes = scenes;
-    c.level_tiles = (n + kLevelTile - 1) / kLevelTile;
+    c.level_tiles = level_tile_count(n);
     return c;
 }
 
@@ -300,7 +300,7 @@ apbf_status relayout(apbf_server *sv)
     sc.n = sv->n_res;
     sc.ncell = sv->c_res;
     sc.scenes = count ? count : 1;
-    sc.level_tiles = (sc.n + kLevelTile - 1) / kLevelTile;
+    sc.level_tiles = level_tile_count(sc.n);
     if (count == 1) {  // the single-scene kernels read the grid from the step constants
         const StepConst &g = sv->resident[0]->geo;
         for (int a = 0; a < 3; ++a)
