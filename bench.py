@@ -55,7 +55,8 @@ STAGE_BYTES = {
     "scatter": (16, "particle", "key, slot read; start gathered; id written"),
     "reorder": (102, "particle", "44 B read (x, v, id, key, start); 58 B written (records, x*, ids, cells, "
                                  "levels in both orders)"),
-    "levels": (5, "particle", "level read, active index written (per-tile counts from the reorder pass)"),
+    "levels": (8, "entry", "per (level bin, tile of 256 sorted slots): count read, offset written (the counts come "
+                           "from the reorder pass; the neighbour search places the particles)"),
     "finalize": (76, "particle", "records, start positions read; x, v, id written (own particle; "
                                  "neighbour records via cache)"),
 }
@@ -192,7 +193,7 @@ def kernels_per_step(cfg) -> int:
     """Kernel launches of one step of a distance-to-camera (or fixed-level) scene."""
     k = 1 + 2 + 1 + 1 + 1 + 1  # predict (with the distance range), scan (2), scatter, reorder, neighbors, finalize
     if cfg.lod_mode != scenes.LOD_FIXED and cfg.n_max > cfg.n_min:
-        k += 2  # level scan, level scatter (the per-tile level counts come from the reorder pass)
+        k += 1  # level scan (the per-tile counts come from the reorder pass, the placement from the neighbour search)
     if getattr(cfg, "stabil_s", 0) > 1 and getattr(cfg, "stabil_iters", 0) > 0:
         k += 1  # pre-stabilisation
     return k + 2 * cfg.n_max
@@ -352,7 +353,15 @@ def copy_us(torch, nbytes: int, reps: int = 50) -> float:
     return 1e3 * a.elapsed_time(z) / reps
 
 
-def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int, torch=None) -> dict:
+def level_entries(cfg) -> int:
+    """(level bin, tile) entries of the active-set partition: K bins x the
+    tiles of 256 sorted slots, rounded up to a multiple of 4 (0 without one)."""
+    if cfg.lod_mode == scenes.LOD_FIXED or cfg.n_max <= cfg.n_min:
+        return 0
+    return (cfg.n_max - cfg.n_min + 1) * (((cfg.n + 255) // 256 + 3) // 4 * 4)
+
+
+def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int, torch=None, n_entries: int = 0) -> dict:
     """Achieved HBM fraction of each HBM-bound stage: its algorithmic bytes per
     step (STAGE_BYTES x particles or cells) over its CUDA-event time per step.
     With torch, each stage also gets the time of a device copy moving the same
@@ -364,7 +373,9 @@ def stage_roofline(stage_ms: dict, n_particles: int, n_cells: int, torch=None) -
         t = stage_ms.get(name, 0.0)
         if t <= 0.0:
             continue
-        units = n_particles if unit == "particle" else n_cells
+        units = {"particle": n_particles, "cell": n_cells, "entry": n_entries}[unit]
+        if units <= 0:
+            continue
         gbs = bpu * units / (t * 1e-3) / 1e9
         out["stages"][name] = {"bytes_per_" + unit: bpu, "units": units, "us_per_step": t * 1e3,
                                "achieved_gbs": gbs, "frac": gbs / peak, "bytes": what}
@@ -1232,7 +1243,7 @@ def main():
                 "avg_launch_us": avg_launch_s * 1e6}
     particle_iters_per_step = iters / args.profile_steps
     dims = apbf.apbf_debug_dims(scene)[0]
-    stage_hbm = stage_roofline(stage_ms, cfg.n, int(dims[0]) * int(dims[1]) * int(dims[2]), torch)
+    stage_hbm = stage_roofline(stage_ms, cfg.n, int(dims[0]) * int(dims[1]) * int(dims[2]), torch, level_entries(cfg))
     value = ms_step
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.ws, "steps": args.steps,

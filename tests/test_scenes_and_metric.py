@@ -125,3 +125,18 @@ def test_reference_arm_runs_the_whole_workload_with_the_same_config():
     assert "whole workload" in line["cpu_baseline"]["sample"] and "x " not in line["cpu_baseline"]["sample"]
     assert line["cpu_baseline"]["cores"] >= 1 and line["value"] > 0
     assert line["e2e"]["value"] == line["value"]
+
+
+def test_claimed_launches_per_step_match_the_committed_launch_list():
+    """bench.py's gpu_launches (kernels per step x steps) agrees with the ncu
+    launch list of the benchmark's DTC step committed under profiles/."""
+    import re
+
+    import bench
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "profiles", "launches_apbf_ocean_1048576.md"), encoding="utf-8").read()
+    m = re.search(r"### DTC: (\d+) steps, (\d+) launches", text)
+    assert m, "no DTC launch table in the committed launch list"
+    steps, launches = int(m.group(1)), int(m.group(2))
+    assert bench.kernels_per_step(bench.workload("ocean_1m", "apbf")) * steps == launches
