@@ -79,7 +79,8 @@ def test_scenes_in_a_batch_match_the_same_scenes_alone_bitwise():
         off += n
     assert off == batch.n
     info = apbf.apbf_get_step_info(batch)
-    assert info["particle_iterations"] == sum(apbf.apbf_get_step_info(a)["particle_iterations"] for a in alone)
+    for key in ("particle_iterations", "neighbor_pairs", "lambda_pairs"):
+        assert info[key] == sum(apbf.apbf_get_step_info(a)[key] for a in alone), key
 
 
 

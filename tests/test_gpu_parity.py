@@ -150,6 +150,28 @@ SMALL = {
 }
 
 
+@pytest.mark.parametrize("name", ["pbf_4096", "apbf_5200", "apbf_ragged_1000_user_range", "apbf_33"])
+def test_step_counters_match_the_oracle(name):
+    """apbf_get_step_info's counts, which the benchmark's roofline divides by,
+    are exact: neighbour pairs = sum_i |N_i|, lambda pairs = sum_i N_i |N_i|
+    (particle i visits its list in N_i lambda passes), particle-iterations =
+    sum_i N_i, and |P_l| per iteration (Eq. 9-10)."""
+    cfg, kw = SMALL[name]()
+    scene, p, x, v = make(cfg, **kw)
+    st = oracle.step(p, x, v, record=True, rec_iters=1)
+    apbf.apbf_step(scene, 1)
+    info = apbf.apbf_get_step_info(scene)
+    deg = np.diff(st.nbr_off).astype(np.int64)          # sorted order
+    lvl = st.level_presort[st.order].astype(np.int64)   # sorted order
+    assert info["neighbor_pairs"] == int(deg.sum())
+    assert info["lambda_pairs"] == int((deg * lvl).sum())
+    assert info["particle_iterations"] == int(lvl.sum())
+    n_max = int(p.n_max)
+    assert np.array_equal(info["active_count"][1:n_max + 1], [int((lvl >= l).sum()) for l in range(1, n_max + 1)])
+    assert not info["active_count"][n_max + 1:].any()
+    apbf.apbf_destroy_scene(scene)
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_stagewise_parity_small(name):
     cfg, kw = SMALL[name]()
