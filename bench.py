@@ -1065,10 +1065,19 @@ def run_reference_batch(args, ws):
     return 0
 
 
+def default_steps(name: str) -> int:
+    """A workload's own length in steps (the batch: its scenes' 100 steps)."""
+    if name in ("batch_256", "serve"):
+        return 100
+    return int(workload(name, "apbf").steps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's own length: 600 for the ocean, 300 for the 131k and "
+                         "225k scenes, 20 for the 4k dam break, 100 for the batch)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ocean_1m",
@@ -1090,6 +1099,8 @@ def main():
     ap.add_argument("--no-dtvs", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = default_steps(args.workload)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
