@@ -140,3 +140,23 @@ def test_claimed_launches_per_step_match_the_committed_launch_list():
     assert m, "no DTC launch table in the committed launch list"
     steps, launches = int(m.group(1)), int(m.group(2))
     assert bench.kernels_per_step(bench.workload("ocean_1m", "apbf")) * steps == launches
+
+
+def test_stage_roofline_units_and_default_steps():
+    """The HBM stage figures use each stage's own unit (particles, cells or
+    (level bin, tile) entries), and each workload times its own length by
+    default."""
+    import bench
+
+    cfg = bench.workload("ocean_1m", "apbf")
+    k = cfg.n_max - cfg.n_min + 1
+    entries = bench.level_entries(cfg)
+    assert entries == k * (((cfg.n + 255) // 256 + 3) // 4 * 4) and entries % (4 * k) == 0
+    assert bench.level_entries(bench.workload("ocean_1m", "pbf")) == 0
+    r = bench.stage_roofline({"predict": 0.010, "scan": 0.005, "levels": 0.002}, cfg.n, 1000, None, entries)
+    st = r["stages"]
+    assert st["predict"]["units"] == cfg.n and st["scan"]["units"] == 1000 and st["levels"]["units"] == entries
+    assert abs(st["predict"]["achieved_gbs"] - 40 * cfg.n / 10e-6 / 1e9) < 1e-6 * st["predict"]["achieved_gbs"]
+    assert "copy_us" not in st["predict"]  # no device copy timed without torch
+    assert {w: bench.default_steps(w) for w in ("ocean_1m", "dam_break_131k", "dam_break_4k", "batch_256")} == {
+        "ocean_1m": 600, "dam_break_131k": 300, "dam_break_4k": 20, "batch_256": 100}
