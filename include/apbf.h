@@ -157,7 +157,9 @@ APBF_API apbf_status apbf_scene_bytes(const apbf_scene_desc *desc, size_t *bytes
  *  device_arena  device memory of at least apbf_scene_bytes() bytes, 256-byte
  *                aligned, owned by the caller and kept alive until
  *                apbf_destroy_scene; or NULL, in which case the library
- *                allocates (cudaMalloc) and frees it.
+ *                allocates (cudaMalloc) and frees it. A misaligned arena is
+ *                APBF_ERR_INVALID_ARG, a short one APBF_ERR_OUT_OF_MEMORY;
+ *                neither touches the GPU.
  *  arena_bytes   size of device_arena (ignored when NULL).
  *  out           host; receives the scene handle (NULL on failure).
  * Synchronises the stream once (the initial upload).

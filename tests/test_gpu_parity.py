@@ -463,3 +463,34 @@ def test_invalid_calls_on_a_live_scene():
         apbf.apbf_debug_step_to(s, apbf.APBF_STAGE_LAMBDA, 99)
     apbf.apbf_step(s, 1)  # still usable
     apbf.apbf_sync(s)
+
+
+def test_caller_arena_refusals_and_use():
+    """A scene in caller-provided device memory: a misaligned arena is refused
+    (INVALID_ARG) and a short one too (OUT_OF_MEMORY), before any device work;
+    an arena of exactly apbf_scene_bytes steps bit-identically to a scene whose
+    memory the library allocates."""
+    import torch
+
+    cfg = scenes.config_dam_break_4k().replace(lattice=(8, 8, 8))
+    x, v = scenes.make_scene(cfg)
+    desc = apbf.desc_from_config(cfg, x, v, rest_density(cfg))
+    need = apbf.apbf_scene_bytes(desc)
+    buf = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    base = (buf.data_ptr() + 255) // 256 * 256
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_create_scene(desc, device_arena=(base + 16, need))
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_create_scene(desc, device_arena=(base, need - 256))
+    assert e.value.status == apbf.APBF_ERR_OUT_OF_MEMORY
+    mine = apbf.apbf_create_scene(desc, device_arena=(base, need))
+    lib_owned = apbf.apbf_create_scene(desc, device_arena=None)
+    for s in (mine, lib_owned):
+        apbf.apbf_step(s, 3)
+    a = apbf.apbf_read_state(mine, pos=True, vel=True)
+    b = apbf.apbf_read_state(lib_owned, pos=True, vel=True)
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["vel"], b["vel"])
+    apbf.apbf_destroy_scene(mine)
+    apbf.apbf_destroy_scene(lib_owned)
+    del buf
