@@ -1192,6 +1192,22 @@ def main():
                      "lod_stage_ms": float(dms[0] / nprof),
                      "particle_iterations_per_step": diters / nprof,
                      "density": [float(v) for v in dtvs_density]}
+        # the same with the particles outside the view at n_max instead of n_min
+        # (apbf_set_view_outside_level), on identical inputs and drivers
+        dtvs_hi = make_scene(apbf, dtvs_cfg, rho0)
+        apbf.apbf_set_view_outside_level(dtvs_hi, dtvs_cfg.n_max)
+        if "apbf_dtvs" in tuning:
+            apbf.apbf_set_tuning(dtvs_hi, tuning["apbf_dtvs"]["block"], tuning["apbf_dtvs"]["mask_threshold"])
+        d.barrier()
+        htot, hper, hs_next = timed_run(apbf, torch, dtvs_hi, dtvs_cfg, args.warmup, args.steps, flush=flush)
+        d.barrier()
+        hdens = apbf.apbf_density_stats(dtvs_hi)
+        _, _, _, _, hiters, _ = stage_profile(apbf, dtvs_hi, dtvs_cfg, hs_next, 5)
+        dtvs_line["outside_nmax"] = {"ms_per_step": d.max(htot / args.steps), "p50_ms": metrics.percentile(hper, 50),
+                                     "p99_ms": metrics.percentile(hper, 99),
+                                     "particle_iterations_per_step": hiters / 5,
+                                     "density": [float(v) for v in hdens]}
+        apbf.apbf_destroy_scene(dtvs_hi)
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:

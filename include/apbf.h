@@ -215,7 +215,8 @@ APBF_API apbf_status apbf_set_camera(apbf_scene *scene, const float eye[3], cons
  *     visible surface along its camera ray; visible particles get 0;
  *  3. N_i follows from d as for DTC (linear interpolation between the
  *     distance range, automatic over the particles in view, or the camera's
- *     d_near..d_far, and n_max..n_min); particles outside the view get n_min.
+ *     d_near..d_far, and n_max..n_min); particles outside the view get n_min
+ *     (or the level set by apbf_set_view_outside_level).
  * All of steps 1-3 is FP32 with every operation rounded (no contraction).
  *  width, height  1..16384 each, width * height <= 2^26.
  *  up             host, 3 floats, finite, not parallel to the camera's dir.
@@ -223,6 +224,17 @@ APBF_API apbf_status apbf_set_camera(apbf_scene *scene, const float eye[3], cons
  * tile, 81 per particle) are device memory the scene allocates here. */
 APBF_API apbf_status apbf_set_view(apbf_scene *scene, uint32_t width, uint32_t height, float tan_half_fov,
                                    const float up[3], float radius);
+
+/*
+ * N_i of the DTVS particles outside the camera image, from the next step on.
+ * The paper renders only what its camera sees and does not say which level an
+ * unseen particle takes (Sec. 4.1); n_min (the default) gives unseen fluid the
+ * least work, while a higher level keeps the density of fluid the camera sees
+ * only in part closer to PBF with n_max iterations (Sec. 4.2: low levels left
+ * without high-level neighbours drift in density). level: 0 (n_min) or
+ * n_min..n_max; APBF_ERR_INVALID_ARG otherwise or for a scene that is not DTVS.
+ */
+APBF_API apbf_status apbf_set_view_outside_level(apbf_scene *scene, uint32_t level);
 
 /*
  * Rigid obstacles (the paper's signed-distance-field obstacles of Sec. 6, here

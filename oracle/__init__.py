@@ -33,11 +33,14 @@ class OrcView(C.Structure):
         ("up", C.c_float * 3),
         ("radius", C.c_float),
         ("brute_force", C.c_int32),
+        ("outside_level", C.c_int32),
     ]
 
 
 def make_view(width: int, height: int, tan_half_fov: float, direction, up=(0.0, 0.0, 1.0), radius: float = 0.025,
-              brute_force: bool = False) -> OrcView:
+              brute_force: bool = False, outside_level: int = 0) -> OrcView:
+    """The DTVS camera image; outside_level is N_i of a particle outside the
+    view (0: n_min, reading 20)."""
     v = OrcView()
     v.width, v.height = int(width), int(height)
     v.tan_half_fov = float(tan_half_fov)
@@ -45,6 +48,7 @@ def make_view(width: int, height: int, tan_half_fov: float, direction, up=(0.0, 
     v.up[:] = [float(a) for a in up]
     v.radius = float(radius)
     v.brute_force = int(bool(brute_force))
+    v.outside_level = int(outside_level)
     return v
 
 

@@ -331,6 +331,9 @@ int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *leve
     }
     if (p->lod_mode != ORC_LOD_DTC && p->lod_mode != ORC_LOD_DTVS)
         return -1;
+    if (p->lod_mode == ORC_LOD_DTVS && p->view.outside_level != 0 &&
+        (p->view.outside_level < p->n_min || p->view.outside_level > p->n_max))
+        return -1;
     float *d = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
     if (!d)
         return -3;
@@ -383,8 +386,8 @@ int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *leve
     int32_t K = p->n_max - p->n_min + 1;
     float span = dmax - dmin;
     for (int32_t i = 0; i < n; ++i) {
-        if (d[i] < 0.0f) {
-            level[i] = p->n_min;
+        if (d[i] < 0.0f) { /* DTVS: outside the view */
+            level[i] = p->view.outside_level ? p->view.outside_level : p->n_min;
             continue;
         }
         float t = 0.0f;

@@ -46,6 +46,7 @@ typedef struct orc_view {
     float up[3];
     float radius;
     int32_t brute_force; /* 1: test every pixel against every sphere (no bounding box) */
+    int32_t outside_level; /* N_i of a particle outside the view; 0: n_min (reading 20) */
 } orc_view;
 
 /* Rigid obstacles (Sec. 6 uses signed-distance fields; these are analytic
@@ -140,7 +141,8 @@ int orc_dtvs_distance(const orc_params *p, int32_t n, const float *x, const floa
 
 /* Sec. 4.1 DTC / DTVS model + Eq. 8: per-particle level from the camera
    distance (DTC) or the distance behind the visible surface (DTVS;
-   particles outside the view get n_min and do not enter the automatic range). */
+   particles outside the view get n_min, or view.outside_level when that is
+   set, and do not enter the automatic range). */
 int orc_lod_levels(const orc_params *p, int32_t n, const float *x, int32_t *level, float range[2]);
 
 /* Nearest surface point of an obstacle for a point strictly inside it (FP64);

@@ -159,7 +159,7 @@ EXPORTS = [
     "apbf_debug_read", "apbf_debug_dims", "apbf_density_stats_static", "apbf_batch_bytes", "apbf_create_batch",
     "apbf_set_camera_at", "apbf_set_box_at", "apbf_set_tuning", "apbf_autotune", "apbf_server_bytes",
     "apbf_server_create", "apbf_server_submit", "apbf_server_tick", "apbf_server_query", "apbf_server_last_error",
-    "apbf_server_destroy", "apbf_set_view", "apbf_set_obstacles", "apbf_read_positions_async",
+    "apbf_server_destroy", "apbf_set_view", "apbf_set_view_outside_level", "apbf_set_obstacles", "apbf_read_positions_async",
     "apbf_debug_checks_enabled", "apbf_debug_plant",
 ]
 APBF_STATIC_MAX_PARTICLES = 65536
@@ -225,6 +225,7 @@ def lib():
                                                 P(C.c_float), V, V]
         L.apbf_set_obstacles.argtypes = [V, C.c_uint32, P(apbf_obstacle), C.c_uint32]
         L.apbf_set_view.argtypes = [V, C.c_uint32, C.c_uint32, C.c_float, P(C.c_float), C.c_float]
+        L.apbf_set_view_outside_level.argtypes = [V, C.c_uint32]
         L.apbf_server_bytes.argtypes = [P(apbf_server_desc), P(C.c_size_t), P(C.c_uint32), P(C.c_uint32)]
         L.apbf_server_create.argtypes = [P(apbf_server_desc), V, P(V)]
         L.apbf_server_submit.argtypes = [V, P(apbf_request), P(C.c_uint64)]
@@ -727,6 +728,11 @@ def apbf_set_view(scene: Scene, width: int, height: int, tan_half_fov: float, up
     u = (C.c_float * 3)(*[float(a) for a in up])
     _check(lib().apbf_set_view(scene.handle, width, height, tan_half_fov, u, radius), "apbf_set_view", scene)
     scene.view = (int(width), int(height))
+
+
+def apbf_set_view_outside_level(scene: Scene, level: int):
+    """N_i of the DTVS particles outside the view (0: n_min; see include/apbf.h)."""
+    _check(lib().apbf_set_view_outside_level(scene.handle, int(level)), "apbf_set_view_outside_level", scene)
 
 
 def apbf_set_obstacles(scene: Scene, obstacles, index: int = 0):

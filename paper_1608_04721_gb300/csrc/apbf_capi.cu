@@ -159,6 +159,7 @@ std::string derive(const apbf_scene_desc *d, StepConst &sc, apbf_status &st)
     sc.scorr_n = d->scorr_n;
     sc.c_xsph = (float)((double)d->xsph_c * (m / rho0) * poly6);
     sc.n_min = d->lod_mode == APBF_LOD_FIXED ? d->n_max : d->n_min;
+    sc.dtvs_outside = sc.n_min;
     sc.n_max = d->n_max;
     sc.K = sc.n_max - sc.n_min + 1;
     sc.lod_mode = d->lod_mode;
@@ -957,6 +958,24 @@ APBF_API apbf_status apbf_set_view(apbf_scene *s, uint32_t width, uint32_t heigh
     }
     s->view_set = true;
     drop_graph(s);
+    return APBF_OK;
+}
+
+APBF_API apbf_status apbf_set_view_outside_level(apbf_scene *s, uint32_t level)
+{
+    apbf_status st = enter(s);
+    if (st != APBF_OK)
+        return st;
+    if (s->sc.lod_mode != APBF_LOD_DTVS)
+        return fail(s, APBF_ERR_INVALID_ARG, "the scene's lod_mode is not APBF_LOD_DTVS");
+    if (level == 0)
+        level = s->sc.n_min;
+    if (level < s->sc.n_min || level > s->sc.n_max)
+        return fail(s, APBF_ERR_INVALID_ARG, "need level = 0 or n_min <= level <= n_max");
+    if (level != s->sc.dtvs_outside) {
+        s->sc.dtvs_outside = level;
+        drop_graph(s);  // the captured step holds the step constants
+    }
     return APBF_OK;
 }
 

@@ -118,6 +118,7 @@ struct StepConst {
     uint32_t scorr_n;
     float c_xsph;       // c (m / rho0) * 315/(64 pi h^9)
     uint32_t n_min, n_max, K, lod_mode;
+    uint32_t dtvs_outside;  // DTVS: N_i of a particle outside the view (n_min unless set)
     uint32_t max_nbr;
     uint32_t level_tiles;
     float rho0;         // rest density as given (FP32)

@@ -1265,9 +1265,9 @@ __global__ void __launch_bounds__(kBlock) reorder_kernel(StepConst sc, Buffers b
                     }
                     if (sc.lod_mode == APBF_LOD_DTC) {
                         lv = lod_level(camera_distance(x, dyn), dmin, dmax, sc);
-                    } else {  // DTVS: outside the view -> n_min
+                    } else {  // DTVS: outside the view -> dtvs_outside (n_min unless set)
                         const float d = b.lodd[i];
-                        lv = d < 0.0f ? sc.n_min : lod_level(d, dmin, dmax, sc);
+                        lv = d < 0.0f ? sc.dtvs_outside : lod_level(d, dmin, dmax, sc);
                     }
                 }
                 b.lvl[i] = (uint8_t)lv;

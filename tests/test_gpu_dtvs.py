@@ -140,6 +140,40 @@ def test_dtvs_looking_away_gives_n_min_and_steps():
     check_final(cfg, scene, p, st)
 
 
+def test_dtvs_outside_level_option():
+    """apbf_set_view_outside_level: particles outside a narrow view take the
+    set level (bit for bit with the oracle's view.outside_level) and the step
+    matches the oracle; 0 restores n_min; levels outside n_min..n_max and
+    non-DTVS scenes are refused."""
+    cfg, eye, direction, view = CASES["narrow_view_5200"]()
+    scene, p, x, v = make(cfg, eye, direction, view)
+    apbf.apbf_set_view_outside_level(scene, cfg.n_max)
+    W, H, t, up, rad = view
+    p.view = oracle.make_view(W, H, t, direction, up=up, radius=rad, outside_level=cfg.n_max)
+    _, dist, lv = check_lod(scene, p, x)
+    assert np.any(dist < 0) and np.all(lv[dist < 0] == cfg.n_max)
+    st = check_stages(cfg, scene, p, x, v, iters=False)
+    check_final(cfg, scene, p, st)
+    for bad in (cfg.n_min - 1, cfg.n_max + 1):
+        with pytest.raises(apbf.ApbfError) as e:
+            apbf.apbf_set_view_outside_level(scene, bad)
+        assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    apbf.apbf_destroy_scene(scene)
+    scene, p, x, v = make(cfg, eye, direction, view)
+    apbf.apbf_set_view_outside_level(scene, cfg.n_max)
+    apbf.apbf_set_view_outside_level(scene, 0)  # back to n_min
+    _, dist, lv = check_lod(scene, p, x)
+    assert np.all(lv[dist < 0] == cfg.n_min)
+    apbf.apbf_destroy_scene(scene)
+    plain = apbf.apbf_create_scene(apbf.desc_from_config(scenes.config_dam_break_4k().replace(lattice=(4, 4, 4)),
+                                                         *scenes.make_scene(scenes.config_dam_break_4k().replace(
+                                                             lattice=(4, 4, 4))), rest_density(cfg)))
+    with pytest.raises(apbf.ApbfError) as e:
+        apbf.apbf_set_view_outside_level(plain, 2)
+    assert e.value.status == apbf.APBF_ERR_INVALID_ARG
+    apbf.apbf_destroy_scene(plain)
+
+
 def test_dtvs_131k_one_step_parity():
     cfg = scenes.config_dam_break_131k(lod_mode=scenes.LOD_DTVS)
     eye, direction = (-4.0, 1.6, 2.6), (1.0, 0.0, -0.35)

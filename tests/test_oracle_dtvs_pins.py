@@ -178,6 +178,25 @@ def test_nothing_in_view_gives_n_min_everywhere():
     assert np.all(lv == 3) and rng[0] == 0.0 and rng[1] == 0.0
 
 
+def test_outside_level_option_changes_only_the_particles_outside_the_view():
+    """view.outside_level gives the particles outside the view that level and
+    leaves every other level and the automatic range as they are; a level
+    outside n_min..n_max is refused."""
+    v0 = O.make_view(64, 64, 0.6, (1.0, 0.0, 0.0), radius=0.05)
+    v1 = O.make_view(64, 64, 0.6, (1.0, 0.0, 0.0), radius=0.05, outside_level=6)
+    rng = np.random.default_rng(3)
+    inside = np.stack([rng.uniform(2.0, 4.0, 40), rng.uniform(-0.5, 0.5, 40), rng.uniform(-0.5, 0.5, 40)], 1)
+    outside = np.stack([rng.uniform(-4.0, -1.0, 10), rng.uniform(-1, 1, 10), rng.uniform(-1, 1, 10)], 1)
+    x = np.concatenate([inside, outside]).astype(np.float32)
+    lv0, r0 = O.lod_levels(_params(np.zeros(3), v0, n_min=2, n_max=6), x)
+    lv1, r1 = O.lod_levels(_params(np.zeros(3), v1, n_min=2, n_max=6), x)
+    assert np.all(lv0[40:] == 2) and np.all(lv1[40:] == 6)
+    assert np.array_equal(lv0[:40], lv1[:40]) and np.array_equal(r0, r1)
+    with pytest.raises(Exception):
+        O.lod_levels(_params(np.zeros(3), O.make_view(64, 64, 0.6, (1.0, 0.0, 0.0), radius=0.05,
+                                                      outside_level=7), n_min=2, n_max=6), x)
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_bounding_box_cull_equals_every_pixel(seed):
     rng = np.random.default_rng(seed)
