@@ -66,6 +66,9 @@ MUTATIONS = [
     ("DTVS cull box without its one-pixel margin",
      "x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) - 1;", "x0 = (int32_t)floorf(fmaxf(fx_lo, -1.0f)) + 1;",
      lambda: dtvs.test_bounding_box_cull_equals_every_pixel(0)),
+    ("DTVS outside level ignored (unseen particles always at n_min)",
+     "level[i] = p->view.outside_level ? p->view.outside_level : p->n_min;", "level[i] = p->n_min;",
+     dtvs.test_outside_level_option_changes_only_the_particles_outside_the_view),
     ("pre-stabilisation moves only the current position",
      "                x0d[3 * s + a] = q[a];\n                xs[3 * s + a] += d;\n",
      "                x0d[3 * s + a] = q[a];\n                (void)d;\n",
